@@ -1,0 +1,277 @@
+"""FP64 CPU oracle for longitudinal multi-bunch macro-particle tracking.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain definition the CUDA
+library is checked against (arXiv:1809.00391, Sec. 2.2-2.4, Eqs. 1, 2, 5, 6).
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference legs of ``bench.py`` may import it.  It shares no code with the
+CUDA path: the C source ``mbt_oracle.c`` is compiled here with gcc, with
+floating-point contraction disabled so that x86-64 and aarch64 builds round
+identically.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "mbt_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB_PATH = _BUILD / "liboracle.so"
+_lock = threading.Lock()
+_lib = None
+
+RANGE_SHORT = 1
+RANGE_LONG = 2
+RANGE_BOTH = 3
+NO_SR = 1
+NO_QE = 2
+KICK_NGP = 4
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, no contraction)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", str(tmp), str(_SRC), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Ring(ctypes.Structure):
+    _fields_ = [("E0_eV", ctypes.c_double), ("T0_s", ctypes.c_double), ("h", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("V_rf_V", ctypes.c_double), ("alpha_c", ctypes.c_double),
+                ("U0_eV", ctypes.c_double), ("sigma_delta", ctypes.c_double), ("tau_z_s", ctypes.c_double)]
+
+
+class Resonator(ctypes.Structure):
+    _fields_ = [("Rs_ohm", ctypes.c_double), ("fr_Hz", ctypes.c_double), ("Q", ctypes.c_double),
+                ("range", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+_P = ctypes.POINTER
+_d = ctypes.c_double
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(str(build()))
+            lib.orc_philox4x32_10.argtypes = [_P(_u32), _P(_u32), _P(_u32)]
+            lib.orc_u01.argtypes = [_u32, _u32]
+            lib.orc_u01.restype = _d
+            lib.orc_box_muller.argtypes = [_d, _d, _P(_d), _P(_d)]
+            lib.orc_normal_pair.argtypes = [_u64, _u32, _u32, _u32, _u32, _P(_d), _P(_d)]
+            lib.orc_derive.argtypes = [_P(Ring), ctypes.c_int, _P(_d)]
+            lib.orc_wake.argtypes = [_P(Resonator), _d]
+            lib.orc_wake.restype = _d
+            lib.orc_create.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator),
+                                       ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
+            lib.orc_create.restype = ctypes.c_void_p
+            lib.orc_destroy.argtypes = [ctypes.c_void_p]
+            lib.orc_get_derived.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_init_particles.argtypes = [ctypes.c_void_p]
+            lib.orc_set_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+            lib.orc_get_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+            lib.orc_cell_coord.argtypes = [ctypes.c_void_p, _d]
+            lib.orc_cell_coord.restype = _d
+            lib.orc_bin.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_i32)]
+            lib.orc_bin.restype = _i64
+            lib.orc_vsr_direct.argtypes = [ctypes.c_void_p, _P(_i32), _d, _P(_d)]
+            lib.orc_track.argtypes = [ctypes.c_void_p, _i64, _P(_d)]
+            lib.orc_get_hist.argtypes = [ctypes.c_void_p, _P(_i32), _P(_i64)]
+            lib.orc_get_vsr.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_get_alr.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_get_wlag.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_feed_histograms.argtypes = [ctypes.c_void_p, _P(_i32)]
+            lib.orc_get_last_emission.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d)]
+            lib.orc_wake_voltage_at.argtypes = [ctypes.c_void_p, ctypes.c_int, _d]
+            lib.orc_wake_voltage_at.restype = _d
+            lib.orc_turn.argtypes = [ctypes.c_void_p]
+            lib.orc_turn.restype = _i64
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(_P(ct))
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block: 4 counter words, 2 key words -> 4 output words."""
+    lib = _load()
+    c = (_u32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (_u32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (_u32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return tuple(int(x) for x in o)
+
+
+def u01(hi: int, lo: int) -> float:
+    return _load().orc_u01(hi & 0xFFFFFFFF, lo & 0xFFFFFFFF)
+
+
+def box_muller(u1: float, u2: float):
+    a, b = _d(), _d()
+    _load().orc_box_muller(u1, u2, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def normal_pair(seed: int, pair: int, bunch: int, turn: int, tag: int):
+    a, b = _d(), _d()
+    _load().orc_normal_pair(seed, pair, bunch, turn, tag, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def make_ring(ring: dict) -> Ring:
+    return Ring(E0_eV=ring["E0_eV"], T0_s=ring["T0_s"], h=int(ring["h"]), pad_=0,
+                V_rf_V=ring["V_rf_V"], alpha_c=ring["alpha_c"], U0_eV=ring["U0_eV"],
+                sigma_delta=ring["sigma_delta"], tau_z_s=ring["tau_z_s"])
+
+
+def make_resonator(res: dict) -> Resonator:
+    return Resonator(Rs_ohm=res["Rs_ohm"], fr_Hz=res["fr_Hz"], Q=res["Q"], range=int(res["range"]), pad_=0)
+
+
+def derive(ring: dict, flags: int = 0) -> dict:
+    """Derived ring quantities (T_rf, omega_rf, phi_s, ...) as the oracle computes them."""
+    out = (_d * 12)()
+    r = make_ring(ring)
+    _load().orc_derive(ctypes.byref(r), flags, out)
+    keys = ["T_rf", "omega_rf", "phi_s", "sin_phi_s", "U0_over_E0", "V_over_E0", "D", "qe_amp",
+            "nu_s", "sigma_tau0"]
+    return {k: out[i] for i, k in enumerate(keys)}
+
+
+def wake(res: dict, t: float) -> float:
+    r = make_resonator(res)
+    return _load().orc_wake(ctypes.byref(r), float(t))
+
+
+class OracleSim:
+    """Plain FP64 multi-bunch tracker (one run)."""
+
+    def __init__(self, ring: dict, resonators: list, nbins: int, half_width_sigmas: float,
+                 buckets, currents_A, n_mp, seed: int, flags: int = 0):
+        self._lib = _load()
+        self.nb = len(buckets)
+        self.nbins = int(nbins)
+        self.nres = len(resonators)
+        self.resonators = list(resonators)
+        self._ring = make_ring(ring)
+        ra = (Resonator * max(1, self.nres))(*[make_resonator(r) for r in resonators])
+        self.buckets = np.ascontiguousarray(buckets, dtype=np.int32)
+        self.currents = np.ascontiguousarray(currents_A, dtype=np.float64)
+        self.n_mp = np.ascontiguousarray(n_mp, dtype=np.int64)
+        self._h = self._lib.orc_create(ctypes.byref(self._ring), int(flags), int(seed), self.nres, ra,
+                                       self.nbins, float(half_width_sigmas), self.nb,
+                                       _ptr(self.buckets, _i32), _ptr(self.currents, _d),
+                                       _ptr(self.n_mp, _i64))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def derived(self) -> dict:
+        out = (_d * 12)()
+        self._lib.orc_get_derived(self._h, out)
+        keys = ["T_rf", "omega_rf", "phi_s", "D", "qe_amp", "nu_s", "sigma_tau0", "H", "Delta",
+                "invDelta", "nhist", "turn"]
+        return {k: out[i] for i, k in enumerate(keys)}
+
+    def init_particles(self):
+        self._lib.orc_init_particles(self._h)
+
+    def set_particles(self, m: int, tau, delta):
+        t = np.ascontiguousarray(tau, dtype=np.float64)
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        assert t.size == self.n_mp[m] and d.size == self.n_mp[m]
+        self._lib.orc_set_particles(self._h, m, _ptr(t, _d), _ptr(d, _d))
+
+    def particles(self, m: int):
+        n = int(self.n_mp[m])
+        t = np.empty(n, np.float64)
+        d = np.empty(n, np.float64)
+        self._lib.orc_get_particles(self._h, m, _ptr(t, _d), _ptr(d, _d))
+        return t, d
+
+    def cell_coord(self, tau: float) -> float:
+        return self._lib.orc_cell_coord(self._h, float(tau))
+
+    def bin(self, tau):
+        """Histogram of arrival times on this run's mesh -> (hist, n_outside)."""
+        t = np.ascontiguousarray(tau, dtype=np.float64)
+        h = np.empty(self.nbins, np.int32)
+        out = self._lib.orc_bin(self._h, t.size, _ptr(t, _d), _ptr(h, _i32))
+        return h, int(out)
+
+    def track(self, nturns: int, record: bool = True):
+        """Track ``nturns``; returns moments [nturns][nb][6] if ``record``."""
+        if record:
+            rec = np.empty((nturns, self.nb, 6), np.float64)
+            self._lib.orc_track(self._h, int(nturns), _ptr(rec, _d))
+            return rec
+        self._lib.orc_track(self._h, int(nturns), None)
+        return None
+
+    def histograms(self):
+        h = np.empty((self.nb, self.nbins), np.int32)
+        o = np.empty(self.nb, np.int64)
+        self._lib.orc_get_hist(self._h, _ptr(h, _i32), _ptr(o, _i64))
+        return h, o
+
+    def vsr(self):
+        v = np.empty((self.nb, self.nbins), np.float64)
+        self._lib.orc_get_vsr(self._h, _ptr(v, _d))
+        return v
+
+    def vsr_direct(self, hist, q: float):
+        h = np.ascontiguousarray(hist, dtype=np.int32)
+        v = np.empty(self.nbins, np.float64)
+        self._lib.orc_vsr_direct(self._h, _ptr(h, _i32), float(q), _ptr(v, _d))
+        return v
+
+    def alr(self):
+        a = np.empty((max(1, self.nres), self.nb, 2), np.float64)
+        self._lib.orc_get_alr(self._h, _ptr(a, _d))
+        return a[..., 0] + 1j * a[..., 1]
+
+    def wlag(self):
+        w = np.empty(self.nbins, np.float64)
+        self._lib.orc_get_wlag(self._h, _ptr(w, _d))
+        return w
+
+    def feed_histograms(self, hist):
+        h = np.ascontiguousarray(hist, dtype=np.int32).reshape(self.nb, self.nbins)
+        self._lib.orc_feed_histograms(self._h, _ptr(h, _i32))
+
+    def last_emission(self, r: int):
+        e = np.empty((self.nb, 2), np.float64)
+        self._lib.orc_get_last_emission(self._h, int(r), _ptr(e, _d))
+        return e[:, 0] + 1j * e[:, 1]
+
+    def wake_voltage_at(self, m: int, tau: float) -> float:
+        return self._lib.orc_wake_voltage_at(self._h, int(m), float(tau))
+
+    @property
+    def turn(self) -> int:
+        return int(self._lib.orc_turn(self._h))

@@ -1,0 +1,616 @@
+/*
+ * FP64 CPU oracle for longitudinal multi-bunch macro-particle tracking
+ * (Xu, Locans, Adelmann, Stingelin, "Calculation of Longitudinal Collective
+ * Instabilities with mbtrack-cuda", arXiv:1809.00391).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * definition that the CUDA path is checked against.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline / reference leg may build, load
+ * or call it.  It shares no code with the CUDA library and includes none of
+ * its headers.
+ *
+ * Everything is double precision, single-threaded, written in the order the
+ * paper gives the per-turn map:
+ *   - energy update with RF gain and mean radiation loss   (Sec. 2.2, Eq. 1)
+ *   - radiation damping and quantum excitation, delta line  (Sec. 2.2, Eq. 5)
+ *   - longitudinal drift                                    (Sec. 2.2, Eq. 2)
+ *   - binning into a fixed longitudinal mesh, counting       (Sec. 2.3)
+ *   - wake potential built from resonators and applied as
+ *     an energy kick per particle                            (Sec. 2.3, Eq. 6)
+ *   - per-bunch mean and rms statistics                      (Sec. 2.4)
+ *   - long-range wake from earlier bunches and turns, applied
+ *     after all bunches have been processed                  (Sec. 2.3, last paragraph)
+ *
+ * Readings of points the paper leaves open (each is listed with its reason in
+ * the design notes of the repository):
+ *   R1 drift uses the energy deviation after the RF, damping and excitation
+ *      steps of the same turn (kick-then-drift, area preserving);
+ *   R2 D_E = D_e = 2 T0 / tau_z with tau_z the longitudinal amplitude damping
+ *      time, sigma_E the natural relative energy spread;
+ *   R3 order within a turn: wake kick (previous turn's wake) -> RF and U0 ->
+ *      damping and excitation -> drift -> binning and statistics -> wakes;
+ *   R4 eps(tau) = (eV/E0) sin(phi_s - omega_rf tau), sin(phi_s) = U0/(eV),
+ *      phi_s on the branch with cos(phi_s) of the sign of alpha_c;
+ *   R5 T_rf = T0 / h, omega_rf = 2 pi h / T0;
+ *   R6 per particle delta -= V(tau)/E0 (V in volts, E0 in eV) with
+ *      V(tau) = sum_k Q_k W(tau - tau_k); the resonator wake
+ *      W(t>0) = 2 a Rs e^{-a t}[cos(wb t) - (a/wb) sin(wb t)], W(t<0) = 0 and
+ *      half of W(0+) at zero lag;
+ *   R7 fixed mesh of nbins cells over [-H, H), H = k sigma_tau0,
+ *      bin = floor((tau + H) * (1/Delta)); outside particles are counted,
+ *      not deposited, and get no short-range kick;
+ *   R8 the short-range voltage is interpolated linearly between cell centres
+ *      (clamped at the end cells); nearest-cell is a flag;
+ *   R9 normal deviates from Philox4x32-10 + Box-Muller (cos and sin branch),
+ *      counter (pair, bunch, turn, tag), key (seed lo, seed hi);
+ *   R10 the long-range wake of a passage is sourced by its binned histogram at
+ *      cell centres, and acts on every particle of every later passage.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_RES 16
+#define ORC_RANGE_SHORT 1
+#define ORC_RANGE_LONG 2
+
+#define ORC_NO_SR 1      /* no radiation: U0 = 0, no damping, no excitation */
+#define ORC_NO_QE 2      /* damping kept, excitation removed                */
+#define ORC_KICK_NGP 4   /* short-range kick from the particle's own cell   */
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC'11.  Ten rounds of the 4x32 Philox S-box with the     */
+/* Weyl key schedule.                                                         */
+/* ------------------------------------------------------------------------- */
+static const uint32_t PHILOX_M0 = 0xD2511F53u;
+static const uint32_t PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u;
+static const uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in the open interval (0,1) from two 32-bit words: the top 53 bits of
+ * the 64-bit integer hi:lo, scaled by 2^-53, plus half a step (2^-54). */
+double orc_u01(uint32_t hi, uint32_t lo)
+{
+    uint64_t x = ((uint64_t)hi << 32) | (uint64_t)lo;
+    return (double)(x >> 11) * 0x1.0p-53 + 0x1.0p-54;
+}
+
+/* Box-Muller: two independent standard normals from two uniforms. */
+void orc_box_muller(double u1, double u2, double *r_cos, double *r_sin)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double R = sqrt(-2.0 * log(u1));
+    *r_cos = R * cos(two_pi * u2);
+    *r_sin = R * sin(two_pi * u2);
+}
+
+/* Normal pair for (pair index, bunch, turn, tag) under a 64-bit seed.
+ * Word layout: u1 from (w0, w1), u2 from (w2, w3); the cos branch goes to the
+ * even particle 2*pair, the sin branch to the odd particle 2*pair+1. */
+void orc_normal_pair(uint64_t seed, uint32_t pair, uint32_t bunch, uint32_t turn, uint32_t tag,
+                     double *r_even, double *r_odd)
+{
+    uint32_t ctr[4] = {pair, bunch, turn, tag};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    orc_box_muller(orc_u01(w[0], w[1]), orc_u01(w[2], w[3]), r_even, r_odd);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ring and wake definitions                                                  */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double E0_eV;        /* reference energy [eV]                        */
+    double T0_s;         /* revolution period [s]                        */
+    int32_t h;           /* harmonic number                              */
+    int32_t pad_;
+    double V_rf_V;       /* peak RF voltage [V]                          */
+    double alpha_c;      /* momentum compaction factor                   */
+    double U0_eV;        /* radiation energy loss per turn [eV]          */
+    double sigma_delta;  /* natural relative energy spread sigma_E       */
+    double tau_z_s;      /* longitudinal amplitude damping time [s]      */
+} orc_ring;
+
+typedef struct {
+    double Rs_ohm;       /* shunt impedance [Ohm]                        */
+    double fr_Hz;        /* resonant frequency [Hz]                      */
+    double Q;            /* quality factor (> 1/2)                       */
+    int32_t range;       /* bit 1: short range, bit 2: long range        */
+    int32_t pad_;
+} orc_resonator;
+
+/* Derived ring quantities, reading R4/R5 and the linear synchrotron motion. */
+typedef struct {
+    double T_rf, omega_rf, phi_s, sin_phi_s, U0_over_E0, V_over_E0;
+    double D;            /* damping decrement per turn, reading R2      */
+    double qe_amp;       /* sigma_E sqrt(2 D)                           */
+    double nu_s;         /* small-amplitude synchrotron tune            */
+    double sigma_tau0;   /* matched rms arrival-time spread            */
+} orc_derived;
+
+void orc_derive(const orc_ring *r, int flags, orc_derived *d)
+{
+    const double pi = 3.14159265358979323846264338327950;
+    int sr = !(flags & ORC_NO_SR);
+    double U0 = sr ? r->U0_eV : 0.0;
+    d->T_rf = r->T0_s / (double)r->h;
+    d->omega_rf = 2.0 * pi * (double)r->h / r->T0_s;
+    d->sin_phi_s = U0 / r->V_rf_V;
+    d->phi_s = asin(d->sin_phi_s);
+    if (r->alpha_c < 0.0)
+        d->phi_s = pi - d->phi_s;
+    d->U0_over_E0 = U0 / r->E0_eV;
+    d->V_over_E0 = r->V_rf_V / r->E0_eV;
+    d->D = sr ? 2.0 * r->T0_s / r->tau_z_s : 0.0;
+    d->qe_amp = (sr && !(flags & ORC_NO_QE)) ? r->sigma_delta * sqrt(2.0 * d->D) : 0.0;
+    d->nu_s = sqrt(r->alpha_c * (double)r->h * r->V_rf_V * cos(d->phi_s) / (2.0 * pi * r->E0_eV));
+    d->sigma_tau0 = fabs(r->alpha_c) * r->sigma_delta * r->T0_s / (2.0 * pi * d->nu_s);
+}
+
+/* Resonator constants: decay rate a = w_r/(2Q), damped frequency wb. */
+static void res_consts(const orc_resonator *q, double *a, double *wb)
+{
+    const double pi = 3.14159265358979323846264338327950;
+    double wr = 2.0 * pi * q->fr_Hz;
+    *a = wr / (2.0 * q->Q);
+    *wb = sqrt(wr * wr - (*a) * (*a));
+}
+
+/* Longitudinal resonator wake function [V/C], reading R6. */
+double orc_wake(const orc_resonator *q, double t)
+{
+    double a, wb;
+    res_consts(q, &a, &wb);
+    if (t < 0.0)
+        return 0.0;
+    if (t == 0.0)
+        return a * q->Rs_ohm; /* half of W(0+) = 2 a Rs */
+    return 2.0 * a * q->Rs_ohm * exp(-a * t) * (cos(wb * t) - (a / wb) * sin(wb * t));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Simulation state                                                           */
+/* ------------------------------------------------------------------------- */
+typedef struct orc_sim {
+    orc_ring ring;
+    orc_derived dv;
+    int flags;
+    uint64_t seed;
+    int nres;
+    orc_resonator res[ORC_MAX_RES];
+    int nbins;
+    double H, Delta, invDelta;
+    int nb;
+    int32_t *bucket;
+    double *current;
+    int64_t *n_mp;
+    double *q_mp;          /* macro-particle charge per bunch [C]           */
+    double **tau, **delta;
+    int32_t *hist;         /* [nb][nbins], this turn                         */
+    int64_t *out_count;    /* [nb], this turn                                */
+    double *Wlag;          /* [nbins] summed short-range wake at lag l*Delta */
+    double *Vsr;           /* [nb][nbins] short-range voltage for the kick   */
+    double complex *Alr;   /* [nres][nb] long-range amplitude for the kick   */
+    /* emission history for the direct long-range sum: [nres][nhist][nb]     */
+    int nhist;
+    double complex *Ehist;
+    int64_t turn;          /* turns completed                                */
+    double *moments;       /* [nb][6]: <tau>, sig_tau, <delta>, sig_delta, n_in, n_out */
+} orc_sim;
+
+/* e^{-a dt} below this is dropped from the direct history sum. */
+static const double ORC_HISTORY_CUTOFF = 1e-18;
+
+orc_sim *orc_create(const orc_ring *ring, int flags, uint64_t seed,
+                    int nres, const orc_resonator *res,
+                    int nbins, double half_width_sigmas,
+                    int nb, const int32_t *bucket, const double *current_A, const int64_t *n_mp)
+{
+    if (nres < 0 || nres > ORC_MAX_RES || nbins < 2 || nb < 1)
+        return NULL;
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    s->ring = *ring;
+    s->flags = flags;
+    s->seed = seed;
+    orc_derive(ring, flags, &s->dv);
+    s->nres = nres;
+    for (int r = 0; r < nres; ++r)
+        s->res[r] = res[r];
+    s->nbins = nbins;
+    s->H = half_width_sigmas * s->dv.sigma_tau0;
+    s->Delta = 2.0 * s->H / (double)nbins;
+    s->invDelta = 1.0 / s->Delta;
+    s->nb = nb;
+    s->bucket = (int32_t *)malloc(sizeof(int32_t) * nb);
+    s->current = (double *)malloc(sizeof(double) * nb);
+    s->n_mp = (int64_t *)malloc(sizeof(int64_t) * nb);
+    s->q_mp = (double *)malloc(sizeof(double) * nb);
+    s->tau = (double **)calloc(nb, sizeof(double *));
+    s->delta = (double **)calloc(nb, sizeof(double *));
+    for (int m = 0; m < nb; ++m) {
+        s->bucket[m] = bucket[m];
+        s->current[m] = current_A[m];
+        s->n_mp[m] = n_mp[m];
+        s->q_mp[m] = n_mp[m] > 0 ? current_A[m] * ring->T0_s / (double)n_mp[m] : 0.0;
+        s->tau[m] = (double *)calloc(n_mp[m] > 0 ? n_mp[m] : 1, sizeof(double));
+        s->delta[m] = (double *)calloc(n_mp[m] > 0 ? n_mp[m] : 1, sizeof(double));
+    }
+    s->hist = (int32_t *)calloc((size_t)nb * nbins, sizeof(int32_t));
+    s->out_count = (int64_t *)calloc(nb, sizeof(int64_t));
+    s->Vsr = (double *)calloc((size_t)nb * nbins, sizeof(double));
+    s->Alr = (double complex *)calloc((size_t)(nres > 0 ? nres : 1) * nb, sizeof(double complex));
+    s->moments = (double *)calloc((size_t)nb * 6, sizeof(double));
+    s->Wlag = (double *)calloc(nbins, sizeof(double));
+    for (int l = 0; l < nbins; ++l) {
+        double w = 0.0;
+        for (int r = 0; r < nres; ++r)
+            if (res[r].range & ORC_RANGE_SHORT)
+                w += orc_wake(&res[r], (double)l * s->Delta);
+        s->Wlag[l] = w;
+    }
+    /* history depth: the slowest-decaying long-range resonator sets it */
+    double amin = 0.0;
+    int any_long = 0;
+    for (int r = 0; r < nres; ++r) {
+        if (!(res[r].range & ORC_RANGE_LONG))
+            continue;
+        double a, wb;
+        res_consts(&res[r], &a, &wb);
+        if (!any_long || a < amin)
+            amin = a;
+        any_long = 1;
+    }
+    s->nhist = any_long ? (int)ceil(-log(ORC_HISTORY_CUTOFF) / (amin * ring->T0_s)) + 2 : 1;
+    s->Ehist = (double complex *)calloc((size_t)(nres > 0 ? nres : 1) * s->nhist * nb, sizeof(double complex));
+    return s;
+}
+
+void orc_destroy(orc_sim *s)
+{
+    if (!s)
+        return;
+    for (int m = 0; m < s->nb; ++m) {
+        free(s->tau[m]);
+        free(s->delta[m]);
+    }
+    free(s->tau); free(s->delta); free(s->bucket); free(s->current); free(s->n_mp); free(s->q_mp);
+    free(s->hist); free(s->out_count); free(s->Vsr); free(s->Alr); free(s->moments);
+    free(s->Wlag); free(s->Ehist); free(s);
+}
+
+void orc_get_derived(const orc_sim *s, double out[12])
+{
+    out[0] = s->dv.T_rf; out[1] = s->dv.omega_rf; out[2] = s->dv.phi_s; out[3] = s->dv.D;
+    out[4] = s->dv.qe_amp; out[5] = s->dv.nu_s; out[6] = s->dv.sigma_tau0; out[7] = s->H;
+    out[8] = s->Delta; out[9] = s->invDelta; out[10] = (double)s->nhist; out[11] = (double)s->turn;
+}
+
+/* Matched Gaussian start: tau ~ N(0, sigma_tau0), delta ~ N(0, sigma_E),
+ * normals from turn 0 with tag 1 (tau) and tag 2 (delta). */
+void orc_init_particles(orc_sim *s)
+{
+    for (int m = 0; m < s->nb; ++m) {
+        int64_t n = s->n_mp[m];
+        for (int64_t i = 0; i < n; i += 2) {
+            double a0, a1, b0, b1;
+            orc_normal_pair(s->seed, (uint32_t)(i / 2), (uint32_t)m, 0u, 1u, &a0, &a1);
+            orc_normal_pair(s->seed, (uint32_t)(i / 2), (uint32_t)m, 0u, 2u, &b0, &b1);
+            s->tau[m][i] = s->dv.sigma_tau0 * a0;
+            s->delta[m][i] = s->ring.sigma_delta * b0;
+            if (i + 1 < n) {
+                s->tau[m][i + 1] = s->dv.sigma_tau0 * a1;
+                s->delta[m][i + 1] = s->ring.sigma_delta * b1;
+            }
+        }
+    }
+}
+
+void orc_set_particles(orc_sim *s, int m, const double *tau, const double *delta)
+{
+    memcpy(s->tau[m], tau, sizeof(double) * s->n_mp[m]);
+    memcpy(s->delta[m], delta, sizeof(double) * s->n_mp[m]);
+}
+
+void orc_get_particles(const orc_sim *s, int m, double *tau, double *delta)
+{
+    memcpy(tau, s->tau[m], sizeof(double) * s->n_mp[m]);
+    memcpy(delta, s->delta[m], sizeof(double) * s->n_mp[m]);
+}
+
+/* Cell coordinate x = (tau + H) * (1/Delta), both operations rounded
+ * separately (the build disables contraction); the cell is floor(x). */
+double orc_cell_coord(const orc_sim *s, double tau)
+{
+    double t = tau + s->H;
+    return t * s->invDelta;
+}
+
+/* Deposit one particle into a bunch histogram (Sec. 2.3, reading R7):
+ * returns 1 if it fell outside the mesh (counted, not deposited). */
+static int bin_one(const orc_sim *s, double tau, int32_t *hist)
+{
+    double x = orc_cell_coord(s, tau);
+    if (x >= 0.0 && x < (double)s->nbins) {
+        hist[(int)floor(x)] += 1;
+        return 0;
+    }
+    return 1;
+}
+
+/* Histogram of n arrival times on the sim's mesh; returns the outside count. */
+int64_t orc_bin(const orc_sim *s, int64_t n, const double *tau, int32_t *hist)
+{
+    memset(hist, 0, sizeof(int32_t) * s->nbins);
+    int64_t out = 0;
+    for (int64_t i = 0; i < n; ++i)
+        out += bin_one(s, tau[i], hist);
+    return out;
+}
+
+/* Short-range voltage at a particle, reading R7/R8. */
+static double vsr_at(const orc_sim *s, int m, double x)
+{
+    const int nb = s->nbins;
+    if (!(x >= 0.0 && x < (double)nb))
+        return 0.0;
+    const double *V = s->Vsr + (size_t)m * nb;
+    if (s->flags & ORC_KICK_NGP)
+        return V[(int)floor(x)];
+    double u = x - 0.5;
+    if (u <= 0.0)
+        return V[0];
+    if (u >= (double)(nb - 1))
+        return V[nb - 1];
+    double j0 = floor(u);
+    double f = u - j0;
+    int j = (int)j0;
+    return (1.0 - f) * V[j] + f * V[j + 1];
+}
+
+/* Long-range voltage at a particle of bunch m: sum over long-range resonators
+ * of Re(A e^{s tau}), s = -a + i wb (reading R10). */
+static double vlr_at(const orc_sim *s, int m, double tau)
+{
+    double v = 0.0;
+    for (int r = 0; r < s->nres; ++r) {
+        if (!(s->res[r].range & ORC_RANGE_LONG))
+            continue;
+        double a, wb;
+        res_consts(&s->res[r], &a, &wb);
+        double complex sr = -a + I * wb;
+        v += creal(s->Alr[(size_t)r * s->nb + m] * cexp(sr * tau));
+    }
+    return v;
+}
+
+/* Short-range voltage of one bunch from its histogram: the direct double sum
+ * V[j] = q * sum_{k<=j} hist[k] * Wtot((j-k) Delta), reading R6. */
+void orc_vsr_direct(const orc_sim *s, const int32_t *hist, double q, double *V)
+{
+    for (int j = 0; j < s->nbins; ++j) {
+        double v = 0.0;
+        for (int k = 0; k <= j; ++k)
+            v += (double)hist[k] * s->Wlag[j - k];
+        V[j] = q * v;
+    }
+}
+
+/* Emission of one passage for resonator r: c q sum_k hist[k] e^{-s tau_k},
+ * c = 2 a Rs (1 + i a/wb), tau_k the cell centres. */
+double complex orc_emission(const orc_sim *s, int r, const int32_t *hist, double q)
+{
+    double a, wb;
+    res_consts(&s->res[r], &a, &wb);
+    double complex sr = -a + I * wb;
+    double complex c = 2.0 * a * s->res[r].Rs_ohm * (1.0 + I * (a / wb));
+    double complex acc = 0.0;
+    for (int k = 0; k < s->nbins; ++k) {
+        if (hist[k] == 0)
+            continue;
+        double tk = -s->H + ((double)k + 0.5) * s->Delta;
+        acc += (double)hist[k] * cexp(-sr * tk);
+    }
+    return c * q * acc;
+}
+
+/* Direct history sum for bunch m after turn n has been binned: every passage
+ * strictly earlier than (n, m), weighted by e^{s dt}, dt = D T_rf with D the
+ * integer bucket distance, truncated at e^{-a dt} < cutoff. */
+static double complex history_sum(const orc_sim *s, int r, int m)
+{
+    double a, wb;
+    res_consts(&s->res[r], &a, &wb);
+    double complex sr = -a + I * wb;
+    const int64_t n = s->turn; /* the turn just binned */
+    const int h = s->ring.h;
+    double complex acc = 0.0;
+    for (int64_t back = 0; back < s->nhist; ++back) {
+        int64_t np = n - back;
+        if (np < 0)
+            break;
+        const double complex *E = s->Ehist + ((size_t)r * s->nhist + (size_t)(np % s->nhist)) * s->nb;
+        for (int mp = 0; mp < s->nb; ++mp) {
+            int64_t D = back * (int64_t)h + (int64_t)s->bucket[m] - (int64_t)s->bucket[mp];
+            if (D <= 0)
+                continue; /* not earlier */
+            double dt = (double)D * s->dv.T_rf;
+            if (exp(-a * dt) < ORC_HISTORY_CUTOFF)
+                continue;
+            acc += cexp(sr * dt) * E[mp];
+        }
+    }
+    return acc;
+}
+
+/* One turn for every bunch in fill order, then the wakes for the next turn. */
+static void one_turn(orc_sim *s)
+{
+    const uint32_t turn32 = (uint32_t)s->turn;
+    for (int m = 0; m < s->nb; ++m) {
+        const int64_t n = s->n_mp[m];
+        int32_t *hist = s->hist + (size_t)m * s->nbins;
+        memset(hist, 0, sizeof(int32_t) * s->nbins);
+        int64_t out = 0;
+        double *tau = s->tau[m], *delta = s->delta[m];
+        for (int64_t i = 0; i < n; i += 2) {
+            double r[2];
+            if (s->dv.qe_amp != 0.0)
+                orc_normal_pair(s->seed, (uint32_t)(i / 2), (uint32_t)m, turn32, 0u, &r[0], &r[1]);
+            else
+                r[0] = r[1] = 0.0;
+            for (int e = 0; e < 2 && i + e < n; ++e) {
+                double t = tau[i + e], d = delta[i + e];
+                /* wake kick with the previous turn's wake (zero on turn 0) */
+                double V = vsr_at(s, m, orc_cell_coord(s, t)) + vlr_at(s, m, t);
+                d = d - V / s->ring.E0_eV;
+                /* Eq. 1: RF gain minus mean radiation loss */
+                d = d + s->dv.V_over_E0 * sin(s->dv.phi_s - s->dv.omega_rf * t) - s->dv.U0_over_E0;
+                /* Eq. 5, delta line: damping and quantum excitation */
+                d = d * (1.0 - s->dv.D) + s->dv.qe_amp * r[e];
+                /* Eq. 2 with the new energy deviation (reading R1) */
+                t = t + s->ring.alpha_c * s->ring.T0_s * d;
+                tau[i + e] = t;
+                delta[i + e] = d;
+                /* binning (Sec. 2.3) */
+                out += bin_one(s, t, hist);
+            }
+        }
+        s->out_count[m] = out;
+        /* statistics of the bunch (Sec. 2.4): two-pass mean and rms */
+        double st = 0.0, sd = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            st += tau[i];
+            sd += delta[i];
+        }
+        double mt = n > 0 ? st / (double)n : 0.0, md = n > 0 ? sd / (double)n : 0.0;
+        double vt = 0.0, vd = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            vt += (tau[i] - mt) * (tau[i] - mt);
+            vd += (delta[i] - md) * (delta[i] - md);
+        }
+        double *mo = s->moments + (size_t)m * 6;
+        mo[0] = mt;
+        mo[1] = n > 0 ? sqrt(vt / (double)n) : 0.0;
+        mo[2] = md;
+        mo[3] = n > 0 ? sqrt(vd / (double)n) : 0.0;
+        mo[4] = (double)(n - out);
+        mo[5] = (double)out;
+    }
+    /* wakes from this turn's histograms, applied at the start of the next */
+    for (int m = 0; m < s->nb; ++m)
+        orc_vsr_direct(s, s->hist + (size_t)m * s->nbins, s->q_mp[m], s->Vsr + (size_t)m * s->nbins);
+    for (int r = 0; r < s->nres; ++r) {
+        if (!(s->res[r].range & ORC_RANGE_LONG))
+            continue;
+        double complex *E = s->Ehist + ((size_t)r * s->nhist + (size_t)(s->turn % s->nhist)) * s->nb;
+        for (int m = 0; m < s->nb; ++m)
+            E[m] = orc_emission(s, r, s->hist + (size_t)m * s->nbins, s->q_mp[m]);
+        for (int m = 0; m < s->nb; ++m)
+            s->Alr[(size_t)r * s->nb + m] = history_sum(s, r, m);
+    }
+    s->turn += 1;
+}
+
+/* Track nturns; if rec is non-null it receives [nturns][nb][6] moments. */
+void orc_track(orc_sim *s, int64_t nturns, double *rec)
+{
+    for (int64_t t = 0; t < nturns; ++t) {
+        one_turn(s);
+        if (rec)
+            memcpy(rec + (size_t)t * s->nb * 6, s->moments, sizeof(double) * s->nb * 6);
+    }
+}
+
+void orc_get_hist(const orc_sim *s, int32_t *hist, int64_t *out_count)
+{
+    memcpy(hist, s->hist, sizeof(int32_t) * (size_t)s->nb * s->nbins);
+    if (out_count)
+        memcpy(out_count, s->out_count, sizeof(int64_t) * s->nb);
+}
+
+void orc_get_vsr(const orc_sim *s, double *V)
+{
+    memcpy(V, s->Vsr, sizeof(double) * (size_t)s->nb * s->nbins);
+}
+
+/* Long-range amplitudes [nres][nb] as interleaved (re, im). */
+void orc_get_alr(const orc_sim *s, double *A)
+{
+    for (size_t i = 0; i < (size_t)s->nres * s->nb; ++i) {
+        A[2 * i] = creal(s->Alr[i]);
+        A[2 * i + 1] = cimag(s->Alr[i]);
+    }
+}
+
+void orc_get_wlag(const orc_sim *s, double *W)
+{
+    memcpy(W, s->Wlag, sizeof(double) * s->nbins);
+}
+
+/* Test hooks for the long-range pieces: feed one turn of histograms without
+ * moving particles (emission + direct history sum), as the end of a turn
+ * does. hist is [nb][nbins]. */
+void orc_feed_histograms(orc_sim *s, const int32_t *hist)
+{
+    memcpy(s->hist, hist, sizeof(int32_t) * (size_t)s->nb * s->nbins);
+    for (int m = 0; m < s->nb; ++m)
+        orc_vsr_direct(s, s->hist + (size_t)m * s->nbins, s->q_mp[m], s->Vsr + (size_t)m * s->nbins);
+    for (int r = 0; r < s->nres; ++r) {
+        if (!(s->res[r].range & ORC_RANGE_LONG))
+            continue;
+        double complex *E = s->Ehist + ((size_t)r * s->nhist + (size_t)(s->turn % s->nhist)) * s->nb;
+        for (int m = 0; m < s->nb; ++m)
+            E[m] = orc_emission(s, r, s->hist + (size_t)m * s->nbins, s->q_mp[m]);
+        for (int m = 0; m < s->nb; ++m)
+            s->Alr[(size_t)r * s->nb + m] = history_sum(s, r, m);
+    }
+    s->turn += 1;
+}
+
+/* Emission values of the last recorded turn for resonator r, (re, im) x nb. */
+void orc_get_last_emission(const orc_sim *s, int r, double *E)
+{
+    int64_t t = s->turn - 1;
+    if (t < 0)
+        t = 0;
+    const double complex *Er = s->Ehist + ((size_t)r * s->nhist + (size_t)(t % s->nhist)) * s->nb;
+    for (int m = 0; m < s->nb; ++m) {
+        E[2 * m] = creal(Er[m]);
+        E[2 * m + 1] = cimag(Er[m]);
+    }
+}
+
+/* Kick-free single-particle evaluation of the wake voltage seen at tau by a
+ * particle of bunch m (short + long range), for tests. */
+double orc_wake_voltage_at(const orc_sim *s, int m, double tau)
+{
+    return vsr_at(s, m, orc_cell_coord(s, tau)) + vlr_at(s, m, tau);
+}
+
+int64_t orc_turn(const orc_sim *s) { return s->turn; }
