@@ -1,0 +1,229 @@
+/*
+ * mbt.h - C ABI of the GB300 longitudinal multi-bunch tracking library (libmbt).
+ *
+ * The library tracks the macro-particles of every bunch of a fill, turn after
+ * turn, on one GPU, with the per-turn map of Xu, Locans, Adelmann and
+ * Stingelin, "Calculation of Longitudinal Collective Instabilities with
+ * mbtrack-cuda" (arXiv:1809.00391):
+ *
+ *   delta -= V_wake(tau) / E0                 wake kick            (Sec. 2.3, Eq. 6)
+ *   delta += eps(tau) - U0/E0                 RF gain, SR loss     (Sec. 2.2, Eq. 1)
+ *   delta  = delta (1 - D) + sigma_E sqrt(2D) r   damping + excitation (Sec. 2.2, Eq. 5)
+ *   tau   += alpha_c T0 delta                 drift                (Sec. 2.2, Eq. 2)
+ *   bin tau into a fixed mesh, per-bunch mean / rms           (Sec. 2.3, Sec. 2.4)
+ *   short-range wake: causal convolution of the line density with the summed
+ *   resonator wake; long-range wake: resonator phasors carried from every
+ *   earlier bunch passage, this turn and earlier turns   (Sec. 2.3, last paragraph)
+ *
+ * with these readings of the paper: the drift uses the updated delta; D =
+ * 2 T0 / tau_z; eps(tau) = (eV/E0) sin(phi_s - omega_rf tau) with sin(phi_s) =
+ * U0 / eV; omega_rf = 2 pi h / T0; the wake W(t) of a resonator (Rs, w_r, Q) is
+ * 2 a Rs e^{-a t}[cos(wb t) - (a/wb) sin(wb t)] for t > 0 (a = w_r/2Q,
+ * wb = sqrt(w_r^2 - a^2)), 0 for t < 0 and half of W(0+) at zero lag.
+ *
+ * Conventions
+ *  - SI units: seconds, volts, ohms, hertz, amperes, coulombs; energies in eV.
+ *  - Every call returns an mbt_status (0 = MBT_OK).  No C++ exception crosses
+ *    the ABI.  On failure mbt_last_error() returns a message.
+ *  - The library owns all device memory it allocates (cudaMalloc inside
+ *    mbt_set_fill); the caller owns every host buffer passed in.  Host
+ *    pointers are only read or written during the call.
+ *  - A context is thread-compatible: one thread at a time.  Contexts are
+ *    independent of each other.
+ *  - "stream" arguments are a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Tracking calls are asynchronous on that stream;
+ *    mbt_sync() or any read call waits for it.
+ *  - Device errors (a kernel that failed, a bounded wait that gave up) are
+ *    reported by the next call that synchronises.
+ */
+#ifndef MBT_H
+#define MBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MBT_VERSION 100
+
+typedef int mbt_status;
+enum {
+    MBT_OK = 0,
+    MBT_ERR_ARG = 1,          /* invalid argument (value out of range, null pointer)   */
+    MBT_ERR_STATE = 2,        /* call not valid in the context's current state         */
+    MBT_ERR_NOMEM = 3,        /* device or host allocation failed                      */
+    MBT_ERR_CUDA = 4,         /* a CUDA runtime call or kernel failed                  */
+    MBT_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up                    */
+    MBT_ERR_UNSUPPORTED = 6,  /* configuration outside what this build implements      */
+    MBT_ERR_BUDGET = 7        /* request exceeds the memory budget (serving)           */
+};
+
+/* Precision of the tracking path. */
+enum {
+    MBT_PREC_F64 = 0,    /* every step in FP64; histograms bit-exact vs an FP64 tracker    */
+    MBT_PREC_MIXED = 1   /* tau FP32; delta stored and accumulated in FP64; push arithmetic
+                            FP32; short-range wake on the tensor cores (BF16 hi/lo split of
+                            the wake, byte-split counts, FP32 accumulation); long-range
+                            phasor scan and moment sums in FP64                           */
+};
+
+/* Resonator range: short range = convolution within the bunch's own passage;
+ * long range = phasor carried to every later passage. */
+enum { MBT_RANGE_SHORT = 1, MBT_RANGE_LONG = 2, MBT_RANGE_BOTH = 3 };
+
+/* Option flags (mbt_create). */
+enum {
+    MBT_NO_SR = 1,     /* no radiation: U0 = 0 (phi_s = 0 or pi), no damping, no excitation */
+    MBT_NO_QE = 2,     /* radiation damping kept, quantum excitation removed                */
+    MBT_KICK_NGP = 4   /* short-range kick from the particle's own cell instead of linear
+                          interpolation between cell centres                                */
+};
+
+/* Ring parameters (Table 1 of the paper lists them for the 'dc12c' lattice). */
+typedef struct {
+    double E0_eV;        /* reference energy [eV], > 0                                  */
+    double T0_s;         /* revolution period [s], > 0                                   */
+    int32_t h;           /* harmonic number, 1..65535                                    */
+    int32_t reserved;    /* must be 0                                                    */
+    double V_rf_V;       /* peak RF voltage [V], > U0                                    */
+    double alpha_c;      /* momentum compaction factor, != 0 (sign selects phi_s branch) */
+    double U0_eV;        /* radiation loss per turn [eV], >= 0                           */
+    double sigma_delta;  /* natural relative energy spread sigma_E, > 0                  */
+    double tau_z_s;      /* longitudinal amplitude damping time [s], > 0                 */
+} mbt_ring;
+
+/* Derived quantities, as the library computes them (mbt_get_info). */
+typedef struct {
+    double T_rf_s, omega_rf, phi_s, nu_s, sigma_tau0_s;
+    double D;                  /* damping decrement per turn                         */
+    double half_width_s;       /* H: the mesh covers [-H, H)                         */
+    double bin_width_s;        /* Delta = 2H / nbins                                 */
+    int64_t n_particles;       /* all bunches                                        */
+    int64_t turn;              /* turns completed                                    */
+    int32_t nb, nbins, n_long, precision;
+    int64_t device_bytes;      /* device memory held by the context                  */
+} mbt_info;
+
+typedef struct mbt_ctx mbt_ctx;
+typedef struct mbt_batch mbt_batch;
+
+/* Library version (MBT_VERSION) and a static message for a status code. */
+int mbt_version(void);
+const char *mbt_status_string(mbt_status s);
+
+/* Create a context for one run.  precision: MBT_PREC_*; flags: MBT_NO_SR |
+ * MBT_NO_QE | MBT_KICK_NGP; seed: 64-bit key of the Philox4x32-10 streams
+ * (Salmon et al., SC'11) that draw the initial distribution and the quantum
+ * excitation (counter = pair index, bunch, turn, tag).  Errors: MBT_ERR_ARG on
+ * a null pointer or an invalid ring. */
+mbt_status mbt_create(const mbt_ring *ring, int precision, int flags, uint64_t seed, mbt_ctx **out);
+
+/* Destroy a context and free its device memory (synchronises its stream).
+ * Accepts NULL. */
+void mbt_destroy(mbt_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  The string
+ * is owned by the context and valid until the next call on it. */
+const char *mbt_last_error(const mbt_ctx *ctx);
+
+/* Add a resonator to the wake model (Sec. 2.3: the wake is the sum of the
+ * resonators').  Rs_ohm > 0, fr_Hz > 0, Q > 0.5, range MBT_RANGE_*.  At most
+ * 8 resonators, at most 4 with the long-range bit.  Only before
+ * mbt_set_fill. */
+mbt_status mbt_add_resonator(mbt_ctx *ctx, double Rs_ohm, double fr_Hz, double Q, int range);
+
+/* Longitudinal mesh (Sec. 2.3): nbins cells over [-H, H), H =
+ * half_width_sigmas * sigma_tau0 with sigma_tau0 = |alpha_c| sigma_E T0 /
+ * (2 pi nu_s).  MBT_PREC_F64: 2 <= nbins <= 1024.  MBT_PREC_MIXED: nbins 128
+ * or 256.  Default 256 cells, 5 sigma.  Only before mbt_set_fill. */
+mbt_status mbt_set_grid(mbt_ctx *ctx, int nbins, double half_width_sigmas);
+
+/* Fill pattern: nb bunches in strictly increasing buckets 0 <= bucket < h,
+ * bunch current current_A[m] >= 0 [A] (macro-charge = I T0 / N) and n_mp[m]
+ * macro-particles (1 .. 2^31-2; MBT_PREC_MIXED: up to 2^24-1 so that a cell
+ * count is exact in three bytes).  Allocates every device buffer.  Particles
+ * start at zero; call mbt_init_particles or mbt_set_particles.  Errors:
+ * MBT_ERR_ARG, MBT_ERR_NOMEM, MBT_ERR_STATE (fill already set). */
+mbt_status mbt_set_fill(mbt_ctx *ctx, int nb, const int32_t *bucket, const double *current_A,
+                        const int64_t *n_mp);
+
+/* Capacity of the device ring buffer of per-turn moments, in turns (default
+ * 4096).  Only before mbt_set_fill. */
+mbt_status mbt_set_record(mbt_ctx *ctx, int64_t capacity_turns);
+
+/* Matched Gaussian start: tau ~ N(0, sigma_tau0), delta ~ N(0, sigma_E), from
+ * the Philox streams with tags 1 (tau) and 2 (delta) at turn 0.  Resets the
+ * turn counter and every wake to zero.  Asynchronous on stream. */
+mbt_status mbt_init_particles(mbt_ctx *ctx, void *stream);
+
+/* Copy one bunch's coordinates from host arrays of n_mp[bunch] doubles
+ * (MBT_PREC_MIXED rounds tau to FP32).  Synchronous. */
+mbt_status mbt_set_particles(mbt_ctx *ctx, int bunch, const double *tau_s, const double *delta);
+
+/* Copy one bunch's coordinates to host arrays of n_mp[bunch] doubles.
+ * Synchronous (waits for tracking in flight). */
+mbt_status mbt_get_particles(mbt_ctx *ctx, int bunch, double *tau_s, double *delta);
+
+/* Track nturns turns (asynchronous on stream).  Each turn runs the push
+ * kernel over every bunch and the post kernel (wakes, moments).  If graph
+ * replay is enabled (mbt_set_graph) whole chunks of turns are replayed from a
+ * captured CUDA graph. */
+mbt_status mbt_track(mbt_ctx *ctx, int64_t nturns, void *stream);
+
+/* Wait for the context's work; report device errors. */
+mbt_status mbt_sync(mbt_ctx *ctx);
+
+/* Per-turn moments of turns [turn0, turn0 + nturns) into out[nturns][nb][6]:
+ * <tau>, rms tau, <delta>, rms delta, particles inside the mesh, outside.
+ * The statistics are taken after the drift of the turn, before the next
+ * turn's wake kick.  Turns older than the record capacity are gone
+ * (MBT_ERR_ARG).  Synchronous. */
+mbt_status mbt_read_moments(mbt_ctx *ctx, int64_t turn0, int64_t nturns, double *out);
+
+/* Histograms [nb][nbins] (int32) and outside counts [nb] (int64, may be NULL)
+ * of the last completed turn.  Synchronous. */
+mbt_status mbt_read_histograms(mbt_ctx *ctx, int32_t *hist, int64_t *outside);
+
+/* Wake state that the next turn's kick will use: short-range voltage
+ * Vsr[nb][nbins] [V] and the long-range phasor Phi[n_long][nb][2] (re, im) such
+ * that V_long(tau) = sum_r Re(Phi_r,m e^{s_r tau}).  Either pointer may be
+ * NULL.  Synchronous. */
+mbt_status mbt_read_wake(mbt_ctx *ctx, double *Vsr, double *Phi);
+
+/* Derived quantities and sizes. */
+mbt_status mbt_get_info(mbt_ctx *ctx, mbt_info *info);
+
+/* CUDA-graph replay: capture turns_per_graph turns once and replay the graph
+ * (0 disables; default 0).  The first mbt_track after a change captures. */
+mbt_status mbt_set_graph(mbt_ctx *ctx, int turns_per_graph);
+
+/* Kernel timing: when enabled, mbt_track records CUDA events around every
+ * push-kernel launch on the tracking stream.  mbt_get_timing returns the sum
+ * of their durations [ms] and the number of timed launches since the last
+ * reset (enable = 1 resets).  Timing forces plain launches (no graph). */
+mbt_status mbt_set_timing(mbt_ctx *ctx, int enable);
+mbt_status mbt_get_timing(mbt_ctx *ctx, double *push_ms, double *post_ms, int64_t *launches);
+
+/* Checkpoint: mbt_state_size gives the bytes of a snapshot (particles, turn,
+ * wake and phasor carry, histograms); mbt_save_state writes it into buf;
+ * mbt_load_state restores it into a context with the same configuration.
+ * A resumed run is bit-identical to an uninterrupted one. */
+mbt_status mbt_state_size(mbt_ctx *ctx, size_t *bytes);
+mbt_status mbt_save_state(mbt_ctx *ctx, void *buf, size_t bytes);
+mbt_status mbt_load_state(mbt_ctx *ctx, const void *buf, size_t bytes);
+
+/* Batched tracking: n contexts with the same precision, each with its fill
+ * set, tracked together in the same kernel launches (one push and one post
+ * launch per turn for all of them).  The contexts stay owned by the caller
+ * and must outlive the batch. */
+mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out);
+mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream);
+mbt_status mbt_batch_sync(mbt_batch *b);   /* wait; report device errors of the batch */
+void mbt_batch_destroy(mbt_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBT_H */

@@ -1,0 +1,276 @@
+"""Python binding of libmbt: GB300-native longitudinal multi-bunch tracking.
+
+A thin ctypes layer over the C ABI in ``include/mbt.h`` (argument marshalling
+only; every step of the tracking runs in the library's CUDA kernels).  CUDA
+streams may be given as ``None`` (legacy default stream), a raw handle
+(``int``) or a ``torch.cuda.Stream``.  The library must have been built
+(``paper_1809_00391_gb300.build()``); there is no fallback: using the binding
+without it raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from pathlib import Path
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+from ._build import build
+
+__all__ = ["build", "lib", "Tracker", "Batch", "MBTError", "PREC_F64", "PREC_MIXED", "RANGE_SHORT",
+           "RANGE_LONG", "RANGE_BOTH", "NO_SR", "NO_QE", "KICK_NGP", "EXPORTS", "tracker_for_run"]
+
+PREC_F64, PREC_MIXED = 0, 1
+RANGE_SHORT, RANGE_LONG, RANGE_BOTH = 1, 2, 3
+NO_SR, NO_QE, KICK_NGP = 1, 2, 4
+
+# every entry point declared in include/mbt.h
+EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt_last_error",
+           "mbt_add_resonator", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
+           "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_sync", "mbt_read_moments",
+           "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_timing",
+           "mbt_get_timing", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_batch_create",
+           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_destroy"]
+
+
+class MBTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmbt status {status}: {msg}")
+        self.status = status
+
+
+class Ring(ctypes.Structure):
+    _fields_ = [("E0_eV", ctypes.c_double), ("T0_s", ctypes.c_double), ("h", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("V_rf_V", ctypes.c_double), ("alpha_c", ctypes.c_double),
+                ("U0_eV", ctypes.c_double), ("sigma_delta", ctypes.c_double), ("tau_z_s", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("T_rf_s", ctypes.c_double), ("omega_rf", ctypes.c_double), ("phi_s", ctypes.c_double),
+                ("nu_s", ctypes.c_double), ("sigma_tau0_s", ctypes.c_double), ("D", ctypes.c_double),
+                ("half_width_s", ctypes.c_double), ("bin_width_s", ctypes.c_double),
+                ("n_particles", ctypes.c_int64), ("turn", ctypes.c_int64), ("nb", ctypes.c_int32),
+                ("nbins", ctypes.c_int32), ("n_long", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_sz = ctypes.c_size_t
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libmbt (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not Path(_LIB_PATH).exists():
+                raise RuntimeError(f"libmbt is not built ({_LIB_PATH} missing): call paper_1809_00391_gb300.build()")
+            L = ctypes.CDLL(str(_LIB_PATH))
+            sig = {
+                "mbt_version": ([], _i), "mbt_status_string": ([_i], ctypes.c_char_p),
+                "mbt_create": ([_P(Ring), _i, _i, ctypes.c_uint64, _P(_vp)], _i),
+                "mbt_destroy": ([_vp], None), "mbt_last_error": ([_vp], ctypes.c_char_p),
+                "mbt_add_resonator": ([_vp, _d, _d, _d, _i], _i), "mbt_set_grid": ([_vp, _i, _d], _i),
+                "mbt_set_fill": ([_vp, _i, _P(_i32), _P(_d), _P(_i64)], _i),
+                "mbt_set_record": ([_vp, _i64], _i), "mbt_init_particles": ([_vp, _vp], _i),
+                "mbt_set_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
+                "mbt_get_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
+                "mbt_track": ([_vp, _i64, _vp], _i), "mbt_sync": ([_vp], _i),
+                "mbt_read_moments": ([_vp, _i64, _i64, _P(_d)], _i),
+                "mbt_read_histograms": ([_vp, _P(_i32), _P(_i64)], _i),
+                "mbt_read_wake": ([_vp, _P(_d), _P(_d)], _i), "mbt_get_info": ([_vp, _P(Info)], _i),
+                "mbt_set_graph": ([_vp, _i], _i), "mbt_set_timing": ([_vp, _i], _i),
+                "mbt_get_timing": ([_vp, _P(_d), _P(_d), _P(_i64)], _i),
+                "mbt_state_size": ([_vp, _P(_sz)], _i), "mbt_save_state": ([_vp, _vp, _sz], _i),
+                "mbt_load_state": ([_vp, _vp, _sz], _i),
+                "mbt_batch_create": ([_P(_vp), _i, _P(_vp)], _i), "mbt_batch_track": ([_vp, _i64, _vp], _i),
+                "mbt_batch_sync": ([_vp], _i), "mbt_batch_destroy": ([_vp], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _stream(s) -> ctypes.c_void_p:
+    if s is None:
+        return ctypes.c_void_p(0)
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    handle = getattr(s, "cuda_stream", None)
+    if handle is None:
+        raise TypeError("stream must be None, an int handle or a torch.cuda.Stream")
+    return ctypes.c_void_p(int(handle))
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(_P(ct))
+
+
+class Tracker:
+    """One run (ring, wakes, mesh, fill) tracked on the GPU through libmbt."""
+
+    def __init__(self, ring: dict, precision: int = PREC_MIXED, flags: int = 0, seed: int = 1,
+                 resonators=(), nbins: int = 256, half_width_sigmas: float = 5.0,
+                 buckets=(0,), currents_A=(1e-3,), n_mp=(10_000,), record_turns: int = 4096):
+        self._L = lib()
+        self._h = ctypes.c_void_p()
+        r = Ring(E0_eV=ring["E0_eV"], T0_s=ring["T0_s"], h=int(ring["h"]), reserved=0, V_rf_V=ring["V_rf_V"],
+                 alpha_c=ring["alpha_c"], U0_eV=ring["U0_eV"], sigma_delta=ring["sigma_delta"],
+                 tau_z_s=ring["tau_z_s"])
+        st = self._L.mbt_create(ctypes.byref(r), int(precision), int(flags), int(seed) & (2 ** 64 - 1),
+                                ctypes.byref(self._h))
+        if st != 0:
+            raise MBTError(st, "mbt_create rejected the ring or options")
+        self.precision = int(precision)
+        for res in resonators:
+            self._chk(self._L.mbt_add_resonator(self._h, res["Rs_ohm"], res["fr_Hz"], res["Q"], int(res["range"])))
+        self._chk(self._L.mbt_set_grid(self._h, int(nbins), float(half_width_sigmas)))
+        self._chk(self._L.mbt_set_record(self._h, int(record_turns)))
+        self.buckets = np.ascontiguousarray(buckets, np.int32)
+        self.currents = np.ascontiguousarray(currents_A, np.float64)
+        self.n_mp = np.ascontiguousarray(n_mp, np.int64)
+        self.nb = len(self.buckets)
+        self.nbins = int(nbins)
+        self._chk(self._L.mbt_set_fill(self._h, self.nb, _ptr(self.buckets, _i32), _ptr(self.currents, _d),
+                                       _ptr(self.n_mp, _i64)))
+
+    def _chk(self, st: int):
+        if st != 0:
+            raise MBTError(st, self._L.mbt_last_error(self._h).decode())
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.mbt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_particles(self, stream=None):
+        self._chk(self._L.mbt_init_particles(self._h, _stream(stream)))
+
+    def set_particles(self, bunch: int, tau, delta):
+        t = np.ascontiguousarray(tau, np.float64)
+        d = np.ascontiguousarray(delta, np.float64)
+        if t.size != self.n_mp[bunch] or d.size != self.n_mp[bunch]:
+            raise ValueError("array sizes must equal n_mp of the bunch")
+        self._chk(self._L.mbt_set_particles(self._h, int(bunch), _ptr(t, _d), _ptr(d, _d)))
+
+    def particles(self, bunch: int):
+        n = int(self.n_mp[bunch])
+        t = np.empty(n, np.float64)
+        d = np.empty(n, np.float64)
+        self._chk(self._L.mbt_get_particles(self._h, int(bunch), _ptr(t, _d), _ptr(d, _d)))
+        return t, d
+
+    def track(self, nturns: int, stream=None):
+        self._chk(self._L.mbt_track(self._h, int(nturns), _stream(stream)))
+
+    def sync(self):
+        self._chk(self._L.mbt_sync(self._h))
+
+    def moments(self, turn0: int, nturns: int) -> np.ndarray:
+        out = np.empty((int(nturns), self.nb, 6), np.float64)
+        self._chk(self._L.mbt_read_moments(self._h, int(turn0), int(nturns), _ptr(out, _d)))
+        return out
+
+    def histograms(self):
+        h = np.empty((self.nb, self.nbins), np.int32)
+        o = np.empty(self.nb, np.int64)
+        self._chk(self._L.mbt_read_histograms(self._h, _ptr(h, _i32), _ptr(o, _i64)))
+        return h, o
+
+    def wake(self):
+        info = self.info
+        v = np.empty((self.nb, self.nbins), np.float64)
+        phi = np.zeros((max(1, info["n_long"]), self.nb, 2), np.float64)
+        self._chk(self._L.mbt_read_wake(self._h, _ptr(v, _d), _ptr(phi, _d)))
+        return v, phi[..., 0] + 1j * phi[..., 1]
+
+    @property
+    def info(self) -> dict:
+        i = Info()
+        self._chk(self._L.mbt_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def set_graph(self, turns_per_graph: int):
+        self._chk(self._L.mbt_set_graph(self._h, int(turns_per_graph)))
+
+    def set_timing(self, enable: bool):
+        self._chk(self._L.mbt_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self):
+        a, b, n = _d(), _d(), _i64()
+        self._chk(self._L.mbt_get_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return a.value, b.value, n.value
+
+    def save_state(self) -> bytes:
+        n = _sz()
+        self._chk(self._L.mbt_state_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._chk(self._L.mbt_save_state(self._h, buf, n))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._chk(self._L.mbt_load_state(self._h, buf, len(blob)))
+
+
+class Batch:
+    """Several trackers (same precision) advanced by the same kernel launches."""
+
+    def __init__(self, trackers):
+        self._L = lib()
+        self.trackers = list(trackers)
+        arr = (ctypes.c_void_p * len(self.trackers))(*[t.handle.value for t in self.trackers])
+        self._h = ctypes.c_void_p()
+        st = self._L.mbt_batch_create(arr, len(self.trackers), ctypes.byref(self._h))
+        if st != 0:
+            raise MBTError(st, "mbt_batch_create failed")
+
+    def track(self, nturns: int, stream=None):
+        st = self._L.mbt_batch_track(self._h, int(nturns), _stream(stream))
+        if st != 0:
+            raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+
+    def sync(self):
+        st = self._L.mbt_batch_sync(self._h)
+        if st != 0:
+            raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.mbt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tracker_for_run(run, precision=None, record_turns: int = 4096) -> Tracker:
+    """A Tracker for an ``mbt_workloads.Run`` description."""
+    return Tracker(run.ring, precision=run.precision if precision is None else precision, flags=run.flags,
+                   seed=run.seed, resonators=run.resonators, nbins=run.nbins,
+                   half_width_sigmas=run.half_width_sigmas, buckets=run.buckets, currents_A=run.currents_A,
+                   n_mp=run.n_mp, record_turns=record_turns)

@@ -1,0 +1,997 @@
+// Host engine and C ABI of libmbt (declarations and conventions in mbt.h).
+//
+// A context holds one run: its ring, wake model, mesh and fill, the device
+// buffers of its state, and a Plan (work lists) for tracking it alone.  A
+// batch holds a Plan over several contexts.  Derived ring quantities and the
+// wake tables are computed here in double precision from the paper's
+// definitions (Sec. 2.2 Eqs. 1, 2, 5; Sec. 2.3 Eq. 6).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mbt.h"
+#include "mbt_internal.h"
+
+using namespace mbt;
+using cplx = std::complex<double>;
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+struct Resonator {
+  double Rs, fr, Q;
+  int range;
+};
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// Plan storage on the device plus its host mirror.
+struct PlanStore {
+  Plan plan{};
+  std::vector<RunDev> runs;
+  std::vector<BunchDev> bunches;
+  std::vector<TileDev> tiles;
+  std::vector<PostJob> jobs;
+  std::vector<void *> allocs;
+  size_t bytes = 0;
+  int precision = 0;
+  ~PlanStore() { release(); }
+  void release() {
+    for (void *a : allocs) cudaFree(a);
+    allocs.clear();
+    bytes = 0;
+    plan = Plan{};
+  }
+};
+
+uint16_t f32_to_bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return 0x7FC0;
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_to_f32(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace
+
+struct mbt_ctx {
+  mbt_ring ring{};
+  int precision = 0, flags = 0;
+  uint64_t seed = 0;
+  std::vector<Resonator> res;
+  int nbins = 256;
+  double half_width_sigmas = 5.0;
+  int64_t cap = 4096;
+  // derived
+  double T_rf = 0, omega_rf = 0, phi_s = 0, sin_phi_s = 0, cos_phi_s = 0, nu_s = 0, sigma_tau0 = 0, D = 0, qe = 0;
+  double H = 0, Delta = 0, invDelta = 0;
+  // fill
+  bool filled = false;
+  int nb = 0, nlong = 0, ntile_b = 0;
+  std::vector<int32_t> bucket;
+  std::vector<double> current;
+  std::vector<int64_t> nmp, off;
+  int64_t n_particles = 0, n_alloc = 0;
+  std::vector<int> long_idx;   // indices into res of long-range resonators
+  // device state
+  std::vector<DevBuf> bufs;
+  void *d_tau = nullptr;
+  double *d_delta = nullptr;
+  int32_t *d_hist = nullptr;
+  void *d_vsr = nullptr;
+  double2 *d_pq = nullptr, *d_y = nullptr, *d_agg = nullptr, *d_carry = nullptr;
+  double *d_rec = nullptr;
+  long long *d_turn = nullptr;
+  double *d_q = nullptr;
+  double2 *d_step = nullptr, *d_emis = nullptr;
+  float2 *d_emis_f = nullptr;
+  void *d_toep = nullptr;
+  size_t device_bytes = 0;
+  RunDev rundev{};
+  PlanStore own;
+  // graph replay
+  int graph_turns = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  // timing
+  bool timing = false;
+  double push_ms = 0, post_ms = 0;
+  int64_t timed_launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::string err;
+};
+
+struct mbt_batch {
+  std::vector<mbt_ctx *> ctx;
+  PlanStore store;
+  int precision = 0;
+};
+
+namespace {
+
+mbt_status fail(mbt_ctx *c, mbt_status s, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+mbt_status cuda_fail(mbt_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, MBT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <class T>
+mbt_status dalloc(mbt_ctx *c, T **ptr, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return fail(c, MBT_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  cudaMemset(p, 0, bytes ? bytes : 16);
+  c->bufs.push_back({p, bytes});
+  c->device_bytes += bytes;
+  *ptr = static_cast<T *>(p);
+  return MBT_OK;
+}
+
+void free_device(mbt_ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  c->capture_stream = nullptr;
+  for (auto &b : c->bufs) cudaFree(b.p);
+  c->bufs.clear();
+  c->device_bytes = 0;
+  c->own.release();
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
+}
+
+// Ring-derived quantities (readings listed in mbt.h).
+void derive(mbt_ctx *c) {
+  const mbt_ring &r = c->ring;
+  const bool sr = !(c->flags & MBT_NO_SR);
+  const double U0 = sr ? r.U0_eV : 0.0;
+  c->T_rf = r.T0_s / (double)r.h;
+  c->omega_rf = 2.0 * kPi * (double)r.h / r.T0_s;
+  c->sin_phi_s = U0 / r.V_rf_V;
+  c->phi_s = std::asin(c->sin_phi_s);
+  if (r.alpha_c < 0.0) c->phi_s = kPi - c->phi_s;
+  c->cos_phi_s = std::cos(c->phi_s);
+  c->nu_s = std::sqrt(r.alpha_c * (double)r.h * r.V_rf_V * c->cos_phi_s / (2.0 * kPi * r.E0_eV));
+  c->sigma_tau0 = std::fabs(r.alpha_c) * r.sigma_delta * r.T0_s / (2.0 * kPi * c->nu_s);
+  c->D = sr ? 2.0 * r.T0_s / r.tau_z_s : 0.0;
+  c->qe = (sr && !(c->flags & MBT_NO_QE)) ? r.sigma_delta * std::sqrt(2.0 * c->D) : 0.0;
+  c->H = c->half_width_sigmas * c->sigma_tau0;
+  c->Delta = 2.0 * c->H / (double)c->nbins;
+  c->invDelta = 1.0 / c->Delta;
+}
+
+void res_consts(const Resonator &q, double &a, double &wb) {
+  const double wr = 2.0 * kPi * q.fr;
+  a = wr / (2.0 * q.Q);
+  wb = std::sqrt(wr * wr - a * a);
+}
+
+// Resonator wake [V/C]; half of W(0+) at t == 0.
+double wake(const Resonator &q, double t) {
+  double a, wb;
+  res_consts(q, a, wb);
+  if (t < 0.0) return 0.0;
+  if (t == 0.0) return a * q.Rs;
+  return 2.0 * a * q.Rs * std::exp(-a * t) * (std::cos(wb * t) - (a / wb) * std::sin(wb * t));
+}
+
+// Upload a plan built in st's host vectors.
+mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
+  st.release();
+  auto up = [&](auto &vec, auto **dst) -> bool {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    void *p = nullptr;
+    size_t bytes = std::max<size_t>(vec.size() * sizeof(T), 16);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return false;
+    st.allocs.push_back(p);
+    st.bytes += bytes;
+    if (!vec.empty() && cudaMemcpy(p, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+    *dst = static_cast<T *>(p);
+    return true;
+  };
+  Plan pl{};
+  if (!up(st.runs, &pl.runs) || !up(st.bunches, &pl.bunches) || !up(st.tiles, &pl.tiles) || !up(st.jobs, &pl.jobs))
+    return fail(c, MBT_ERR_NOMEM, "plan upload failed");
+  void *p = nullptr;
+  size_t pb = std::max<size_t>(st.tiles.size() * kPartials * sizeof(double), 16);
+  if (cudaMalloc(&p, pb) != cudaSuccess) return fail(c, MBT_ERR_NOMEM, "plan partials");
+  cudaMemset(p, 0, pb);
+  st.allocs.push_back(p);
+  pl.partial = static_cast<double *>(p);
+  if (cudaMalloc(&p, 16) != cudaSuccess) return fail(c, MBT_ERR_NOMEM, "plan counters");
+  cudaMemset(p, 0, 16);
+  st.allocs.push_back(p);
+  pl.done = static_cast<unsigned int *>(p);
+  pl.error = reinterpret_cast<int *>(static_cast<char *>(p) + 8);
+  pl.nruns = (int)st.runs.size();
+  pl.nbunches = (int)st.bunches.size();
+  pl.ntiles = (int)st.tiles.size();
+  pl.njobs = (int)st.jobs.size();
+  pl.max_nbins = 0;
+  for (auto &r : st.runs) pl.max_nbins = std::max(pl.max_nbins, r.nbins);
+  st.bytes += pb + 16;
+  st.plan = pl;
+  return MBT_OK;
+}
+
+// Append one context's run to a plan under construction.
+void append_run(PlanStore &st, mbt_ctx *c) {
+  const int ri = (int)st.runs.size();
+  RunDev rd = c->rundev;
+  rd.bunch_base = (int)st.bunches.size();
+  st.runs.push_back(rd);
+  const int tile = c->precision == MBT_PREC_MIXED ? kMixedTile : kF64Tile;
+  for (int m = 0; m < c->nb; ++m) {
+    BunchDev bd{};
+    bd.run = ri;
+    bd.m = m;
+    bd.off = c->off[m];
+    bd.n = c->nmp[m];
+    bd.tile0 = (int)st.tiles.size();
+    for (int64_t s = 0; s < c->nmp[m]; s += tile) {
+      TileDev t{};
+      t.bunch = (int)st.bunches.size();
+      t.run = ri;
+      t.m = m;
+      t.start = s;
+      t.count = (int)std::min<int64_t>(tile, c->nmp[m] - s);
+      st.tiles.push_back(t);
+    }
+    bd.ntiles = (int)st.tiles.size() - bd.tile0;
+    st.bunches.push_back(bd);
+  }
+  for (int bt = 0; bt < c->ntile_b; ++bt) {
+    st.jobs.push_back(PostJob{ri, kJobTile, bt, 0});
+    if (c->precision == MBT_PREC_MIXED) {
+      for (int mt = 0; mt < c->nbins / 128; ++mt) st.jobs.push_back(PostJob{ri, kJobWake, bt, mt});
+    }
+  }
+  if (c->precision == MBT_PREC_F64) {
+    const int nchunk = (c->nbins + kF64RowChunk - 1) / kF64RowChunk;
+    for (int m = 0; m < c->nb; ++m)
+      for (int ch = 0; ch < nchunk; ++ch) st.jobs.push_back(PostJob{ri, kJobWake, m, ch});
+  }
+}
+
+mbt_status check_device(mbt_ctx *c, const Plan &pl) {
+  int err = 0;
+  cudaError_t e = cudaMemcpy(&err, pl.error, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device error word");
+  if (err != 0) {
+    int zero = 0;
+    cudaMemcpy(pl.error, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(c, MBT_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", err);
+  }
+  return MBT_OK;
+}
+
+mbt_status launch_turns(mbt_ctx *c, const Plan &pl, int prec, int64_t nturns, cudaStream_t s, bool timed) {
+  if (!timed) {
+    for (int64_t t = 0; t < nturns; ++t) {
+      cudaError_t e = launch_push(pl, prec, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "push launch");
+      e = launch_post(pl, prec, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "post launch");
+    }
+    return MBT_OK;
+  }
+  // events around every launch, drained in chunks
+  const int chunk = 512;
+  if (c->ev_pool.size() < (size_t)(3 * chunk)) {
+    while (c->ev_pool.size() < (size_t)(3 * chunk)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(c, MBT_ERR_CUDA, "event create");
+      c->ev_pool.push_back(e);
+    }
+  }
+  for (int64_t t0 = 0; t0 < nturns; t0 += chunk) {
+    const int n = (int)std::min<int64_t>(chunk, nturns - t0);
+    for (int i = 0; i < n; ++i) {
+      cudaEventRecord(c->ev_pool[3 * i], s);
+      cudaError_t e = launch_push(pl, prec, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "push launch");
+      cudaEventRecord(c->ev_pool[3 * i + 1], s);
+      e = launch_post(pl, prec, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "post launch");
+      cudaEventRecord(c->ev_pool[3 * i + 2], s);
+    }
+    cudaError_t e = cudaEventSynchronize(c->ev_pool[3 * (n - 1) + 2]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "timed turns");
+    for (int i = 0; i < n; ++i) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, c->ev_pool[3 * i], c->ev_pool[3 * i + 1]);
+      cudaEventElapsedTime(&b, c->ev_pool[3 * i + 1], c->ev_pool[3 * i + 2]);
+      c->push_ms += a;
+      c->post_ms += b;
+      c->timed_launches += 1;
+    }
+  }
+  return MBT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int mbt_version(void) { return MBT_VERSION; }
+
+const char *mbt_status_string(mbt_status s) {
+  switch (s) {
+    case MBT_OK: return "ok";
+    case MBT_ERR_ARG: return "invalid argument";
+    case MBT_ERR_STATE: return "invalid state";
+    case MBT_ERR_NOMEM: return "out of memory";
+    case MBT_ERR_CUDA: return "CUDA error";
+    case MBT_ERR_TIMEOUT: return "device wait timed out";
+    case MBT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MBT_ERR_BUDGET: return "memory budget exceeded";
+    default: return "unknown status";
+  }
+}
+
+mbt_status mbt_create(const mbt_ring *ring, int precision, int flags, uint64_t seed, mbt_ctx **out) {
+  if (!ring || !out) return MBT_ERR_ARG;
+  *out = nullptr;
+  if (!(ring->E0_eV > 0) || !(ring->T0_s > 0) || ring->h < 1 || ring->h > 65535 || ring->reserved != 0 ||
+      !(ring->V_rf_V > 0) || !(ring->alpha_c != 0) || !(ring->U0_eV >= 0) || !(ring->U0_eV < ring->V_rf_V) ||
+      !(ring->sigma_delta > 0) || !(ring->tau_z_s > 0))
+    return MBT_ERR_ARG;
+  if (precision != MBT_PREC_F64 && precision != MBT_PREC_MIXED) return MBT_ERR_ARG;
+  if (flags & ~(MBT_NO_SR | MBT_NO_QE | MBT_KICK_NGP)) return MBT_ERR_ARG;
+  mbt_ctx *c = new (std::nothrow) mbt_ctx();
+  if (!c) return MBT_ERR_NOMEM;
+  c->ring = *ring;
+  c->precision = precision;
+  c->flags = flags;
+  c->seed = seed;
+  derive(c);
+  *out = c;
+  return MBT_OK;
+}
+
+void mbt_destroy(mbt_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_device(c);
+  delete c;
+}
+
+const char *mbt_last_error(const mbt_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+mbt_status mbt_add_resonator(mbt_ctx *c, double Rs, double fr, double Q, int range) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "resonators must be added before mbt_set_fill");
+  if (!(Rs > 0) || !(fr > 0) || !(Q > 0.5) || range < 1 || range > 3)
+    return fail(c, MBT_ERR_ARG, "resonator needs Rs > 0, fr > 0, Q > 0.5, range 1..3");
+  if ((int)c->res.size() >= kMaxRes) return fail(c, MBT_ERR_UNSUPPORTED, "at most %d resonators", kMaxRes);
+  int nl = 0;
+  for (auto &r : c->res) nl += (r.range & MBT_RANGE_LONG) ? 1 : 0;
+  if ((range & MBT_RANGE_LONG) && nl >= kMaxLong)
+    return fail(c, MBT_ERR_UNSUPPORTED, "at most %d long-range resonators", kMaxLong);
+  c->res.push_back(Resonator{Rs, fr, Q, range});
+  return MBT_OK;
+}
+
+mbt_status mbt_set_grid(mbt_ctx *c, int nbins, double hw) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "grid must be set before mbt_set_fill");
+  if (!(hw > 0)) return fail(c, MBT_ERR_ARG, "half width must be > 0");
+  if (c->precision == MBT_PREC_MIXED) {
+    if (nbins != 128 && nbins != 256) return fail(c, MBT_ERR_UNSUPPORTED, "mixed precision needs nbins 128 or 256");
+  } else if (nbins < 2 || nbins > 1024) {
+    return fail(c, MBT_ERR_ARG, "nbins must be 2..1024");
+  }
+  c->nbins = nbins;
+  c->half_width_sigmas = hw;
+  derive(c);
+  return MBT_OK;
+}
+
+mbt_status mbt_set_record(mbt_ctx *c, int64_t cap) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "record capacity must be set before mbt_set_fill");
+  if (cap < 1 || cap > (int64_t)1 << 30) return fail(c, MBT_ERR_ARG, "capacity out of range");
+  c->cap = cap;
+  return MBT_OK;
+}
+
+mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double *current, const int64_t *nmp) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "fill already set");
+  if (nb < 1 || nb > kMaxBunches || !bucket || !current || !nmp)
+    return fail(c, MBT_ERR_ARG, "need 1..%d bunches and non-null arrays", kMaxBunches);
+  const int64_t nmax = c->precision == MBT_PREC_MIXED ? ((int64_t)1 << 24) - 1 : ((int64_t)1 << 31) - 2;
+  for (int m = 0; m < nb; ++m) {
+    if (bucket[m] < 0 || bucket[m] >= c->ring.h || (m > 0 && bucket[m] <= bucket[m - 1]))
+      return fail(c, MBT_ERR_ARG, "buckets must be strictly increasing in [0, h)");
+    if (!(current[m] >= 0) || nmp[m] < 1 || nmp[m] > nmax)
+      return fail(c, MBT_ERR_ARG, "bunch %d: current >= 0 and 1 <= n_mp <= %lld required", m, (long long)nmax);
+  }
+  cudaError_t ce = cudaFree(0);
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "CUDA initialisation");
+  c->nb = nb;
+  c->bucket.assign(bucket, bucket + nb);
+  c->current.assign(current, current + nb);
+  c->nmp.assign(nmp, nmp + nb);
+  c->off.resize(nb);
+  int64_t o = 0;
+  c->n_particles = 0;
+  for (int m = 0; m < nb; ++m) {
+    c->off[m] = o;
+    o += (nmp[m] + 3) / 4 * 4;
+    c->n_particles += nmp[m];
+  }
+  c->n_alloc = o + 4;
+  c->ntile_b = (nb + kBunchTile - 1) / kBunchTile;
+  c->long_idx.clear();
+  for (int i = 0; i < (int)c->res.size(); ++i)
+    if (c->res[i].range & MBT_RANGE_LONG) c->long_idx.push_back(i);
+  c->nlong = (int)c->long_idx.size();
+  const int nl = std::max(1, c->nlong);
+  const bool mixed = c->precision == MBT_PREC_MIXED;
+  const int nbins = c->nbins;
+
+  mbt_status st;
+#define ALLOC(ptr, bytes)                                  \
+  if ((st = dalloc(c, &(ptr), (bytes))) != MBT_OK) {       \
+    free_device(c);                                        \
+    return st;                                             \
+  }
+  ALLOC(c->d_tau, (size_t)c->n_alloc * (mixed ? sizeof(float) : sizeof(double)));
+  ALLOC(c->d_delta, (size_t)c->n_alloc * sizeof(double));
+  ALLOC(c->d_hist, (size_t)2 * nb * nbins * sizeof(int32_t));
+  ALLOC(c->d_vsr, (size_t)nb * nbins * (mixed ? sizeof(float) : sizeof(double)));
+  ALLOC(c->d_pq, (size_t)nl * nb * 2 * sizeof(double2));
+  ALLOC(c->d_y, (size_t)nl * c->ntile_b * sizeof(double2));
+  ALLOC(c->d_agg, (size_t)nl * c->ntile_b * 2 * sizeof(double2));
+  ALLOC(c->d_carry, (size_t)nl * sizeof(double2));
+  ALLOC(c->d_rec, (size_t)c->cap * nb * kRecord * sizeof(double));
+  ALLOC(c->d_turn, 16);
+  ALLOC(c->d_q, (size_t)nb * sizeof(double));
+  ALLOC(c->d_step, (size_t)nl * nb * sizeof(double2));
+  ALLOC(c->d_emis, (size_t)nl * nbins * sizeof(double2));
+  ALLOC(c->d_emis_f, (size_t)nl * nbins * sizeof(float2));
+  const size_t toep_bytes = mixed ? (size_t)(nbins / 128) * nbins * 512 : (size_t)nbins * sizeof(double);
+  ALLOC(c->d_toep, toep_bytes);
+#undef ALLOC
+
+  // macro-particle charge
+  std::vector<double> q(nb);
+  for (int m = 0; m < nb; ++m) q[m] = c->current[m] * c->ring.T0_s / (double)c->nmp[m];
+  cudaMemcpy(c->d_q, q.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+
+  // summed short-range wake per lag (half of W(0+) at lag 0)
+  std::vector<double> lag(nbins, 0.0);
+  for (int l = 0; l < nbins; ++l)
+    for (auto &r : c->res)
+      if (r.range & MBT_RANGE_SHORT) lag[l] += wake(r, (double)l * c->Delta);
+  if (mixed) {
+    // operand images: per M-tile, 128 rows x [hi | lo] (2 nbins columns) in
+    // K-major 8x8 core matrices: byte ((kg * 16 + mg) * 128 + (row % 8) * 16 + (k % 8) * 2)
+    const int nmt = nbins / 128;
+    std::vector<uint16_t> img((size_t)nmt * 128 * 2 * nbins, 0);
+    for (int mt = 0; mt < nmt; ++mt)
+      for (int row = 0; row < 128; ++row)
+        for (int k = 0; k < nbins; ++k) {
+          const int j = mt * 128 + row;
+          const double T = j >= k ? lag[j - k] : 0.0;
+          const uint16_t hi = f32_to_bf16_rne((float)T);
+          const uint16_t lo = f32_to_bf16_rne((float)(T - (double)bf16_to_f32(hi)));
+          for (int half = 0; half < 2; ++half) {
+            const int kk = k + half * nbins;
+            const size_t byte = (size_t)mt * nbins * 512 + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 +
+                                (kk % 8) * 2;
+            img[byte / 2] = half ? lo : hi;
+          }
+        }
+    cudaMemcpy(c->d_toep, img.data(), toep_bytes, cudaMemcpyHostToDevice);
+  } else {
+    cudaMemcpy(c->d_toep, lag.data(), toep_bytes, cudaMemcpyHostToDevice);
+  }
+
+  // long-range tables: emission e^{-s tau_k}, step maps a_m = e^{s dt_m}
+  RunDev &rd = c->rundev;
+  rd = RunDev{};
+  {
+    std::vector<double2> emis((size_t)nl * nbins, make_double2(0, 0));
+    std::vector<float2> emis_f((size_t)nl * nbins, make_float2(0, 0));
+    std::vector<double2> step((size_t)nl * nb, make_double2(1, 0));
+    for (int li = 0; li < c->nlong; ++li) {
+      const Resonator &r = c->res[c->long_idx[li]];
+      double a, wb;
+      res_consts(r, a, wb);
+      const cplx s(-a, wb);
+      const cplx cc = 2.0 * a * r.Rs * cplx(1.0, a / wb);
+      rd.lr_s[li] = make_double2(s.real(), s.imag());
+      rd.lr_c[li] = make_double2(cc.real(), cc.imag());
+      for (int k = 0; k < nbins; ++k) {
+        const double tk = -c->H + ((double)k + 0.5) * c->Delta;
+        const cplx e = std::exp(-s * tk);
+        emis[(size_t)li * nbins + k] = make_double2(e.real(), e.imag());
+        emis_f[(size_t)li * nbins + k] = make_float2((float)e.real(), (float)e.imag());
+      }
+      for (int m = 0; m < nb; ++m) {
+        const int64_t dbk = m > 0 ? (int64_t)c->bucket[m] - c->bucket[m - 1]
+                                  : (int64_t)c->ring.h - c->bucket[nb - 1] + c->bucket[0];
+        const double dt = (double)dbk * c->T_rf;
+        const cplx z = std::exp(s * dt);
+        step[(size_t)li * nb + m] = make_double2(z.real(), z.imag());
+      }
+    }
+    cudaMemcpy(c->d_emis, emis.data(), emis.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_emis_f, emis_f.data(), emis_f.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_step, step.data(), step.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  }
+
+  rd.tau = c->d_tau;
+  rd.delta = c->d_delta;
+  rd.hist = c->d_hist;
+  rd.vsr = c->d_vsr;
+  rd.pq = c->d_pq;
+  rd.y = c->d_y;
+  rd.agg = c->d_agg;
+  rd.carry = c->d_carry;
+  rd.rec = c->d_rec;
+  rd.turn = c->d_turn;
+  rd.q_mp = c->d_q;
+  rd.step = c->d_step;
+  rd.emis = c->d_emis;
+  rd.emis_f = c->d_emis_f;
+  rd.toep = c->d_toep;
+  rd.nb = nb;
+  rd.nbins = nbins;
+  rd.nlong = c->nlong;
+  rd.ntile_b = c->ntile_b;
+  rd.cap = (int)c->cap;
+  rd.flags = c->flags;
+  rd.precision = c->precision;
+  rd.key0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
+  rd.key1 = (uint32_t)(c->seed >> 32);
+  rd.inv_E0 = 1.0 / c->ring.E0_eV;
+  rd.V_over_E0 = c->ring.V_rf_V / c->ring.E0_eV;
+  rd.sin_phi_s = c->sin_phi_s;
+  rd.cos_phi_s = c->cos_phi_s;
+  rd.U0_over_E0 = (c->flags & MBT_NO_SR) ? 0.0 : c->ring.U0_eV / c->ring.E0_eV;
+  rd.omega_rf = c->omega_rf;
+  rd.phi_s = c->phi_s;
+  rd.one_minus_D = 1.0 - c->D;
+  rd.qe_amp = c->qe;
+  rd.aT0 = c->ring.alpha_c * c->ring.T0_s;
+  rd.H = c->H;
+  rd.invDelta = c->invDelta;
+  rd.Delta = c->Delta;
+  rd.sigma_tau0 = c->sigma_tau0;
+  rd.sigma_E = c->ring.sigma_delta;
+
+  PlanStore &ps = c->own;
+  ps.runs.clear();
+  ps.bunches.clear();
+  ps.tiles.clear();
+  ps.jobs.clear();
+  ps.precision = c->precision;
+  append_run(ps, c);
+  if ((st = upload_plan(c, ps)) != MBT_OK) {
+    free_device(c);
+    return st;
+  }
+  cudaError_t e = configure_kernels();
+  if (e != cudaSuccess) {
+    free_device(c);
+    return cuda_fail(c, e, "kernel attributes");
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_device(c);
+    return cuda_fail(c, e, "fill setup");
+  }
+  c->filled = true;
+  return MBT_OK;
+}
+
+mbt_status mbt_init_particles(mbt_ctx *c, void *stream) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nl = std::max(1, c->nlong);
+  cudaMemsetAsync(c->d_hist, 0, (size_t)2 * c->nb * c->nbins * sizeof(int32_t), s);
+  cudaMemsetAsync(c->d_vsr, 0,
+                  (size_t)c->nb * c->nbins * (c->precision == MBT_PREC_MIXED ? sizeof(float) : sizeof(double)), s);
+  cudaMemsetAsync(c->d_pq, 0, (size_t)nl * c->nb * 2 * sizeof(double2), s);
+  cudaMemsetAsync(c->d_y, 0, (size_t)nl * c->ntile_b * sizeof(double2), s);
+  cudaMemsetAsync(c->d_agg, 0, (size_t)nl * c->ntile_b * 2 * sizeof(double2), s);
+  cudaMemsetAsync(c->d_carry, 0, (size_t)nl * sizeof(double2), s);
+  cudaMemsetAsync(c->d_turn, 0, 16, s);
+  cudaError_t e = launch_init(c->own.plan, c->precision, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init launch");
+  return MBT_OK;
+}
+
+mbt_status mbt_set_particles(mbt_ctx *c, int bunch, const double *tau, const double *delta) {
+  if (!c || !tau || !delta) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (bunch < 0 || bunch >= c->nb) return fail(c, MBT_ERR_ARG, "bunch out of range");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  const int64_t n = c->nmp[bunch];
+  if (c->precision == MBT_PREC_MIXED) {
+    std::vector<float> tf(n);
+    for (int64_t i = 0; i < n; ++i) tf[i] = (float)tau[i];
+    e = cudaMemcpy(static_cast<float *>(c->d_tau) + c->off[bunch], tf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+  } else {
+    e = cudaMemcpy(static_cast<double *>(c->d_tau) + c->off[bunch], tau, n * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_delta + c->off[bunch], delta, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set particles");
+  return MBT_OK;
+}
+
+mbt_status mbt_get_particles(mbt_ctx *c, int bunch, double *tau, double *delta) {
+  if (!c || !tau || !delta) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (bunch < 0 || bunch >= c->nb) return fail(c, MBT_ERR_ARG, "bunch out of range");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  const int64_t n = c->nmp[bunch];
+  if (c->precision == MBT_PREC_MIXED) {
+    std::vector<float> tf(n);
+    e = cudaMemcpy(tf.data(), static_cast<float *>(c->d_tau) + c->off[bunch], n * sizeof(float), cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < n; ++i) tau[i] = tf[i];
+  } else {
+    e = cudaMemcpy(tau, static_cast<double *>(c->d_tau) + c->off[bunch], n * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(delta, c->d_delta + c->off[bunch], n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get particles");
+  return MBT_OK;
+}
+
+mbt_status mbt_set_graph(mbt_ctx *c, int turns) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (turns < 0 || turns > 100000) return fail(c, MBT_ERR_ARG, "turns_per_graph out of range");
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  c->graph_turns = turns;
+  return MBT_OK;
+}
+
+mbt_status mbt_set_timing(mbt_ctx *c, int enable) {
+  if (!c) return MBT_ERR_ARG;
+  c->timing = enable != 0;
+  if (enable) {
+    c->push_ms = c->post_ms = 0;
+    c->timed_launches = 0;
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_get_timing(mbt_ctx *c, double *push_ms, double *post_ms, int64_t *launches) {
+  if (!c) return MBT_ERR_ARG;
+  if (push_ms) *push_ms = c->push_ms;
+  if (post_ms) *post_ms = c->post_ms;
+  if (launches) *launches = c->timed_launches;
+  return MBT_OK;
+}
+
+mbt_status mbt_track(mbt_ctx *c, int64_t nturns, void *stream) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (nturns < 0) return fail(c, MBT_ERR_ARG, "nturns < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Plan &pl = c->own.plan;
+  if (c->timing || c->graph_turns == 0 || nturns < c->graph_turns)
+    return launch_turns(c, pl, c->precision, nturns, s, c->timing);
+  if (!c->graph_exec) {
+    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, MBT_ERR_CUDA, "capture stream");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+    mbt_status st = launch_turns(c, pl, c->precision, c->graph_turns, c->capture_stream, false);
+    e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (st != MBT_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  }
+  int64_t done = 0;
+  while (nturns - done >= c->graph_turns) {
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    done += c->graph_turns;
+  }
+  return launch_turns(c, pl, c->precision, nturns - done, s, false);
+}
+
+mbt_status mbt_sync(mbt_ctx *c) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  if (!c->filled) return MBT_OK;
+  return check_device(c, c->own.plan);
+}
+
+static mbt_status current_turn(mbt_ctx *c, long long *turn) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  e = cudaMemcpy(turn, c->d_turn, sizeof(long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "turn read");
+  return check_device(c, c->own.plan);
+}
+
+mbt_status mbt_read_moments(mbt_ctx *c, int64_t turn0, int64_t nturns, double *out) {
+  if (!c || !out) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  long long turn;
+  mbt_status st = current_turn(c, &turn);
+  if (st != MBT_OK) return st;
+  if (turn0 < 0 || nturns < 0 || turn0 + nturns > turn || turn0 < turn - c->cap)
+    return fail(c, MBT_ERR_ARG, "turns [%lld, %lld) not in the record [%lld, %lld)", (long long)turn0,
+                (long long)(turn0 + nturns), (long long)std::max<long long>(0, turn - c->cap), turn);
+  const size_t per = (size_t)c->nb * kRecord;
+  for (int64_t t = 0; t < nturns; ++t) {
+    const size_t slot = (size_t)((turn0 + t) % c->cap);
+    cudaError_t e = cudaMemcpy(out + t * per, c->d_rec + slot * per, per * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read moments");
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_read_histograms(mbt_ctx *c, int32_t *hist, int64_t *outside) {
+  if (!c || !hist) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  long long turn;
+  mbt_status st = current_turn(c, &turn);
+  if (st != MBT_OK) return st;
+  if (turn < 1) return fail(c, MBT_ERR_STATE, "no turn tracked yet");
+  const int par = (int)((turn - 1) & 1);
+  const size_t n = (size_t)c->nb * c->nbins;
+  cudaError_t e = cudaMemcpy(hist, c->d_hist + par * n, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read histograms");
+  if (outside) {
+    std::vector<double> rec((size_t)c->nb * kRecord);
+    const size_t slot = (size_t)((turn - 1) % c->cap);
+    e = cudaMemcpy(rec.data(), c->d_rec + slot * rec.size(), rec.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read outside counts");
+    for (int m = 0; m < c->nb; ++m) outside[m] = (int64_t)llround(rec[(size_t)m * kRecord + 5]);
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_read_wake(mbt_ctx *c, double *Vsr, double *Phi) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  const size_t n = (size_t)c->nb * c->nbins;
+  if (Vsr) {
+    if (c->precision == MBT_PREC_MIXED) {
+      std::vector<float> v(n);
+      e = cudaMemcpy(v.data(), c->d_vsr, n * sizeof(float), cudaMemcpyDeviceToHost);
+      for (size_t i = 0; i < n; ++i) Vsr[i] = v[i];
+    } else {
+      e = cudaMemcpy(Vsr, c->d_vsr, n * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "read wake");
+  }
+  if (Phi && c->nlong > 0) {
+    std::vector<double2> pq((size_t)c->nlong * c->nb * 2), y((size_t)c->nlong * c->ntile_b);
+    e = cudaMemcpy(pq.data(), c->d_pq, pq.size() * sizeof(double2), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(y.data(), c->d_y, y.size() * sizeof(double2), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read phasors");
+    for (int r = 0; r < c->nlong; ++r)
+      for (int m = 0; m < c->nb; ++m) {
+        const double2 P = pq[((size_t)r * c->nb + m) * 2], Q = pq[((size_t)r * c->nb + m) * 2 + 1];
+        const double2 yy = y[(size_t)r * c->ntile_b + m / kBunchTile];
+        const cplx phi = cplx(P.x, P.y) * cplx(yy.x, yy.y) + cplx(Q.x, Q.y);
+        Phi[((size_t)r * c->nb + m) * 2] = phi.real();
+        Phi[((size_t)r * c->nb + m) * 2 + 1] = phi.imag();
+      }
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_get_info(mbt_ctx *c, mbt_info *info) {
+  if (!c || !info) return MBT_ERR_ARG;
+  c->err.clear();
+  std::memset(info, 0, sizeof *info);
+  info->T_rf_s = c->T_rf;
+  info->omega_rf = c->omega_rf;
+  info->phi_s = c->phi_s;
+  info->nu_s = c->nu_s;
+  info->sigma_tau0_s = c->sigma_tau0;
+  info->D = c->D;
+  info->half_width_s = c->H;
+  info->bin_width_s = c->Delta;
+  info->n_particles = c->n_particles;
+  info->nb = c->nb;
+  info->nbins = c->nbins;
+  info->n_long = c->nlong;
+  info->precision = c->precision;
+  info->device_bytes = (int64_t)(c->device_bytes + c->own.bytes);
+  if (c->filled) {
+    long long turn = 0;
+    mbt_status st = current_turn(c, &turn);
+    if (st != MBT_OK) return st;
+    info->turn = turn;
+  }
+  return MBT_OK;
+}
+
+// --------------------------------------------------------------------------- checkpoint
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, precision, nb, nbins, nlong, ntile_b;
+  int64_t n_alloc;
+  uint64_t seed;
+};
+struct Section {
+  void *dev;
+  size_t bytes;
+};
+std::vector<Section> state_sections(mbt_ctx *c) {
+  const bool mixed = c->precision == MBT_PREC_MIXED;
+  const int nl = std::max(1, c->nlong);
+  return {
+      {c->d_tau, (size_t)c->n_alloc * (mixed ? sizeof(float) : sizeof(double))},
+      {c->d_delta, (size_t)c->n_alloc * sizeof(double)},
+      {c->d_hist, (size_t)2 * c->nb * c->nbins * sizeof(int32_t)},
+      {c->d_vsr, (size_t)c->nb * c->nbins * (mixed ? sizeof(float) : sizeof(double))},
+      {c->d_pq, (size_t)nl * c->nb * 2 * sizeof(double2)},
+      {c->d_y, (size_t)nl * c->ntile_b * sizeof(double2)},
+      {c->d_agg, (size_t)nl * c->ntile_b * 2 * sizeof(double2)},
+      {c->d_carry, (size_t)nl * sizeof(double2)},
+      {c->d_turn, 16},
+  };
+}
+}  // namespace
+
+mbt_status mbt_state_size(mbt_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  size_t b = sizeof(StateHeader);
+  for (auto &s : state_sections(c)) b += s.bytes;
+  *bytes = b;
+  return MBT_OK;
+}
+
+mbt_status mbt_save_state(mbt_ctx *c, void *buf, size_t bytes) {
+  size_t need = 0;
+  mbt_status st = mbt_state_size(c, &need);
+  if (st != MBT_OK) return st;
+  if (!buf || bytes < need) return fail(c, MBT_ERR_ARG, "buffer needs %zu bytes", need);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  StateHeader h{};
+  std::memcpy(h.magic, "MBTSTATE", 8);
+  h.version = MBT_VERSION;
+  h.precision = c->precision;
+  h.nb = c->nb;
+  h.nbins = c->nbins;
+  h.nlong = c->nlong;
+  h.ntile_b = c->ntile_b;
+  h.n_alloc = c->n_alloc;
+  h.seed = c->seed;
+  char *p = static_cast<char *>(buf);
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  for (auto &s : state_sections(c)) {
+    e = cudaMemcpy(p, s.dev, s.bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "save state");
+    p += s.bytes;
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_load_state(mbt_ctx *c, const void *buf, size_t bytes) {
+  size_t need = 0;
+  mbt_status st = mbt_state_size(c, &need);
+  if (st != MBT_OK) return st;
+  if (!buf || bytes < need) return fail(c, MBT_ERR_ARG, "buffer needs %zu bytes", need);
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, "MBTSTATE", 8) != 0 || h.version != MBT_VERSION || h.precision != c->precision ||
+      h.nb != c->nb || h.nbins != c->nbins || h.nlong != c->nlong || h.n_alloc != c->n_alloc || h.seed != c->seed)
+    return fail(c, MBT_ERR_ARG, "snapshot does not match this context's configuration");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  const char *p = static_cast<const char *>(buf) + sizeof h;
+  for (auto &s : state_sections(c)) {
+    e = cudaMemcpy(s.dev, p, s.bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "load state");
+    p += s.bytes;
+  }
+  return MBT_OK;
+}
+
+// --------------------------------------------------------------------------- batch
+mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out) {
+  if (!ctxs || n < 1 || !out) return MBT_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !ctxs[i]->filled) return MBT_ERR_STATE;
+    if (ctxs[i]->precision != ctxs[0]->precision) return MBT_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return MBT_ERR_ARG;
+  }
+  mbt_batch *b = new (std::nothrow) mbt_batch();
+  if (!b) return MBT_ERR_NOMEM;
+  b->ctx.assign(ctxs, ctxs + n);
+  b->precision = ctxs[0]->precision;
+  b->store.precision = b->precision;
+  for (int i = 0; i < n; ++i) append_run(b->store, ctxs[i]);
+  mbt_status st = upload_plan(ctxs[0], b->store);
+  if (st != MBT_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return MBT_OK;
+}
+
+mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream) {
+  if (!b || nturns < 0) return MBT_ERR_ARG;
+  return launch_turns(b->ctx[0], b->store.plan, b->precision, nturns, static_cast<cudaStream_t>(stream), false);
+}
+
+mbt_status mbt_batch_sync(mbt_batch *b) {
+  if (!b) return MBT_ERR_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(b->ctx[0], e, "sync");
+  return check_device(b->ctx[0], b->store.plan);
+}
+
+void mbt_batch_destroy(mbt_batch *b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,364 @@
+// Post-turn kernel: everything that follows the push of a turn, for every run
+// of the plan, in one launch.  Two kinds of CTA (PostJob):
+//
+//  kJobWake  short-range wake voltage of a tile of bunches (Sec. 2.3, Eq. 6):
+//            V[j, m] = q_m sum_{k<=j} W~((j-k) Delta) count[m, k], a lower
+//            triangular Toeplitz matrix (cells x cells) times the counts
+//            (cells x bunches).  kMixed: tcgen05 MMA on the tensor cores;
+//            the Toeplitz matrix is split into BF16 hi + lo halves laid side
+//            by side along K, the integer counts into three exact BF16 byte
+//            planes laid side by side along N; FP32 accumulation in tensor
+//            memory; the planes are recombined in the epilogue.  kF64: FP64
+//            on the CUDA cores.
+//  kJobTile  for a tile of up to 32 bunches: per-bunch moments of the turn
+//            into the record ring (Sec. 2.4), zeroing of the other histogram
+//            buffer, and for each long-range resonator the emission
+//            E_m = c q_m sum_k count[m,k] e^{-s tau_k} and the warp-level
+//            prefix scan of the phasor affine maps x -> a_m (x + E_{m-1})
+//            across the tile (long-range wake, Sec. 2.3 last paragraph).
+//
+// The last CTA to finish (completion counter) composes the tile aggregates
+// of each (run, resonator) with the carried phasor of the previous turn,
+// writes the value entering every tile and the new carry, and advances the
+// turn counter of every run.
+#include <cuda_bf16.h>
+#include "device_common.cuh"
+
+namespace mbt {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded device waits: 2 s
+
+// ---------------------------------------------------------------------------
+// Tile job: moments, histogram reset, long-range emission + local scan.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, long long turn,
+                         double2 *sE) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = kPostThreads / 32;
+  const int nb = R->nb, nbins = R->nbins;
+  const int m0 = job.bt * kBunchTile;
+  const int nbt = min(kBunchTile, nb - m0);
+
+  // moments of the turn (FP64 sums of the push tiles' partials, fixed order)
+  const size_t slot = (size_t)(turn % R->cap);
+  for (int b = warp; b < nbt; b += nwarps) {
+    const BunchDev bd = p.bunches[R->bunch_base + m0 + b];
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = lane; i < bd.ntiles; i += 32) {
+      const double *pp = p.partial + (size_t)(bd.tile0 + i) * kPartials;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) s[c] += pp[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) s[c] = warp_sum_d(s[c]);
+    if (lane == 0) {
+      const double n = (double)bd.n;
+      const double mt = bd.n > 0 ? s[0] / n : 0.0, md = bd.n > 0 ? s[2] / n : 0.0;
+      const double vt = bd.n > 0 ? fmax(s[1] / n - mt * mt, 0.0) : 0.0;
+      const double vd = bd.n > 0 ? fmax(s[3] / n - md * md, 0.0) : 0.0;
+      double *rec = R->rec + (slot * nb + m0 + b) * kRecord;
+      rec[0] = mt;
+      rec[1] = sqrt(vt);
+      rec[2] = md;
+      rec[3] = sqrt(vd);
+      rec[4] = n - s[4];
+      rec[5] = s[4];
+    }
+  }
+  // the other histogram buffer is filled by the next turn's push
+  int32_t *hz = R->hist + ((size_t)(par ^ 1) * nb + m0) * nbins;
+  for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) hz[i] = 0;
+
+  const int32_t *hcur = R->hist + ((size_t)par * nb + m0) * nbins;
+  for (int r = 0; r < R->nlong; ++r) {
+    const double2 cr = R->lr_c[r];
+    for (int b = warp; b < nbt; b += nwarps) {
+      const int32_t *hrow = hcur + (size_t)b * nbins;
+      double2 E;
+      if (PREC == kMixed) {
+        const float2 *tab = R->emis_f + (size_t)r * nbins;
+        float ax = 0.f, ay = 0.f;
+        for (int k = lane; k < nbins; k += 32) {
+          const float c = (float)hrow[k];
+          ax = fmaf(c, tab[k].x, ax);
+          ay = fmaf(c, tab[k].y, ay);
+        }
+        E = make_double2((double)warp_sum_f(ax), (double)warp_sum_f(ay));
+      } else {
+        const double2 *tab = R->emis + (size_t)r * nbins;
+        double ax = 0.0, ay = 0.0;
+        for (int k = lane; k < nbins; k += 32) {
+          const double c = (double)hrow[k];
+          ax = fma(c, tab[k].x, ax);
+          ay = fma(c, tab[k].y, ay);
+        }
+        E = make_double2(warp_sum_d(ax), warp_sum_d(ay));
+      }
+      if (lane == 0) {
+        const double q = R->q_mp[m0 + b];
+        sE[b] = cmul(cr, make_double2(q * E.x, q * E.y));
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // lane b: map of bunch m0+b; bunch m0 maps the tile's entering value
+      const int m = m0 + lane;
+      double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+      if (lane < nbt) {
+        A = R->step[(size_t)r * nb + m];
+        if (lane > 0) B = cmul(A, sE[lane - 1]);
+      }
+      warp_scan_affine(A, B);
+      if (lane < nbt) {
+        R->pq[((size_t)r * nb + m) * 2] = A;
+        R->pq[((size_t)r * nb + m) * 2 + 1] = B;
+      }
+      if (lane == nbt - 1) {
+        R->agg[((size_t)r * R->ntile_b + job.bt) * 2] = A;
+        R->agg[((size_t)r * R->ntile_b + job.bt) * 2 + 1] = cadd(B, sE[lane]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Last CTA: compose tile aggregates with the carry, advance the turns.
+// ---------------------------------------------------------------------------
+__device__ void finish_turn(const Plan &p) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(p.done, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // one warp per (run, long-range resonator)
+  int pair = 0;
+  for (int ri = 0; ri < p.nruns; ++ri) {
+    const RunDev *R = p.runs + ri;
+    for (int r = 0; r < R->nlong; ++r, ++pair) {
+      if (pair % (kPostThreads / 32) != warp) continue;
+      const int nt = R->ntile_b;
+      const double2 K = __ldcg(R->carry + r);
+      double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+      if (lane < nt) {
+        A = __ldcg(R->agg + ((size_t)r * nt + lane) * 2);
+        B = __ldcg(R->agg + ((size_t)r * nt + lane) * 2 + 1);
+      }
+      warp_scan_affine(A, B);
+      const double2 yn = cfma(A, K, B);   // value leaving tile `lane`
+      if (lane + 1 < nt) R->y[(size_t)r * nt + lane + 1] = yn;
+      if (lane == 0) R->y[(size_t)r * nt] = K;
+      __syncwarp();
+      if (lane == nt - 1) R->carry[r] = yn;
+    }
+  }
+  __syncthreads();
+  for (int ri = threadIdx.x; ri < p.nruns; ri += kPostThreads) p.runs[ri].turn[0] += 1;
+  if (threadIdx.x == 0) *p.done = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// kMixed wake job: tcgen05 Toeplitz contraction of one M-tile (128 cells) for
+// a tile of 32 bunches.
+//   A (shared) = [T_hi | T_lo], 128 x 2 nbins BF16, K-major core matrices,
+//                bulk-copied from a pre-laid-out image (constant per run);
+//   B (shared) = 96 x nbins BF16, rows = (byte plane, bunch), built here from
+//                the int32 counts of the turn;
+//   D (tensor memory) = 128 lanes x 96 FP32 columns.
+// ---------------------------------------------------------------------------
+constexpr int kWakeN = 3 * kBunchTile;   // 96
+constexpr uint32_t kTmemCols = 256;      // power of two >= kWakeN, with headroom
+
+__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par,
+                            uint8_t *smem, uint64_t *bars, uint32_t *tmem_slot, int *s_flag) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbins = R->nbins;
+  const int nb = R->nb;
+  const int mt = job.sub;
+  const int m0 = job.bt * kBunchTile;
+  const int nbt = min(kBunchTile, nb - m0);
+  const uint32_t a_bytes = (uint32_t)nbins * 512u;   // 128 rows x 2 nbins x 2 B
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + a_bytes;
+  const uint32_t lboA = 16u * 128u;                   // next 8-column K group: 16 row groups later
+  const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+    *s_flag = 0;
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (tid == 0) {
+    const uint8_t *src = static_cast<const uint8_t *>(R->toep) + (size_t)mt * a_bytes;
+    mbar_arrive_expect_tx(&bars[0], a_bytes);
+    for (uint32_t off = 0; off < a_bytes; off += 32768u)
+      bulk_g2s(sA + off, src + off, min(32768u, a_bytes - off), &bars[0]);
+  }
+  // B: counts of the 32 bunches split into three exact BF16 byte planes
+  const int32_t *hg = R->hist + ((size_t)par * nb + m0) * nbins;
+  const int KG = nbins / 8;
+  for (int idx = tid; idx < kBunchTile * KG; idx += kPostThreads) {
+    const int b = idx % kBunchTile, kg = idx / kBunchTile;
+    int c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (b < nbt) {
+      const int4 c0 = *reinterpret_cast<const int4 *>(hg + (size_t)b * nbins + kg * 8);
+      const int4 c1 = *reinterpret_cast<const int4 *>(hg + (size_t)b * nbins + kg * 8 + 4);
+      c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
+      c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+    }
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float lo = (float)((c[2 * e] >> (8 * pl)) & 0xFF);
+        const float hi = (float)((c[2 * e + 1] >> (8 * pl)) & 0xFF);
+        const __nv_bfloat162 v2 = __floats2bfloat162_rn(lo, hi);
+        w[e] = *reinterpret_cast<const uint32_t *>(&v2);
+      }
+      const int n = pl * kBunchTile + b;
+      uint8_t *dst = sB + ((size_t)kg * (kWakeN / 8) + (n >> 3)) * 128 + (n & 7) * 16;
+      *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  if (tid == 0) {
+    if (!mbar_wait_bounded(&bars[0], 0, kWaitLimitNs)) {
+      atomicExch(p.error, kErrTimeout);
+      *s_flag = 1;
+    } else {
+      tc_fence_after();
+      const uint32_t idesc = idesc_bf16_f32(128, kWakeN);
+      const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+      const int ks_half = nbins / 16;
+      for (int ks = 0; ks < 2 * ks_half; ++ks) {
+        const uint64_t ad = smem_desc_kmajor(a0 + (uint32_t)ks * 2u * lboA, lboA, 128u);
+        const uint64_t bd = smem_desc_kmajor(b0 + (uint32_t)(ks % ks_half) * 2u * lboB, lboB, 128u);
+        umma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
+      umma_commit(&bars[1]);
+    }
+  }
+  __syncthreads();
+  const bool aborted = *s_flag != 0;
+  if (!aborted && warp < 4) {
+    if (!mbar_wait_bounded(&bars[1], 0, kWaitLimitNs)) {
+      if (lane == 0) atomicExch(p.error, kErrTimeout);
+    } else {
+      tc_fence_after();
+      float d0[32], d1[32], d2[32];
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+      tmem_ld32(tl + 0, d0);
+      tmem_ld32(tl + 32, d1);
+      tmem_ld32(tl + 64, d2);
+      const int j = mt * 128 + warp * 32 + lane;
+      float *vsr = static_cast<float *>(R->vsr);
+#pragma unroll
+      for (int b = 0; b < kBunchTile; ++b) {
+        if (b < nbt) {
+          const float q = (float)R->q_mp[m0 + b];
+          vsr[(size_t)(m0 + b) * nbins + j] = q * fmaf(65536.f, d2[b], fmaf(256.f, d1[b], d0[b]));
+        }
+      }
+    }
+  }
+  if (aborted && tid == 0) mbar_wait_bounded(&bars[0], 0, kWaitLimitNs);   // let the copy land before exit
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+__global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
+  extern __shared__ __align__(1024) uint8_t sm_post[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_flag;
+  __shared__ double2 sE[kBunchTile];
+  const PostJob job = p.jobs[blockIdx.x];
+  const RunDev *R = p.runs + job.run;
+  const long long turn = *R->turn;
+  const int par = (int)(turn & 1);
+  if (job.type == kJobWake) wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag);
+  else tile_job<kMixed>(p, R, job, par, turn, sE);
+  finish_turn(p);
+}
+
+// ---------------------------------------------------------------------------
+// kF64 wake job: rows [32 c, 32 c + 32) of one bunch, 8 threads per row.
+// ---------------------------------------------------------------------------
+__device__ void wake_job_f64(const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem) {
+  const int nbins = R->nbins;
+  const int m = job.bt, chunk = job.sub;
+  double *sW = reinterpret_cast<double *>(smem);
+  int *sHc = reinterpret_cast<int *>(sW + nbins);
+  const double *lag = static_cast<const double *>(R->toep);
+  const int32_t *hg = R->hist + ((size_t)par * R->nb + m) * nbins;
+  for (int k = threadIdx.x; k < nbins; k += kPostThreads) {
+    sW[k] = lag[k];
+    sHc[k] = hg[k];
+  }
+  __syncthreads();
+  const int row = threadIdx.x >> 3, sub = threadIdx.x & 7;
+  const int j = chunk * kF64RowChunk + row;
+  double acc = 0.0;
+  if (j < nbins)
+    for (int k = sub; k <= j; k += 8) acc = fma((double)sHc[k], sW[j - k], acc);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+  if (sub == 0 && j < nbins) static_cast<double *>(R->vsr)[(size_t)m * nbins + j] = R->q_mp[m] * acc;
+}
+
+__global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
+  extern __shared__ __align__(16) uint8_t sm_post64[];
+  __shared__ double2 sE[kBunchTile];
+  const PostJob job = p.jobs[blockIdx.x];
+  const RunDev *R = p.runs + job.run;
+  const long long turn = *R->turn;
+  const int par = (int)(turn & 1);
+  if (job.type == kJobWake) wake_job_f64(R, job, par, sm_post64);
+  else tile_job<kF64>(p, R, job, par, turn, sE);
+  finish_turn(p);
+}
+
+size_t post_smem_bytes(int precision, int max_nbins) {
+  // A image + B operand, plus a margin so that every address an MMA could
+  // form from these descriptors (even with the K and M/N strides exchanged)
+  // stays inside the allocation
+  if (precision == kMixed) return (size_t)max_nbins * 512u + (size_t)max_nbins * 2u * kWakeN + 24576u;
+  return (size_t)max_nbins * (sizeof(double) + sizeof(int));
+}
+
+cudaError_t configure_kernels() {
+  return cudaFuncSetAttribute(k_post_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)post_smem_bytes(kMixed, 256));
+}
+
+cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s) {
+  if (p.njobs == 0) return cudaSuccess;
+  const size_t smem = post_smem_bytes(precision, p.max_nbins);
+  if (precision == kMixed) k_post_mixed<<<p.njobs, kPostThreads, smem, s>>>(p);
+  else k_post_f64<<<p.njobs, kPostThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace mbt

@@ -1,0 +1,96 @@
+// Internal layout shared by the host engine and the kernels of libmbt.
+//
+// Device state of one run (a fill of bunches on one ring), the per-batch work
+// lists, and the launch entry points of the kernels.  Everything here is
+// plain data: pointers into device memory plus constants derived on the host.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mbt {
+
+constexpr int kMaxRes = 8;           // resonators per run
+constexpr int kMaxLong = 4;          // resonators with the long-range bit
+constexpr int kBunchTile = 32;       // bunches per post-kernel tile (one lane per bunch)
+constexpr int kMaxBunches = 1024;    // one warp scans the tile aggregates
+constexpr int kPushThreads = 256;
+constexpr int kMixedQuadsPerThread = 8;                                    // 4 particles per quad
+constexpr int kMixedTile = kPushThreads * 4 * kMixedQuadsPerThread;        // 8192 particles
+constexpr int kF64PairsPerThread = 4;                                      // 2 particles per pair
+constexpr int kF64Tile = kPushThreads * 2 * kF64PairsPerThread;            // 2048 particles
+constexpr int kPartials = 6;         // sum tau, sum tau^2, sum delta, sum delta^2, n_out, pad
+constexpr int kRecord = 6;           // <tau>, rms tau, <delta>, rms delta, n_in, n_out
+constexpr int kPostThreads = 256;
+constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
+
+enum Precision { kF64 = 0, kMixed = 1 };
+enum Flags { kNoSR = 1, kNoQE = 2, kKickNGP = 4 };
+enum JobType { kJobWake = 0, kJobTile = 1 };
+enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2 };
+
+// One run's device state and constants.
+struct RunDev {
+  // particle state: tau (float for kMixed, double for kF64), delta (double)
+  void *tau;
+  double *delta;
+  int32_t *hist;        // [2][nb][nbins]; turn parity selects the buffer
+  void *vsr;            // [nb][nbins] short-range voltage for the next kick (float / double)
+  double2 *pq;          // [nlong][nb][2]: P_m, Q_m with Phi_m = P_m y_tile + Q_m
+  double2 *y;           // [nlong][ntile_b]: value entering each bunch tile
+  double2 *agg;         // [nlong][ntile_b][2]: tile aggregate affine maps (A, B)
+  double2 *carry;       // [nlong]: value after the last bunch of the previous turn
+  double *rec;          // [cap][nb][kRecord]
+  long long *turn;      // turns completed (device counter)
+  const double *q_mp;   // [nb] macro-particle charge [C]
+  const double2 *step;  // [nlong][nb] a_m = e^{s dt_m}
+  const double2 *emis;  // [nlong][nbins] e^{-s tau_k} (double)
+  const float2 *emis_f; // [nlong][nbins] same in float
+  const void *toep;     // kMixed: bf16 operand images [nbins/128][128 x 2 nbins]; kF64: double lag table [nbins]
+  int nb, nbins, nlong, ntile_b;
+  int cap, flags, precision, bunch_base;   // bunch_base: index of bunch 0 in the plan's bunch list
+  uint32_t key0, key1;
+  // ring constants
+  double inv_E0, V_over_E0, sin_phi_s, cos_phi_s, U0_over_E0, omega_rf, phi_s;
+  double one_minus_D, qe_amp, aT0, H, invDelta, Delta;
+  double sigma_tau0, sigma_E;   // matched start
+  double2 lr_s[kMaxLong];   // s = -a + i wb
+  double2 lr_c[kMaxLong];   // c = 2 a Rs (1 + i a / wb)
+};
+
+struct BunchDev {
+  int run, m;
+  long long off;        // first particle of the bunch in the run's arrays (multiple of 4)
+  long long n;          // macro-particles
+  int tile0, ntiles;    // push tiles of this bunch in the plan
+};
+
+struct TileDev {
+  int bunch, run, m, count;   // count <= tile size
+  long long start;            // first particle of the tile within its bunch (even)
+};
+
+struct PostJob {
+  int run, type, bt, sub;     // kJobWake: sub = M-tile (kMixed) or (bunch, row chunk) (kF64)
+};
+
+// A batch of runs tracked by the same launches.
+struct Plan {
+  RunDev *runs;
+  BunchDev *bunches;
+  TileDev *tiles;
+  PostJob *jobs;
+  double *partial;            // [ntiles][kPartials]
+  unsigned int *done;         // post-kernel completion counter (last-block pattern)
+  int *error;                 // device error word (DeviceError)
+  int nruns, nbunches, ntiles, njobs;
+  int max_nbins;              // largest mesh of the plan's runs (shared-memory sizing)
+};
+
+// Kernel launchers (one translation unit each).
+cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s);
+cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s);
+cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s);
+size_t post_smem_bytes(int precision, int max_nbins);
+cudaError_t configure_kernels();
+
+}  // namespace mbt

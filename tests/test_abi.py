@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point that include/mbt.h declares, validates arguments, and
+derives the ring quantities from the same definitions as the oracle."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import mbt_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1809_00391_gb300 as p
+    p.build()
+    return p
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mbt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mbt_[a-z_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree(pkg):
+    assert _declared() == sorted(pkg.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    L = pkg.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert L.mbt_version() == 100
+    assert L.mbt_status_string(0) == b"ok"
+    assert L.mbt_status_string(5) == b"device wait timed out"
+
+
+def _create(pkg, ring, prec=0, flags=0):
+    import ctypes
+    L = pkg.lib()
+    r = pkg.Ring(E0_eV=ring["E0_eV"], T0_s=ring["T0_s"], h=ring["h"], reserved=0, V_rf_V=ring["V_rf_V"],
+                 alpha_c=ring["alpha_c"], U0_eV=ring["U0_eV"], sigma_delta=ring["sigma_delta"],
+                 tau_z_s=ring["tau_z_s"])
+    h = ctypes.c_void_p()
+    st = L.mbt_create(ctypes.byref(r), prec, flags, 7, ctypes.byref(h))
+    return st, h
+
+
+def test_argument_validation(pkg):
+    L = pkg.lib()
+    for bad in (dict(E0_eV=0.0), dict(h=0), dict(alpha_c=0.0), dict(U0_eV=3e6), dict(tau_z_s=-1.0)):
+        ring = W.ring_r0()
+        ring.update(bad)
+        st, h = _create(pkg, ring)
+        assert st == 1 and not h.value
+    st, h = _create(pkg, W.ring_r0(), prec=7)
+    assert st == 1
+    st, h = _create(pkg, W.ring_r0(), prec=1)
+    assert st == 0
+    assert L.mbt_add_resonator(h, 1e3, 1e9, 0.4, 1) == 1          # Q <= 1/2
+    assert L.mbt_add_resonator(h, 1e3, 1e9, 2.0, 0) == 1          # no range
+    for _ in range(4):
+        assert L.mbt_add_resonator(h, 1e3, 1e9, 2.0, 3) == 0
+    assert L.mbt_add_resonator(h, 1e3, 1e9, 2.0, 2) == 6          # fifth long-range resonator
+    assert b"long-range" in L.mbt_last_error(h)
+    assert L.mbt_set_grid(h, 200, 5.0) == 6                        # mixed needs 128 or 256
+    assert L.mbt_set_grid(h, 128, 5.0) == 0
+    assert L.mbt_set_grid(h, 256, -1.0) == 1
+    assert L.mbt_track(h, 10, None) == 2                           # no fill yet
+    L.mbt_destroy(h)
+
+
+@pytest.mark.parametrize("ring,flags", [(W.ring_r0(), 0), (W.ring_r0(), W.NO_SR), (W.ring_dc12c(), 0)],
+                         ids=["R0", "R0-noSR", "dc12c"])
+def test_derived_quantities_match_the_oracle(pkg, oracle_mod, ring, flags):
+    import ctypes
+    st, h = _create(pkg, ring, prec=0, flags=flags)
+    assert st == 0
+    L = pkg.lib()
+    assert L.mbt_set_grid(h, 256, 5.0) == 0
+    info = pkg.Info()
+    assert L.mbt_get_info(h, ctypes.byref(info)) == 0
+    o = oracle_mod.OracleSim(ring, [], 256, 5.0, [0], [0.0], [2], 7, flags)
+    d = o.derived
+    assert info.phi_s == pytest.approx(d["phi_s"], rel=1e-15)
+    assert info.nu_s == pytest.approx(d["nu_s"], rel=1e-15)
+    assert info.sigma_tau0_s == pytest.approx(d["sigma_tau0"], rel=1e-15)
+    assert info.half_width_s == pytest.approx(d["H"], rel=1e-15)
+    assert info.bin_width_s == pytest.approx(d["Delta"], rel=1e-15)
+    assert info.D == pytest.approx(d["D"], rel=1e-15)
+    assert info.T_rf_s == pytest.approx(d["T_rf"], rel=1e-15)
+    L.mbt_destroy(h)
+
+
+def test_binding_fails_loudly_without_library(pkg, monkeypatch, tmp_path):
+    import paper_1809_00391_gb300 as p
+    monkeypatch.setattr(p, "_lib", None)
+    monkeypatch.setattr(p, "_LIB_PATH", tmp_path / "missing.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        p.lib()
