@@ -70,10 +70,10 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(str(build()))
             lib.orc_philox4x32_10.argtypes = [_P(_u32), _P(_u32), _P(_u32)]
-            lib.orc_u01.argtypes = [_u32, _u32]
+            lib.orc_u01.argtypes = [_u32]
             lib.orc_u01.restype = _d
             lib.orc_box_muller.argtypes = [_d, _d, _P(_d), _P(_d)]
-            lib.orc_normal_pair.argtypes = [_u64, _u32, _u32, _u32, _u32, _P(_d), _P(_d)]
+            lib.orc_normal_quad.argtypes = [_u64, _u32, _u32, _u32, _u32, _P(_d)]
             lib.orc_derive.argtypes = [_P(Ring), ctypes.c_int, _P(_d)]
             lib.orc_wake.argtypes = [_P(Resonator), _d]
             lib.orc_wake.restype = _d
@@ -119,8 +119,9 @@ def philox4x32_10(ctr, key):
     return tuple(int(x) for x in o)
 
 
-def u01(hi: int, lo: int) -> float:
-    return _load().orc_u01(hi & 0xFFFFFFFF, lo & 0xFFFFFFFF)
+def u01(w: int) -> float:
+    """Uniform on (0,1) from one 32-bit word: (w + 1/2) 2^-32."""
+    return _load().orc_u01(w & 0xFFFFFFFF)
 
 
 def box_muller(u1: float, u2: float):
@@ -129,10 +130,11 @@ def box_muller(u1: float, u2: float):
     return a.value, b.value
 
 
-def normal_pair(seed: int, pair: int, bunch: int, turn: int, tag: int):
-    a, b = _d(), _d()
-    _load().orc_normal_pair(seed, pair, bunch, turn, tag, ctypes.byref(a), ctypes.byref(b))
-    return a.value, b.value
+def normal_quad(seed: int, quad: int, bunch: int, turn: int, tag: int):
+    """The four normals of particles 4 quad .. 4 quad + 3."""
+    r = (_d * 4)()
+    _load().orc_normal_quad(seed, quad, bunch, turn, tag, r)
+    return tuple(r)
 
 
 def make_ring(ring: dict) -> Ring:

@@ -41,8 +41,9 @@
  *      not deposited, and get no short-range kick;
  *   R8 the short-range voltage is interpolated linearly between cell centres
  *      (clamped at the end cells); nearest-cell is a flag;
- *   R9 normal deviates from Philox4x32-10 + Box-Muller (cos and sin branch),
- *      counter (pair, bunch, turn, tag), key (seed lo, seed hi);
+ *   R9 normal deviates from Philox4x32-10 + Box-Muller: one block per quad of
+ *      consecutive particles, counter (quad, bunch, turn, tag), key (seed lo,
+ *      seed hi), each 32-bit word a uniform (w + 1/2) 2^-32;
  *   R10 the long-range wake of a passage is sourced by its binned histogram at
  *      cell centres, and acts on every particle of every later passage.
  */
@@ -92,12 +93,10 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Uniform in the open interval (0,1) from two 32-bit words: the top 53 bits of
- * the 64-bit integer hi:lo, scaled by 2^-53, plus half a step (2^-54). */
-double orc_u01(uint32_t hi, uint32_t lo)
+/* Uniform in the open interval (0,1) from one 32-bit word: (w + 1/2) 2^-32. */
+double orc_u01(uint32_t w)
 {
-    uint64_t x = ((uint64_t)hi << 32) | (uint64_t)lo;
-    return (double)(x >> 11) * 0x1.0p-53 + 0x1.0p-54;
+    return ((double)w + 0.5) * 0x1.0p-32;
 }
 
 /* Box-Muller: two independent standard normals from two uniforms. */
@@ -109,17 +108,18 @@ void orc_box_muller(double u1, double u2, double *r_cos, double *r_sin)
     *r_sin = R * sin(two_pi * u2);
 }
 
-/* Normal pair for (pair index, bunch, turn, tag) under a 64-bit seed.
- * Word layout: u1 from (w0, w1), u2 from (w2, w3); the cos branch goes to the
- * even particle 2*pair, the sin branch to the odd particle 2*pair+1. */
-void orc_normal_pair(uint64_t seed, uint32_t pair, uint32_t bunch, uint32_t turn, uint32_t tag,
-                     double *r_even, double *r_odd)
+/* Four normals for the quad of consecutive particles 4q .. 4q+3 of a bunch,
+ * for (quad, bunch, turn, tag) under a 64-bit seed (reading R9): one Philox
+ * block, Box-Muller on (u(w0), u(w1)) for particles 4q (cos) and 4q+1 (sin),
+ * on (u(w2), u(w3)) for 4q+2 (cos) and 4q+3 (sin). */
+void orc_normal_quad(uint64_t seed, uint32_t quad, uint32_t bunch, uint32_t turn, uint32_t tag, double r[4])
 {
-    uint32_t ctr[4] = {pair, bunch, turn, tag};
+    uint32_t ctr[4] = {quad, bunch, turn, tag};
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
-    orc_box_muller(orc_u01(w[0], w[1]), orc_u01(w[2], w[3]), r_even, r_odd);
+    orc_box_muller(orc_u01(w[0]), orc_u01(w[1]), &r[0], &r[1]);
+    orc_box_muller(orc_u01(w[2]), orc_u01(w[3]), &r[2], &r[3]);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -317,15 +317,13 @@ void orc_init_particles(orc_sim *s)
 {
     for (int m = 0; m < s->nb; ++m) {
         int64_t n = s->n_mp[m];
-        for (int64_t i = 0; i < n; i += 2) {
-            double a0, a1, b0, b1;
-            orc_normal_pair(s->seed, (uint32_t)(i / 2), (uint32_t)m, 0u, 1u, &a0, &a1);
-            orc_normal_pair(s->seed, (uint32_t)(i / 2), (uint32_t)m, 0u, 2u, &b0, &b1);
-            s->tau[m][i] = s->dv.sigma_tau0 * a0;
-            s->delta[m][i] = s->ring.sigma_delta * b0;
-            if (i + 1 < n) {
-                s->tau[m][i + 1] = s->dv.sigma_tau0 * a1;
-                s->delta[m][i + 1] = s->ring.sigma_delta * b1;
+        for (int64_t i = 0; i < n; i += 4) {
+            double a[4], b[4];
+            orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, 0u, 1u, a);
+            orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, 0u, 2u, b);
+            for (int e = 0; e < 4 && i + e < n; ++e) {
+                s->tau[m][i + e] = s->dv.sigma_tau0 * a[e];
+                s->delta[m][i + e] = s->ring.sigma_delta * b[e];
             }
         }
     }
@@ -478,13 +476,11 @@ static void one_turn(orc_sim *s)
         memset(hist, 0, sizeof(int32_t) * s->nbins);
         int64_t out = 0;
         double *tau = s->tau[m], *delta = s->delta[m];
-        for (int64_t i = 0; i < n; i += 2) {
-            double r[2];
+        for (int64_t i = 0; i < n; i += 4) {
+            double r[4] = {0.0, 0.0, 0.0, 0.0};
             if (s->dv.qe_amp != 0.0)
-                orc_normal_pair(s->seed, (uint32_t)(i / 2), (uint32_t)m, turn32, 0u, &r[0], &r[1]);
-            else
-                r[0] = r[1] = 0.0;
-            for (int e = 0; e < 2 && i + e < n; ++e) {
+                orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, turn32, 0u, r);
+            for (int e = 0; e < 4 && i + e < n; ++e) {
                 double t = tau[i + e], d = delta[i + e];
                 /* wake kick with the previous turn's wake (zero on turn 0) */
                 double V = vsr_at(s, m, orc_cell_coord(s, t)) + vlr_at(s, m, t);

@@ -49,12 +49,10 @@ def test_philox_known_answers(oracle_mod):
 
 
 def test_uniform_open_interval(oracle_mod):
-    assert oracle_mod.u01(0, 0) == 2.0 ** -54
-    assert oracle_mod.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -54
-    assert oracle_mod.u01(0x80000000, 0) == 0.5 + 2.0 ** -54
-    # the low 11 bits of the 64-bit word are dropped, the rest is exact
-    assert oracle_mod.u01(0, 0x800) == 2.0 ** -53 + 2.0 ** -54
-    assert oracle_mod.u01(0, 0x7FF) == 2.0 ** -54
+    assert oracle_mod.u01(0) == 2.0 ** -33
+    assert oracle_mod.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -33
+    assert oracle_mod.u01(0x80000000) == 0.5 + 2.0 ** -33
+    assert oracle_mod.u01(1) == 1.5 * 2.0 ** -32
 
 
 def test_box_muller_closed_forms(oracle_mod):
@@ -69,19 +67,23 @@ def test_box_muller_closed_forms(oracle_mod):
 
 
 def test_normals_are_standard_and_independent(oracle_mod):
-    n = 20000
-    ev = np.empty(n)
-    od = np.empty(n)
-    for i in range(n):
-        ev[i], od[i] = oracle_mod.normal_pair(12345, i, 3, 7, 0)
-    z = np.concatenate([ev, od])
+    n = 10000
+    r = np.array([oracle_mod.normal_quad(12345, i, 3, 7, 0) for i in range(n)])
+    z = r.ravel()
     assert stats.kstest(z, "norm").pvalue > 1e-3
     assert abs(z.mean()) < 5 / math.sqrt(z.size)
     assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
-    assert abs(np.corrcoef(ev, od)[0, 1]) < 5 / math.sqrt(n)
-    # different counters give different streams
-    assert oracle_mod.normal_pair(12345, 0, 3, 7, 0) != oracle_mod.normal_pair(12345, 0, 3, 8, 0)
-    assert oracle_mod.normal_pair(12345, 0, 3, 7, 0) != oracle_mod.normal_pair(12346, 0, 3, 7, 0)
+    c = np.corrcoef(r.T)
+    assert np.max(np.abs(c - np.eye(4))) < 5 / math.sqrt(n)
+    # the quad is Box-Muller on the block's four words
+    w = oracle_mod.philox4x32_10((17, 3, 7, 0), (12345, 0))
+    a = oracle_mod.box_muller(oracle_mod.u01(w[0]), oracle_mod.u01(w[1]))
+    b = oracle_mod.box_muller(oracle_mod.u01(w[2]), oracle_mod.u01(w[3]))
+    assert oracle_mod.normal_quad(12345, 17, 3, 7, 0) == (a[0], a[1], b[0], b[1])
+    # different counters or seeds give different streams
+    assert oracle_mod.normal_quad(12345, 0, 3, 7, 0) != oracle_mod.normal_quad(12345, 0, 3, 8, 0)
+    assert oracle_mod.normal_quad(12345, 0, 3, 7, 0) != oracle_mod.normal_quad(12346, 0, 3, 7, 0)
+    assert oracle_mod.normal_quad(2 ** 32 + 5, 0, 3, 7, 0) != oracle_mod.normal_quad(5, 0, 3, 7, 0)
 
 
 # --------------------------------------------------------------------------- single-particle map
