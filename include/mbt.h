@@ -206,6 +206,16 @@ mbt_status mbt_set_graph(mbt_ctx *ctx, int turns_per_graph);
 mbt_status mbt_set_timing(mbt_ctx *ctx, int enable);
 mbt_status mbt_get_timing(mbt_ctx *ctx, double *push_ms, double *post_ms, int64_t *launches);
 
+/* Post-kernel trace: when enabled, every CTA of the post kernel records
+ * %globaltimer [ns] at its start, when its own job is done, and at exit (the
+ * last CTA to finish also composes the phasor tiles and advances the turn).
+ * mbt_read_trace copies the record of the last post launch into
+ * out[min(max_jobs, njobs)][5] = job type (0 wake, 1 tile), bunch tile,
+ * start, job done, exit; *njobs receives the number of post CTAs (out may be
+ * NULL to query it).  Enabling or disabling drops a captured graph. */
+mbt_status mbt_set_trace(mbt_ctx *ctx, int enable);
+mbt_status mbt_read_trace(mbt_ctx *ctx, int64_t *out, int max_jobs, int *njobs);
+
 /* Checkpoint: mbt_state_size gives the bytes of a snapshot (particles, turn,
  * wake and phasor carry, histograms); mbt_save_state writes it into buf;
  * mbt_load_state restores it into a context with the same configuration.

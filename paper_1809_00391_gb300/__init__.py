@@ -30,7 +30,7 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_add_resonator", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
            "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_timing",
-           "mbt_get_timing", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_batch_create",
+           "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_batch_create",
            "mbt_batch_track", "mbt_batch_sync", "mbt_batch_destroy"]
 
 
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_read_wake": ([_vp, _P(_d), _P(_d)], _i), "mbt_get_info": ([_vp, _P(Info)], _i),
                 "mbt_set_graph": ([_vp, _i], _i), "mbt_set_timing": ([_vp, _i], _i),
                 "mbt_get_timing": ([_vp, _P(_d), _P(_d), _P(_i64)], _i),
+                "mbt_set_trace": ([_vp, _i], _i), "mbt_read_trace": ([_vp, _P(_i64), _i, _P(_i)], _i),
                 "mbt_state_size": ([_vp, _P(_sz)], _i), "mbt_save_state": ([_vp, _vp, _sz], _i),
                 "mbt_load_state": ([_vp, _vp, _sz], _i),
                 "mbt_batch_create": ([_P(_vp), _i, _P(_vp)], _i), "mbt_batch_track": ([_vp, _i64, _vp], _i),
@@ -221,6 +222,17 @@ class Tracker:
         a, b, n = _d(), _d(), _i64()
         self._chk(self._L.mbt_get_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
         return a.value, b.value, n.value
+
+    def set_trace(self, enable: bool):
+        self._chk(self._L.mbt_set_trace(self._h, 1 if enable else 0))
+
+    def trace(self) -> np.ndarray:
+        """[njobs][5]: job type, bunch tile, start, job done, exit (ns) of the last post launch."""
+        n = _i()
+        self._chk(self._L.mbt_read_trace(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 5), np.int64)
+        self._chk(self._L.mbt_read_trace(self._h, _ptr(out, _i64), n.value, ctypes.byref(n)))
+        return out
 
     def save_state(self) -> bytes:
         n = _sz()

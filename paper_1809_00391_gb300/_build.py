@@ -18,6 +18,8 @@ INCLUDE = PKG.parent / "include"
 SOURCES = ["k_push.cu", "k_post.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE)]
+# extra nvcc flags for tuning experiments (e.g. "-DMBT_PUSH_STAGES=2"); part of the staleness key
+EXTRA = os.environ.get("MBT_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:
@@ -29,6 +31,9 @@ def _nvcc() -> str:
 
 def _stale() -> bool:
     if not LIB.exists():
+        return True
+    stamp = BUILD / "flags.txt"
+    if not stamp.exists() or stamp.read_text() != " ".join(EXTRA):
         return True
     t = LIB.stat().st_mtime
     deps = list(CSRC.glob("*.cu")) + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
@@ -46,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     for src in SOURCES:
         obj = BUILD / (Path(src).stem + ".o")
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", str(CSRC / src), "-o", str(obj)]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA, "-c", str(CSRC / src), "-o", str(obj)]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
@@ -65,6 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout)
     os.replace(tmp, LIB)
+    (BUILD / "flags.txt").write_text(" ".join(EXTRA))
     return LIB
 
 

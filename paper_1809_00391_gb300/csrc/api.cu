@@ -100,6 +100,8 @@ struct mbt_ctx {
   long long *d_turn = nullptr;
   double *d_q = nullptr;
   double2 *d_step = nullptr, *d_emis = nullptr;
+  float *d_qf = nullptr;
+  double *d_inv_n = nullptr;
   float2 *d_emis_f = nullptr;
   void *d_toep = nullptr;
   size_t device_bytes = 0;
@@ -114,6 +116,11 @@ struct mbt_ctx {
   double push_ms = 0, post_ms = 0;
   int64_t timed_launches = 0;
   std::vector<cudaEvent_t> ev_pool;
+  // post-kernel trace
+  unsigned long long *d_trace = nullptr;
+  // pinned host staging for particle copies
+  void *h_stage = nullptr;
+  size_t h_stage_bytes = 0;
   std::string err;
 };
 
@@ -164,6 +171,22 @@ void free_device(mbt_ctx *c) {
   c->own.release();
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  c->h_stage = nullptr;
+  c->h_stage_bytes = 0;
+  if (c->d_trace) cudaFree(c->d_trace);
+  c->d_trace = nullptr;
+}
+
+// Pinned staging buffer of at least `bytes` (grown on demand).
+void *stage(mbt_ctx *c, size_t bytes) {
+  if (c->h_stage_bytes >= bytes) return c->h_stage;
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  c->h_stage = nullptr;
+  c->h_stage_bytes = 0;
+  if (cudaMallocHost(&c->h_stage, bytes) != cudaSuccess) return nullptr;
+  c->h_stage_bytes = bytes;
+  return c->h_stage;
 }
 
 // Ring-derived quantities (readings listed in mbt.h).
@@ -235,7 +258,11 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
   pl.ntiles = (int)st.tiles.size();
   pl.njobs = (int)st.jobs.size();
   pl.max_nbins = 0;
-  for (auto &r : st.runs) pl.max_nbins = std::max(pl.max_nbins, r.nbins);
+  pl.max_nlong = 0;
+  for (auto &r : st.runs) {
+    pl.max_nbins = std::max(pl.max_nbins, r.nbins);
+    pl.max_nlong = std::max(pl.max_nlong, r.nlong);
+  }
   st.bytes += pb + 16;
   st.plan = pl;
   return MBT_OK;
@@ -292,17 +319,20 @@ mbt_status check_device(mbt_ctx *c, const Plan &pl) {
   return MBT_OK;
 }
 
+// Turns as push + post launches.  Plain: the first push of the call is an
+// ordinary launch and every later kernel uses programmatic dependent launch
+// (its prologue overlaps the previous kernel's tail).  Timed: ordinary
+// launches with CUDA events around each kernel, drained in chunks.
 mbt_status launch_turns(mbt_ctx *c, const Plan &pl, int prec, int64_t nturns, cudaStream_t s, bool timed) {
   if (!timed) {
     for (int64_t t = 0; t < nturns; ++t) {
-      cudaError_t e = launch_push(pl, prec, s);
+      cudaError_t e = launch_push(pl, prec, s, t > 0);
       if (e != cudaSuccess) return cuda_fail(c, e, "push launch");
-      e = launch_post(pl, prec, s);
+      e = launch_post(pl, prec, s, true);
       if (e != cudaSuccess) return cuda_fail(c, e, "post launch");
     }
     return MBT_OK;
   }
-  // events around every launch, drained in chunks
   const int chunk = 512;
   if (c->ev_pool.size() < (size_t)(3 * chunk)) {
     while (c->ev_pool.size() < (size_t)(3 * chunk)) {
@@ -315,10 +345,10 @@ mbt_status launch_turns(mbt_ctx *c, const Plan &pl, int prec, int64_t nturns, cu
     const int n = (int)std::min<int64_t>(chunk, nturns - t0);
     for (int i = 0; i < n; ++i) {
       cudaEventRecord(c->ev_pool[3 * i], s);
-      cudaError_t e = launch_push(pl, prec, s);
+      cudaError_t e = launch_push(pl, prec, s, false);
       if (e != cudaSuccess) return cuda_fail(c, e, "push launch");
       cudaEventRecord(c->ev_pool[3 * i + 1], s);
-      e = launch_post(pl, prec, s);
+      e = launch_post(pl, prec, s, false);
       if (e != cudaSuccess) return cuda_fail(c, e, "post launch");
       cudaEventRecord(c->ev_pool[3 * i + 2], s);
     }
@@ -482,10 +512,16 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   ALLOC(c->d_rec, (size_t)c->cap * nb * kRecord * sizeof(double));
   ALLOC(c->d_turn, 16);
   ALLOC(c->d_q, (size_t)nb * sizeof(double));
+  ALLOC(c->d_qf, (size_t)nb * sizeof(float));
+  ALLOC(c->d_inv_n, (size_t)nb * sizeof(double));
   ALLOC(c->d_step, (size_t)nl * nb * sizeof(double2));
   ALLOC(c->d_emis, (size_t)nl * nbins * sizeof(double2));
   ALLOC(c->d_emis_f, (size_t)nl * nbins * sizeof(float2));
-  const size_t toep_bytes = mixed ? (size_t)(nbins / 128) * nbins * 512 : (size_t)nbins * sizeof(double);
+  size_t toep_bytes = (size_t)nbins * sizeof(double);
+  if (mixed) {
+    toep_bytes = 0;
+    for (int mt = 0; mt < nbins / 128; ++mt) toep_bytes += (size_t)512 * std::min(nbins, 128 * (mt + 1));
+  }
   ALLOC(c->d_toep, toep_bytes);
 #undef ALLOC
 
@@ -493,6 +529,16 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   std::vector<double> q(nb);
   for (int m = 0; m < nb; ++m) q[m] = c->current[m] * c->ring.T0_s / (double)c->nmp[m];
   cudaMemcpy(c->d_q, q.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+  {
+    std::vector<float> qf(nb);
+    std::vector<double> inv_n(nb);
+    for (int m = 0; m < nb; ++m) {
+      qf[m] = (float)q[m];
+      inv_n[m] = 1.0 / (double)c->nmp[m];
+    }
+    cudaMemcpy(c->d_qf, qf.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_inv_n, inv_n.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+  }
 
   // summed short-range wake per lag (half of W(0+) at lag 0)
   std::vector<double> lag(nbins, 0.0);
@@ -500,24 +546,29 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     for (auto &r : c->res)
       if (r.range & MBT_RANGE_SHORT) lag[l] += wake(r, (double)l * c->Delta);
   if (mixed) {
-    // operand images: per M-tile, 128 rows x [hi | lo] (2 nbins columns) in
-    // K-major 8x8 core matrices: byte ((kg * 16 + mg) * 128 + (row % 8) * 16 + (k % 8) * 2)
+    // operand images, per M-tile mt: rows [128 mt, 128 mt + 128) of the lower
+    // triangular Toeplitz matrix need only columns k < Kmt = 128 (mt + 1):
+    // 128 rows x [T_hi | T_lo] (2 Kmt columns) of BF16 in K-major 8x8 core
+    // matrices, byte ((kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2
     const int nmt = nbins / 128;
-    std::vector<uint16_t> img((size_t)nmt * 128 * 2 * nbins, 0);
-    for (int mt = 0; mt < nmt; ++mt)
+    std::vector<uint16_t> img(toep_bytes / 2, 0);
+    size_t base = 0;
+    for (int mt = 0; mt < nmt; ++mt) {
+      const int kmt = std::min(nbins, 128 * (mt + 1));
       for (int row = 0; row < 128; ++row)
-        for (int k = 0; k < nbins; ++k) {
+        for (int k = 0; k < kmt; ++k) {
           const int j = mt * 128 + row;
           const double T = j >= k ? lag[j - k] : 0.0;
           const uint16_t hi = f32_to_bf16_rne((float)T);
           const uint16_t lo = f32_to_bf16_rne((float)(T - (double)bf16_to_f32(hi)));
           for (int half = 0; half < 2; ++half) {
-            const int kk = k + half * nbins;
-            const size_t byte = (size_t)mt * nbins * 512 + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 +
-                                (kk % 8) * 2;
+            const int kk = k + half * kmt;
+            const size_t byte = base + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2;
             img[byte / 2] = half ? lo : hi;
           }
         }
+      base += (size_t)512 * kmt;
+    }
     cudaMemcpy(c->d_toep, img.data(), toep_bytes, cudaMemcpyHostToDevice);
   } else {
     cudaMemcpy(c->d_toep, lag.data(), toep_bytes, cudaMemcpyHostToDevice);
@@ -596,6 +647,23 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   rd.Delta = c->Delta;
   rd.sigma_tau0 = c->sigma_tau0;
   rd.sigma_E = c->ring.sigma_delta;
+  rd.q_mp_f = c->d_qf;
+  rd.inv_n = c->d_inv_n;
+  rd.f_invD = (float)rd.invDelta;
+  rd.f_HinvD = (float)(rd.H * rd.invDelta);
+  rd.f_nbins = (float)nbins;
+  rd.f_invE0 = (float)rd.inv_E0;
+  rd.f_twoVoE0 = (float)(2.0 * rd.V_over_E0);
+  rd.f_cphi = (float)rd.cos_phi_s;
+  rd.f_sphi = (float)rd.sin_phi_s;
+  rd.f_halfw = (float)(0.5 * rd.omega_rf);
+  rd.f_omD = (float)rd.one_minus_D;
+  rd.f_qe = (float)rd.qe_amp;
+  rd.f_aT0 = (float)rd.aT0;
+  for (int li = 0; li < kMaxLong; ++li) {
+    rd.f_la[li] = li < c->nlong ? (float)(-rd.lr_s[li].x) : 0.f;
+    rd.f_lw[li] = li < c->nlong ? (float)rd.lr_s[li].y : 0.f;
+  }
 
   PlanStore &ps = c->own;
   ps.runs.clear();
@@ -609,6 +677,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     return st;
   }
   cudaError_t e = configure_kernels();
+  if (e == cudaSuccess) e = configure_push_kernels();
   if (e != cudaSuccess) {
     free_device(c);
     return cuda_fail(c, e, "kernel attributes");
@@ -649,15 +718,20 @@ mbt_status mbt_set_particles(mbt_ctx *c, int bunch, const double *tau, const dou
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "sync");
   const int64_t n = c->nmp[bunch];
-  if (c->precision == MBT_PREC_MIXED) {
-    std::vector<float> tf(n);
+  const bool mixed = c->precision == MBT_PREC_MIXED;
+  const size_t tb = (size_t)n * (mixed ? sizeof(float) : sizeof(double));
+  char *h = static_cast<char *>(stage(c, tb + (size_t)n * sizeof(double)));
+  if (!h) return fail(c, MBT_ERR_NOMEM, "pinned staging buffer");
+  if (mixed) {
+    float *tf = reinterpret_cast<float *>(h);
     for (int64_t i = 0; i < n; ++i) tf[i] = (float)tau[i];
-    e = cudaMemcpy(static_cast<float *>(c->d_tau) + c->off[bunch], tf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
   } else {
-    e = cudaMemcpy(static_cast<double *>(c->d_tau) + c->off[bunch], tau, n * sizeof(double), cudaMemcpyHostToDevice);
+    std::memcpy(h, tau, tb);
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->d_delta + c->off[bunch], delta, n * sizeof(double), cudaMemcpyHostToDevice);
+  std::memcpy(h + tb, delta, (size_t)n * sizeof(double));
+  char *dt = static_cast<char *>(c->d_tau) + (size_t)c->off[bunch] * (mixed ? sizeof(float) : sizeof(double));
+  e = cudaMemcpy(dt, h, tb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_delta + c->off[bunch], h + tb, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "set particles");
   return MBT_OK;
 }
@@ -670,15 +744,21 @@ mbt_status mbt_get_particles(mbt_ctx *c, int bunch, double *tau, double *delta) 
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "sync");
   const int64_t n = c->nmp[bunch];
-  if (c->precision == MBT_PREC_MIXED) {
-    std::vector<float> tf(n);
-    e = cudaMemcpy(tf.data(), static_cast<float *>(c->d_tau) + c->off[bunch], n * sizeof(float), cudaMemcpyDeviceToHost);
+  const bool mixed = c->precision == MBT_PREC_MIXED;
+  const size_t tb = (size_t)n * (mixed ? sizeof(float) : sizeof(double));
+  char *h = static_cast<char *>(stage(c, tb + (size_t)n * sizeof(double)));
+  if (!h) return fail(c, MBT_ERR_NOMEM, "pinned staging buffer");
+  const char *dt = static_cast<const char *>(c->d_tau) + (size_t)c->off[bunch] * (mixed ? sizeof(float) : sizeof(double));
+  e = cudaMemcpy(h, dt, tb, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(h + tb, c->d_delta + c->off[bunch], (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get particles");
+  if (mixed) {
+    const float *tf = reinterpret_cast<const float *>(h);
     for (int64_t i = 0; i < n; ++i) tau[i] = tf[i];
   } else {
-    e = cudaMemcpy(tau, static_cast<double *>(c->d_tau) + c->off[bunch], n * sizeof(double), cudaMemcpyDeviceToHost);
+    std::memcpy(tau, h, tb);
   }
-  if (e == cudaSuccess) e = cudaMemcpy(delta, c->d_delta + c->off[bunch], n * sizeof(double), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(c, e, "get particles");
+  std::memcpy(delta, h + tb, (size_t)n * sizeof(double));
   return MBT_OK;
 }
 
@@ -691,6 +771,46 @@ mbt_status mbt_set_graph(mbt_ctx *c, int turns) {
     c->graph_exec = nullptr;
   }
   c->graph_turns = turns;
+  return MBT_OK;
+}
+
+mbt_status mbt_set_trace(mbt_ctx *c, int enable) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  if (enable && !c->d_trace) {
+    const size_t bytes = (size_t)c->own.plan.njobs * 3 * sizeof(unsigned long long);
+    if (cudaMalloc(&c->d_trace, bytes) != cudaSuccess) return fail(c, MBT_ERR_NOMEM, "trace buffer");
+    cudaMemset(c->d_trace, 0, bytes);
+  }
+  c->own.plan.trace = enable ? c->d_trace : nullptr;
+  return MBT_OK;
+}
+
+mbt_status mbt_read_trace(mbt_ctx *c, int64_t *out, int max_jobs, int *njobs) {
+  if (!c || !njobs) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  *njobs = c->own.plan.njobs;
+  if (!out || !c->d_trace) return MBT_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  const int n = std::min(max_jobs, c->own.plan.njobs);
+  std::vector<unsigned long long> t((size_t)n * 3);
+  e = cudaMemcpy(t.data(), c->d_trace, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read trace");
+  for (int j = 0; j < n; ++j) {
+    const PostJob &pj = c->own.jobs[j];
+    out[(size_t)j * 5 + 0] = pj.type;
+    out[(size_t)j * 5 + 1] = pj.bt;
+    out[(size_t)j * 5 + 2] = (int64_t)t[(size_t)j * 3 + 0];
+    out[(size_t)j * 5 + 3] = (int64_t)t[(size_t)j * 3 + 1];
+    out[(size_t)j * 5 + 4] = (int64_t)t[(size_t)j * 3 + 2];
+  }
   return MBT_OK;
 }
 
@@ -771,11 +891,16 @@ mbt_status mbt_read_moments(mbt_ctx *c, int64_t turn0, int64_t nturns, double *o
   if (turn0 < 0 || nturns < 0 || turn0 + nturns > turn || turn0 < turn - c->cap)
     return fail(c, MBT_ERR_ARG, "turns [%lld, %lld) not in the record [%lld, %lld)", (long long)turn0,
                 (long long)(turn0 + nturns), (long long)std::max<long long>(0, turn - c->cap), turn);
+  // at most two contiguous segments of the ring buffer
   const size_t per = (size_t)c->nb * kRecord;
-  for (int64_t t = 0; t < nturns; ++t) {
-    const size_t slot = (size_t)((turn0 + t) % c->cap);
-    cudaError_t e = cudaMemcpy(out + t * per, c->d_rec + slot * per, per * sizeof(double), cudaMemcpyDeviceToHost);
+  int64_t t = 0;
+  while (t < nturns) {
+    const int64_t slot = (turn0 + t) % c->cap;
+    const int64_t len = std::min<int64_t>(nturns - t, c->cap - slot);
+    cudaError_t e = cudaMemcpy(out + (size_t)t * per, c->d_rec + (size_t)slot * per, (size_t)len * per * sizeof(double),
+                               cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "read moments");
+    t += len;
   }
   return MBT_OK;
 }

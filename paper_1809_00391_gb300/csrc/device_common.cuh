@@ -11,7 +11,7 @@ namespace mbt {
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
 // S-box, each a pair of 32x32->64 multiplications, with the Weyl key bump
-// between rounds.  counter = (pair, bunch, turn, tag), key = seed.
+// between rounds.  counter = (quad, bunch, turn, tag), key = seed.
 // ---------------------------------------------------------------------------
 struct Words4 { uint32_t w0, w1, w2, w3; };
 
@@ -33,67 +33,67 @@ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32
   return Words4{c0, c1, c2, c3};
 }
 
-// FP64 uniform on (0,1): top 53 bits of hi:lo times 2^-53, plus 2^-54.
-__device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo) {
-  const uint64_t x = ((uint64_t)hi << 32) | lo;
-  return __dadd_rn(__dmul_rn((double)(x >> 11), 0x1.0p-53), 0x1.0p-54);
-}
-
-// The same uniform to FP32 accuracy (relative error ~2^-24 everywhere, never 0).
-__device__ __forceinline__ float u01_f32(uint32_t hi, uint32_t lo) {
-  return fmaf(__uint2float_rn(lo), 0x1.0p-64f, __uint2float_rn(hi) * 0x1.0p-32f) + 0x1.0p-54f;
-}
-
-// Box-Muller pair: r_even = R cos(2 pi u2), r_odd = R sin(2 pi u2), R = sqrt(-2 ln u1).
-__device__ __forceinline__ void normal_pair_f64(const Words4 &w, double &r_even, double &r_odd) {
-  const double u1 = u01_f64(w.w0, w.w1);
-  const double u2 = u01_f64(w.w2, w.w3);
+// Box-Muller on two 32-bit words, u = (w + 1/2) 2^-32: r_cos = R cos(2 pi u2),
+// r_sin = R sin(2 pi u2), R = sqrt(-2 ln u1).  The four words of one Philox
+// block give the normals of the quad of consecutive particles 4q .. 4q+3.
+__device__ __forceinline__ void box_muller_f64(uint32_t a, uint32_t b, double &r_cos, double &r_sin) {
+  const double u1 = ((double)a + 0.5) * 0x1.0p-32;
+  const double u2 = ((double)b + 0.5) * 0x1.0p-32;
   const double R = sqrt(-2.0 * log(u1));
   double s, c;
   sincospi(2.0 * u2, &s, &c);
-  r_even = R * c;
-  r_odd = R * s;
+  r_cos = R * c;
+  r_sin = R * s;
 }
 
-__device__ __forceinline__ void normal_pair_f32(const Words4 &w, float &r_even, float &r_odd) {
-  const float u1 = u01_f32(w.w0, w.w1);
-  const float u2 = u01_f32(w.w2, w.w3);
-  const float R = sqrtf(-2.0f * logf(u1));
+__device__ __forceinline__ void normal_quad_f64(const Words4 &w, double (&r)[4]) {
+  box_muller_f64(w.w0, w.w1, r[0], r[1]);
+  box_muller_f64(w.w2, w.w3, r[2], r[3]);
+}
+
+// The same to FP32 accuracy with the special-function unit.  cos(2 pi u2) =
+// -cos(2 pi u2 - pi), likewise sin, so the MUFU argument lies in [-pi, pi)
+// where its absolute error is about 2^-21.
+__device__ __forceinline__ void box_muller_f32(uint32_t a, uint32_t b, float &r_cos, float &r_sin) {
+  const float u1 = fmaf(__uint2float_rn(a), 0x1.0p-32f, 0x1.0p-33f);
+  const float u2 = fmaf(__uint2float_rn(b), 0x1.0p-32f, 0x1.0p-33f);
+  const float R2 = -2.0f * __logf(u1);
+  const float R = R2 * rsqrtf(fmaxf(R2, 1e-30f));
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  r_even = R * c;
-  r_odd = R * s;
+  __sincosf(fmaf(6.28318530717958647f, u2, -3.14159265358979324f), &s, &c);
+  r_cos = -R * c;
+  r_sin = -R * s;
+}
+
+__device__ __forceinline__ void normal_quad_f32(const Words4 &w, float (&r)[4]) {
+  box_muller_f32(w.w0, w.w1, r[0], r[1]);
+  box_muller_f32(w.w2, w.w3, r[2], r[3]);
 }
 
 // ---------------------------------------------------------------------------
-// float <-> double on the integer pipe.  GB300's FP64 unit issues ~1.7
-// operations per clock per SM; these keep the mixed-precision push to one
-// FP64 instruction (the delta accumulation) per particle.
+// float <-> double on the integer pipe.  GB300's FP64 unit issues ~1.6 lanes
+// per clock per SM (20 clocks per warp instruction), conversions included;
+// these keep the mixed-precision push to one FP64 instruction (the delta
+// accumulation) per particle.
 // ---------------------------------------------------------------------------
-// Exact widening of a normal float; zero and subnormal inputs give a signed
-// zero, infinities and NaN keep their class.
+// Widening of a float by exponent rebias (exact for normal floats).  Zero and
+// subnormals map to +-2^-127 and non-finite values to +-2^128: both far
+// outside anything a particle increment can be, and harmless there.
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t sign = u & 0x80000000u;
-  const uint32_t mag = u & 0x7FFFFFFFu;
-  uint32_t hi = sign | ((mag >> 3) + (896u << 20));
-  uint32_t lo = mag << 29;
-  if (mag < 0x00800000u) { hi = sign; lo = 0u; }
-  if (mag >= 0x7F800000u) { hi = sign | 0x7FF00000u | ((mag & 0x007FFFFFu) >> 3); lo = mag << 29; }
-  return __hiloint2double((int)hi, (int)lo);
+  const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-// Narrowing by truncation toward zero of the significand (error < 1 float
-// ulp); magnitudes below 2^-126 give a signed zero, NaN stays NaN.
+// Narrowing by truncation of the significand (error below one float ulp),
+// exact in exponent for 2^-126 <= |d| < 2^128.  The caller guarantees d is
+// never exactly zero (the widened increments above are never zero, so no
+// accumulated delta is); magnitudes below 2^-126 come out as tiny subnormal
+// floats, non-finite values as arbitrary finite ones.
 __device__ __forceinline__ float f64_to_f32_trunc(double d) {
   const uint32_t hi = (uint32_t)__double2hiint(d);
   const uint32_t lo = (uint32_t)__double2loint(d);
-  const uint32_t sign = hi & 0x80000000u;
-  const uint32_t mag = hi & 0x7FFFFFFFu;
-  uint32_t f = sign | (((mag - (896u << 20)) << 3) | (lo >> 29));
-  if (mag < (897u << 20)) f = sign;
-  if (mag >= (1151u << 20)) f = sign | 0x7F800000u | ((mag > 0x7FF00000u || (mag == 0x7FF00000u && lo)) ? 0x400000u : 0u);
-  return __uint_as_float(f);
+  return __uint_as_float((__funnelshift_l(lo, hi, 3) - (896u << 23)) | (hi & 0x80000000u));
 }
 
 // ---------------------------------------------------------------------------
@@ -136,6 +136,12 @@ __device__ __forceinline__ void warp_scan_affine(double2 &A, double2 &B) {
     }
   }
 }
+
+// Programmatic dependent launch: let the next kernel of the stream begin its
+// prologue, and wait until the previous kernel has completed (its memory
+// visible).  Both are no-ops when the launch did not opt in.
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
   unsigned long long t;

@@ -31,83 +31,119 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded device w
 // ---------------------------------------------------------------------------
 // Tile job: moments, histogram reset, long-range emission + local scan.
 // ---------------------------------------------------------------------------
-template <int PREC>
-__device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, long long turn,
-                         double2 *sE) {
+// Per-bunch moments of the turn into the record ring (Sec. 2.4): thread
+// (value c, bunch b) sums the push-tile partials of bunch m0+b in a fixed
+// order (independent loads, FP64 adds), then lane b of warp 0 forms the
+// moments.  FP64 stays lane-parallel: GB300 spends ~20 FP64-pipe clocks on a
+// warp instruction whatever its active lanes.  Also zeroes the other
+// histogram buffer of these bunches (the next turn's push fills it).
+__device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0, int nbt, int par, long long turn,
+                            double (*s_sum)[kBunchTile]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = kPostThreads / 32;
+  const int nb = R->nb, nbins = R->nbins;
+  {
+    const int b = threadIdx.x & 31, cidx = threadIdx.x >> 5;
+    if (cidx < 5 && b < nbt) {
+      const BunchDev bd = p.bunches[R->bunch_base + m0 + b];
+      const double *pp = p.partial + (size_t)bd.tile0 * kPartials + cidx;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = 0;
+      for (; i + 4 <= bd.ntiles; i += 4) {
+        a0 += pp[(size_t)(i + 0) * kPartials];
+        a1 += pp[(size_t)(i + 1) * kPartials];
+        a2 += pp[(size_t)(i + 2) * kPartials];
+        a3 += pp[(size_t)(i + 3) * kPartials];
+      }
+      for (; i < bd.ntiles; ++i) a0 += pp[(size_t)i * kPartials];
+      s_sum[cidx][b] = (a0 + a1) + (a2 + a3);
+    }
+  }
+  int32_t *hz = R->hist + ((size_t)(par ^ 1) * nb + m0) * nbins;
+  for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) hz[i] = 0;
+  __syncthreads();
+  if (warp == 0 && lane < nbt) {
+    const double inv_n = R->inv_n[m0 + lane];
+    const double s0 = s_sum[0][lane], s1 = s_sum[1][lane], s2 = s_sum[2][lane], s3 = s_sum[3][lane];
+    const double s4 = s_sum[4][lane];
+    const double mt = s0 * inv_n, md = s2 * inv_n;
+    const double vt = fmax(fma(s1, inv_n, -mt * mt), 0.0);
+    const double vd = fmax(fma(s3, inv_n, -md * md), 0.0);
+    double *rec = R->rec + ((size_t)(turn % R->cap) * nb + m0 + lane) * kRecord;
+    rec[0] = mt;
+    rec[1] = sqrt(vt);
+    rec[2] = md;
+    rec[3] = sqrt(vd);
+    rec[4] = (double)p.bunches[R->bunch_base + m0 + lane].n - s4;
+    rec[5] = s4;
+  }
+}
+
+// Long-range emission and the tile's affine scan, per long-range resonator.
+// Emission sums sum_k count[m,k] e^{-s tau_k}: 8 threads per bunch, all 32
+// bunches of the tile at once.
+template <int PREC>
+__device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, double2 *sE,
+                         float2 *sEf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = R->nb, nbins = R->nbins;
   const int m0 = job.bt * kBunchTile;
   const int nbt = min(kBunchTile, nb - m0);
-
-  // moments of the turn (FP64 sums of the push tiles' partials, fixed order)
-  const size_t slot = (size_t)(turn % R->cap);
-  for (int b = warp; b < nbt; b += nwarps) {
-    const BunchDev bd = p.bunches[R->bunch_base + m0 + b];
-    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int i = lane; i < bd.ntiles; i += 32) {
-      const double *pp = p.partial + (size_t)(bd.tile0 + i) * kPartials;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) s[c] += pp[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) s[c] = warp_sum_d(s[c]);
-    if (lane == 0) {
-      const double n = (double)bd.n;
-      const double mt = bd.n > 0 ? s[0] / n : 0.0, md = bd.n > 0 ? s[2] / n : 0.0;
-      const double vt = bd.n > 0 ? fmax(s[1] / n - mt * mt, 0.0) : 0.0;
-      const double vd = bd.n > 0 ? fmax(s[3] / n - md * md, 0.0) : 0.0;
-      double *rec = R->rec + (slot * nb + m0 + b) * kRecord;
-      rec[0] = mt;
-      rec[1] = sqrt(vt);
-      rec[2] = md;
-      rec[3] = sqrt(vd);
-      rec[4] = n - s[4];
-      rec[5] = s[4];
-    }
-  }
-  // the other histogram buffer is filled by the next turn's push
-  int32_t *hz = R->hist + ((size_t)(par ^ 1) * nb + m0) * nbins;
-  for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) hz[i] = 0;
-
   const int32_t *hcur = R->hist + ((size_t)par * nb + m0) * nbins;
+  const int b = threadIdx.x >> 3, sub = threadIdx.x & 7;   // kPostThreads / 8 == kBunchTile
   for (int r = 0; r < R->nlong; ++r) {
-    const double2 cr = R->lr_c[r];
-    for (int b = warp; b < nbt; b += nwarps) {
-      const int32_t *hrow = hcur + (size_t)b * nbins;
-      double2 E;
-      if (PREC == kMixed) {
+    if (PREC == kMixed) {
+      float ax = 0.f, ay = 0.f;
+      if (b < nbt) {
+        const int32_t *hrow = hcur + (size_t)b * nbins;
         const float2 *tab = R->emis_f + (size_t)r * nbins;
-        float ax = 0.f, ay = 0.f;
-        for (int k = lane; k < nbins; k += 32) {
-          const float c = (float)hrow[k];
-          ax = fmaf(c, tab[k].x, ax);
-          ay = fmaf(c, tab[k].y, ay);
+#pragma unroll 8
+        for (int k = sub; k < nbins; k += 8) {
+          const float cnt = (float)hrow[k];
+          const float2 e = tab[k];
+          ax = fmaf(cnt, e.x, ax);
+          ay = fmaf(cnt, e.y, ay);
         }
-        E = make_double2((double)warp_sum_f(ax), (double)warp_sum_f(ay));
-      } else {
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xFFFFFFFFu, ax, o);
+        ay += __shfl_xor_sync(0xFFFFFFFFu, ay, o);
+      }
+      if (sub == 0 && b < nbt) sEf[b] = make_float2(ax, ay);
+    } else {
+      double ax = 0.0, ay = 0.0;
+      if (b < nbt) {
+        const int32_t *hrow = hcur + (size_t)b * nbins;
         const double2 *tab = R->emis + (size_t)r * nbins;
-        double ax = 0.0, ay = 0.0;
-        for (int k = lane; k < nbins; k += 32) {
-          const double c = (double)hrow[k];
-          ax = fma(c, tab[k].x, ax);
-          ay = fma(c, tab[k].y, ay);
+        for (int k = sub; k < nbins; k += 8) {
+          const double cnt = (double)hrow[k];
+          ax = fma(cnt, tab[k].x, ax);
+          ay = fma(cnt, tab[k].y, ay);
         }
-        E = make_double2(warp_sum_d(ax), warp_sum_d(ay));
       }
-      if (lane == 0) {
-        const double q = R->q_mp[m0 + b];
-        sE[b] = cmul(cr, make_double2(q * E.x, q * E.y));
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xFFFFFFFFu, ax, o);
+        ay += __shfl_xor_sync(0xFFFFFFFFu, ay, o);
       }
+      if (sub == 0 && b < nbt) sE[b] = make_double2(ax, ay);
     }
     __syncthreads();
     if (warp == 0) {
-      // lane b: map of bunch m0+b; bunch m0 maps the tile's entering value
+      // E_m = c q_m sum (lane-parallel), then the affine scan across the tile:
+      // lane b holds x -> a_m (x + E_{m-1}); bunch m0 maps the tile's entering value
       const int m = m0 + lane;
+      double2 E = make_double2(0.0, 0.0);
+      if (lane < nbt) {
+        const double2 sum = PREC == kMixed ? make_double2((double)sEf[lane].x, (double)sEf[lane].y) : sE[lane];
+        const double q = R->q_mp[m];
+        E = cmul(R->lr_c[r], make_double2(q * sum.x, q * sum.y));
+      }
+      const double2 Eprev = shfl_up_d2(E, 1);
       double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
       if (lane < nbt) {
         A = R->step[(size_t)r * nb + m];
-        if (lane > 0) B = cmul(A, sE[lane - 1]);
+        if (lane > 0) B = cmul(A, Eprev);
       }
       warp_scan_affine(A, B);
       if (lane < nbt) {
@@ -116,7 +152,7 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
       }
       if (lane == nbt - 1) {
         R->agg[((size_t)r * R->ntile_b + job.bt) * 2] = A;
-        R->agg[((size_t)r * R->ntile_b + job.bt) * 2 + 1] = cadd(B, sE[lane]);
+        R->agg[((size_t)r * R->ntile_b + job.bt) * 2 + 1] = cadd(B, E);
       }
     }
     __syncthreads();
@@ -176,41 +212,60 @@ __device__ void finish_turn(const Plan &p) {
 constexpr int kWakeN = 3 * kBunchTile;   // 96
 constexpr uint32_t kTmemCols = 256;      // power of two >= kWakeN, with headroom
 
-__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par,
-                            uint8_t *smem, uint64_t *bars, uint32_t *tmem_slot, int *s_flag) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nbins = R->nbins;
-  const int nb = R->nb;
-  const int mt = job.sub;
-  const int m0 = job.bt * kBunchTile;
-  const int nbt = min(kBunchTile, nb - m0);
-  const uint32_t a_bytes = (uint32_t)nbins * 512u;   // 128 rows x 2 nbins x 2 B
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + a_bytes;
-  const uint32_t lboA = 16u * 128u;                   // next 8-column K group: 16 row groups later
-  const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
+// Operand A of M-tile mt: rows [128 mt, 128 mt + 128) of the lower triangular
+// Toeplitz matrix only involve columns k < Kmt = 128 (mt + 1), so the image
+// holds [T_hi | T_lo] over 2 Kmt columns: 512 Kmt bytes at offset 512 * 128
+// * mt (mt + 1) (the images of the earlier M-tiles).
+__device__ __forceinline__ int wake_kmt(int mt, int nbins) { return min(nbins, 128 * (mt + 1)); }
+__device__ __forceinline__ size_t wake_img_offset(int mt) { return (size_t)512 * 128 * mt * (mt + 1) / 2; }
 
+// Prologue: barriers, tensor memory, and the bulk copy of the constant A
+// image; safe to run before the push kernel of the turn has completed.
+__device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, uint8_t *smem, uint64_t *bars,
+                              uint32_t *tmem_slot, int *s_flag) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int mt = job.sub;
+  const int kmt = wake_kmt(mt, R->nbins);
+  const uint32_t a_bytes = (uint32_t)kmt * 512u;
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_mbar_init();
     *s_flag = 0;
+    const uint8_t *src = static_cast<const uint8_t *>(R->toep) + wake_img_offset(mt);
+    mbar_arrive_expect_tx(&bars[0], a_bytes);
+    for (uint32_t off = 0; off < a_bytes; off += 32768u)
+      bulk_g2s(smem + off, src + off, min(32768u, a_bytes - off), &bars[0]);
   }
   if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+}
+
+// Main part: B from the turn's counts, the MMAs (issued by one thread, run
+// asynchronously), the moments of the bunch tile while they run (M-tile 0),
+// then the epilogue from tensor memory.
+__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, long long turn,
+                            uint8_t *smem, uint64_t *bars, uint32_t *tmem_slot, int *s_flag,
+                            double (*s_sum)[kBunchTile]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbins = R->nbins;
+  const int nb = R->nb;
+  const int mt = job.sub;
+  const int kmt = wake_kmt(mt, nbins);
+  const int m0 = job.bt * kBunchTile;
+  const int nbt = min(kBunchTile, nb - m0);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + (size_t)nbins * 512u;   // after the largest A image
+  const uint32_t lboA = 16u * 128u;           // next 8-column K group: 16 row groups later
+  const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
   const uint32_t tmem = *tmem_slot;
 
-  if (tid == 0) {
-    const uint8_t *src = static_cast<const uint8_t *>(R->toep) + (size_t)mt * a_bytes;
-    mbar_arrive_expect_tx(&bars[0], a_bytes);
-    for (uint32_t off = 0; off < a_bytes; off += 32768u)
-      bulk_g2s(sA + off, src + off, min(32768u, a_bytes - off), &bars[0]);
-  }
   // B: counts of the 32 bunches split into three exact BF16 byte planes
   const int32_t *hg = R->hist + ((size_t)par * nb + m0) * nbins;
-  const int KG = nbins / 8;
+  const int KG = kmt / 8;
+#pragma unroll 4
   for (int idx = tid; idx < kBunchTile * KG; idx += kPostThreads) {
     const int b = idx % kBunchTile, kg = idx / kBunchTile;
     int c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -246,7 +301,7 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       tc_fence_after();
       const uint32_t idesc = idesc_bf16_f32(128, kWakeN);
       const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
-      const int ks_half = nbins / 16;
+      const int ks_half = kmt / 16;
       for (int ks = 0; ks < 2 * ks_half; ++ks) {
         const uint64_t ad = smem_desc_kmajor(a0 + (uint32_t)ks * 2u * lboA, lboA, 128u);
         const uint64_t bd = smem_desc_kmajor(b0 + (uint32_t)(ks % ks_half) * 2u * lboB, lboB, 128u);
@@ -255,6 +310,7 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       umma_commit(&bars[1]);
     }
   }
+  if (mt == 0) moments_job(p, R, m0, nbt, par, turn, s_sum);   // overlaps the MMAs
   __syncthreads();
   const bool aborted = *s_flag != 0;
   if (!aborted && warp < 4) {
@@ -272,7 +328,7 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
 #pragma unroll
       for (int b = 0; b < kBunchTile; ++b) {
         if (b < nbt) {
-          const float q = (float)R->q_mp[m0 + b];
+          const float q = R->q_mp_f[m0 + b];
           vsr[(size_t)(m0 + b) * nbins + j] = q * fmaf(65536.f, d2[b], fmaf(256.f, d1[b], d0[b]));
         }
       }
@@ -287,19 +343,31 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
   }
 }
 
+__device__ __forceinline__ void trace_mark(const Plan &p, int slot) {
+  if (p.trace != nullptr && threadIdx.x == 0) p.trace[(size_t)blockIdx.x * 3 + slot] = global_timer_ns();
+}
+
 __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   extern __shared__ __align__(1024) uint8_t sm_post[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_flag;
   __shared__ double2 sE[kBunchTile];
+  __shared__ float2 sEf[kBunchTile];
+  __shared__ double s_sum[5][kBunchTile];
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
+  trace_mark(p, 0);
+  if (job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);
+  grid_dependency_wait();     // the push of this turn has completed
+  grid_dependents_launch();   // the next push may start its prologue (particle prefetch)
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
-  if (job.type == kJobWake) wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag);
-  else tile_job<kMixed>(p, R, job, par, turn, sE);
+  if (job.type == kJobWake) wake_job_tc(p, R, job, par, turn, sm_post, bars, &tmem_slot, &s_flag, s_sum);
+  else tile_job<kMixed>(p, R, job, par, sE, sEf);
+  trace_mark(p, 1);
   finish_turn(p);
+  trace_mark(p, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,13 +399,26 @@ __device__ void wake_job_f64(const RunDev *__restrict__ R, const PostJob &job, i
 __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
   extern __shared__ __align__(16) uint8_t sm_post64[];
   __shared__ double2 sE[kBunchTile];
+  __shared__ float2 sEf[kBunchTile];
+  __shared__ double s_sum[5][kBunchTile];
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
+  trace_mark(p, 0);
+  grid_dependency_wait();
+  grid_dependents_launch();
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
-  if (job.type == kJobWake) wake_job_f64(R, job, par, sm_post64);
-  else tile_job<kF64>(p, R, job, par, turn, sE);
+  if (job.type == kJobWake) {
+    wake_job_f64(R, job, par, sm_post64);
+  } else {
+    const int m0 = job.bt * kBunchTile;
+    moments_job(p, R, m0, min(kBunchTile, R->nb - m0), par, turn, s_sum);
+    __syncthreads();
+    tile_job<kF64>(p, R, job, par, sE, sEf);
+  }
+  trace_mark(p, 1);
   finish_turn(p);
+  trace_mark(p, 2);
 }
 
 size_t post_smem_bytes(int precision, int max_nbins) {
@@ -353,12 +434,20 @@ cudaError_t configure_kernels() {
                               (int)post_smem_bytes(kMixed, 256));
 }
 
-cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s) {
+cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s, bool pdl) {
   if (p.njobs == 0) return cudaSuccess;
-  const size_t smem = post_smem_bytes(precision, p.max_nbins);
-  if (precision == kMixed) k_post_mixed<<<p.njobs, kPostThreads, smem, s>>>(p);
-  else k_post_f64<<<p.njobs, kPostThreads, smem, s>>>(p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)p.njobs);
+  cfg.blockDim = dim3((unsigned)kPostThreads);
+  cfg.dynamicSmemBytes = post_smem_bytes(precision, p.max_nbins);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if (precision == kMixed) return cudaLaunchKernelEx(&cfg, k_post_mixed, p);
+  return cudaLaunchKernelEx(&cfg, k_post_f64, p);
 }
 
 }  // namespace mbt

@@ -13,32 +13,155 @@
 namespace mbt {
 
 // ---------------------------------------------------------------------------
-// Mixed precision: tau in FP32, delta stored and accumulated in FP64,
-// everything else in FP32.  Each thread handles quads of 4 consecutive
-// particles (float4 / 2x double2 accesses), two Philox calls per quad.
+// Mixed precision: tau in FP32, delta stored and accumulated in FP64 (one
+// DFMA per particle), everything else in FP32 on the FMA / MUFU pipes.  Each
+// thread handles quads of 4 consecutive particles, one Philox block per
+// quad.  NLONG_MAX bounds the number of long-range resonators of any run in
+// the plan.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPushThreads, 4) k_push_mixed(const Plan p) {
-  extern __shared__ __align__(16) float sm_push[];
+struct PushConstF {
+  float invD, HinvD, fnb, invE0, twoVoE0, cphi, sphi, halfw, omD, qe, aT0;
+  int nbins;
+};
+
+// One particle: kick with the previous turn's wake, RF, damping + excitation,
+// drift.  Returns the new tau; delta is updated in place.
+template <int NLONG_MAX, bool NGP>
+__device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd, int nlong,
+                                          const float *la, const float *lw, const float2 *phi, double omD_d,
+                                          float t0, double &d, float r, float &df) {
+  const float x = fmaf(t0, c.invD, c.HinvD);
+  float v;
+  if (NGP) {
+    const int k = min(max((int)x, 0), c.nbins - 1);
+    v = sVd[k].x;
+  } else {
+    // linear interpolation between cell centres, clamped to the end cells
+    const float u = fminf(fmaxf(x - 0.5f, 0.f), c.fnb - 1.f);
+    const int j = min((int)u, c.nbins - 2);
+    const float2 vd = sVd[j];
+    v = fmaf(u - (float)j, vd.y, vd.x);
+  }
+  v = (x >= 0.f && x < c.fnb) ? v : 0.f;
+#pragma unroll
+  for (int r2 = 0; r2 < NLONG_MAX; ++r2) {
+    if (r2 < nlong) {
+      float sn, cs;
+      __sincosf(lw[r2] * t0, &sn, &cs);
+      const float ea = __expf(-la[r2] * t0);
+      v = fmaf(ea, fmaf(phi[r2].x, cs, -phi[r2].y * sn), v);
+    }
+  }
+  // (V/E0)[sin(phi_s - w t) - sin(phi_s)] = -2 (V/E0) sin(w t / 2) cos(phi_s - w t / 2)
+  float sh, ch;
+  __sincosf(c.halfw * t0, &sh, &ch);
+  // c.twoVoE0 and c.invE0 carry the damping factor (1 - D) already
+  const float rf = -c.twoVoE0 * sh * fmaf(ch, c.cphi, sh * c.sphi);
+  const float inc = fmaf(-v, c.invE0, fmaf(c.qe, r, rf));
+  d = fma(d, omD_d, f32_to_f64_bits(inc));
+  df = f64_to_f32_trunc(d);
+  return fmaf(c.aT0, df, t0);
+}
+
+// The particle stream of a tile is staged through shared memory by the TMA
+// bulk-copy engine: chunks of kChunk particles (tau 4 KB + delta 8 KB) in a
+// kStages-deep ring, refilled by one thread as soon as the CTA has consumed a
+// stage, so the bytes in flight do not depend on registers or occupancy.
+// Thread t handles the quad of particles 4t .. 4t+3 of each chunk (one
+// Philox block, two Box-Muller pairs); results are stored straight to global
+// memory with 16-byte stores.
+// 2 stages x 12 KB with 6 CTAs (40 registers) per SM measured fastest on
+// GB300 among {4, 5, 6, 8} CTAs x {2, 3} stages for the 390-bunch fill
+#ifndef MBT_PUSH_STAGES
+#define MBT_PUSH_STAGES 2
+#endif
+#ifndef MBT_PUSH_MIN_BLOCKS
+#define MBT_PUSH_MIN_BLOCKS 6
+#endif
+constexpr int kChunk = 1024;
+constexpr int kStages = MBT_PUSH_STAGES;
+constexpr int kStageBytes = kChunk * (int)(sizeof(float) + sizeof(double));
+constexpr unsigned long long kPushWaitNs = 2000000000ull;
+
+__device__ __forceinline__ void issue_chunk(const TileDev &t, const float *tau, const double *del, uint8_t *stage,
+                                            uint64_t *bar, int c) {
+  const int n = min(kChunk, t.count - c * kChunk);
+  const int n4 = (n + 3) & ~3;   // segments are padded to 4 particles: 16-byte multiples
+  const uint32_t tb = (uint32_t)n4 * 4u, db = (uint32_t)n4 * 8u;
+  mbar_arrive_expect_tx(bar, tb + db);
+  bulk_g2s(stage, tau + (size_t)c * kChunk, tb, bar);
+  bulk_g2s(stage + kChunk * sizeof(float), del + (size_t)c * kChunk, db, bar);
+}
+
+// Four consecutive particles: push, deposit, moment partials.  Full quads
+// (nvalid == 4, all but a bunch's last) take no per-particle validity tests.
+template <int NLONG_MAX, bool NGP>
+__device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd, int *sH, int nlong, const float *la,
+                                          const float *lw, const float2 *phi, double omD_d, float (&tt)[4],
+                                          double (&dd)[4], const float (&rr)[4], int nvalid, float &st, float &st2,
+                                          float &sd, float &sd2, int &nout) {
+  const bool full = nvalid == 4;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (full || e < nvalid) {
+      float df;
+      const float t1 = push_one<NLONG_MAX, NGP>(c, sVd, nlong, la, lw, phi, omD_d, tt[e], dd[e], rr[e], df);
+      tt[e] = t1;
+      const float xb = fmaf(t1, c.invD, c.HinvD);
+      if (xb >= 0.f && xb < c.fnb) atomicAdd(&sH[(int)xb], 1);
+      else ++nout;
+      st += t1;
+      st2 = fmaf(t1, t1, st2);
+      sd += df;
+      sd2 = fmaf(df, df, sd2);
+    }
+  }
+}
+
+template <int NLONG_MAX>
+__global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixed(const Plan p) {
+  extern __shared__ __align__(128) uint8_t sm_push[];
   __shared__ float s_red[kPushThreads / 32][5];
   __shared__ float2 s_phi[kMaxLong];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int s_abort;
 
+  // Prologue that reads only the plan and the particle state: with
+  // programmatic dependent launch it overlaps the previous post kernel, which
+  // signals its dependents only after the previous push has completed.
   const TileDev t = p.tiles[blockIdx.x];
   const RunDev *__restrict__ R = p.runs + t.run;
   const BunchDev bd = p.bunches[t.bunch];
-  const int nbins = R->nbins;
+  PushConstF c;
+  c.nbins = R->nbins;
+  const int nbins = c.nbins;
   const int nlong = R->nlong;
-  float *sV = sm_push;
-  int *sH = reinterpret_cast<int *>(sm_push + nbins);
+  uint8_t *stages = sm_push;
+  float2 *sVd = reinterpret_cast<float2 *>(sm_push + kStages * kStageBytes);   // (V[j], V[j+1] - V[j])
+  int *sH = reinterpret_cast<int *>(sVd + nbins);
+  float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
+  double *del = R->delta + bd.off + t.start;
+  const int nchunks = (t.count + kChunk - 1) / kChunk;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&full[st], 1);
+    fence_mbar_init();
+    s_abort = 0;
+    for (int ch = 0; ch < min(kStages, nchunks); ++ch) issue_chunk(t, tau, del, stages + ch * kStageBytes, &full[ch], ch);
+  }
+  grid_dependents_launch();
+  grid_dependency_wait();   // the previous post kernel's wake, phasors and turn counter are complete
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
-
   const float *vsr = static_cast<const float *>(R->vsr) + (size_t)t.m * nbins;
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
-    sV[k] = vsr[k];
+    const float v0 = vsr[k];
+    const float v1 = k + 1 < nbins ? vsr[k + 1] : v0;
+    sVd[k] = make_float2(v0, v1 - v0);
     sH[k] = 0;
   }
   if (threadIdx.x < nlong) {
-    // Phi_m = P_m y_tile + Q_m of this bunch, then narrowed to FP32
+    // Phi_m = P_m y_tile + Q_m of this bunch, narrowed to FP32
     const int r = threadIdx.x;
     const double2 P = R->pq[((size_t)r * R->nb + t.m) * 2];
     const double2 Q = R->pq[((size_t)r * R->nb + t.m) * 2 + 1];
@@ -46,105 +169,69 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_push_mixed(const Plan p) {
     const double2 phi = cfma(P, y, Q);
     s_phi[r] = make_float2((float)phi.x, (float)phi.y);
   }
-  __syncthreads();
-
-  const float invDf = (float)R->invDelta;
-  const float HinvDf = (float)(R->H * R->invDelta);
-  const float fnb = (float)nbins;
-  const float invE0 = (float)R->inv_E0;
-  const float twoVoE0 = (float)(2.0 * R->V_over_E0);
-  const float cphi = (float)R->cos_phi_s, sphi = (float)R->sin_phi_s;
-  const float halfw = (float)(0.5 * R->omega_rf);
-  const float omD = (float)R->one_minus_D;
+  c.invD = R->f_invD;
+  c.HinvD = R->f_HinvD;
+  c.fnb = R->f_nbins;
+  c.invE0 = R->f_invE0 * R->f_omD;
+  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
+  c.cphi = R->f_cphi;
+  c.sphi = R->f_sphi;
+  c.halfw = R->f_halfw;
+  c.omD = R->f_omD;
+  c.qe = R->f_qe;
+  c.aT0 = R->f_aT0;
   const double omD_d = R->one_minus_D;
-  const float qe = (float)R->qe_amp;
-  const float aT0 = (float)R->aT0;
   const bool ngp = (R->flags & kKickNGP) != 0;
-  float la[kMaxLong], lw[kMaxLong];
+  float la[NLONG_MAX > 0 ? NLONG_MAX : 1], lw[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  float2 phi[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kMaxLong; ++r) {
-    la[r] = r < nlong ? (float)(-R->lr_s[r].x) : 0.f;
-    lw[r] = r < nlong ? (float)R->lr_s[r].y : 0.f;
+  for (int r = 0; r < NLONG_MAX; ++r) {
+    la[r] = R->f_la[r];
+    lw[r] = R->f_lw[r];
+    phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
   }
   const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
 
-  float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
-  double *del = R->delta + bd.off + t.start;
   float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;
   int nout = 0;
 
 #pragma unroll 1
-  for (int it = 0; it < kMixedQuadsPerThread; ++it) {
-    const int q = (it * kPushThreads + (int)threadIdx.x) * 4;
-    if (q >= t.count) break;
-    const float4 tv = *reinterpret_cast<const float4 *>(tau + q);
-    const double2 da = *reinterpret_cast<const double2 *>(del + q);
-    const double2 db = *reinterpret_cast<const double2 *>(del + q + 2);
-    float rr[4] = {0.f, 0.f, 0.f, 0.f};
-    if (qe != 0.f) {
-      const uint32_t pair0 = (uint32_t)((t.start + q) >> 1);
-      normal_pair_f32(philox4x32_10(pair0, bunch32, turn32, 0u, k0, k1), rr[0], rr[1]);
-      normal_pair_f32(philox4x32_10(pair0 + 1u, bunch32, turn32, 0u, k0, k1), rr[2], rr[3]);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int slot = ch % kStages;
+    uint8_t *sg = stages + slot * kStageBytes;
+    if (!mbar_wait_bounded(&full[slot], (uint32_t)((ch / kStages) & 1), kPushWaitNs)) {
+      atomicExch(p.error, kErrTimeout);
+      s_abort = 1;
     }
-    float tt[4] = {tv.x, tv.y, tv.z, tv.w};
-    double dd[4] = {da.x, da.y, db.x, db.y};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float t0 = tt[e];
-      // wake kick (previous turn's wake)
-      const float x = fmaf(t0, invDf, HinvDf);
-      float v = 0.f;
-      if (x >= 0.f && x < fnb) {
-        if (ngp) {
-          v = sV[(int)x];
-        } else {
-          const float u = x - 0.5f;
-          if (u <= 0.f) v = sV[0];
-          else if (u >= fnb - 1.f) v = sV[nbins - 1];
-          else {
-            const int j = (int)u;
-            const float f = u - (float)j;
-            v = fmaf(f, sV[j + 1] - sV[j], sV[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < kMaxLong; ++r) {
-        if (r < nlong) {
-          float sn, cs;
-          __sincosf(lw[r] * t0, &sn, &cs);
-          const float ea = __expf(-la[r] * t0);
-          v = fmaf(ea, s_phi[r].x * cs - s_phi[r].y * sn, v);
-        }
-      }
-      // RF gain minus U0: (V/E0)[sin(phi_s - w t) - sin(phi_s)] = -2 (V/E0) sin(w t / 2) cos(phi_s - w t / 2)
-      float sh, ch;
-      sincosf(halfw * t0, &sh, &ch);
-      const float rf = -twoVoE0 * sh * fmaf(ch, cphi, sh * sphi);
-      // damping + excitation applied to (delta + kick + rf); delta itself in FP64
-      const float inc = fmaf(fmaf(-v, invE0, rf), omD, qe * rr[e]);
-      const double d1 = fma(dd[e], omD_d, f32_to_f64_bits(inc));
-      const float d1f = f64_to_f32_trunc(d1);
-      const float t1 = fmaf(aT0, d1f, t0);
-      const bool valid = q + e < t.count;
-      tt[e] = valid ? t1 : t0;
-      dd[e] = valid ? d1 : dd[e];
-      if (valid) {
-        const float xb = fmaf(t1, invDf, HinvDf);
-        if (xb >= 0.f && xb < fnb) atomicAdd(&sH[(int)xb], 1);
-        else ++nout;
-        st += t1;
-        st2 = fmaf(t1, t1, st2);
-        sd += d1f;
-        sd2 = fmaf(d1f, d1f, sd2);
-      }
+    const int q = ch * kChunk + 4 * (int)threadIdx.x;   // first particle of this thread's quad in the tile
+    if (!s_abort && q < t.count) {
+      const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
+      const double2 da = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x];
+      const double2 db = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x + 1];
+      float rr[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c.qe != 0.f) normal_quad_f32(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
+      float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+      double dd[4] = {da.x, da.y, db.x, db.y};
+      const int nvalid = min(4, t.count - q);
+      if (ngp) quad_push<NLONG_MAX, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, tt, dd, rr, nvalid, st, st2, sd, sd2, nout);
+      else quad_push<NLONG_MAX, false>(c, sVd, sH, nlong, la, lw, phi, omD_d, tt, dd, rr, nvalid, st, st2, sd, sd2, nout);
+      *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+      *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
+      *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
     }
-    *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
-    *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
-    *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+    __syncthreads();   // stage `slot` consumed by every thread
+    if (threadIdx.x == 0 && !s_abort && ch + kStages < nchunks) {
+      fence_proxy_async_smem();   // order the generic-proxy reads of the stage before its refill
+      issue_chunk(t, tau, del, sg, &full[slot], ch + kStages);
+    }
+  }
+  if (s_abort && threadIdx.x == 0) {
+    // let the copies still in flight land before the CTA exits
+    for (int ch = 0; ch < nchunks; ++ch) mbar_wait_bounded(&full[ch % kStages], (uint32_t)((ch / kStages) & 1), kPushWaitNs);
   }
 
-  // moment partials: FP32 within a warp, FP64 across warps
+  // moment partials: FP32 within a warp, FP64 across the CTA's warps
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   st = warp_sum_f(st);
   st2 = warp_sum_f(st2);
@@ -167,14 +254,14 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_push_mixed(const Plan p) {
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
-    const int c = sH[k];
-    if (c) atomicAdd(hg + k, c);
+    const int cnt = sH[k];
+    if (cnt) atomicAdd(hg + k, cnt);
   }
 }
 
 // ---------------------------------------------------------------------------
-// FP64: the oracle's arithmetic step for step.  Each thread handles pairs of
-// consecutive particles (one Philox call per pair).  The cell index is formed
+// FP64: the oracle's arithmetic step for step.  Each thread handles quads of
+// consecutive particles (one Philox block per quad).  The cell index is formed
 // with explicitly rounded operations so it cannot be contracted into an FMA.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double vsr_at_f64(const double *sV, double x, int nbins, bool ngp) {
@@ -199,6 +286,8 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   const BunchDev bd = p.bunches[t.bunch];
   const int nbins = R->nbins;
   const int nlong = R->nlong;
+  grid_dependents_launch();
+  grid_dependency_wait();
   double *sV = sm_push64;
   int *sH = reinterpret_cast<int *>(sm_push64 + nbins);
   const long long turn = *R->turn;
@@ -230,18 +319,22 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   int nout = 0;
 
 #pragma unroll 1
-  for (int it = 0; it < kF64PairsPerThread; ++it) {
-    const int q = (it * kPushThreads + (int)threadIdx.x) * 2;
+  for (int it = 0; it < kF64QuadsPerThread; ++it) {
+    const int q = (it * kPushThreads + (int)threadIdx.x) * 4;
     if (q >= t.count) break;
-    const double2 tv = *reinterpret_cast<const double2 *>(tau + q);
-    const double2 dv = *reinterpret_cast<const double2 *>(del + q);
-    double rr[2] = {0.0, 0.0};
-    if (qe != 0.0)
-      normal_pair_f64(philox4x32_10((uint32_t)((t.start + q) >> 1), bunch32, turn32, 0u, k0, k1), rr[0], rr[1]);
-    double tt[2] = {tv.x, tv.y};
-    double dd[2] = {dv.x, dv.y};
+    double tt[4], dd[4];
+    {
+      const double2 t0 = *reinterpret_cast<const double2 *>(tau + q);
+      const double2 t1 = *reinterpret_cast<const double2 *>(tau + q + 2);
+      const double2 d0 = *reinterpret_cast<const double2 *>(del + q);
+      const double2 d1 = *reinterpret_cast<const double2 *>(del + q + 2);
+      tt[0] = t0.x; tt[1] = t0.y; tt[2] = t1.x; tt[3] = t1.y;
+      dd[0] = d0.x; dd[1] = d0.y; dd[2] = d1.x; dd[3] = d1.y;
+    }
+    double rr[4] = {0.0, 0.0, 0.0, 0.0};
+    if (qe != 0.0) normal_quad_f64(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int e = 0; e < 4; ++e) {
       if (q + e >= t.count) continue;
       double tp = tt[e], d = dd[e];
       double v = vsr_at_f64(sV, __dmul_rn(__dadd_rn(tp, H), invD), nbins, ngp);
@@ -267,7 +360,9 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
       sd2 += d * d;
     }
     *reinterpret_cast<double2 *>(tau + q) = make_double2(tt[0], tt[1]);
+    *reinterpret_cast<double2 *>(tau + q + 2) = make_double2(tt[2], tt[3]);
     *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
+    *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
   }
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -300,48 +395,68 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
 // Matched Gaussian start from Philox tags 1 (tau) and 2 (delta) at turn 0, in
 // FP64 for both precisions (tau narrowed to FP32 by rounding for kMixed).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPushThreads) k_init(const Plan p, int precision, int tile_size) {
+__global__ void __launch_bounds__(kPushThreads) k_init(const Plan p, int precision) {
   const TileDev t = p.tiles[blockIdx.x];
   const RunDev *__restrict__ R = p.runs + t.run;
   const BunchDev bd = p.bunches[t.bunch];
-  for (int q = 2 * (int)threadIdx.x; q < t.count; q += 2 * kPushThreads) {
-    const uint32_t pair = (uint32_t)((t.start + q) >> 1);
-    double a0, a1, b0, b1;
-    normal_pair_f64(philox4x32_10(pair, (uint32_t)t.m, 0u, 1u, R->key0, R->key1), a0, a1);
-    normal_pair_f64(philox4x32_10(pair, (uint32_t)t.m, 0u, 2u, R->key0, R->key1), b0, b1);
+  for (int q = 4 * (int)threadIdx.x; q < t.count; q += 4 * kPushThreads) {
+    const uint32_t quad = (uint32_t)((t.start + q) >> 2);
+    double a[4], b[4];
+    normal_quad_f64(philox4x32_10(quad, (uint32_t)t.m, 0u, 1u, R->key0, R->key1), a);
+    normal_quad_f64(philox4x32_10(quad, (uint32_t)t.m, 0u, 2u, R->key0, R->key1), b);
     const long long i = bd.off + t.start + q;
-    const bool two = q + 1 < t.count;
-    if (precision == kMixed) {
-      float *tau = static_cast<float *>(R->tau);
-      tau[i] = (float)(R->sigma_tau0 * a0);
-      if (two) tau[i + 1] = (float)(R->sigma_tau0 * a1);
-    } else {
-      double *tau = static_cast<double *>(R->tau);
-      tau[i] = R->sigma_tau0 * a0;
-      if (two) tau[i + 1] = R->sigma_tau0 * a1;
+    const int nv = min(4, t.count - q);
+    for (int e = 0; e < nv; ++e) {
+      if (precision == kMixed) static_cast<float *>(R->tau)[i + e] = (float)(R->sigma_tau0 * a[e]);
+      else static_cast<double *>(R->tau)[i + e] = R->sigma_tau0 * a[e];
+      R->delta[i + e] = R->sigma_E * b[e];
     }
-    R->delta[i] = R->sigma_E * b0;
-    if (two) R->delta[i + 1] = R->sigma_E * b1;
   }
-  (void)tile_size;
 }
 
-cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s) {
+template <typename... Args>
+static cudaError_t launch_ex(void (*kern)(Args...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                             Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) {
   if (p.ntiles == 0) return cudaSuccess;
   const int max_nbins = p.max_nbins;
   if (precision == kMixed) {
-    const size_t smem = (size_t)max_nbins * (sizeof(float) + sizeof(int));
-    k_push_mixed<<<p.ntiles, kPushThreads, smem, s>>>(p);
-  } else {
-    const size_t smem = (size_t)max_nbins * (sizeof(double) + sizeof(int));
-    k_push_f64<<<p.ntiles, kPushThreads, smem, s>>>(p);
+    const size_t smem = (size_t)kStages * kStageBytes + (size_t)max_nbins * (sizeof(float2) + sizeof(int));
+    switch (p.max_nlong) {
+      case 0: return launch_ex(k_push_mixed<0>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 1: return launch_ex(k_push_mixed<1>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 2: return launch_ex(k_push_mixed<2>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      default: return launch_ex(k_push_mixed<kMaxLong>, p.ntiles, kPushThreads, smem, s, pdl, p);
+    }
   }
-  return cudaGetLastError();
+  const size_t smem = (size_t)max_nbins * (sizeof(double) + sizeof(int));
+  return launch_ex(k_push_f64, p.ntiles, kPushThreads, smem, s, pdl, p);
+}
+
+cudaError_t configure_push_kernels() {
+  const int bytes = (int)((size_t)kStages * kStageBytes + 1024 * (sizeof(float2) + sizeof(int)));
+  cudaError_t e = cudaSuccess;
+  for (auto k : {k_push_mixed<0>, k_push_mixed<1>, k_push_mixed<2>, k_push_mixed<kMaxLong>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s) {
   if (p.ntiles == 0) return cudaSuccess;
-  k_init<<<p.ntiles, kPushThreads, 0, s>>>(p, precision, 0);
+  k_init<<<p.ntiles, kPushThreads, 0, s>>>(p, precision);
   return cudaGetLastError();
 }
 

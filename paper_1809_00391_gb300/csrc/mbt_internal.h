@@ -16,8 +16,8 @@ constexpr int kMaxBunches = 1024;    // one warp scans the tile aggregates
 constexpr int kPushThreads = 256;
 constexpr int kMixedQuadsPerThread = 8;                                    // 4 particles per quad
 constexpr int kMixedTile = kPushThreads * 4 * kMixedQuadsPerThread;        // 8192 particles
-constexpr int kF64PairsPerThread = 4;                                      // 2 particles per pair
-constexpr int kF64Tile = kPushThreads * 2 * kF64PairsPerThread;            // 2048 particles
+constexpr int kF64QuadsPerThread = 2;                                      // 4 particles per quad
+constexpr int kF64Tile = kPushThreads * 4 * kF64QuadsPerThread;            // 2048 particles
 constexpr int kPartials = 6;         // sum tau, sum tau^2, sum delta, sum delta^2, n_out, pad
 constexpr int kRecord = 6;           // <tau>, rms tau, <delta>, rms delta, n_in, n_out
 constexpr int kPostThreads = 256;
@@ -55,6 +55,12 @@ struct RunDev {
   double sigma_tau0, sigma_E;   // matched start
   double2 lr_s[kMaxLong];   // s = -a + i wb
   double2 lr_c[kMaxLong];   // c = 2 a Rs (1 + i a / wb)
+  // FP32 copies for the mixed-precision push (GB300 issues FP64 and its
+  // conversions at ~1.6 lanes per clock per SM: none of them per thread)
+  float f_invD, f_HinvD, f_nbins, f_invE0, f_twoVoE0, f_cphi, f_sphi, f_halfw, f_omD, f_qe, f_aT0;
+  float f_la[kMaxLong], f_lw[kMaxLong];
+  const float *q_mp_f;      // [nb] macro-particle charge (float)
+  const double *inv_n;      // [nb] 1 / n_mp
 };
 
 struct BunchDev {
@@ -66,7 +72,7 @@ struct BunchDev {
 
 struct TileDev {
   int bunch, run, m, count;   // count <= tile size
-  long long start;            // first particle of the tile within its bunch (even)
+  long long start;            // first particle of the tile within its bunch (multiple of 4)
 };
 
 struct PostJob {
@@ -84,13 +90,18 @@ struct Plan {
   int *error;                 // device error word (DeviceError)
   int nruns, nbunches, ntiles, njobs;
   int max_nbins;              // largest mesh of the plan's runs (shared-memory sizing)
+  int max_nlong;              // most long-range resonators of any run of the plan
+  unsigned long long *trace;  // null, or [njobs][3] post-kernel CTA timestamps (start, job done, exit) [ns]
 };
 
 // Kernel launchers (one translation unit each).
-cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s);
-cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s);
+// pdl: launch with programmatic stream serialisation (the kernel's prologue
+// may overlap the previous kernel of the stream, which must be one of ours)
+cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl);
+cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s, bool pdl);
 cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s);
 size_t post_smem_bytes(int precision, int max_nbins);
 cudaError_t configure_kernels();
+cudaError_t configure_push_kernels();
 
 }  // namespace mbt
