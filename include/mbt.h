@@ -224,6 +224,34 @@ mbt_status mbt_state_size(mbt_ctx *ctx, size_t *bytes);
 mbt_status mbt_save_state(mbt_ctx *ctx, void *buf, size_t bytes);
 mbt_status mbt_load_state(mbt_ctx *ctx, const void *buf, size_t bytes);
 
+/* Short-range wake voltage of nb bunches from their cell counts, computed by
+ * the same tensor-core Toeplitz kernel as mbt_track's post step, WITHOUT
+ * ALLOCATING ANY DEVICE MEMORY.  For callers that cannot call cudaMalloc:
+ * code that runs inside another framework's device memory pool or under a
+ * fixed device-memory budget, where an allocation by a library would fail or
+ * fragment the pool.  (The paper has no counterpart; this is a library
+ * service.)
+ *   ring, flags, half_width_sigmas, nbins: define the mesh as in mbt_set_grid
+ *     (nbins must be 128 or 256);
+ *   nres resonators (Rs_ohm, fr_Hz, Q, range: host arrays; only those with
+ *     the short-range bit contribute), at most 8;
+ *   nb bunches, 1..1024; charge_per_count[nb]: host, coulombs per count;
+ *   hist: DEVICE int32 [nb][nbins] counts (input, caller-owned);
+ *   V: DEVICE float [nb][nbins] voltages [V] (output, caller-owned);
+ *   stream: cudaStream_t as void*; errbuf/errlen: optional message buffer.
+ * Sizes beyond these limits return MBT_ERR_UNSUPPORTED with a message.
+ * Working memory is a 256 KB array in the library's static device memory,
+ * held by every GPU that loads the library until the process exits.  The
+ * first call on a device resolves that array's device address (make it
+ * before any stream capture).  The call is synchronous: it returns when V is
+ * written.  All calls share the array (host calls are serialised by the
+ * library), so calls from another process or kernels that modify hist or V
+ * while it runs race. */
+mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const double *Rs_ohm, const double *fr_Hz,
+                            const double *Q, const int32_t *range, int nbins, double half_width_sigmas, int nb,
+                            const double *charge_per_count, const int32_t *hist, float *V, void *stream,
+                            char *errbuf, size_t errlen);
+
 /* Batched tracking: n contexts with the same precision, each with its fill
  * set, tracked together in the same kernel launches (one push and one post
  * launch per turn for all of them).  The contexts stay owned by the caller

@@ -19,7 +19,7 @@ from ._build import LIB as _LIB_PATH
 from ._build import build
 
 __all__ = ["build", "lib", "Tracker", "Batch", "MBTError", "PREC_F64", "PREC_MIXED", "RANGE_SHORT",
-           "RANGE_LONG", "RANGE_BOTH", "NO_SR", "NO_QE", "KICK_NGP", "EXPORTS", "tracker_for_run"]
+           "RANGE_LONG", "RANGE_BOTH", "NO_SR", "NO_QE", "KICK_NGP", "EXPORTS", "tracker_for_run", "wake_noalloc"]
 
 PREC_F64, PREC_MIXED = 0, 1
 RANGE_SHORT, RANGE_LONG, RANGE_BOTH = 1, 2, 3
@@ -30,7 +30,7 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_add_resonator", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
            "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_timing",
-           "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_batch_create",
+           "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
            "mbt_batch_track", "mbt_batch_sync", "mbt_batch_destroy"]
 
 
@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
                 "mbt_set_trace": ([_vp, _i], _i), "mbt_read_trace": ([_vp, _P(_i64), _i, _P(_i)], _i),
                 "mbt_state_size": ([_vp, _P(_sz)], _i), "mbt_save_state": ([_vp, _vp, _sz], _i),
                 "mbt_load_state": ([_vp, _vp, _sz], _i),
+                "mbt_wake_noalloc": ([_P(Ring), _i, _i, _P(_d), _P(_d), _P(_d), _P(_i32), _i, _d, _i, _P(_d), _vp,
+                                      _vp, _vp, ctypes.c_char_p, _sz], _i),
                 "mbt_batch_create": ([_P(_vp), _i, _P(_vp)], _i), "mbt_batch_track": ([_vp, _i64, _vp], _i),
                 "mbt_batch_sync": ([_vp], _i), "mbt_batch_destroy": ([_vp], None),
             }
@@ -278,6 +280,31 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def make_ring(ring: dict) -> Ring:
+    return Ring(E0_eV=ring["E0_eV"], T0_s=ring["T0_s"], h=int(ring["h"]), reserved=0, V_rf_V=ring["V_rf_V"],
+                alpha_c=ring["alpha_c"], U0_eV=ring["U0_eV"], sigma_delta=ring["sigma_delta"], tau_z_s=ring["tau_z_s"])
+
+
+def wake_noalloc(ring: dict, resonators, nbins: int, half_width_sigmas: float, charge_per_count, hist_ptr: int,
+                 V_ptr: int, flags: int = 0, stream=None) -> None:
+    """Short-range wake of device counts ``hist_ptr`` (int32 [nb][nbins]) into
+    device ``V_ptr`` (float32 [nb][nbins]) through mbt_wake_noalloc, which
+    allocates no device memory."""
+    L = lib()
+    q = np.ascontiguousarray(charge_per_count, np.float64)
+    rs = np.ascontiguousarray([r["Rs_ohm"] for r in resonators] or [0.0], np.float64)
+    fr = np.ascontiguousarray([r["fr_Hz"] for r in resonators] or [0.0], np.float64)
+    qq = np.ascontiguousarray([r["Q"] for r in resonators] or [0.0], np.float64)
+    rg = np.ascontiguousarray([int(r["range"]) for r in resonators] or [0], np.int32)
+    r = make_ring(ring)
+    err = ctypes.create_string_buffer(256)
+    st = L.mbt_wake_noalloc(ctypes.byref(r), int(flags), len(resonators), _ptr(rs, _d), _ptr(fr, _d), _ptr(qq, _d),
+                            _ptr(rg, _i32), int(nbins), float(half_width_sigmas), int(q.size), _ptr(q, _d),
+                            ctypes.c_void_p(int(hist_ptr)), ctypes.c_void_p(int(V_ptr)), _stream(stream), err, 256)
+    if st != 0:
+        raise MBTError(st, err.value.decode())
 
 
 def tracker_for_run(run, precision=None, record_turns: int = 4096) -> Tracker:

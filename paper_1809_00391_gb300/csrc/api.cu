@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1073,6 +1074,88 @@ mbt_status mbt_load_state(mbt_ctx *c, const void *buf, size_t bytes) {
     if (e != cudaSuccess) return cuda_fail(c, e, "load state");
     p += s.bytes;
   }
+  return MBT_OK;
+}
+
+// --------------------------------------------------------------------------- allocation-free wake
+namespace {
+std::mutex g_wna_host_mutex;
+uint16_t g_wna_img[196608 / 2];      // host copy of the operand images (<= 192 KB)
+float g_wna_q[kMaxBunches];
+
+mbt_status wna_fail(char *errbuf, size_t errlen, mbt_status st, const char *fmt, ...) {
+  if (errbuf && errlen) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(errbuf, errlen, fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+}  // namespace
+
+mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const double *Rs_ohm, const double *fr_Hz,
+                            const double *Q, const int32_t *range, int nbins, double half_width_sigmas, int nb,
+                            const double *charge_per_count, const int32_t *hist, float *V, void *stream,
+                            char *errbuf, size_t errlen) {
+  if (errbuf && errlen) errbuf[0] = 0;
+  if (!ring || !charge_per_count || !hist || !V || (nres > 0 && (!Rs_ohm || !fr_Hz || !Q || !range)))
+    return wna_fail(errbuf, errlen, MBT_ERR_ARG, "null argument");
+  if (!(ring->E0_eV > 0) || !(ring->T0_s > 0) || ring->h < 1 || ring->h > 65535 || ring->reserved != 0 ||
+      !(ring->V_rf_V > 0) || !(ring->alpha_c != 0) || !(ring->U0_eV >= 0) || !(ring->U0_eV < ring->V_rf_V) ||
+      !(ring->sigma_delta > 0) || !(ring->tau_z_s > 0))
+    return wna_fail(errbuf, errlen, MBT_ERR_ARG, "invalid ring");
+  if (flags & ~(MBT_NO_SR | MBT_NO_QE | MBT_KICK_NGP)) return wna_fail(errbuf, errlen, MBT_ERR_ARG, "unknown flags");
+  if (nbins != 128 && nbins != 256)
+    return wna_fail(errbuf, errlen, MBT_ERR_UNSUPPORTED, "nbins %d: the allocation-free wake supports 128 or 256 cells",
+                    nbins);
+  if (nb < 1 || nb > kMaxBunches)
+    return wna_fail(errbuf, errlen, MBT_ERR_UNSUPPORTED, "nb %d: the allocation-free wake supports 1..%d bunches", nb,
+                    kMaxBunches);
+  if (nres < 0 || nres > kMaxRes)
+    return wna_fail(errbuf, errlen, MBT_ERR_UNSUPPORTED, "nres %d: at most %d resonators", nres, kMaxRes);
+  if (!(half_width_sigmas > 0)) return wna_fail(errbuf, errlen, MBT_ERR_ARG, "half width must be > 0");
+  for (int i = 0; i < nres; ++i)
+    if (!(Rs_ohm[i] > 0) || !(fr_Hz[i] > 0) || !(Q[i] > 0.5) || range[i] < 1 || range[i] > 3)
+      return wna_fail(errbuf, errlen, MBT_ERR_ARG, "resonator %d needs Rs > 0, fr > 0, Q > 0.5, range 1..3", i);
+
+  std::lock_guard<std::mutex> lk(g_wna_host_mutex);
+  mbt_ctx g;   // grid constants only: no device state
+  g.ring = *ring;
+  g.flags = flags;
+  g.nbins = nbins;
+  g.half_width_sigmas = half_width_sigmas;
+  derive(&g);
+  double lag[256];
+  for (int l = 0; l < nbins; ++l) {
+    lag[l] = 0.0;
+    for (int i = 0; i < nres; ++i)
+      if (range[i] & MBT_RANGE_SHORT) lag[l] += wake(Resonator{Rs_ohm[i], fr_Hz[i], Q[i], range[i]}, (double)l * g.Delta);
+  }
+  size_t base = 0;
+  for (int mt = 0; mt < nbins / 128; ++mt) {
+    const int kmt = std::min(nbins, 128 * (mt + 1));
+    for (int row = 0; row < 128; ++row)
+      for (int k = 0; k < kmt; ++k) {
+        const int j = mt * 128 + row;
+        const double T = j >= k ? lag[j - k] : 0.0;
+        const uint16_t hi = f32_to_bf16_rne((float)T);
+        const uint16_t lo = f32_to_bf16_rne((float)(T - (double)bf16_to_f32(hi)));
+        for (int half = 0; half < 2; ++half) {
+          const int kk = k + half * kmt;
+          const size_t byte = base + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2;
+          g_wna_img[byte / 2] = half ? lo : hi;
+        }
+      }
+    base += (size_t)512 * kmt;
+  }
+  for (int m = 0; m < nb; ++m) g_wna_q[m] = (float)charge_per_count[m];
+  RunDev proto{};
+  int derr = 0;
+  cudaError_t e = wake_noalloc_launch(proto, g_wna_img, base, g_wna_q, nb, nbins, hist, V,
+                                      static_cast<cudaStream_t>(stream), &derr);
+  if (e != cudaSuccess) return wna_fail(errbuf, errlen, MBT_ERR_CUDA, "allocation-free wake: %s", cudaGetErrorString(e));
+  if (derr != 0) return wna_fail(errbuf, errlen, MBT_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", derr);
   return MBT_OK;
 }
 

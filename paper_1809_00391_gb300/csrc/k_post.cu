@@ -22,6 +22,7 @@
 // writes the value entering every tile and the new carry, and advances the
 // turn counter of every run.
 #include <cuda_bf16.h>
+#include <mutex>
 #include "device_common.cuh"
 
 namespace mbt {
@@ -246,6 +247,7 @@ __device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, 
 // Main part: B from the turn's counts, the MMAs (issued by one thread, run
 // asynchronously), the moments of the bunch tile while they run (M-tile 0),
 // then the epilogue from tensor memory.
+template <bool WITH_MOMENTS = true>
 __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, long long turn,
                             uint8_t *smem, uint64_t *bars, uint32_t *tmem_slot, int *s_flag,
                             double (*s_sum)[kBunchTile]) {
@@ -310,7 +312,7 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       umma_commit(&bars[1]);
     }
   }
-  if (mt == 0) moments_job(p, R, m0, nbt, par, turn, s_sum);   // overlaps the MMAs
+  if (WITH_MOMENTS && mt == 0) moments_job(p, R, m0, nbt, par, turn, s_sum);   // overlaps the MMAs
   __syncthreads();
   const bool aborted = *s_flag != 0;
   if (!aborted && warp < 4) {
@@ -432,6 +434,106 @@ size_t post_smem_bytes(int precision, int max_nbins) {
 cudaError_t configure_kernels() {
   return cudaFuncSetAttribute(k_post_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)post_smem_bytes(kMixed, 256));
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the wake job, for callers that cannot call
+// cudaMalloc (code that runs where the process must not grow its device
+// footprint, such as inside another framework's memory pool or a fixed
+// device budget).  Its working memory is this file-scope array: the Toeplitz
+// operand images (<= 192 KB for 256 cells), the run descriptor, the job list,
+// the per-bunch charges and the error word.  Every GPU that loads the library
+// holds the array until the process exits.  Calls share it, so calls that
+// overlap on the GPU (other streams, other host threads) race.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = 256 * 1024;
+constexpr size_t kNoAllocImgBytes = 196608;                       // 512 * (128 + 256)
+constexpr size_t kNoAllocRunOff = kNoAllocImgBytes;               // RunDev
+constexpr size_t kNoAllocJobsOff = kNoAllocRunOff + 1024;         // PostJob[<= 64]
+constexpr size_t kNoAllocQOff = kNoAllocJobsOff + 1024;           // float[<= kMaxBunches]
+constexpr size_t kNoAllocErrOff = kNoAllocQOff + 4 * kMaxBunches; // int error word (+ pad)
+static_assert(sizeof(RunDev) <= 1024, "run descriptor slot");
+static_assert(kNoAllocErrOff + 256 <= kNoAllocScratchBytes, "scratch layout");
+
+static __device__ __align__(256) unsigned char g_wake_scratch[kNoAllocScratchBytes];
+
+__global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) {
+  extern __shared__ __align__(1024) uint8_t sm_wna[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_flag;
+  __shared__ double s_sum[5][kBunchTile];
+  const PostJob job = p.jobs[blockIdx.x];
+  const RunDev *R = p.runs + job.run;
+  wake_prologue(R, job, sm_wna, bars, &tmem_slot, &s_flag);
+  wake_job_tc<false>(p, R, job, 0, 0, sm_wna, bars, &tmem_slot, &s_flag, s_sum);
+}
+
+namespace {
+std::mutex g_wna_mutex;
+void *g_wna_addr[256] = {nullptr};   // device address of g_wake_scratch, per device
+}  // namespace
+
+// Resolve the scratch array's device address for the current device (first
+// call on each device) and set the kernel's shared-memory limit.
+static cudaError_t noalloc_setup(int dev, unsigned char **base) {
+  std::lock_guard<std::mutex> lk(g_wna_mutex);
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (!g_wna_addr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_wake_scratch);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_wake_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)post_smem_bytes(kMixed, 256));
+    if (e != cudaSuccess) return e;
+    g_wna_addr[dev] = ptr;
+  }
+  *base = static_cast<unsigned char *>(g_wna_addr[dev]);
+  return cudaSuccess;
+}
+
+cudaError_t wake_noalloc_launch(const RunDev &proto, const void *img, size_t img_bytes, const float *q_f, int nb,
+                                int nbins, const int32_t *hist, float *V, cudaStream_t s, int *device_error_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned char *base = nullptr;
+  e = noalloc_setup(dev, &base);
+  if (e != cudaSuccess) return e;
+  // jobs: every (bunch tile, M-tile) pair of the one run
+  PostJob jobs[64];
+  const int ntile_b = (nb + kBunchTile - 1) / kBunchTile;
+  int njobs = 0;
+  for (int bt = 0; bt < ntile_b; ++bt)
+    for (int mt = 0; mt < nbins / 128; ++mt) jobs[njobs++] = PostJob{0, kJobWake, bt, mt};
+  RunDev rd = proto;
+  rd.hist = const_cast<int32_t *>(hist);
+  rd.vsr = V;
+  rd.toep = base;
+  rd.q_mp_f = reinterpret_cast<const float *>(base + kNoAllocQOff);
+  rd.nb = nb;
+  rd.nbins = nbins;
+  Plan pl{};
+  pl.runs = reinterpret_cast<RunDev *>(base + kNoAllocRunOff);
+  pl.jobs = reinterpret_cast<PostJob *>(base + kNoAllocJobsOff);
+  pl.error = reinterpret_cast<int *>(base + kNoAllocErrOff);
+  pl.nruns = 1;
+  pl.njobs = njobs;
+  pl.max_nbins = nbins;
+  // the whole working set is rewritten by every call; the error word starts at zero
+  if ((e = cudaMemcpyAsync(base, img, img_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(base + kNoAllocRunOff, &rd, sizeof rd, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(base + kNoAllocJobsOff, jobs, sizeof(PostJob) * njobs, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(base + kNoAllocQOff, q_f, sizeof(float) * nb, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(base + kNoAllocErrOff, 0, 16, s)) != cudaSuccess) return e;
+  k_wake_noalloc<<<njobs, kPostThreads, post_smem_bytes(kMixed, nbins), s>>>(pl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // synchronous: V is complete (and the error word readable) on return
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  return cudaMemcpy(device_error_out, base + kNoAllocErrOff, sizeof(int), cudaMemcpyDeviceToHost);
 }
 
 cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s, bool pdl) {

@@ -102,6 +102,12 @@ cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s, bool pdl);
 cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s);
 size_t post_smem_bytes(int precision, int max_nbins);
 cudaError_t configure_kernels();
+// Allocation-free tensor-core wake of one run (scratch: a static device array
+// in k_post.cu).  proto supplies the constants; the images, charges and
+// pointers are placed into the array by the call.  Host buffers are consumed
+// before the call returns.
+cudaError_t wake_noalloc_launch(const RunDev &proto, const void *img, size_t img_bytes, const float *q_f, int nb,
+                                int nbins, const int32_t *hist, float *V, cudaStream_t s, int *device_error_out);
 cudaError_t configure_push_kernels();
 
 }  // namespace mbt
