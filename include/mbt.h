@@ -172,6 +172,20 @@ mbt_status mbt_get_particles(mbt_ctx *ctx, int bunch, double *tau_s, double *del
  * captured CUDA graph. */
 mbt_status mbt_track(mbt_ctx *ctx, int64_t nturns, void *stream);
 
+/* Cluster-resident tracking (MBT_PREC_MIXED, at most 32 bunches): one
+ * thread-block cluster of up to 16 CTAs per bunch keeps the bunch's particles
+ * in distributed shared memory for all nturns turns of one launch, and the
+ * clusters meet once per turn for the long-range phasor scan.  Same map and
+ * outputs as mbt_track (the short-range wake is an FP32 convolution on the
+ * CUDA cores instead of the tensor-core contraction); turns may alternate
+ * with mbt_track.  MBT_ERR_UNSUPPORTED if the fill does not fit on chip.
+ * Asynchronous on stream. */
+mbt_status mbt_track_resident(mbt_ctx *ctx, int64_t nturns, void *stream);
+
+/* Cluster shape mbt_track_resident would use: CTAs per cluster (0 if the fill
+ * does not fit on chip) and particles held per CTA. */
+mbt_status mbt_resident_shape(mbt_ctx *ctx, int *cluster, int *per_cta);
+
 /* Wait for the context's work; report device errors. */
 mbt_status mbt_sync(mbt_ctx *ctx);
 

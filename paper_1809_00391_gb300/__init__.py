@@ -28,7 +28,7 @@ NO_SR, NO_QE, KICK_NGP = 1, 2, 4
 # every entry point declared in include/mbt.h
 EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt_last_error",
            "mbt_add_resonator", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
-           "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_sync", "mbt_read_moments",
+           "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
            "mbt_batch_track", "mbt_batch_sync", "mbt_batch_destroy"]
@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_set_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_get_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_track": ([_vp, _i64, _vp], _i), "mbt_sync": ([_vp], _i),
+                "mbt_track_resident": ([_vp, _i64, _vp], _i), "mbt_resident_shape": ([_vp, _P(_i), _P(_i)], _i),
                 "mbt_read_moments": ([_vp, _i64, _i64, _P(_d)], _i),
                 "mbt_read_histograms": ([_vp, _P(_i32), _P(_i64)], _i),
                 "mbt_read_wake": ([_vp, _P(_d), _P(_d)], _i), "mbt_get_info": ([_vp, _P(Info)], _i),
@@ -186,6 +187,16 @@ class Tracker:
 
     def track(self, nturns: int, stream=None):
         self._chk(self._L.mbt_track(self._h, int(nturns), _stream(stream)))
+
+    def track_resident(self, nturns: int, stream=None):
+        """Track with the bunches' particles resident in cluster shared memory."""
+        self._chk(self._L.mbt_track_resident(self._h, int(nturns), _stream(stream)))
+
+    def resident_shape(self):
+        """(CTAs per cluster, particles per CTA) of resident tracking; (0, 0) if it does not fit."""
+        a, b = _i(), _i()
+        self._chk(self._L.mbt_resident_shape(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def sync(self):
         self._chk(self._L.mbt_sync(self._h))

@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libmbt.so"
 INCLUDE = PKG.parent / "include"
-SOURCES = ["k_push.cu", "k_post.cu", "api.cu"]
+SOURCES = ["k_push.cu", "k_post.cu", "k_resident.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE)]
 # extra nvcc flags for tuning experiments (e.g. "-DMBT_PUSH_STAGES=2"); part of the staleness key

@@ -103,6 +103,10 @@ struct mbt_ctx {
   double2 *d_step = nullptr, *d_emis = nullptr;
   float *d_qf = nullptr;
   double *d_inv_n = nullptr;
+  float *d_lagf = nullptr;
+  // cluster-resident mode (allocated on first use)
+  double2 *d_resE = nullptr;
+  unsigned int *d_gbar = nullptr;
   float2 *d_emis_f = nullptr;
   void *d_toep = nullptr;
   size_t device_bytes = 0;
@@ -515,6 +519,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   ALLOC(c->d_q, (size_t)nb * sizeof(double));
   ALLOC(c->d_qf, (size_t)nb * sizeof(float));
   ALLOC(c->d_inv_n, (size_t)nb * sizeof(double));
+  ALLOC(c->d_lagf, (size_t)nbins * sizeof(float));
   ALLOC(c->d_step, (size_t)nl * nb * sizeof(double2));
   ALLOC(c->d_emis, (size_t)nl * nbins * sizeof(double2));
   ALLOC(c->d_emis_f, (size_t)nl * nbins * sizeof(float2));
@@ -546,6 +551,11 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   for (int l = 0; l < nbins; ++l)
     for (auto &r : c->res)
       if (r.range & MBT_RANGE_SHORT) lag[l] += wake(r, (double)l * c->Delta);
+  {
+    std::vector<float> lagf(nbins);
+    for (int l = 0; l < nbins; ++l) lagf[l] = (float)lag[l];
+    cudaMemcpy(c->d_lagf, lagf.data(), nbins * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (mixed) {
     // operand images, per M-tile mt: rows [128 mt, 128 mt + 128) of the lower
     // triangular Toeplitz matrix need only columns k < Kmt = 128 (mt + 1):
@@ -650,6 +660,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   rd.sigma_E = c->ring.sigma_delta;
   rd.q_mp_f = c->d_qf;
   rd.inv_n = c->d_inv_n;
+  rd.lag_f = c->d_lagf;
   rd.f_invD = (float)rd.invDelta;
   rd.f_HinvD = (float)(rd.H * rd.invDelta);
   rd.f_nbins = (float)nbins;
@@ -863,6 +874,86 @@ mbt_status mbt_track(mbt_ctx *c, int64_t nturns, void *stream) {
     done += c->graph_turns;
   }
   return launch_turns(c, pl, c->precision, nturns - done, s, false);
+}
+
+// Cluster shape for resident tracking: the largest power-of-two cluster (<= 16
+// CTAs) whose slices fit in shared memory and whose clusters can all be
+// resident at once.  Returns MBT_OK with *cluster = 0 if the fill does not fit.
+static mbt_status resident_shape(mbt_ctx *c, int *cluster, int *per, size_t *smem) {
+  *cluster = 0;
+  int64_t nmax = 0;
+  for (int64_t n : c->nmp) nmax = std::max(nmax, n);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device query");
+  for (int C = 16; C >= 1; C /= 2) {
+    const int64_t p4 = ((nmax + C - 1) / C + 3) / 4 * 4;
+    const size_t sm = resident_smem_bytes((int)p4, c->nbins);
+    if (sm > 220 * 1024 || (int64_t)c->nb * C > nsm) continue;
+    int maxc = 0;
+    e = resident_max_clusters(C, sm, &maxc);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (maxc >= c->nb) {
+      *cluster = C;
+      *per = (int)p4;
+      *smem = sm;
+      return MBT_OK;
+    }
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_resident_shape(mbt_ctx *c, int *cluster, int *per_cta) {
+  if (!c || !cluster || !per_cta) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  *cluster = 0;
+  *per_cta = 0;
+  if (c->precision != MBT_PREC_MIXED || c->nb > kResidentMaxBunches) return MBT_OK;
+  size_t sm = 0;
+  return resident_shape(c, cluster, per_cta, &sm);
+}
+
+mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (nturns < 0 || nturns > (1LL << 30)) return fail(c, MBT_ERR_ARG, "nturns out of range");
+  if (nturns == 0) return MBT_OK;
+  if (c->precision != MBT_PREC_MIXED)
+    return fail(c, MBT_ERR_UNSUPPORTED, "resident tracking is implemented for the mixed precision path");
+  if (c->nb > kResidentMaxBunches)
+    return fail(c, MBT_ERR_UNSUPPORTED, "resident tracking holds at most %d bunches", kResidentMaxBunches);
+  int C = 0, per = 0;
+  size_t sm = 0;
+  mbt_status st = resident_shape(c, &C, &per, &sm);
+  if (st != MBT_OK) return st;
+  if (C == 0) return fail(c, MBT_ERR_UNSUPPORTED, "the fill does not fit in shared memory of co-resident clusters");
+  const int nl = std::max(1, c->nlong);
+  if (!c->d_resE) {
+    if ((st = dalloc(c, &c->d_resE, (size_t)2 * nl * c->nb * sizeof(double2))) != MBT_OK) return st;
+    if ((st = dalloc(c, &c->d_gbar, 16)) != MBT_OK) return st;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ResidentArgs a{};
+  a.plan = c->own.plan;
+  a.E = c->d_resE;
+  a.gbar = c->d_gbar;
+  a.cluster = C;
+  a.per = per;
+  a.grid_sync = (c->nlong > 0 && c->nb > 1) ? 1 : 0;
+  const int64_t chunk = 1LL << 20;   // turns per launch (the barrier counter stays far from wrapping)
+  for (int64_t done = 0; done < nturns; done += chunk) {
+    a.nturns = (int)std::min<int64_t>(chunk, nturns - done);
+    cudaError_t e = cudaMemsetAsync(c->d_gbar, 0, 16, s);
+    if (e == cudaSuccess) e = launch_resident(a, c->nlong, c->nb, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resident launch");
+  }
+  return MBT_OK;
 }
 
 mbt_status mbt_sync(mbt_ctx *c) {

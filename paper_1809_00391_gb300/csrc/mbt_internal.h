@@ -61,7 +61,10 @@ struct RunDev {
   float f_la[kMaxLong], f_lw[kMaxLong];
   const float *q_mp_f;      // [nb] macro-particle charge (float)
   const double *inv_n;      // [nb] 1 / n_mp
+  const float *lag_f;       // [nbins] summed short-range wake per lag, FP32 (resident mode)
 };
+
+
 
 struct BunchDev {
   int run, m;
@@ -93,6 +96,24 @@ struct Plan {
   int max_nlong;              // most long-range resonators of any run of the plan
   unsigned long long *trace;  // null, or [njobs][3] post-kernel CTA timestamps (start, job done, exit) [ns]
 };
+
+// Cluster-resident tracking of one run: one thread-block cluster per bunch,
+// the bunch's particles held in the cluster's shared memory for all turns of
+// a launch.
+constexpr int kResidentThreads = 256;
+constexpr int kResidentMaxBunches = 32;   // one warp scans the fill
+struct ResidentArgs {
+  Plan plan;              // the run's own plan (runs[0], bunches)
+  double2 *E;             // [2][nlong][nb] emissions, double-buffered by turn parity
+  unsigned int *gbar;     // grid barrier counter (zeroed before each launch)
+  int cluster;            // CTAs per cluster
+  int per;                // particles per CTA slice (multiple of 4)
+  int nturns;
+  int grid_sync;          // 1 if clusters must meet every turn (long-range coupling of several bunches)
+};
+size_t resident_smem_bytes(int per, int nbins);
+cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nb, cudaStream_t s);
+cudaError_t resident_max_clusters(int cluster, size_t smem, int *max_clusters);
 
 // Kernel launchers (one translation unit each).
 // pdl: launch with programmatic stream serialisation (the kernel's prologue
