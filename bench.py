@@ -42,6 +42,7 @@ PUSH_SOURCES = ["paper_1809_00391_gb300/csrc/k_push.cu", "paper_1809_00391_gb300
                 "paper_1809_00391_gb300/csrc/mbt_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_mixed_fill390_traffic.json")
 GRAPH_TURNS = 100      # turns per captured CUDA graph
+AUTOTUNE_TURNS = 20    # timed turns per push-tile candidate
 ROOFLINE_TURNS = 4000  # turns of the event-timed roofline region
 
 
@@ -236,8 +237,9 @@ def main():
     K, Wm = args.steps, args.warmup
     G = max(1, min(GRAPH_TURNS, K))
     stream = torch.cuda.current_stream()
-    tr = pkg.tracker_for_run(run, record_turns=max(K + Wm + G, 16))
+    tr = pkg.tracker_for_run(run, record_turns=max(K + Wm + G + 17 * (AUTOTUNE_TURNS + 2), 16))
     tr.init_particles(stream)
+    tile = tr.autotune(AUTOTUNE_TURNS)  # push-tile autotuner: its trial turns are real warm-up turns
     tr.set_graph(G)
     tr.track(max(Wm, G), stream)       # warm-up; also captures the G-turn graph
     tr.sync()
@@ -296,6 +298,7 @@ def main():
         host_tau = [np.ascontiguousarray(rng.normal(0.0, 13.2e-12, n), np.float64) for n in run.n_mp]
         host_del = [np.ascontiguousarray(rng.normal(0.0, 9e-4, n), np.float64) for n in run.n_mp]
         tr2 = pkg.tracker_for_run(run, record_turns=max(K, 16))
+        tr2.set_tile(tile)
         tr2.set_graph(G)
         barrier()
         t0 = time.perf_counter()
@@ -329,6 +332,7 @@ def main():
                            "turns_timed": K, "precision": "tau f32, delta f64-accumulated, wake bf16x2 on tcgen05 "
                            "(fp32 accumulate), phasor scan + moments f64",
                            "l2": "state 468 MB > 129 MB L2 (no flush needed)",
+                           "push_tile": tile,
                            "parallelism": f"{world} independent fill(s), one per GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K,
                 "launch_mode": f"CUDA graph of {G} turns, programmatic dependent launch between kernels",

@@ -213,6 +213,21 @@ mbt_status mbt_get_info(mbt_ctx *ctx, mbt_info *info);
  * (0 disables; default 0).  The first mbt_track after a change captures. */
 mbt_status mbt_set_graph(mbt_ctx *ctx, int turns_per_graph);
 
+/* Push tile: at most this many macro-particles per CTA of the mixed-precision
+ * push kernel, a multiple of 4 in [1024, 65536] (default 8192); each bunch is
+ * split into ceil(n / tile) tiles of equal size.  Changing it rebuilds the
+ * work lists (and drops a captured graph); results do not depend on it except
+ * for the summation order of the moment sums. */
+mbt_status mbt_set_tile(mbt_ctx *ctx, int particles);
+
+/* Autotuner: times turns_per_trial turns for each candidate push tile (2048
+ * .. 32768 particles, plus tiles that make the tile count a whole multiple of
+ * the push CTAs the GPU holds at once) and keeps the fastest (written to
+ * *chosen_tile, may be NULL).  The trial turns are real tracking turns: the
+ * run advances by (turns_per_trial + 2) turns per candidate (at most 17).
+ * Synchronous.  No-op for MBT_PREC_F64. */
+mbt_status mbt_autotune(mbt_ctx *ctx, int turns_per_trial, int *chosen_tile);
+
 /* Kernel timing: when enabled, mbt_track records CUDA events around every
  * push-kernel launch on the tracking stream.  mbt_get_timing returns the sum
  * of their durations [ms] and the number of timed launches since the last
@@ -273,6 +288,9 @@ mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const dou
 mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out);
 mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream);
 mbt_status mbt_batch_sync(mbt_batch *b);   /* wait; report device errors of the batch */
+/* Graph replay and push-tile autotuning for a batch, as for a context. */
+mbt_status mbt_batch_set_graph(mbt_batch *b, int turns_per_graph);
+mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_tile);
 void mbt_batch_destroy(mbt_batch *b);
 
 #ifdef __cplusplus

@@ -29,9 +29,10 @@ NO_SR, NO_QE, KICK_NGP = 1, 2, 4
 EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt_last_error",
            "mbt_add_resonator", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
            "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
-           "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_timing",
+           "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
+           "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
-           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_destroy"]
+           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy"]
 
 
 class MBTError(RuntimeError):
@@ -89,6 +90,8 @@ def lib() -> ctypes.CDLL:
                 "mbt_read_histograms": ([_vp, _P(_i32), _P(_i64)], _i),
                 "mbt_read_wake": ([_vp, _P(_d), _P(_d)], _i), "mbt_get_info": ([_vp, _P(Info)], _i),
                 "mbt_set_graph": ([_vp, _i], _i), "mbt_set_timing": ([_vp, _i], _i),
+                "mbt_set_tile": ([_vp, _i], _i), "mbt_autotune": ([_vp, _i, _P(_i)], _i),
+                "mbt_batch_set_graph": ([_vp, _i], _i), "mbt_batch_autotune": ([_vp, _i, _P(_i)], _i),
                 "mbt_get_timing": ([_vp, _P(_d), _P(_d), _P(_i64)], _i),
                 "mbt_set_trace": ([_vp, _i], _i), "mbt_read_trace": ([_vp, _P(_i64), _i, _P(_i)], _i),
                 "mbt_state_size": ([_vp, _P(_sz)], _i), "mbt_save_state": ([_vp, _vp, _sz], _i),
@@ -228,6 +231,15 @@ class Tracker:
     def set_graph(self, turns_per_graph: int):
         self._chk(self._L.mbt_set_graph(self._h, int(turns_per_graph)))
 
+    def set_tile(self, particles: int):
+        self._chk(self._L.mbt_set_tile(self._h, int(particles)))
+
+    def autotune(self, turns_per_trial: int = 20) -> int:
+        """Pick the fastest push tile by timing real turns; returns it."""
+        t = _i()
+        self._chk(self._L.mbt_autotune(self._h, int(turns_per_trial), ctypes.byref(t)))
+        return t.value
+
     def set_timing(self, enable: bool):
         self._chk(self._L.mbt_set_timing(self._h, 1 if enable else 0))
 
@@ -275,6 +287,18 @@ class Batch:
         st = self._L.mbt_batch_track(self._h, int(nturns), _stream(stream))
         if st != 0:
             raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+
+    def set_graph(self, turns_per_graph: int):
+        st = self._L.mbt_batch_set_graph(self._h, int(turns_per_graph))
+        if st != 0:
+            raise MBTError(st, "mbt_batch_set_graph failed")
+
+    def autotune(self, turns_per_trial: int = 5) -> int:
+        t = _i()
+        st = self._L.mbt_batch_autotune(self._h, int(turns_per_trial), ctypes.byref(t))
+        if st != 0:
+            raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+        return t.value
 
     def sync(self):
         st = self._L.mbt_batch_sync(self._h)

@@ -112,6 +112,7 @@ struct mbt_ctx {
   size_t device_bytes = 0;
   RunDev rundev{};
   PlanStore own;
+  int tile = kMixedTile;       // particles per push CTA (mixed precision)
   // graph replay
   int graph_turns = 0;
   cudaGraphExec_t graph_exec = nullptr;
@@ -133,6 +134,10 @@ struct mbt_batch {
   std::vector<mbt_ctx *> ctx;
   PlanStore store;
   int precision = 0;
+  int tile = kMixedTile;
+  int graph_turns = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -274,12 +279,12 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
 }
 
 // Append one context's run to a plan under construction.
-void append_run(PlanStore &st, mbt_ctx *c) {
+void append_run(PlanStore &st, mbt_ctx *c, int mixed_tile) {
   const int ri = (int)st.runs.size();
   RunDev rd = c->rundev;
   rd.bunch_base = (int)st.bunches.size();
   st.runs.push_back(rd);
-  const int tile = c->precision == MBT_PREC_MIXED ? kMixedTile : kF64Tile;
+  const int tile = c->precision == MBT_PREC_MIXED ? mixed_tile : kF64Tile;
   for (int m = 0; m < c->nb; ++m) {
     BunchDev bd{};
     bd.run = ri;
@@ -287,13 +292,17 @@ void append_run(PlanStore &st, mbt_ctx *c) {
     bd.off = c->off[m];
     bd.n = c->nmp[m];
     bd.tile0 = (int)st.tiles.size();
-    for (int64_t s = 0; s < c->nmp[m]; s += tile) {
+    // k = ceil(n / tile) tiles of equal size (multiples of 4 particles, the last one shorter)
+    const int64_t n = c->nmp[m];
+    const int64_t k = (n + tile - 1) / tile;
+    const int64_t base = c->precision == MBT_PREC_MIXED ? ((n + k - 1) / k + 3) / 4 * 4 : tile;
+    for (int64_t s = 0; s < n; s += base) {
       TileDev t{};
       t.bunch = (int)st.bunches.size();
       t.run = ri;
       t.m = m;
       t.start = s;
-      t.count = (int)std::min<int64_t>(tile, c->nmp[m] - s);
+      t.count = (int)std::min<int64_t>(base, n - s);
       st.tiles.push_back(t);
     }
     bd.ntiles = (int)st.tiles.size() - bd.tile0;
@@ -683,7 +692,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   ps.tiles.clear();
   ps.jobs.clear();
   ps.precision = c->precision;
-  append_run(ps, c);
+  append_run(ps, c, c->tile);
   if ((st = upload_plan(c, ps)) != MBT_OK) {
     free_device(c);
     return st;
@@ -844,6 +853,91 @@ mbt_status mbt_get_timing(mbt_ctx *c, double *push_ms, double *post_ms, int64_t 
   return MBT_OK;
 }
 
+// Track with an optional captured graph of `graph_turns` turns (captured on
+// first use on `cap_stream`, replayed on s); remaining turns as plain launches.
+static mbt_status track_plan(mbt_ctx *c, const Plan &pl, int prec, int64_t nturns, cudaStream_t s, int graph_turns,
+                             cudaGraphExec_t *exec, cudaStream_t *cap_stream) {
+  if (graph_turns == 0 || nturns < graph_turns) return launch_turns(c, pl, prec, nturns, s, false);
+  if (!*exec) {
+    if (!*cap_stream && cudaStreamCreateWithFlags(cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, MBT_ERR_CUDA, "capture stream");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(*cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+    mbt_status st = launch_turns(c, pl, prec, graph_turns, *cap_stream, false);
+    e = cudaStreamEndCapture(*cap_stream, &g);
+    if (st != MBT_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  }
+  int64_t done = 0;
+  while (nturns - done >= graph_turns) {
+    cudaError_t e = cudaGraphLaunch(*exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    done += graph_turns;
+  }
+  return launch_turns(c, pl, prec, nturns - done, s, false);
+}
+
+// Rebuild a context's own plan with another push tile size.
+static mbt_status rebuild_own_plan(mbt_ctx *c) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  unsigned long long *trace = c->own.plan.trace;
+  PlanStore &ps = c->own;
+  ps.runs.clear();
+  ps.bunches.clear();
+  ps.tiles.clear();
+  ps.jobs.clear();
+  append_run(ps, c, c->tile);
+  mbt_status st = upload_plan(c, ps);
+  if (st != MBT_OK) return st;
+  c->own.plan.trace = trace;   // the post jobs (and so the trace layout) do not depend on the tile
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_set_tile(mbt_ctx *c, int particles) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (particles < 1024 || particles > 65536 || particles % 4)
+    return fail(c, MBT_ERR_ARG, "tile must be a multiple of 4 in [1024, 65536]");
+  c->tile = particles;
+  if (!c->filled || c->precision != MBT_PREC_MIXED) return MBT_OK;
+  return rebuild_own_plan(c);
+}
+
+// Candidate push tiles for the autotuner: fixed sizes, plus "wave-aligned"
+// sizes for which the runs' tile count is a whole multiple of the push
+// kernel's resident CTA slots (no partly filled last wave).
+static std::vector<int> tile_candidates(const std::vector<mbt_ctx *> &ctxs) {
+  std::vector<int> cand = {2048, 4096, 8192, 16384, 32768};
+  int slots = 0;
+  if (push_resident_slots(&slots) != cudaSuccess || slots <= 0) {
+    cudaGetLastError();
+    return cand;
+  }
+  int64_t nb = 0, nmax = 0;
+  for (mbt_ctx *c : ctxs) {
+    nb += c->nb;
+    for (int64_t n : c->nmp) nmax = std::max(nmax, n);
+  }
+  for (int w = 1; w <= 12; ++w) {
+    const int64_t k = (int64_t)w * slots / std::max<int64_t>(1, nb);   // tiles per bunch
+    if (k < 1) continue;
+    const int64_t t = ((nmax + k - 1) / k + 3) / 4 * 4;
+    if (t >= 1024 && t <= 65536) cand.push_back((int)t);
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  return cand;
+}
+
 mbt_status mbt_track(mbt_ctx *c, int64_t nturns, void *stream) {
   if (!c) return MBT_ERR_ARG;
   c->err.clear();
@@ -851,29 +945,51 @@ mbt_status mbt_track(mbt_ctx *c, int64_t nturns, void *stream) {
   if (nturns < 0) return fail(c, MBT_ERR_ARG, "nturns < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Plan &pl = c->own.plan;
-  if (c->timing || c->graph_turns == 0 || nturns < c->graph_turns)
-    return launch_turns(c, pl, c->precision, nturns, s, c->timing);
-  if (!c->graph_exec) {
-    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return fail(c, MBT_ERR_CUDA, "capture stream");
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
-    mbt_status st = launch_turns(c, pl, c->precision, c->graph_turns, c->capture_stream, false);
-    e = cudaStreamEndCapture(c->capture_stream, &g);
+  if (c->timing) return launch_turns(c, pl, c->precision, nturns, s, true);
+  return track_plan(c, pl, c->precision, nturns, s, c->graph_turns, &c->graph_exec, &c->capture_stream);
+}
+
+// Time `turns` turns of a plan on stream s with CUDA events [ms].
+static mbt_status time_turns(mbt_ctx *c, const Plan &pl, int prec, int turns, cudaStream_t s, float *ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(c, MBT_ERR_CUDA, "event create");
+  mbt_status st = launch_turns(c, pl, prec, 2, s, false);   // warm-up (real turns)
+  cudaEventRecord(e0, s);
+  if (st == MBT_OK) st = launch_turns(c, pl, prec, turns, s, false);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (st == MBT_OK && e != cudaSuccess) st = cuda_fail(c, e, "autotune timing");
+  if (st == MBT_OK) cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+mbt_status mbt_autotune(mbt_ctx *c, int turns_per_trial, int *chosen_tile) {
+  if (!c || turns_per_trial < 1) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (c->precision != MBT_PREC_MIXED) {
+    if (chosen_tile) *chosen_tile = kF64Tile;
+    return MBT_OK;
+  }
+  float best = 1e30f;
+  int best_tile = c->tile;
+  for (int tile : tile_candidates({c})) {
+    c->tile = tile;
+    mbt_status st = rebuild_own_plan(c);
+    float ms = 0.f;
+    if (st == MBT_OK) st = time_turns(c, c->own.plan, c->precision, turns_per_trial, nullptr, &ms);
     if (st != MBT_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    if (ms < best) {
+      best = ms;
+      best_tile = tile;
+    }
   }
-  int64_t done = 0;
-  while (nturns - done >= c->graph_turns) {
-    cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
-    done += c->graph_turns;
-  }
-  return launch_turns(c, pl, c->precision, nturns - done, s, false);
+  c->tile = best_tile;
+  if (chosen_tile) *chosen_tile = best_tile;
+  return rebuild_own_plan(c);
 }
 
 // Cluster shape for resident tracking: the largest power-of-two cluster (<= 16
@@ -1265,7 +1381,7 @@ mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out) {
   b->ctx.assign(ctxs, ctxs + n);
   b->precision = ctxs[0]->precision;
   b->store.precision = b->precision;
-  for (int i = 0; i < n; ++i) append_run(b->store, ctxs[i]);
+  for (int i = 0; i < n; ++i) append_run(b->store, ctxs[i], b->tile);
   mbt_status st = upload_plan(ctxs[0], b->store);
   if (st != MBT_OK) {
     delete b;
@@ -1277,7 +1393,57 @@ mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out) {
 
 mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream) {
   if (!b || nturns < 0) return MBT_ERR_ARG;
-  return launch_turns(b->ctx[0], b->store.plan, b->precision, nturns, static_cast<cudaStream_t>(stream), false);
+  return track_plan(b->ctx[0], b->store.plan, b->precision, nturns, static_cast<cudaStream_t>(stream), b->graph_turns,
+                    &b->graph_exec, &b->capture_stream);
+}
+
+mbt_status mbt_batch_set_graph(mbt_batch *b, int turns) {
+  if (!b || turns < 0 || turns > 100000) return MBT_ERR_ARG;
+  if (b->graph_exec) {
+    cudaGraphExecDestroy(b->graph_exec);
+    b->graph_exec = nullptr;
+  }
+  b->graph_turns = turns;
+  return MBT_OK;
+}
+
+static mbt_status rebuild_batch_plan(mbt_batch *b) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(b->ctx[0], e, "sync");
+  b->store.runs.clear();
+  b->store.bunches.clear();
+  b->store.tiles.clear();
+  b->store.jobs.clear();
+  for (mbt_ctx *c : b->ctx) append_run(b->store, c, b->tile);
+  if (b->graph_exec) {
+    cudaGraphExecDestroy(b->graph_exec);
+    b->graph_exec = nullptr;
+  }
+  return upload_plan(b->ctx[0], b->store);
+}
+
+mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_tile) {
+  if (!b || turns_per_trial < 1) return MBT_ERR_ARG;
+  if (b->precision != MBT_PREC_MIXED) {
+    if (chosen_tile) *chosen_tile = kF64Tile;
+    return MBT_OK;
+  }
+  float best = 1e30f;
+  int best_tile = b->tile;
+  for (int tile : tile_candidates(b->ctx)) {
+    b->tile = tile;
+    mbt_status st = rebuild_batch_plan(b);
+    float ms = 0.f;
+    if (st == MBT_OK) st = time_turns(b->ctx[0], b->store.plan, b->precision, turns_per_trial, nullptr, &ms);
+    if (st != MBT_OK) return st;
+    if (ms < best) {
+      best = ms;
+      best_tile = tile;
+    }
+  }
+  b->tile = best_tile;
+  if (chosen_tile) *chosen_tile = best_tile;
+  return rebuild_batch_plan(b);
 }
 
 mbt_status mbt_batch_sync(mbt_batch *b) {
@@ -1290,6 +1456,8 @@ mbt_status mbt_batch_sync(mbt_batch *b) {
 void mbt_batch_destroy(mbt_batch *b) {
   if (!b) return;
   cudaDeviceSynchronize();
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   delete b;
 }
 

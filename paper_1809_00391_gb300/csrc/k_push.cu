@@ -377,6 +377,16 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   return launch_ex(k_push_f64, p.ntiles, kPushThreads, smem, s, pdl, p);
 }
 
+cudaError_t push_resident_slots(int *slots) {
+  const size_t smem = (size_t)kStages * kStageBytes + 256 * (sizeof(float2) + sizeof(int));
+  int dev = 0, nsm = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1>, kPushThreads, smem);
+  *slots = per * nsm;
+  return e;
+}
+
 cudaError_t configure_push_kernels() {
   const int bytes = (int)((size_t)kStages * kStageBytes + 1024 * (sizeof(float2) + sizeof(int)));
   cudaError_t e = cudaSuccess;

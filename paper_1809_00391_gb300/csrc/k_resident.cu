@@ -215,14 +215,15 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     }
     // rows [rank B, rank B + B) of V = q sum_{k<=j} lag[j-k] count[k]
     {
-      const int G = kResidentThreads / B;   // threads per row (<= 32, a power of two)
+      const int G = min(32, kResidentThreads / B);   // threads per row (a power of two, <= 32)
       const int row = tid / G, sub = tid % G;
       const int j = rank * B + row;
-      float acc = 0.f;
-      if (row < B)
+      if (row < B) {
+        float acc = 0.f;
         for (int k = sub; k <= j; k += G) acc = fmaf(S.lag[j - k], (float)S.bh[k], acc);
-      for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o, G);
-      if (sub == 0 && row < B) S.vrow[j] = qf * acc;
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o, G);
+        if (sub == 0) S.vrow[j] = qf * acc;
+      }
     }
     // long range: emission, grid barrier, scan over the fill
     if (nlong > 0 && rank == 0) {

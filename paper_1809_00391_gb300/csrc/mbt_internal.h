@@ -100,7 +100,10 @@ struct Plan {
 // Cluster-resident tracking of one run: one thread-block cluster per bunch,
 // the bunch's particles held in the cluster's shared memory for all turns of
 // a launch.
-constexpr int kResidentThreads = 256;
+#ifndef MBT_RESIDENT_THREADS
+#define MBT_RESIDENT_THREADS 512
+#endif
+constexpr int kResidentThreads = MBT_RESIDENT_THREADS;
 constexpr int kResidentMaxBunches = 32;   // one warp scans the fill
 struct ResidentArgs {
   Plan plan;              // the run's own plan (runs[0], bunches)
@@ -130,5 +133,6 @@ cudaError_t configure_kernels();
 cudaError_t wake_noalloc_launch(const RunDev &proto, const void *img, size_t img_bytes, const float *q_f, int nb,
                                 int nbins, const int32_t *hist, float *V, cudaStream_t s, int *device_error_out);
 cudaError_t configure_push_kernels();
+cudaError_t push_resident_slots(int *slots);   // push CTAs resident at once on this device (256 cells)
 
 }  // namespace mbt
