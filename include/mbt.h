@@ -293,6 +293,79 @@ mbt_status mbt_batch_set_graph(mbt_batch *b, int turns_per_graph);
 mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_tile);
 void mbt_batch_destroy(mbt_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Serving: instability-scan requests tracked with continuous batching.
+ * A server thread owns the device work.  Requests wait in a FIFO queue and are
+ * admitted in order while at most max_active requests are active and their
+ * estimated device memory stays within hbm_budget_bytes (the first request is
+ * always admitted).  All active requests advance together through the batched
+ * kernels, turns_per_step turns between admission points (fewer when a
+ * request is about to finish); finished requests are retired at once, which
+ * frees their memory for the queue.  A request's result does not depend on
+ * what it was batched with: it equals the same request tracked alone.
+ * ------------------------------------------------------------------------ */
+typedef struct mbt_server mbt_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory admitted requests may hold (estimate), > 0 */
+    int max_active;           /* requests tracked together, >= 1                          */
+    int turns_per_step;       /* turns between admission points, >= 1                     */
+} mbt_server_config;
+
+/* One request: a run as for mbt_create / mbt_add_resonator / mbt_set_grid /
+ * mbt_set_fill, tracked for `turns` turns from a matched Gaussian start.  All
+ * arrays are copied by mbt_server_submit. */
+typedef struct {
+    mbt_ring ring;
+    int precision, flags;
+    uint64_t seed;
+    int nres;
+    const double *Rs_ohm, *fr_Hz, *Q;
+    const int32_t *range;
+    int nbins;
+    double half_width_sigmas;
+    int nb;
+    const int32_t *bucket;
+    const double *current_A;
+    const int64_t *n_mp;
+    int64_t turns;
+} mbt_request;
+
+enum { MBT_REQ_QUEUED = 0, MBT_REQ_RUNNING = 1, MBT_REQ_DONE = 2, MBT_REQ_FAILED = 3 };
+
+typedef struct {
+    int state;                 /* MBT_REQ_*                                              */
+    int64_t turns_done;
+    double t_submit, t_start, t_finish;   /* seconds since the server started (host clock) */
+    int64_t device_bytes;      /* device memory the request held while active            */
+    char error[128];
+} mbt_request_status;
+
+typedef struct {
+    int64_t submitted, completed, failed, queued, active, max_active_seen, steps;
+    int64_t used_bytes, max_bytes_seen;
+    double busy_seconds;       /* time spent in tracking steps                            */
+    double mp_turns;           /* macro-particle-turns tracked                            */
+    double now;                /* seconds since the server started                        */
+} mbt_server_stats;
+
+/* Start a server on the calling thread's current device. */
+mbt_status mbt_server_create(const mbt_server_config *cfg, mbt_server **out);
+/* Queue a request (non-blocking); *id identifies it.  MBT_ERR_BUDGET if its
+ * estimated memory alone exceeds the budget, MBT_ERR_ARG on a malformed request. */
+mbt_status mbt_server_submit(mbt_server *s, const mbt_request *req, int64_t *id);
+/* State and timestamps of a request; once it is done, final_moments[nb][6]
+ * (the last turn's moments, as mbt_read_moments) and history[turns][2] (per
+ * turn, the rms over bunches of <tau> and of <delta>) are copied if non-NULL. */
+mbt_status mbt_server_poll(mbt_server *s, int64_t id, mbt_request_status *status, double *final_moments,
+                           double *history);
+/* Block until the request is done (MBT_OK), failed (MBT_ERR_CUDA) or timeout_s
+ * passed (MBT_ERR_TIMEOUT). */
+mbt_status mbt_server_wait(mbt_server *s, int64_t id, double timeout_s);
+mbt_status mbt_server_get_stats(mbt_server *s, mbt_server_stats *out);
+/* Stop the server thread and free every request's device memory. */
+void mbt_server_destroy(mbt_server *s);
+
 #ifdef __cplusplus
 }
 #endif

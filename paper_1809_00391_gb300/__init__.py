@@ -19,7 +19,8 @@ from ._build import LIB as _LIB_PATH
 from ._build import build
 
 __all__ = ["build", "lib", "Tracker", "Batch", "MBTError", "PREC_F64", "PREC_MIXED", "RANGE_SHORT",
-           "RANGE_LONG", "RANGE_BOTH", "NO_SR", "NO_QE", "KICK_NGP", "EXPORTS", "tracker_for_run", "wake_noalloc"]
+           "RANGE_LONG", "RANGE_BOTH", "NO_SR", "NO_QE", "KICK_NGP", "EXPORTS", "tracker_for_run", "wake_noalloc",
+           "Server"]
 
 PREC_F64, PREC_MIXED = 0, 1
 RANGE_SHORT, RANGE_LONG, RANGE_BOTH = 1, 2, 3
@@ -32,7 +33,9 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
-           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy"]
+           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy",
+           "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
+           "mbt_server_destroy"]
 
 
 class MBTError(RuntimeError):
@@ -54,6 +57,32 @@ class Info(ctypes.Structure):
                 ("n_particles", ctypes.c_int64), ("turn", ctypes.c_int64), ("nb", ctypes.c_int32),
                 ("nbins", ctypes.c_int32), ("n_long", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("turns_per_step", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("ring", Ring), ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("nres", ctypes.c_int), ("Rs_ohm", ctypes.POINTER(ctypes.c_double)),
+                ("fr_Hz", ctypes.POINTER(ctypes.c_double)), ("Q", ctypes.POINTER(ctypes.c_double)),
+                ("range", ctypes.POINTER(ctypes.c_int32)), ("nbins", ctypes.c_int),
+                ("half_width_sigmas", ctypes.c_double), ("nb", ctypes.c_int),
+                ("bucket", ctypes.POINTER(ctypes.c_int32)), ("current_A", ctypes.POINTER(ctypes.c_double)),
+                ("n_mp", ctypes.POINTER(ctypes.c_int64)), ("turns", ctypes.c_int64)]
+
+
+class RequestStatus(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("turns_done", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_finish", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("error", ctypes.c_char * 128)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "queued", "active",
+                                              "max_active_seen", "steps", "used_bytes", "max_bytes_seen")] + \
+               [("busy_seconds", ctypes.c_double), ("mp_turns", ctypes.c_double), ("now", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -100,6 +129,11 @@ def lib() -> ctypes.CDLL:
                                       _vp, _vp, ctypes.c_char_p, _sz], _i),
                 "mbt_batch_create": ([_P(_vp), _i, _P(_vp)], _i), "mbt_batch_track": ([_vp, _i64, _vp], _i),
                 "mbt_batch_sync": ([_vp], _i), "mbt_batch_destroy": ([_vp], None),
+                "mbt_server_create": ([_P(ServerConfig), _P(_vp)], _i),
+                "mbt_server_submit": ([_vp, _P(Request), _P(_i64)], _i),
+                "mbt_server_poll": ([_vp, _i64, _P(RequestStatus), _P(_d), _P(_d)], _i),
+                "mbt_server_wait": ([_vp, _i64, _d], _i), "mbt_server_get_stats": ([_vp, _P(ServerStats)], _i),
+                "mbt_server_destroy": ([_vp], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -308,6 +342,83 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._L.mbt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server for instability-scan requests (mbt_server_*)."""
+
+    STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, turns_per_step: int = 100):
+        self._L = lib()
+        self._h = ctypes.c_void_p()
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_active), int(turns_per_step))
+        st = self._L.mbt_server_create(ctypes.byref(cfg), ctypes.byref(self._h))
+        if st != 0:
+            raise MBTError(st, "mbt_server_create failed")
+        self._runs = {}
+
+    def submit(self, run) -> int:
+        """Queue an ``mbt_workloads.Run`` (tracked for run.turns turns); returns its id."""
+        keep = dict(
+            rs=np.ascontiguousarray([r["Rs_ohm"] for r in run.resonators] or [0.0], np.float64),
+            fr=np.ascontiguousarray([r["fr_Hz"] for r in run.resonators] or [0.0], np.float64),
+            q=np.ascontiguousarray([r["Q"] for r in run.resonators] or [0.0], np.float64),
+            rg=np.ascontiguousarray([int(r["range"]) for r in run.resonators] or [0], np.int32),
+            b=np.ascontiguousarray(run.buckets, np.int32), c=np.ascontiguousarray(run.currents_A, np.float64),
+            n=np.ascontiguousarray(run.n_mp, np.int64))
+        req = Request(ring=make_ring(run.ring), precision=int(run.precision), flags=int(run.flags),
+                      seed=int(run.seed), nres=len(run.resonators), Rs_ohm=_ptr(keep["rs"], _d),
+                      fr_Hz=_ptr(keep["fr"], _d), Q=_ptr(keep["q"], _d), range=_ptr(keep["rg"], _i32),
+                      nbins=int(run.nbins), half_width_sigmas=float(run.half_width_sigmas), nb=run.nb,
+                      bucket=_ptr(keep["b"], _i32), current_A=_ptr(keep["c"], _d), n_mp=_ptr(keep["n"], _i64),
+                      turns=int(run.turns))
+        rid = _i64()
+        st = self._L.mbt_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid))
+        if st != 0:
+            raise MBTError(st, "mbt_server_submit rejected the request")
+        self._runs[rid.value] = run
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 600.0):
+        st = self._L.mbt_server_wait(self._h, int(rid), float(timeout_s))
+        if st != 0:
+            raise MBTError(st, f"request {rid} did not complete: {self.status(rid)['error']}")
+
+    def status(self, rid: int) -> dict:
+        s = RequestStatus()
+        st = self._L.mbt_server_poll(self._h, int(rid), ctypes.byref(s), None, None)
+        if st != 0:
+            raise MBTError(st, "unknown request")
+        return dict(state=self.STATES[s.state], turns_done=s.turns_done, t_submit=s.t_submit, t_start=s.t_start,
+                    t_finish=s.t_finish, device_bytes=s.device_bytes, error=s.error.decode())
+
+    def result(self, rid: int):
+        """(final moments [nb][6], history [turns][2]) of a finished request."""
+        run = self._runs[rid]
+        fm = np.zeros((run.nb, 6), np.float64)
+        hist = np.zeros((run.turns, 2), np.float64)
+        s = RequestStatus()
+        st = self._L.mbt_server_poll(self._h, int(rid), ctypes.byref(s), _ptr(fm, _d), _ptr(hist, _d))
+        if st != 0 or s.state != 2:
+            raise MBTError(st or 4, f"request {rid} is not done")
+        return fm, hist
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._L.mbt_server_get_stats(self._h, ctypes.byref(s))
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.mbt_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -15,9 +15,12 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libmbt.so"
 INCLUDE = PKG.parent / "include"
-SOURCES = ["k_push.cu", "k_post.cu", "k_resident.cu", "api.cu"]
+SOURCES = ["k_push.cu", "k_post.cu", "k_resident.cu", "api.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE)]
+# Host code is built without floating-point contraction so that it rounds the
+# same on x86-64 and aarch64 (gcc fuses a*b+c into an FMA by default on Arm).
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I", str(INCLUDE)]
 # extra nvcc flags for tuning experiments (e.g. "-DMBT_PUSH_STAGES=2"); part of the staleness key
 EXTRA = os.environ.get("MBT_NVCC_EXTRA", "").split()
 
@@ -33,10 +36,10 @@ def _stale() -> bool:
     if not LIB.exists():
         return True
     stamp = BUILD / "flags.txt"
-    if not stamp.exists() or stamp.read_text() != " ".join(EXTRA):
+    if not stamp.exists() or stamp.read_text() != " ".join(FLAGS + EXTRA):
         return True
     t = LIB.stat().st_mtime
-    deps = list(CSRC.glob("*.cu")) + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
+    deps = [Path(__file__)] + list(CSRC.glob("*.cu")) + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
     return any(p.stat().st_mtime > t for p in deps)
 
 
@@ -70,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout)
     os.replace(tmp, LIB)
-    (BUILD / "flags.txt").write_text(" ".join(EXTRA))
+    (BUILD / "flags.txt").write_text(" ".join(FLAGS + EXTRA))
     return LIB
 
 
