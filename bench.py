@@ -14,6 +14,12 @@ long-range phasor scan, moments).  The state (468 MB) is larger than the
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank tracks its own fill (weak scaling, no data-path
 collective); rank 0 prints one JSON line.
+
+Serving: python bench.py --workload serving [--requests R] [--rate HZ]
+replays an open-loop Poisson stream of instability-scan requests (sizes
+drawn as in mbt_workloads.serving_stream) into the continuous-batching
+server and prints one JSON line with the p50/p99 latency (arrival to
+result) and the delivered throughput.
 """
 from __future__ import annotations
 
@@ -38,8 +44,8 @@ METRIC = "macro-particle-turns/s (390-bunch fill)"
 UNIT = "mp-turns/s"
 BYTES_PER_MP_TURN = 24          # tau f32 + delta f64, read + written once per turn
 FALLBACK_HBM_GBS = 6800.0
-PUSH_SOURCES = ["paper_1809_00391_gb300/csrc/k_push.cu", "paper_1809_00391_gb300/csrc/device_common.cuh",
-                "paper_1809_00391_gb300/csrc/mbt_internal.h"]
+PUSH_SOURCES = ["paper_1809_00391_gb300/csrc/k_push.cu", "paper_1809_00391_gb300/csrc/push_core.cuh",
+                "paper_1809_00391_gb300/csrc/device_common.cuh", "paper_1809_00391_gb300/csrc/mbt_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_mixed_fill390_traffic.json")
 GRAPH_TURNS = 100      # turns per captured CUDA graph
 AUTOTUNE_TURNS = 20    # timed turns per push-tile candidate
@@ -54,6 +60,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
+    ap.add_argument("--workload", choices=["fill390", "serving"], default="fill390")
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
+    ap.add_argument("--max-active", type=int, default=16, help="serving: requests tracked together")
+    ap.add_argument("--turns-per-step", type=int, default=200, help="serving: turns between admissions")
     return ap.parse_args()
 
 
@@ -217,11 +230,71 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def serving_bench(args, rank, local):
+    """Open-loop replay of a Poisson request stream into mbt_server: each
+    request is submitted at its arrival time (a host thread sleeps until
+    then); latency = result time - submission time on the server's clock."""
+    if rank != 0:
+        return 0
+    import threading
+
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    stream = W.serving_stream(args.requests, rate_hz=args.rate, seed=7)
+    work = np.array([rq.run.turns * rq.run.n_particles for rq in stream], np.float64)
+    budget = 64 << 30
+    srv = pkg.Server(hbm_budget_bytes=budget, max_active=args.max_active, turns_per_step=args.turns_per_step)
+    ids = [None] * len(stream)
+    t_wall0 = time.perf_counter()
+
+    def feeder():
+        for i, rq in enumerate(stream):
+            delay = rq.arrival_s - (time.perf_counter() - t_wall0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(rq.run)
+
+    with ClockSampler(local) as clk:
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        for rid in ids:
+            srv.wait(rid, timeout_s=3600)
+    clocks = clk.summary()
+    st = [srv.status(rid) for rid in ids]
+    lat = np.array([s["t_finish"] - s["t_submit"] for s in st])
+    queue = np.array([s["t_start"] - s["t_submit"] for s in st])
+    span = max(s["t_finish"] for s in st) - min(s["t_submit"] for s in st)
+    stats = srv.stats()
+    srv.close()
+    thr = work.sum() / span
+    line = {"metric": "serving latency p99 (instability-scan requests, open-loop Poisson stream)",
+            "value": float(np.percentile(lat, 99)), "unit": "s", "n_gpus": 1, "higher_is_better": False,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "queue_p50_s": float(np.percentile(queue, 50)), "queue_p99_s": float(np.percentile(queue, 99)),
+            "throughput": thr, "throughput_unit": UNIT, "span_s": span,
+            "busy_s": stats["busy_seconds"], "steps": stats["steps"],
+            "capacity_rate_hz": thr / work.mean(),
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Poisson stream, {args.requests} requests at {args.rate} /s (seed 7)",
+                       "mean_mp_turns_per_request": float(work.mean()), "offered_mp_turns_per_s":
+                       float(work.mean() * args.rate), "max_active": args.max_active,
+                       "turns_per_step": args.turns_per_step, "hbm_budget_bytes": budget,
+                       "max_active_seen": stats["max_active_seen"], "max_bytes_seen": stats["max_bytes_seen"]},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "serving":
+        return serving_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -239,7 +312,11 @@ def main():
     stream = torch.cuda.current_stream()
     tr = pkg.tracker_for_run(run, record_turns=max(K + Wm + G + 17 * (AUTOTUNE_TURNS + 2), 16))
     tr.init_particles(stream)
-    tile = tr.autotune(AUTOTUNE_TURNS)  # push-tile autotuner: its trial turns are real warm-up turns
+    if args.tile > 0:
+        tr.set_tile(args.tile)
+        tile = args.tile
+    else:
+        tile = tr.autotune(AUTOTUNE_TURNS)  # push-tile autotuner: its trial turns are real warm-up turns
     tr.set_graph(G)
     tr.track(max(Wm, G), stream)       # warm-up; also captures the G-turn graph
     tr.sync()

@@ -30,6 +30,54 @@ namespace mbt {
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded device waits: 2 s
 
 // ---------------------------------------------------------------------------
+// Run-constant inputs of a job, staged into shared memory before the kernel
+// waits for the push of the turn (they do not depend on it), so that the
+// dependent chain after the wait touches only data the push has just written
+// (histograms, partial sums, in L2) instead of cold lines in DRAM: after the
+// push has streamed the particle state through L2, every table the post
+// kernel reads would otherwise be a DRAM round trip on its critical path.
+// ---------------------------------------------------------------------------
+struct PostStage {
+  double2 step[kMaxLong][kBunchTile];   // a_m of the tile's bunches (tile jobs)
+  double q[kBunchTile];                 // macro-particle charge (tile jobs)
+  float qf[kBunchTile];                 // same in float (wake jobs)
+  double inv_n[kBunchTile];             // 1 / N_m (wake job of M-tile 0: moments)
+  long long n[kBunchTile];
+  int tile0[kBunchTile], ntiles[kBunchTile];
+};
+
+__device__ __forceinline__ void prefetch_l2(const void *ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
+// tabf: nlong x nbins emission factors (tile jobs), in dynamic shared memory.
+__device__ void post_stage(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, PostStage *st,
+                           float2 *tabf) {
+  const int tid = threadIdx.x;
+  const int nb = R->nb, m0 = job.bt * kBunchTile, nbt = min(kBunchTile, nb - m0);
+  if (job.type == kJobTile) {
+    const int nl = R->nlong, nbins = R->nbins;
+    for (int i = tid; i < nl * nbins; i += kPostThreads) tabf[i] = R->emis_f[i];
+    for (int i = tid; i < nl * kBunchTile; i += kPostThreads) {
+      const int r = i / kBunchTile, b = i % kBunchTile;
+      st->step[r][b] = b < nbt ? R->step[(size_t)r * nb + m0 + b] : make_double2(1.0, 0.0);
+    }
+    if (tid < kBunchTile) st->q[tid] = tid < nbt ? R->q_mp[m0 + tid] : 0.0;
+    if (tid == 32) prefetch_l2(R->carry);   // read by whichever CTA finishes last
+  } else if (tid < kBunchTile) {
+    st->qf[tid] = tid < nbt ? R->q_mp_f[m0 + tid] : 0.f;
+    if (job.sub == 0 && tid < nbt) {
+      const BunchDev bd = p.bunches[R->bunch_base + m0 + tid];
+      st->tile0[tid] = bd.tile0;
+      st->ntiles[tid] = bd.ntiles;
+      st->n[tid] = bd.n;
+      st->inv_n[tid] = R->inv_n[m0 + tid];
+    }
+  }
+  if (tid == 64) prefetch_l2(R->turn);
+}
+
+// ---------------------------------------------------------------------------
 // Tile job: moments, histogram reset, long-range emission + local scan.
 // ---------------------------------------------------------------------------
 // Per-bunch moments of the turn into the record ring (Sec. 2.4): thread
@@ -38,24 +86,33 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded device w
 // moments.  FP64 stays lane-parallel: GB300 spends ~20 FP64-pipe clocks on a
 // warp instruction whatever its active lanes.  Also zeroes the other
 // histogram buffer of these bunches (the next turn's push fills it).
+// st: the tile's staged bunch descriptors, or nullptr to read them from the plan.
 __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0, int nbt, int par, long long turn,
-                            double (*s_sum)[kBunchTile]) {
+                            double (*s_sum)[kBunchTile], const PostStage *st) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = R->nb, nbins = R->nbins;
   {
     const int b = threadIdx.x & 31, cidx = threadIdx.x >> 5;
     if (cidx < 5 && b < nbt) {
-      const BunchDev bd = p.bunches[R->bunch_base + m0 + b];
-      const double *pp = p.partial + (size_t)bd.tile0 * kPartials + cidx;
+      int tile0, ntiles;
+      if (st) {
+        tile0 = st->tile0[b];
+        ntiles = st->ntiles[b];
+      } else {
+        const BunchDev bd = p.bunches[R->bunch_base + m0 + b];
+        tile0 = bd.tile0;
+        ntiles = bd.ntiles;
+      }
+      const double *pp = p.partial + (size_t)tile0 * kPartials + cidx;
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       int i = 0;
-      for (; i + 4 <= bd.ntiles; i += 4) {
+      for (; i + 4 <= ntiles; i += 4) {
         a0 += pp[(size_t)(i + 0) * kPartials];
         a1 += pp[(size_t)(i + 1) * kPartials];
         a2 += pp[(size_t)(i + 2) * kPartials];
         a3 += pp[(size_t)(i + 3) * kPartials];
       }
-      for (; i < bd.ntiles; ++i) a0 += pp[(size_t)i * kPartials];
+      for (; i < ntiles; ++i) a0 += pp[(size_t)i * kPartials];
       s_sum[cidx][b] = (a0 + a1) + (a2 + a3);
     }
   }
@@ -63,7 +120,7 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
   for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) hz[i] = 0;
   __syncthreads();
   if (warp == 0 && lane < nbt) {
-    const double inv_n = R->inv_n[m0 + lane];
+    const double inv_n = st ? st->inv_n[lane] : R->inv_n[m0 + lane];
     const double s0 = s_sum[0][lane], s1 = s_sum[1][lane], s2 = s_sum[2][lane], s3 = s_sum[3][lane];
     const double s4 = s_sum[4][lane];
     const double mt = s0 * inv_n, md = s2 * inv_n;
@@ -74,7 +131,7 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
     rec[1] = sqrt(vt);
     rec[2] = md;
     rec[3] = sqrt(vd);
-    rec[4] = (double)p.bunches[R->bunch_base + m0 + lane].n - s4;
+    rec[4] = (double)(st ? st->n[lane] : p.bunches[R->bunch_base + m0 + lane].n) - s4;
     rec[5] = s4;
   }
 }
@@ -82,9 +139,11 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
 // Long-range emission and the tile's affine scan, per long-range resonator.
 // Emission sums sum_k count[m,k] e^{-s tau_k}: 8 threads per bunch, all 32
 // bunches of the tile at once.
+// tabf, st: staged emission table and bunch constants (kMixed), or nullptr
+// to read them from the run (kF64).
 template <int PREC>
 __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, double2 *sE,
-                         float2 *sEf) {
+                         float2 *sEf, const float2 *tabf, const PostStage *st) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = R->nb, nbins = R->nbins;
   const int m0 = job.bt * kBunchTile;
@@ -96,7 +155,7 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
       float ax = 0.f, ay = 0.f;
       if (b < nbt) {
         const int32_t *hrow = hcur + (size_t)b * nbins;
-        const float2 *tab = R->emis_f + (size_t)r * nbins;
+        const float2 *tab = (tabf ? tabf : R->emis_f) + (size_t)r * nbins;
 #pragma unroll 8
         for (int k = sub; k < nbins; k += 8) {
           const float cnt = (float)hrow[k];
@@ -137,13 +196,13 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
       double2 E = make_double2(0.0, 0.0);
       if (lane < nbt) {
         const double2 sum = PREC == kMixed ? make_double2((double)sEf[lane].x, (double)sEf[lane].y) : sE[lane];
-        const double q = R->q_mp[m];
+        const double q = st ? st->q[lane] : R->q_mp[m];
         E = cmul(R->lr_c[r], make_double2(q * sum.x, q * sum.y));
       }
       const double2 Eprev = shfl_up_d2(E, 1);
       double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
       if (lane < nbt) {
-        A = R->step[(size_t)r * nb + m];
+        A = st ? st->step[r][lane] : R->step[(size_t)r * nb + m];
         if (lane > 0) B = cmul(A, Eprev);
       }
       warp_scan_affine(A, B);
@@ -247,10 +306,12 @@ __device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, 
 // Main part: B from the turn's counts, the MMAs (issued by one thread, run
 // asynchronously), the moments of the bunch tile while they run (M-tile 0),
 // then the epilogue from tensor memory.
+// qf: the charges of the tile's 32 bunches (staged, or the run's array at
+// the tile); st: staged descriptors for the moments (or nullptr).
 template <bool WITH_MOMENTS = true>
 __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, long long turn,
                             uint8_t *smem, uint64_t *bars, uint32_t *tmem_slot, int *s_flag,
-                            double (*s_sum)[kBunchTile]) {
+                            double (*s_sum)[kBunchTile], const float *qf, const PostStage *st) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbins = R->nbins;
   const int nb = R->nb;
@@ -312,7 +373,7 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       umma_commit(&bars[1]);
     }
   }
-  if (WITH_MOMENTS && mt == 0) moments_job(p, R, m0, nbt, par, turn, s_sum);   // overlaps the MMAs
+  if (WITH_MOMENTS && mt == 0) moments_job(p, R, m0, nbt, par, turn, s_sum, st);   // overlaps the MMAs
   __syncthreads();
   const bool aborted = *s_flag != 0;
   if (!aborted && warp < 4) {
@@ -330,7 +391,7 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
 #pragma unroll
       for (int b = 0; b < kBunchTile; ++b) {
         if (b < nbt) {
-          const float q = R->q_mp_f[m0 + b];
+          const float q = qf[b];
           vsr[(size_t)(m0 + b) * nbins + j] = q * fmaf(65536.f, d2[b], fmaf(256.f, d1[b], d0[b]));
         }
       }
@@ -357,16 +418,22 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   __shared__ double2 sE[kBunchTile];
   __shared__ float2 sEf[kBunchTile];
   __shared__ double s_sum[5][kBunchTile];
+  __shared__ PostStage st;
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   trace_mark(p, 0);
-  if (job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);
+  // tile jobs keep the emission table where wake jobs keep their operands
+  float2 *tabf = reinterpret_cast<float2 *>(sm_post);
+  if (job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);   // A-image copy first
+  post_stage(p, R, job, &st, tabf);
+  __syncthreads();
   grid_dependency_wait();     // the push of this turn has completed
   grid_dependents_launch();   // the next push may start its prologue (particle prefetch)
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
-  if (job.type == kJobWake) wake_job_tc(p, R, job, par, turn, sm_post, bars, &tmem_slot, &s_flag, s_sum);
-  else tile_job<kMixed>(p, R, job, par, sE, sEf);
+  if (job.type == kJobWake)
+    wake_job_tc(p, R, job, par, turn, sm_post, bars, &tmem_slot, &s_flag, s_sum, st.qf, &st);
+  else tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
   trace_mark(p, 1);
   finish_turn(p);
   trace_mark(p, 2);
@@ -414,9 +481,9 @@ __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
     wake_job_f64(R, job, par, sm_post64);
   } else {
     const int m0 = job.bt * kBunchTile;
-    moments_job(p, R, m0, min(kBunchTile, R->nb - m0), par, turn, s_sum);
+    moments_job(p, R, m0, min(kBunchTile, R->nb - m0), par, turn, s_sum, nullptr);
     __syncthreads();
-    tile_job<kF64>(p, R, job, par, sE, sEf);
+    tile_job<kF64>(p, R, job, par, sE, sEf, nullptr, nullptr);
   }
   trace_mark(p, 1);
   finish_turn(p);
@@ -466,7 +533,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) 
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   wake_prologue(R, job, sm_wna, bars, &tmem_slot, &s_flag);
-  wake_job_tc<false>(p, R, job, 0, 0, sm_wna, bars, &tmem_slot, &s_flag, s_sum);
+  wake_job_tc<false>(p, R, job, 0, 0, sm_wna, bars, &tmem_slot, &s_flag, s_sum, R->q_mp_f + job.bt * kBunchTile,
+                     nullptr);
 }
 
 namespace {
