@@ -20,6 +20,12 @@ replays an open-loop Poisson stream of instability-scan requests (sizes
 drawn as in mbt_workloads.serving_stream) into the continuous-batching
 server and prints one JSON line with the p50/p99 latency (arrival to
 result) and the delivered throughput.
+
+L5 scan: python bench.py --workload l5scan tracks the SLS-2 L5 HOM detuning
+scan (Sec. 5: the 400 mA uniform and 3/4 fills of the h = 484 ring, 25 HOM
+frequencies across one revolution-harmonic period) as one batch and prints
+its throughput and the growth-rate table (measured, and Eq. 7 for the
+uniform fill).
 """
 from __future__ import annotations
 
@@ -62,7 +68,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
-    ap.add_argument("--workload", choices=["fill390", "serving"], default="fill390")
+    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan"], default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests tracked together")
@@ -288,6 +294,78 @@ def serving_bench(args, rank, local):
     return 0
 
 
+def l5scan_bench(args, rank, local):
+    """The L5 detuning scan as one batch: throughput of the tracking (CUDA
+    events around the batched turns) and the growth rates per detuning."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    from paper_1809_00391_gb300 import scan as S
+    pkg.build()
+    ring = W.ring_dc12c()
+    f0 = 1.0 / ring["T0_s"]
+    det = np.linspace(-600e3, 600e3, 25)
+    turns, n_mp = 6000, 5000
+    runs = W.l5_scan_runs(det, "uniform", n_mp=n_mp, turns=turns) + \
+        W.l5_scan_runs(det, "three_quarter", n_mp=n_mp, turns=turns, seed=211)
+    trackers = [pkg.tracker_for_run(r, record_turns=turns) for r in runs]
+    stream = torch.cuda.current_stream()
+    for t in trackers:
+        t.init_particles(stream)
+    b = pkg.Batch(trackers)
+    b.set_graph(GRAPH_TURNS)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        b.track(turns, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    b.sync()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    mp = sum(r.n_particles for r in runs)
+    recs = [t.moments(0, turns) for t in trackers]
+    b.close()
+    for t in trackers:
+        t.close()
+    damp = 1.0 / ring["tau_z_s"]
+    fit = (1500, 4500)   # mode fits: clear of the start-up and of the nonlinear regime
+    table = []
+    for i, df in enumerate(det):
+        ru, rq = recs[i], recs[len(det) + i]
+        eq7 = S.eq7_growth_rates(ring, ring["h"], 0.4 / ring["h"], W.L5_RS_OHM, W.L5_FR_HZ + df, W.L5_Q)
+        mu, rate = S.dominant_mode(ru, ring, *fit)
+
+        def factor(rec):
+            a = S.rms_amplitude(rec, ring)
+            return round(float(np.nanmean(a[turns - 1100:turns - 250]) / np.nanmean(a[250:1100])), 2)
+
+        amp = S.oscillation_amplitudes(rq, ring)
+        cap = 0.2 * float(np.mean(rq[:200, :, 1]))
+        fml = [S.adaptive_rate(amp[:, m], ring["T0_s"], cap=cap) for m in (0, 181, 362)]
+        table.append({"detuning_kHz": round(df / 1e3, 1),
+                      "eq7_fastest_mode": int(np.argmax(eq7)),
+                      "eq7_max_minus_damping_per_s": round(float(eq7.max() - damp), 1),
+                      "uniform_dominant_mode": mu,
+                      "uniform_dominant_mode_rate_per_s": None if np.isnan(rate) else round(rate, 1),
+                      "uniform_rms_growth_factor": factor(ru),
+                      "three_quarter_first_mid_last_per_s": [None if np.isnan(x) else round(x, 1) for x in fml],
+                      "three_quarter_rms_growth_factor": factor(rq)})
+    line = {"metric": "L5 HOM detuning scan throughput (macro-particle-turns/s)", "value": mp * turns / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": turns, "ms_per_step": ms / turns, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"SLS-2 L5 scan: {len(det)} HOM detunings x (uniform 484 + 3/4 363 bunches), "
+                                   f"{n_mp} mp per bunch, 400 mA, {turns} turns, one batch of {len(runs)} runs",
+                       "revolution_frequency_Hz": f0, "hom": {"fr_Hz": W.L5_FR_HZ, "Rs_ohm": W.L5_RS_OHM, "Q": W.L5_Q},
+                       "radiation_damping_per_s": damp, "fit_turns": list(fit)},
+            "growth_rates": table, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -295,6 +373,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "serving":
         return serving_bench(args, rank, local)
+    if args.workload == "l5scan":
+        return l5scan_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)

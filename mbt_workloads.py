@@ -130,6 +130,33 @@ def batched_runs(n_runs: int = 64, seed: int = 42, turns: int = 5000) -> List[Ru
     return runs
 
 
+# L5 longitudinal HOM of the ELETTRA-type cavity #3 at 45 C (Sec. 5).  Its
+# shunt impedance and quality factor are not given: a synthetic pair stands in,
+# sized so that the 400 mA uniform fill of the h = 484 ring shows both unstable
+# lobes and stable windows within one revolution-harmonic period of detuning.
+L5_FR_HZ = 1606.862e6
+L5_RS_OHM = 2e5
+L5_Q = 3e4
+
+
+def l5_scan_runs(detunings_Hz, fill: str = "uniform", n_mp: int = 5000, turns: int = 4000, seed: int = 11,
+                 total_current_A: float = 0.4, Rs_ohm: float = L5_RS_OHM, Q: float = L5_Q) -> List[Run]:
+    """One run per HOM detuning on the 'dc12c' ring (h = 484): the L5 mode
+    (short and long range) is the only wake; fill 'uniform' = all 484 buckets,
+    'three_quarter' = buckets 0..362; equal bunches sharing total_current_A."""
+    ring = ring_dc12c()
+    nb = ring["h"] if fill == "uniform" else 363
+    if fill not in ("uniform", "three_quarter"):
+        raise ValueError("fill must be 'uniform' or 'three_quarter'")
+    b, c, n = _fill(range(nb), total_current_A / nb, n_mp)
+    runs = []
+    for i, df in enumerate(detunings_Hz):
+        hom = dict(Rs_ohm=Rs_ohm, fr_Hz=L5_FR_HZ + float(df), Q=Q, range=RANGE_BOTH)
+        runs.append(Run(ring, [hom], b, c, n, seed=seed + i, turns=turns, precision=PREC_MIXED,
+                        name=f"L5 {fill} fill, detuning {float(df) / 1e3:+.1f} kHz"))
+    return runs
+
+
 @dataclass
 class ScanRequest:
     arrival_s: float

@@ -1,0 +1,103 @@
+"""SLS-2 L5 HOM scan (Sec. 5) on the GPU, through the C ABI: the 400 mA fills
+of the h = 484 'dc12c' ring with the L5 mode detuned across an unstable lobe
+and a stable window, every detuning tracked in one batch.
+
+* uniform fill: the measured growth rate of the fastest coupled-bunch mode
+  equals Eq. 7 (independent implementation of the physics tests) minus the
+  radiation damping rate, within 10 %;
+* stable window: no bunch amplitude grows, for the uniform and the 3/4 fill
+  (the paper's finding that the stable windows do not move with the fill);
+* 3/4 fill on the lobe: the first, middle and last bunch of the train grow;
+* the same configuration at small size against the FP64 oracle (negative
+  momentum compaction, h = 484, moments within 1e-3 of the rms).
+"""
+import numpy as np
+import pytest
+
+import mbt_workloads as W
+from physics_helpers import eq7_rate
+
+pytestmark = pytest.mark.gpu
+
+UNSTABLE = [-545e3, -535e3, -525e3]
+STABLE = 0.0
+TURNS = 6000
+FIT = (1500, 4500)   # mode fits: clear of the start-up and of the nonlinear regime
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1809_00391_gb300 as p
+    p.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def scan_results(pkg):
+    from paper_1809_00391_gb300 import scan as S
+    uni = W.l5_scan_runs(UNSTABLE + [STABLE], fill="uniform", n_mp=20000, turns=TURNS)
+    tq = W.l5_scan_runs([UNSTABLE[1], STABLE], fill="three_quarter", n_mp=20000, turns=TURNS, seed=31)
+    recs = S.track_scan(uni + tq)
+    return S, recs[:4], recs[4:]
+
+
+def _growth_factor(S, rec, ring):
+    """Ratio of the fill's rms oscillation amplitude over two synchrotron
+    periods near the end to that over two periods near the start."""
+    a = S.rms_amplitude(rec, ring)
+    return float(np.nanmean(a[TURNS - 1100:TURNS - 250]) / np.nanmean(a[250:1100]))
+
+
+def test_uniform_fill_fastest_mode_matches_eq7(scan_results):
+    S, uni, _ = scan_results
+    ring = W.ring_dc12c()
+    M, Ib = ring["h"], 0.4 / ring["h"]
+    nu = S.synchrotron_tune(ring)
+    damp = 1.0 / ring["tau_z_s"]
+    for df, rec in zip(UNSTABLE, uni[:3]):
+        fr = W.L5_FR_HZ + df
+        pred = np.array([eq7_rate(M, mu, fr, W.L5_RS_OHM, W.L5_Q, Ib, nu, ring) for mu in range(M)])
+        mu = int(np.argmax(pred))
+        meas = S.mode_growth_rates(rec, ring, *FIT)
+        assert meas[mu] == pytest.approx(pred[mu] - damp, rel=0.10), f"detuning {df / 1e3:+.0f} kHz, mode {mu}"
+        # the dominant mode at the end (well above the noise of the other modes) is the predicted one
+        dom, rate = S.dominant_mode(rec, ring, *FIT)
+        assert abs(dom - mu) <= 1 and np.isfinite(rate)
+
+
+def test_stable_window_is_stable_for_both_fills(scan_results):
+    S, uni, tq = scan_results
+    ring = W.ring_dc12c()
+    assert _growth_factor(S, uni[3], ring) < 1.5
+    assert _growth_factor(S, tq[1], ring) < 1.5
+
+
+def test_three_quarter_fill_train_grows_on_the_lobe(scan_results):
+    S, uni, tq = scan_results
+    ring = W.ring_dc12c()
+    assert _growth_factor(S, tq[0], ring) > 3.0
+    # first, middle and last bunch of the train: growth measured where each
+    # stands clear of its noise, below 20 % of the bunch length
+    amp = S.oscillation_amplitudes(tq[0], ring)
+    cap = 0.2 * float(np.mean(tq[0][:200, :, 1]))
+    rates = [S.adaptive_rate(amp[:, m], ring["T0_s"], cap=cap) for m in (0, 181, 362)]
+    _, uni_rate = S.dominant_mode(uni[1], ring, *FIT)
+    assert np.all(np.isfinite(rates)), rates
+    assert np.all(np.array(rates) > 0.3 * uni_rate), (rates, uni_rate)
+
+
+def test_l5_configuration_against_oracle(pkg, oracle_mod):
+    run = W.l5_scan_runs([UNSTABLE[1]], fill="uniform", n_mp=300, turns=30)[0]
+    tr = pkg.tracker_for_run(run, record_turns=run.turns)
+    orc = oracle_mod.OracleSim(run.ring, run.resonators, run.nbins, run.half_width_sigmas, run.buckets,
+                               run.currents_A, run.n_mp, run.seed, run.flags)
+    tr.init_particles()
+    orc.init_particles()
+    tr.track(run.turns)
+    rec_o = orc.track(run.turns)
+    rec_g = tr.moments(0, run.turns)
+    st, sd = rec_o[:, :, 1], rec_o[:, :, 3]
+    for c, s in ((0, st), (1, st), (2, sd), (3, sd)):
+        assert np.max(np.abs(rec_g[:, :, c] - rec_o[:, :, c]) / s) <= 1e-3
+    assert np.array_equal(rec_g[:, :, 4] + rec_g[:, :, 5], np.full((run.turns, run.nb), 300.0))
+    tr.close()
