@@ -101,6 +101,8 @@ def _load():
             lib.orc_wake_voltage_at.restype = _d
             lib.orc_turn.argtypes = [ctypes.c_void_p]
             lib.orc_turn.restype = _i64
+            lib.orc_add_wake_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+            lib.orc_add_wake_table.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -162,11 +164,52 @@ def wake(res: dict, t: float) -> float:
     return _load().orc_wake(ctypes.byref(r), float(t))
 
 
+Z0_OHM = 376.730313668          # impedance of free space (mu_0 c)
+C_LIGHT = 299_792_458.0
+
+
+def resistive_wall_wake(t, radius_m: float, conductivity_S_per_m: float, length_m: float) -> np.ndarray:
+    """Short-range longitudinal resistive-wall wake W(t) [V/C] of a round pipe
+    (radius b, conductivity sigma, length L), t >= 0 the delay behind the
+    source: with s = c t, s0 = (2 b^2 / (Z0 sigma))^(1/3), u = s / s0,
+      W = (4 Z0 c L / (pi b^2)) [ e^{-u} cos(sqrt(3) u) / 3
+                                  - (sqrt(2) / pi) int_0^inf x^2 e^{-x^2 u} / (x^6 + 8) dx ]
+    (K. Bane and M. Sands, 'The short-range resistive wall wakefields', 1995,
+    written in SI units); each integral by adaptive quadrature.  Positive =
+    energy loss, as the resonator wake."""
+    from scipy import integrate
+    b, sig, L = float(radius_m), float(conductivity_S_per_m), float(length_m)
+    s0 = (2.0 * b * b / (Z0_OHM * sig)) ** (1.0 / 3.0)
+    pref = 4.0 * Z0_OHM * C_LIGHT * L / (np.pi * b * b)
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    out = np.empty_like(t)
+    for i, ti in enumerate(t):
+        u = C_LIGHT * ti / s0
+        integral = integrate.quad(lambda x: x * x * np.exp(-x * x * u) / (x ** 6 + 8.0), 0.0, np.inf,
+                                  epsabs=0.0, epsrel=1e-12, limit=400)[0]
+        out[i] = pref * (np.exp(-u) * np.cos(np.sqrt(3.0) * u) / 3.0 - np.sqrt(2.0) / np.pi * integral)
+    return out
+
+
+def resistive_wall_table(radius_m: float, conductivity_S_per_m: float, length_m: float, t_max: float):
+    """(t, W) samples of resistive_wall_wake on [0, t_max]: uniform to 20 s0/c
+    (the oscillating head), geometric beyond (the t^-3/2 tail)."""
+    s0 = (2.0 * radius_m ** 2 / (Z0_OHM * conductivity_S_per_m)) ** (1.0 / 3.0)
+    t1 = 20.0 * s0 / C_LIGHT
+    t = np.linspace(0.0, t1, 2001)
+    if t_max > t1:
+        t = np.concatenate([t, np.geomspace(t1, t_max, 3000)[1:]])
+    return t, resistive_wall_wake(t, radius_m, conductivity_S_per_m, length_m)
+
+
 class OracleSim:
-    """Plain FP64 multi-bunch tracker (one run)."""
+    """Plain FP64 multi-bunch tracker (one run).  wake_tables: extra
+    short-range wakes as (t, W) samples; resistive_wall: round pipes as dicts
+    radius_m, conductivity_S_per_m, length_m (tabulated here with
+    resistive_wall_table)."""
 
     def __init__(self, ring: dict, resonators: list, nbins: int, half_width_sigmas: float,
-                 buckets, currents_A, n_mp, seed: int, flags: int = 0):
+                 buckets, currents_A, n_mp, seed: int, flags: int = 0, wake_tables=(), resistive_wall=()):
         self._lib = _load()
         self.nb = len(buckets)
         self.nbins = int(nbins)
@@ -183,6 +226,17 @@ class OracleSim:
                                        _ptr(self.n_mp, _i64))
         if not self._h:
             raise ValueError("oracle rejected the configuration")
+        tables = list(wake_tables)
+        if resistive_wall:
+            t_max = (self.nbins + 1) * self.derived["Delta"]
+            for rw in resistive_wall:
+                tables.append(resistive_wall_table(rw["radius_m"], rw["conductivity_S_per_m"], rw["length_m"],
+                                                   t_max))
+        for t, w in tables:
+            t = np.ascontiguousarray(t, np.float64)
+            w = np.ascontiguousarray(w, np.float64)
+            if self._lib.orc_add_wake_table(self._h, len(t), _ptr(t, _d), _ptr(w, _d)) != 0:
+                raise ValueError("wake table needs t[0] = 0 and increasing samples")
 
     def close(self):
         if getattr(self, "_h", None):

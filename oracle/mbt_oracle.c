@@ -45,7 +45,9 @@
  *      consecutive particles, counter (quad, bunch, turn, tag), key (seed lo,
  *      seed hi), each 32-bit word a uniform (w + 1/2) 2^-32;
  *   R10 the long-range wake of a passage is sourced by its binned histogram at
- *      cell centres, and acts on every particle of every later passage.
+ *      cell centres, and acts on every particle of every later passage;
+ *   R11 a tabulated short-range wake (e.g. the resistive wall) acts through
+ *      its average over each lag cell (see orc_add_wake_table).
  */
 #include <complex.h>
 #include <math.h>
@@ -289,6 +291,45 @@ orc_sim *orc_create(const orc_ring *ring, int flags, uint64_t seed,
     s->nhist = any_long ? (int)ceil(-log(ORC_HISTORY_CUTOFF) / (amin * ring->T0_s)) + 2 : 1;
     s->Ehist = (double complex *)calloc((size_t)(nres > 0 ? nres : 1) * s->nhist * nb, sizeof(double complex));
     return s;
+}
+
+/* A tabulated short-range wake W(t) (V/C), given at n samples t[0] = 0 <
+ * t[1] < ... (s): linear between samples, zero beyond the last one.  It acts
+ * on the mesh through its average over each lag cell (reading R11):
+ *   lag l >= 1: (1/Delta) * integral of W over [(l - 1/2) Delta, (l + 1/2) Delta],
+ *   lag 0:      (1/Delta) * integral of W over [0, Delta / 2]
+ * (for a smooth W these are W(l Delta) and W(0+)/2 up to O(Delta^2)), added
+ * to the resonators' lag wake.  The integrals are exact for the piecewise
+ * linear W. */
+static double table_integral(int n, const double *t, const double *W, double lo, double hi)
+{
+    double acc = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+        double a = t[i] > lo ? t[i] : lo;
+        double b = t[i + 1] < hi ? t[i + 1] : hi;
+        if (b <= a)
+            continue;
+        double slope = (W[i + 1] - W[i]) / (t[i + 1] - t[i]);
+        double wa = W[i] + slope * (a - t[i]);
+        double wb = W[i] + slope * (b - t[i]);
+        acc += 0.5 * (wa + wb) * (b - a);
+    }
+    return acc;
+}
+
+int orc_add_wake_table(orc_sim *s, int n, const double *t, const double *W)
+{
+    if (n < 2 || t[0] != 0.0)
+        return -1;
+    for (int i = 0; i + 1 < n; ++i)
+        if (!(t[i + 1] > t[i]))
+            return -1;
+    for (int l = 0; l < s->nbins; ++l) {
+        double lo = l == 0 ? 0.0 : ((double)l - 0.5) * s->Delta;
+        double hi = ((double)l + 0.5) * s->Delta;
+        s->Wlag[l] += table_integral(n, t, W, lo, hi) / s->Delta;
+    }
+    return 0;
 }
 
 void orc_destroy(orc_sim *s)

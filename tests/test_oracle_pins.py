@@ -514,3 +514,90 @@ def test_four_bunch_mode_eq7(oracle_mod):
     assert _rate(X[3], 0, 600) == pytest.approx(pred[3], rel=0.05)
     assert abs(_rate(X[0], 1000, 2000)) < 0.1 * pred[1]
     assert abs(_rate(X[2], 1000, 2000)) < 0.1 * pred[1]
+
+
+# ----------------------------------------------------------------------------- tabulated wakes, resistive wall
+RW = dict(radius_m=0.01, conductivity_S_per_m=5.8e7, length_m=290.4)   # copper, 10 mm, the dc12c circumference
+
+
+def _rw_consts():
+    b, sig, L = RW["radius_m"], RW["conductivity_S_per_m"], RW["length_m"]
+    Z0, c = 376.730313668, 299792458.0
+    s0 = (2 * b * b / (Z0 * sig)) ** (1 / 3)
+    tail = c * L / (4 * math.pi * b) * math.sqrt(Z0 / (math.pi * sig))   # W ~ -tail (c t)^(-3/2)
+    return b, sig, L, Z0, c, s0, tail
+
+
+def test_resistive_wall_head_value(oracle_mod):
+    """W(0+) = Z0 c L / (pi b^2), independent of the conductivity."""
+    b, sig, L, Z0, c, s0, tail = _rw_consts()
+    w0 = oracle_mod.resistive_wall_wake([0.0], b, sig, L)[0]
+    assert w0 == pytest.approx(Z0 * c * L / (math.pi * b * b), rel=1e-9)
+    w0b = oracle_mod.resistive_wall_wake([0.0], b, 10 * sig, L)[0]
+    assert w0b == pytest.approx(w0, rel=1e-9)
+
+
+def test_resistive_wall_long_range_tail(oracle_mod):
+    """Far behind the head (s >> s0) the classic resistive-wall wake
+    W = -(c L / (4 pi b)) sqrt(Z0 / (pi sigma)) s^(-3/2)."""
+    b, sig, L, Z0, c, s0, tail = _rw_consts()
+    for u in (50.0, 200.0):
+        t = u * s0 / c
+        w = oracle_mod.resistive_wall_wake([t], b, sig, L)[0]
+        assert w == pytest.approx(-tail * (c * t) ** -1.5, rel=2e-4)
+
+
+def test_resistive_wall_wake_integrates_to_zero(oracle_mod):
+    """A resistive wall has no impedance at zero frequency, so the wake
+    integrates to zero: the integral up to T equals minus the tail beyond T."""
+    b, sig, L, Z0, c, s0, tail = _rw_consts()
+    T = 500 * s0 / c
+    t, w = oracle_mod.resistive_wall_table(b, sig, L, T)
+    head = np.trapezoid(w, t)
+    beyond = -tail * 2.0 * (c * T) ** -0.5 / c     # integral of -tail (c t)^(-3/2) dt from T to infinity
+    scale = np.trapezoid(np.abs(w), t)
+    assert abs(head + beyond) < 2e-4 * scale
+
+
+def test_wake_table_cell_averages_are_exact_for_a_linear_wake(oracle_mod):
+    """A linear table A + B t on [0, T]: lag l >= 1 gets its cell average, lag 0
+    the integral over the half cell / Delta, lags past T nothing."""
+    s = _sim(oracle_mod, nbins=64)
+    D = s.derived["Delta"]
+    A, B, T = 3.0e12, -2.0e23, 20.5 * D
+    t = np.linspace(0.0, T, 7)
+    s2 = _sim(oracle_mod, nbins=64)
+    base = s2.wlag()
+    s3 = oracle_mod.OracleSim(W.ring_r0(), [], 64, 5.0, [0], [0.0], [2], 1, 0, wake_tables=[(t, A + B * t)])
+    got = s3.wlag() - base
+    for l in range(64):
+        lo, hi = (0.0 if l == 0 else (l - 0.5) * D), min((l + 0.5) * D, T)
+        exact = 0.0 if hi <= lo else (A * (hi - lo) + 0.5 * B * (hi * hi - lo * lo)) / D
+        assert got[l] == pytest.approx(exact, rel=1e-12, abs=1e-3)
+    assert got[0] == pytest.approx(A / 2 + B * D / 8, rel=1e-12)
+    assert np.all(got[21:] == 0.0)
+
+
+def test_wake_table_of_a_resonator_differs_by_the_cell_curvature(oracle_mod):
+    """The broadband resonator given as a fine table: cell averages differ from
+    the resonator's point samples by (Delta^2 / 24) W''(l Delta) (lag 0: W'(0)
+    Delta / 8 + W''(0) Delta^2 / 48), to fourth order."""
+    res = dict(W.BROADBAND)
+    s = _sim(oracle_mod, res=[res], nbins=256)
+    point = s.wlag()
+    D = s.derived["Delta"]
+    wr = 2 * math.pi * res["fr_Hz"]
+    a = wr / (2 * res["Q"])
+    wb = math.sqrt(wr * wr - a * a)
+    Rs = res["Rs_ohm"]
+    tt = np.linspace(0.0, 258 * D, 258 * 400 + 1)
+    Wt = 2 * a * Rs * np.exp(-a * tt) * (np.cos(wb * tt) - (a / wb) * np.sin(wb * tt))
+    tab = oracle_mod.OracleSim(W.ring_r0(), [], 256, 5.0, [0], [0.0], [2], 1, 0, wake_tables=[(tt, Wt)]).wlag()
+    # derivatives of W(t) = Re(C e^{s t}), s = -a + i wb, C = 2 a Rs (1 + i a / wb)
+    sc = complex(-a, wb)
+    C = 2 * a * Rs * complex(1.0, a / wb)
+    l = np.arange(1, 256)
+    w2 = (C * sc * sc * np.exp(sc * l * D)).real
+    assert np.max(np.abs(tab[1:] - point[1:] - D * D / 24 * w2)) < 1e-3 * np.max(np.abs(point))
+    w1_0, w2_0 = (C * sc).real, (C * sc * sc).real
+    assert tab[0] - point[0] == pytest.approx(w1_0 * D / 8 + w2_0 * D * D / 48, rel=2e-2)
