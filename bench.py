@@ -26,6 +26,12 @@ scan (Sec. 5: the 400 mA uniform and 3/4 fills of the h = 484 ring, 25 HOM
 frequencies across one revolution-harmonic period) as one batch and prints
 its throughput and the growth-rate table (measured, and Eq. 7 for the
 uniform fill).
+
+Resistive-wall current scan: python bench.py --workload rwscan tracks a
+single bunch of the 'dc12c' ring in the short-range resistive-wall wake of a
+copper pipe of 10 mm radius around the ring (Sec. 3) at 12 currents, one
+batch, 50 000 turns, and prints the 'equilibrium' bunch length and energy
+spread (averages over the last 5000 turns) per current.
 """
 from __future__ import annotations
 
@@ -68,7 +74,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
-    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan"], default="fill390")
+    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan"], default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests tracked together")
@@ -366,6 +372,62 @@ def l5scan_bench(args, rank, local):
     return 0
 
 
+def rwscan_bench(args, rank, local):
+    """Single-bunch current scan in the resistive-wall wake, one batch."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    ring = W.ring_dc12c()
+    rw = dict(radius_m=0.01, conductivity_S_per_m=5.8e7, length_m=290.4)
+    currents_mA = [0.1, 0.5, 1, 2, 3, 5, 7.5, 10, 15, 20, 30, 40]
+    turns, n_mp, hw, last = 50_000, 100_000, 10.0, 5000
+    runs = []
+    for k, I in enumerate(currents_mA):
+        b, c, n = W._fill([0], I * 1e-3, n_mp)
+        runs.append(W.Run(ring, [], b, c, n, seed=700 + k, turns=turns, precision=W.PREC_MIXED,
+                          half_width_sigmas=hw, resistive_wall=[dict(rw)], name=f"rw {I} mA"))
+    trackers = [pkg.tracker_for_run(r, record_turns=turns) for r in runs]
+    stream = torch.cuda.current_stream()
+    for t in trackers:
+        t.init_particles(stream)
+    b = pkg.Batch(trackers)
+    b.set_graph(GRAPH_TURNS)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        b.track(turns, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    b.sync()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    table = []
+    for I, r, t in zip(currents_mA, runs, trackers):
+        rec = t.moments(turns - last, last)[:, 0, :]
+        table.append({"current_mA": I, "sigma_tau_ps": round(float(rec[:, 1].mean()) * 1e12, 4),
+                      "sigma_tau_spread_ps": round(float(rec[:, 1].std()) * 1e12, 4),
+                      "sigma_delta_over_sigma_E": round(float(rec[:, 3].mean()) / ring["sigma_delta"], 5),
+                      "centroid_ps": round(float(rec[:, 0].mean()) * 1e12, 4),
+                      "outside_fraction": round(float(rec[:, 5].mean()) / n_mp, 6)})
+    b.close()
+    for t in trackers:
+        t.close()
+    mp = sum(r.n_particles for r in runs)
+    line = {"metric": "resistive-wall current scan throughput (macro-particle-turns/s)",
+            "value": mp * turns / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": turns, "ms_per_step": ms / turns,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"dc12c single bunch x {len(runs)} currents ({n_mp} mp), copper pipe b = 10 mm "
+                                   f"around the ring, {turns} turns, one batch; mesh 256 cells over +-{hw} sigma",
+                       "equilibrium": f"averages over the last {last} turns", "sigma_E": ring["sigma_delta"]},
+            "scan": table, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -375,6 +437,8 @@ def main():
         return serving_bench(args, rank, local)
     if args.workload == "l5scan":
         return l5scan_bench(args, rank, local)
+    if args.workload == "rwscan":
+        return rwscan_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)

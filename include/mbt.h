@@ -134,6 +134,29 @@ const char *mbt_last_error(const mbt_ctx *ctx);
  * mbt_set_fill. */
 mbt_status mbt_add_resonator(mbt_ctx *ctx, double Rs_ohm, double fr_Hz, double Q, int range);
 
+/* Add a tabulated short-range wake (Sec. 2.3: other wakes, such as the
+ * resistive wall, are added to the same wake).  W_V_per_C[i] is W(t_s[i]) in
+ * V/C (positive = energy loss), t_s[0] = 0 (W(0+)) and t_s strictly
+ * increasing; W is linear between samples and zero beyond the last one.  It
+ * acts on the mesh through its average over each lag cell: lag l >= 1 gets
+ * (1/Delta) times the integral of W over [(l - 1/2) Delta, (l + 1/2) Delta],
+ * lag 0 the integral over [0, Delta / 2] (the half value of W(0+) for a
+ * smooth wake), so a wake whose head is much shorter than a cell keeps its
+ * integral.  Short range only.  The arrays are copied.  Only before
+ * mbt_set_fill; at most 8 tables. */
+mbt_status mbt_add_wake_table(mbt_ctx *ctx, int n, const double *t_s, const double *W_V_per_C);
+
+/* Add the short-range longitudinal resistive-wall wake of a round pipe of
+ * radius_m, wall conductivity_S_per_m and length_m (no counterpart call in the
+ * paper, whose resistive-wall test is a copper pipe of 10 mm radius around
+ * the ring): with s = c t, s0 = (2 b^2 / (Z0 sigma))^(1/3), u = s / s0,
+ *   W(t) = (4 Z0 c L / (pi b^2)) [ e^{-u} cos(sqrt(3) u) / 3
+ *                                  - (sqrt(2) / pi) int_0^inf x^2 e^{-x^2 u} / (x^6 + 8) dx ]
+ * (Bane and Sands, 1995), applied through its cell averages like
+ * mbt_add_wake_table (computed from the closed form, not from samples).
+ * All arguments > 0.  Only before mbt_set_fill; at most 8 pipes. */
+mbt_status mbt_add_resistive_wall(mbt_ctx *ctx, double radius_m, double conductivity_S_per_m, double length_m);
+
 /* Longitudinal mesh (Sec. 2.3): nbins cells over [-H, H), H =
  * half_width_sigmas * sigma_tau0 with sigma_tau0 = |alpha_c| sigma_E T0 /
  * (2 pi nu_s).  MBT_PREC_F64: 2 <= nbins <= 1024.  MBT_PREC_MIXED: nbins 128

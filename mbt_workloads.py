@@ -66,6 +66,8 @@ class Run:
     nbins: int = 256
     half_width_sigmas: float = 5.0
     name: str = ""
+    wake_tables: list = field(default_factory=list)      # [(t [s], W [V/C])] short range
+    resistive_wall: list = field(default_factory=list)   # [dict(radius_m, conductivity_S_per_m, length_m)]
 
     @property
     def nb(self) -> int:

@@ -193,10 +193,12 @@ def resistive_wall_wake(t, radius_m: float, conductivity_S_per_m: float, length_
 
 def resistive_wall_table(radius_m: float, conductivity_S_per_m: float, length_m: float, t_max: float):
     """(t, W) samples of resistive_wall_wake on [0, t_max]: uniform to 20 s0/c
-    (the oscillating head), geometric beyond (the t^-3/2 tail)."""
+    (the oscillating head, 500 samples per s0/c: the linear interpolant's
+    integral over a cell is then within ~1e-6 of the wake's), geometric beyond
+    (the t^-3/2 tail)."""
     s0 = (2.0 * radius_m ** 2 / (Z0_OHM * conductivity_S_per_m)) ** (1.0 / 3.0)
     t1 = 20.0 * s0 / C_LIGHT
-    t = np.linspace(0.0, t1, 2001)
+    t = np.linspace(0.0, t1, 10001)
     if t_max > t1:
         t = np.concatenate([t, np.geomspace(t1, t_max, 3000)[1:]])
     return t, resistive_wall_wake(t, radius_m, conductivity_S_per_m, length_m)

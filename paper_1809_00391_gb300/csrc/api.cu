@@ -6,6 +6,7 @@
 // wake tables are computed here in double precision from the paper's
 // definitions (Sec. 2.2 Eqs. 1, 2, 5; Sec. 2.3 Eq. 6).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -110,6 +111,9 @@ struct mbt_ctx {
   float2 *d_emis_f = nullptr;
   void *d_toep = nullptr;
   size_t device_bytes = 0;
+  // tabulated short-range wakes (t, W) and resistive-wall pipes (b, sigma, L)
+  std::vector<std::vector<double>> wt_t, wt_w;
+  std::vector<std::array<double, 3>> rwalls;
   RunDev rundev{};
   PlanStore own;
   int tile = kMixedTile;       // particles per push CTA (mixed precision)
@@ -232,6 +236,58 @@ double wake(const Resonator &q, double t) {
   if (t < 0.0) return 0.0;
   if (t == 0.0) return a * q.Rs;
   return 2.0 * a * q.Rs * std::exp(-a * t) * (std::cos(wb * t) - (a / wb) * std::sin(wb * t));
+}
+
+// Integral over [lo, hi] of the piecewise linear wake through (t[i], w[i]),
+// zero beyond the last sample.
+double table_integral(const std::vector<double> &t, const std::vector<double> &w, double lo, double hi) {
+  double acc = 0.0;
+  for (size_t i = 0; i + 1 < t.size(); ++i) {
+    const double a = std::max(t[i], lo), b = std::min(t[i + 1], hi);
+    if (!(b > a)) continue;
+    const double k = (w[i + 1] - w[i]) / (t[i + 1] - t[i]);
+    acc += 0.5 * ((w[i] + k * (a - t[i])) + (w[i] + k * (b - t[i]))) * (b - a);
+  }
+  return acc;
+}
+
+// Adaptive Simpson quadrature of f over [a, b] to absolute tolerance eps.
+template <class F>
+double simpson(F &f, double a, double b, double fa, double fm, double fb, double whole, double eps, int depth) {
+  const double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  const double flm = f(lm), frm = f(rm);
+  const double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm), right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  if (depth <= 0 || std::fabs(left + right - whole) <= 15.0 * eps) return left + right + (left + right - whole) / 15.0;
+  return simpson(f, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) + simpson(f, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+// Integral over t in [ta, tb] (s) of the resistive-wall wake of a round pipe
+// (radius b, conductivity sigma, length L) in the short-range form
+// W = (4 Z0 c L / (pi b^2)) [e^{-u} cos(sqrt3 u) / 3 - (sqrt2 / pi) int x^2 e^{-x^2 u} / (x^6 + 8) dx],
+// u = c t / s0, s0 = (2 b^2 / (Z0 sigma))^(1/3).  In u the first term has the
+// antiderivative e^{-u} (sqrt3 sin(sqrt3 u) - cos(sqrt3 u)) / 4; the second,
+// integrated over u first, is int_0^inf (e^{-x^2 ua} - e^{-x^2 ub}) / (x^6 + 8) dx
+// (adaptive Simpson on [0, 40] split at x = 2^-10, 2^-9, ... so that the
+// narrow peak near x = 0 of a large u is resolved; the rest beyond 40 is
+// below 2e-9 of the lag-0 value).
+double rw_integral(double b, double sigma, double L, double ta, double tb) {
+  constexpr double kZ0 = 376.730313668, kC = 299792458.0;
+  const double s0 = std::cbrt(2.0 * b * b / (kZ0 * sigma));
+  const double ua = kC * ta / s0, ub = kC * tb / s0;
+  const double r3 = std::sqrt(3.0);
+  auto P = [&](double u) { return std::exp(-u) * (r3 * std::sin(r3 * u) - std::cos(r3 * u)) / 4.0; };
+  auto g = [&](double x) {
+    const double x2 = x * x;
+    return (std::exp(-x2 * ua) - std::exp(-x2 * ub)) / (x2 * x2 * x2 + 8.0);
+  };
+  double G = 0.0, x0 = 0.0, x1 = std::ldexp(1.0, -10);
+  while (x0 < 40.0) {
+    const double fa = g(x0), fm = g(0.5 * (x0 + x1)), fb = g(x1);
+    G += simpson(g, x0, x1, fa, fm, fb, (x1 - x0) / 6.0 * (fa + 4.0 * fm + fb), 1e-17, 40);
+    x0 = x1;
+    x1 = std::min(40.0, 2.0 * x1);
+  }
+  return 4.0 * kZ0 * L * s0 / (kPi * b * b) * ((P(ub) - P(ua)) / 3.0 - std::sqrt(2.0) / kPi * G);
 }
 
 // Upload a plan built in st's host vectors.
@@ -447,6 +503,32 @@ mbt_status mbt_add_resonator(mbt_ctx *c, double Rs, double fr, double Q, int ran
   return MBT_OK;
 }
 
+mbt_status mbt_add_wake_table(mbt_ctx *c, int n, const double *t, const double *w) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "wake tables must be added before mbt_set_fill");
+  if (n < 2 || !t || !w || t[0] != 0.0) return fail(c, MBT_ERR_ARG, "a wake table needs n >= 2 samples from t = 0");
+  for (int i = 0; i < n; ++i) {
+    if (!std::isfinite(t[i]) || !std::isfinite(w[i])) return fail(c, MBT_ERR_ARG, "wake table sample %d is not finite", i);
+    if (i > 0 && !(t[i] > t[i - 1])) return fail(c, MBT_ERR_ARG, "wake table times must increase strictly");
+  }
+  if (c->wt_t.size() >= 8) return fail(c, MBT_ERR_UNSUPPORTED, "at most 8 wake tables");
+  c->wt_t.emplace_back(t, t + n);
+  c->wt_w.emplace_back(w, w + n);
+  return MBT_OK;
+}
+
+mbt_status mbt_add_resistive_wall(mbt_ctx *c, double b, double sigma, double L) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "resistive walls must be added before mbt_set_fill");
+  if (!(b > 0) || !(sigma > 0) || !(L > 0) || !std::isfinite(b) || !std::isfinite(sigma) || !std::isfinite(L))
+    return fail(c, MBT_ERR_ARG, "a resistive wall needs radius, conductivity and length > 0");
+  if (c->rwalls.size() >= 8) return fail(c, MBT_ERR_UNSUPPORTED, "at most 8 resistive walls");
+  c->rwalls.push_back({b, sigma, L});
+  return MBT_OK;
+}
+
 mbt_status mbt_set_grid(mbt_ctx *c, int nbins, double hw) {
   if (!c) return MBT_ERR_ARG;
   c->err.clear();
@@ -560,6 +642,13 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   for (int l = 0; l < nbins; ++l)
     for (auto &r : c->res)
       if (r.range & MBT_RANGE_SHORT) lag[l] += wake(r, (double)l * c->Delta);
+  // tabulated wakes and resistive walls: averages over the lag cells
+  // [(l - 1/2) Delta, (l + 1/2) Delta], the half cell [0, Delta / 2] at lag 0
+  for (int l = 0; l < nbins; ++l) {
+    const double lo = l == 0 ? 0.0 : ((double)l - 0.5) * c->Delta, hi = ((double)l + 0.5) * c->Delta;
+    for (size_t i = 0; i < c->wt_t.size(); ++i) lag[l] += table_integral(c->wt_t[i], c->wt_w[i], lo, hi) / c->Delta;
+    for (auto &rw : c->rwalls) lag[l] += rw_integral(rw[0], rw[1], rw[2], lo, hi) / c->Delta;
+  }
   {
     std::vector<float> lagf(nbins);
     for (int l = 0; l < nbins; ++l) lagf[l] = (float)lag[l];
