@@ -56,6 +56,11 @@ class Resonator(ctypes.Structure):
                 ("range", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
+class Harmonic(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("pad_", ctypes.c_int32), ("V_V", ctypes.c_double),
+                ("phi_rad", ctypes.c_double)]
+
+
 _P = ctypes.POINTER
 _d = ctypes.c_double
 _i32 = ctypes.c_int32
@@ -80,6 +85,10 @@ def _load():
             lib.orc_create.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator),
                                        ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
             lib.orc_create.restype = ctypes.c_void_p
+            lib.orc_create_h.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator), ctypes.c_int,
+                                         _P(Harmonic), ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
+            lib.orc_create_h.restype = ctypes.c_void_p
+            lib.orc_derive_h.argtypes = [_P(Ring), ctypes.c_int, ctypes.c_int, _P(Harmonic), _P(_d)]
             lib.orc_destroy.argtypes = [ctypes.c_void_p]
             lib.orc_get_derived.argtypes = [ctypes.c_void_p, _P(_d)]
             lib.orc_init_particles.argtypes = [ctypes.c_void_p]
@@ -159,6 +168,24 @@ def derive(ring: dict, flags: int = 0) -> dict:
     return {k: out[i] for i, k in enumerate(keys)}
 
 
+def make_harmonic(hc: dict) -> Harmonic:
+    return Harmonic(n=int(hc["n"]), pad_=0, V_V=float(hc["V_V"]), phi_rad=float(hc["phi_rad"]))
+
+
+def derive_h(ring: dict, harmonic_cavities=(), flags: int = 0) -> dict:
+    """Derived quantities with harmonic cavities (the main cavity's phase
+    balances U0 against them)."""
+    lib = _load()
+    r = make_ring(ring)
+    hs = list(harmonic_cavities)
+    ha = (Harmonic * max(1, len(hs)))(*[make_harmonic(hc) for hc in hs])
+    out = (_d * 12)()
+    lib.orc_derive_h(ctypes.byref(r), int(flags), len(hs), ha, out)
+    keys = ["T_rf", "omega_rf", "phi_s", "sin_phi_s", "U0_over_E0", "V_over_E0", "D", "qe_amp", "nu_s",
+            "sigma_tau0"]
+    return {k: out[i] for i, k in enumerate(keys)}
+
+
 def wake(res: dict, t: float) -> float:
     r = make_resonator(res)
     return _load().orc_wake(ctypes.byref(r), float(t))
@@ -211,7 +238,8 @@ class OracleSim:
     resistive_wall_table)."""
 
     def __init__(self, ring: dict, resonators: list, nbins: int, half_width_sigmas: float,
-                 buckets, currents_A, n_mp, seed: int, flags: int = 0, wake_tables=(), resistive_wall=()):
+                 buckets, currents_A, n_mp, seed: int, flags: int = 0, wake_tables=(), resistive_wall=(),
+                 harmonic_cavities=()):
         self._lib = _load()
         self.nb = len(buckets)
         self.nbins = int(nbins)
@@ -222,8 +250,10 @@ class OracleSim:
         self.buckets = np.ascontiguousarray(buckets, dtype=np.int32)
         self.currents = np.ascontiguousarray(currents_A, dtype=np.float64)
         self.n_mp = np.ascontiguousarray(n_mp, dtype=np.int64)
-        self._h = self._lib.orc_create(ctypes.byref(self._ring), int(flags), int(seed), self.nres, ra,
-                                       self.nbins, float(half_width_sigmas), self.nb,
+        self.harmonics = list(harmonic_cavities)
+        ha = (Harmonic * max(1, len(self.harmonics)))(*[make_harmonic(hc) for hc in self.harmonics])
+        self._h = self._lib.orc_create_h(ctypes.byref(self._ring), int(flags), int(seed), self.nres, ra,
+                                         len(self.harmonics), ha, self.nbins, float(half_width_sigmas), self.nb,
                                        _ptr(self.buckets, _i32), _ptr(self.currents, _d),
                                        _ptr(self.n_mp, _i64))
         if not self._h:

@@ -47,7 +47,9 @@
  *   R10 the long-range wake of a passage is sourced by its binned histogram at
  *      cell centres, and acts on every particle of every later passage;
  *   R11 a tabulated short-range wake (e.g. the resistive wall) acts through
- *      its average over each lag cell (see orc_add_wake_table).
+ *      its average over each lag cell (see orc_add_wake_table);
+ *   R14 harmonic cavities add (V_h/E0) sin(phi_h - n_h omega_rf tau) each;
+ *      the main cavity's phase balances U0 (see orc_derive_h).
  */
 #include <complex.h>
 #include <math.h>
@@ -147,6 +149,18 @@ typedef struct {
     int32_t pad_;
 } orc_resonator;
 
+/* An active harmonic RF cavity: voltage V_V at n times the RF frequency,
+ * phase phi_rad at the synchronous particle; it adds
+ * (V_V/E0) sin(phi_rad - n omega_rf tau) to the energy change of a turn. */
+typedef struct {
+    int32_t n;
+    int32_t pad_;
+    double V_V;
+    double phi_rad;
+} orc_harmonic;
+
+#define ORC_MAX_HARM 4
+
 /* Derived ring quantities, reading R4/R5 and the linear synchrotron motion. */
 typedef struct {
     double T_rf, omega_rf, phi_s, sin_phi_s, U0_over_E0, V_over_E0;
@@ -156,14 +170,23 @@ typedef struct {
     double sigma_tau0;   /* matched rms arrival-time spread            */
 } orc_derived;
 
-void orc_derive(const orc_ring *r, int flags, orc_derived *d)
+/* With harmonic cavities (reading R14) the main cavity's phase makes the
+ * synchronous particle lose nothing on average:
+ *   V sin(phi_s) + sum_h V_h sin(phi_h) = U0,
+ * and nu_s, sigma_tau0 (the mesh unit and the matched start) come from the
+ * main cavity's slope V cos(phi_s) alone: the small-amplitude tune of a
+ * double-RF system can vanish (flat potential). */
+void orc_derive_h(const orc_ring *r, int flags, int nharm, const orc_harmonic *harm, orc_derived *d)
 {
     const double pi = 3.14159265358979323846264338327950;
     int sr = !(flags & ORC_NO_SR);
     double U0 = sr ? r->U0_eV : 0.0;
+    double Uh = 0.0;
+    for (int k = 0; k < nharm; ++k)
+        Uh += harm[k].V_V * sin(harm[k].phi_rad);
     d->T_rf = r->T0_s / (double)r->h;
     d->omega_rf = 2.0 * pi * (double)r->h / r->T0_s;
-    d->sin_phi_s = U0 / r->V_rf_V;
+    d->sin_phi_s = (U0 - Uh) / r->V_rf_V;
     d->phi_s = asin(d->sin_phi_s);
     if (r->alpha_c < 0.0)
         d->phi_s = pi - d->phi_s;
@@ -173,6 +196,11 @@ void orc_derive(const orc_ring *r, int flags, orc_derived *d)
     d->qe_amp = (sr && !(flags & ORC_NO_QE)) ? r->sigma_delta * sqrt(2.0 * d->D) : 0.0;
     d->nu_s = sqrt(r->alpha_c * (double)r->h * r->V_rf_V * cos(d->phi_s) / (2.0 * pi * r->E0_eV));
     d->sigma_tau0 = fabs(r->alpha_c) * r->sigma_delta * r->T0_s / (2.0 * pi * d->nu_s);
+}
+
+void orc_derive(const orc_ring *r, int flags, orc_derived *d)
+{
+    orc_derive_h(r, flags, 0, NULL, d);
 }
 
 /* Resonator constants: decay rate a = w_r/(2Q), damped frequency wb. */
@@ -217,6 +245,9 @@ typedef struct orc_sim {
     int32_t *hist;         /* [nb][nbins], this turn                         */
     int64_t *out_count;    /* [nb], this turn                                */
     double *Wlag;          /* [nbins] summed short-range wake at lag l*Delta */
+    int nharm;
+    orc_harmonic harm[ORC_MAX_HARM];
+    double harm_VoE0[ORC_MAX_HARM], harm_nw[ORC_MAX_HARM];
     double *Vsr;           /* [nb][nbins] short-range voltage for the kick   */
     double complex *Alr;   /* [nres][nb] long-range amplitude for the kick   */
     /* emission history for the direct long-range sum: [nres][nhist][nb]     */
@@ -229,18 +260,28 @@ typedef struct orc_sim {
 /* e^{-a dt} below this is dropped from the direct history sum. */
 static const double ORC_HISTORY_CUTOFF = 1e-18;
 
-orc_sim *orc_create(const orc_ring *ring, int flags, uint64_t seed,
-                    int nres, const orc_resonator *res,
-                    int nbins, double half_width_sigmas,
-                    int nb, const int32_t *bucket, const double *current_A, const int64_t *n_mp)
+orc_sim *orc_create_h(const orc_ring *ring, int flags, uint64_t seed,
+                      int nres, const orc_resonator *res, int nharm, const orc_harmonic *harm,
+                      int nbins, double half_width_sigmas,
+                      int nb, const int32_t *bucket, const double *current_A, const int64_t *n_mp)
 {
-    if (nres < 0 || nres > ORC_MAX_RES || nbins < 2 || nb < 1)
+    if (nres < 0 || nres > ORC_MAX_RES || nharm < 0 || nharm > ORC_MAX_HARM || nbins < 2 || nb < 1)
         return NULL;
+    orc_derived dv;
+    orc_derive_h(ring, flags, nharm, harm, &dv);
+    if (!(fabs(dv.sin_phi_s) <= 1.0) || !(dv.sigma_tau0 > 0.0))
+        return NULL;   /* no synchronous phase, or an unstable main cavity */
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->ring = *ring;
     s->flags = flags;
     s->seed = seed;
-    orc_derive(ring, flags, &s->dv);
+    s->dv = dv;
+    s->nharm = nharm;
+    for (int k = 0; k < nharm; ++k) {
+        s->harm[k] = harm[k];
+        s->harm_VoE0[k] = harm[k].V_V / ring->E0_eV;
+        s->harm_nw[k] = (double)harm[k].n * dv.omega_rf;
+    }
     s->nres = nres;
     for (int r = 0; r < nres; ++r)
         s->res[r] = res[r];
@@ -330,6 +371,14 @@ int orc_add_wake_table(orc_sim *s, int n, const double *t, const double *W)
         s->Wlag[l] += table_integral(n, t, W, lo, hi) / s->Delta;
     }
     return 0;
+}
+
+orc_sim *orc_create(const orc_ring *ring, int flags, uint64_t seed,
+                    int nres, const orc_resonator *res,
+                    int nbins, double half_width_sigmas,
+                    int nb, const int32_t *bucket, const double *current_A, const int64_t *n_mp)
+{
+    return orc_create_h(ring, flags, seed, nres, res, 0, NULL, nbins, half_width_sigmas, nb, bucket, current_A, n_mp);
 }
 
 void orc_destroy(orc_sim *s)
@@ -526,8 +575,11 @@ static void one_turn(orc_sim *s)
                 /* wake kick with the previous turn's wake (zero on turn 0) */
                 double V = vsr_at(s, m, orc_cell_coord(s, t)) + vlr_at(s, m, t);
                 d = d - V / s->ring.E0_eV;
-                /* Eq. 1: RF gain minus mean radiation loss */
-                d = d + s->dv.V_over_E0 * sin(s->dv.phi_s - s->dv.omega_rf * t) - s->dv.U0_over_E0;
+                /* Eq. 1: RF gain (main and harmonic cavities) minus mean radiation loss */
+                d = d + s->dv.V_over_E0 * sin(s->dv.phi_s - s->dv.omega_rf * t);
+                for (int k = 0; k < s->nharm; ++k)
+                    d = d + s->harm_VoE0[k] * sin(s->harm[k].phi_rad - s->harm_nw[k] * t);
+                d = d - s->dv.U0_over_E0;
                 /* Eq. 5, delta line: damping and quantum excitation */
                 d = d * (1.0 - s->dv.D) + s->dv.qe_amp * r[e];
                 /* Eq. 2 with the new energy deviation (reading R1) */

@@ -601,3 +601,81 @@ def test_wake_table_of_a_resonator_differs_by_the_cell_curvature(oracle_mod):
     assert np.max(np.abs(tab[1:] - point[1:] - D * D / 24 * w2)) < 1e-3 * np.max(np.abs(point))
     w1_0, w2_0 = (C * sc).real, (C * sc * sc).real
     assert tab[0] - point[0] == pytest.approx(w1_0 * D / 8 + w2_0 * D * D / 48, rel=2e-2)
+
+
+# ----------------------------------------------------------------------------- harmonic cavities
+def _flat_potential(ring, n=3):
+    """Textbook flat-potential setting of an n-th harmonic cavity: the energy
+    change of a turn and its first two derivatives vanish at tau = 0:
+      V sin(phi_s) + k V sin(phi_h) = U0,  cos(phi_s) + n k cos(phi_h) = 0,
+      sin(phi_s) + n^2 k sin(phi_h) = 0
+    => sin(phi_s) = n^2/(n^2-1) U0/V, k = sqrt(1/n^2 - (U0/V)^2/(n^2-1))."""
+    u = ring["U0_eV"] / ring["V_rf_V"]
+    sphi = n * n / (n * n - 1) * u
+    cphi = math.sqrt(1 - sphi * sphi)
+    k = math.sqrt(1 / n ** 2 - u * u / (n * n - 1))
+    phih = math.atan2(-sphi / (n * n * k), -cphi / (n * k))
+    return dict(n=n, V_V=k * ring["V_rf_V"], phi_rad=phih), sphi, cphi, k
+
+
+def test_flat_potential_phase_and_cubic_energy_change(oracle_mod):
+    ring = W.ring_r0()
+    hc, sphi, cphi, k = _flat_potential(ring)
+    dv = oracle_mod.derive_h(ring, [hc])
+    assert dv["sin_phi_s"] == pytest.approx(sphi, rel=1e-12)
+    # one turn of particles at rest at small offsets (no wake, no excitation)
+    taus = np.array([-4, -3, -2, -1, 0, 1, 2, 3, 4], float) * 1e-12
+    s = oracle_mod.OracleSim(ring, [], 64, 5.0, [0], [0.0], [len(taus)], 1, W.NO_QE, harmonic_cavities=[hc])
+    s.set_particles(0, taus, np.zeros_like(taus))
+    s.track(1, record=False)
+    _, d1 = s.particles(0)
+    D = 2 * ring["T0_s"] / ring["tau_z_s"]
+    w = 2 * math.pi * ring["h"] / ring["T0_s"]
+    VoE = ring["V_rf_V"] / ring["E0_eV"]
+    assert abs(d1[4]) < 1e-18                  # the synchronous particle gains nothing
+    c = np.polyfit(taus / 1e-12, d1 / (1 - D), 5)[::-1]   # c[j]: coefficient of (tau / 1 ps)^j
+    K = VoE * w * cphi * 1e-12                 # main cavity alone: first-order change per ps
+    assert abs(c[1]) < 1e-7 * K and abs(c[2]) < 1e-7 * K
+    assert c[3] == pytest.approx(VoE * w ** 3 * cphi * (1 - 9) / 6 * 1e-36, rel=1e-3)
+
+
+def _double_rf_equilibrium(ring, hcs, L):
+    """Stationary line density exp(-Phi / (alpha_c T0 sigma_E^2)) with Phi the
+    exact potential of the main and harmonic cavities and the mean loss."""
+    E0, T0, V, ac, sd = ring["E0_eV"], ring["T0_s"], ring["V_rf_V"], ring["alpha_c"], ring["sigma_delta"]
+    w = 2 * math.pi * ring["h"] / T0
+    Uh = sum(hc["V_V"] * math.sin(hc["phi_rad"]) for hc in hcs)
+    phis = math.asin((ring["U0_eV"] - Uh) / V)
+    tau = np.linspace(-L, L, 20001)
+    Phi = -((V / w) * (np.cos(phis - w * tau) - math.cos(phis)) - ring["U0_eV"] * tau)
+    for hc in hcs:
+        nw = hc["n"] * w
+        Phi -= (hc["V_V"] / nw) * (np.cos(hc["phi_rad"] - nw * tau) - math.cos(hc["phi_rad"]))
+    Phi /= E0
+    lam = np.exp(-(Phi - Phi.min()) / (ac * T0 * sd * sd))
+    lam /= np.trapezoid(lam, tau)
+    return tau, lam
+
+
+def test_flat_potential_equilibrium_is_stationary(oracle_mod):
+    """Particles drawn from the analytic double-RF equilibrium stay in it (rms
+    length within 2.5 % over 2000 turns after 1000), which is far from the
+    single-cavity length."""
+    ring = W.ring_r0()
+    hc = _flat_potential(ring)[0]
+    st0 = oracle_mod.derive(ring)["sigma_tau0"]
+    tau, lam = _double_rf_equilibrium(ring, [hc], 12 * st0)
+    mean = np.trapezoid(tau * lam, tau)
+    sig = math.sqrt(np.trapezoid((tau - mean) ** 2 * lam, tau))
+    assert sig > 1.8 * st0                       # strongly lengthened
+    N = 6000
+    g = np.random.default_rng(17)
+    cdf = np.cumsum(lam)
+    cdf /= cdf[-1]
+    t0 = np.interp(g.random(N), cdf, tau)
+    d0 = g.normal(0.0, ring["sigma_delta"], N)
+    s = oracle_mod.OracleSim(ring, [], 256, 12.0, [0], [0.0], [N], 3, 0, harmonic_cavities=[hc])
+    s.set_particles(0, t0, d0)
+    rec = s.track(3000)
+    assert rec[1000:, 0, 1].mean() == pytest.approx(sig, rel=0.025)
+    assert abs(rec[1000:, 0, 0].mean() - mean) < 0.03 * sig
