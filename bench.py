@@ -32,6 +32,11 @@ single bunch of the 'dc12c' ring in the short-range resistive-wall wake of a
 copper pipe of 10 mm radius around the ring (Sec. 3) at 12 currents, one
 batch, 50 000 turns, and prints the 'equilibrium' bunch length and energy
 spread (averages over the last 5000 turns) per current.
+
+Harmonic-cavity scan: python bench.py --workload hcscan tracks a single 1 mA
+bunch of ring R0 with the broadband wake and an active third-harmonic
+cavity at fractions 0 ... 1.2 of the flat-potential voltage (one batch) and
+prints the equilibrium bunch length per setting.
 """
 from __future__ import annotations
 
@@ -74,7 +79,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
-    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan"], default="fill390")
+    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan"], default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests tracked together")
@@ -428,6 +433,67 @@ def rwscan_bench(args, rank, local):
     return 0
 
 
+def hcscan_bench(args, rank, local):
+    """Bunch lengthening by an active third-harmonic cavity, one batch."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    ring = W.ring_r0()
+    n = 3
+    u = ring["U0_eV"] / ring["V_rf_V"]
+    k_flat = math.sqrt(1 / n ** 2 - u * u / (n * n - 1))
+    s_flat = n * n / (n * n - 1) * u
+    phih = math.atan2(-s_flat / (n * n * k_flat), -math.sqrt(1 - s_flat * s_flat) / (n * k_flat))
+    fractions = [0.0, 0.25, 0.5, 0.75, 0.9, 1.0, 1.1, 1.2]
+    turns, n_mp, last = 20_000, 100_000, 4000
+    runs = []
+    for i, f in enumerate(fractions):
+        b, c, nn = W._fill([0], 1e-3, n_mp)
+        hcs = [dict(n=n, V_V=f * k_flat * ring["V_rf_V"], phi_rad=phih)] if f > 0 else []
+        runs.append(W.Run(ring, [dict(W.BROADBAND)], b, c, nn, seed=900 + i, turns=turns, precision=W.PREC_MIXED,
+                          half_width_sigmas=12.0, harmonic_cavities=hcs, name=f"harmonic {f:.2f} x flat"))
+    trackers = [pkg.tracker_for_run(r, record_turns=turns) for r in runs]
+    stream = torch.cuda.current_stream()
+    for t in trackers:
+        t.init_particles(stream)
+    b = pkg.Batch(trackers)
+    b.set_graph(GRAPH_TURNS)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        b.track(turns, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    b.sync()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    table = []
+    for f, t in zip(fractions, trackers):
+        rec = t.moments(turns - last, last)[:, 0, :]
+        table.append({"fraction_of_flat_voltage": f, "V_h_kV": round(f * k_flat * ring["V_rf_V"] / 1e3, 2),
+                      "sigma_tau_ps": round(float(rec[:, 1].mean()) * 1e12, 3),
+                      "sigma_delta_over_sigma_E": round(float(rec[:, 3].mean()) / ring["sigma_delta"], 4),
+                      "centroid_ps": round(float(rec[:, 0].mean()) * 1e12, 3)})
+    b.close()
+    for t in trackers:
+        t.close()
+    mp = sum(r.n_particles for r in runs)
+    line = {"metric": "harmonic-cavity scan throughput (macro-particle-turns/s)", "value": mp * turns / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": turns, "ms_per_step": ms / turns, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"R0 single bunch 1 mA + broadband wake, third-harmonic cavity at "
+                                   f"{len(fractions)} voltages (flat potential: {k_flat * ring['V_rf_V'] / 1e3:.1f} kV,"
+                                   f" phase {phih:.4f} rad), {n_mp} mp, {turns} turns, one batch",
+                       "equilibrium": f"averages over the last {last} turns"},
+            "scan": table, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -439,6 +505,8 @@ def main():
         return l5scan_bench(args, rank, local)
     if args.workload == "rwscan":
         return rwscan_bench(args, rank, local)
+    if args.workload == "hcscan":
+        return hcscan_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)

@@ -134,6 +134,19 @@ const char *mbt_last_error(const mbt_ctx *ctx);
  * mbt_set_fill. */
 mbt_status mbt_add_resonator(mbt_ctx *ctx, double Rs_ohm, double fr_Hz, double Q, int range);
 
+/* Add an active harmonic RF cavity (the paper's RF step holds "additional
+ * harmonic cavities"): its voltage V_V at n x the RF frequency and phase
+ * phi_rad at the synchronous particle add (V_V / E0) sin(phi_rad - n
+ * omega_rf tau) to a turn's energy change.  The main cavity's phase then
+ * balances the mean loss against them: V sin(phi_s) + sum V_h sin(phi_h) =
+ * U0 (MBT_ERR_ARG at mbt_set_fill if no such phase exists); sigma_tau0 (the
+ * mesh unit and the matched start) keeps the main cavity's slope V
+ * cos(phi_s), since a double-RF system can have no small-amplitude tune (a
+ * flat potential).  1 <= n <= 16, V_V >= 0.  Only before mbt_set_grid /
+ * mbt_set_fill; at most 2 cavities.  A passive (beam-loaded) harmonic cavity
+ * is a resonator near n f_rf with the long-range bit instead. */
+mbt_status mbt_add_harmonic_cavity(mbt_ctx *ctx, int n, double V_V, double phi_rad);
+
 /* Add a tabulated short-range wake (Sec. 2.3: other wakes, such as the
  * resistive wall, are added to the same wake).  W_V_per_C[i] is W(t_s[i]) in
  * V/C (positive = energy loss), t_s[0] = 0 (W(0+)) and t_s strictly

@@ -28,7 +28,8 @@ NO_SR, NO_QE, KICK_NGP = 1, 2, 4
 
 # every entry point declared in include/mbt.h
 EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt_last_error",
-           "mbt_add_resonator", "mbt_add_wake_table", "mbt_add_resistive_wall", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
+           "mbt_add_resonator", "mbt_add_wake_table", "mbt_add_resistive_wall",
+           "mbt_add_harmonic_cavity", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
            "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
@@ -111,6 +112,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_add_resonator": ([_vp, _d, _d, _d, _i], _i), "mbt_set_grid": ([_vp, _i, _d], _i),
                 "mbt_add_wake_table": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_add_resistive_wall": ([_vp, _d, _d, _d], _i),
+                "mbt_add_harmonic_cavity": ([_vp, _i, _d, _d], _i),
                 "mbt_set_fill": ([_vp, _i, _P(_i32), _P(_d), _P(_i64)], _i),
                 "mbt_set_record": ([_vp, _i64], _i), "mbt_init_particles": ([_vp, _vp], _i),
                 "mbt_set_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
@@ -166,7 +168,7 @@ class Tracker:
     def __init__(self, ring: dict, precision: int = PREC_MIXED, flags: int = 0, seed: int = 1,
                  resonators=(), nbins: int = 256, half_width_sigmas: float = 5.0,
                  buckets=(0,), currents_A=(1e-3,), n_mp=(10_000,), record_turns: int = 4096,
-                 wake_tables=(), resistive_wall=()):
+                 wake_tables=(), resistive_wall=(), harmonic_cavities=()):
         self._L = lib()
         self._h = ctypes.c_void_p()
         r = Ring(E0_eV=ring["E0_eV"], T0_s=ring["T0_s"], h=int(ring["h"]), reserved=0, V_rf_V=ring["V_rf_V"],
@@ -185,6 +187,8 @@ class Tracker:
             if t.shape != w.shape:
                 raise ValueError("wake table: t and W differ in length")
             self._chk(self._L.mbt_add_wake_table(self._h, len(t), _ptr(t, _d), _ptr(w, _d)))
+        for hc in harmonic_cavities:
+            self._chk(self._L.mbt_add_harmonic_cavity(self._h, int(hc["n"]), float(hc["V_V"]), float(hc["phi_rad"])))
         for rw in resistive_wall:
             self._chk(self._L.mbt_add_resistive_wall(self._h, float(rw["radius_m"]), float(rw["conductivity_S_per_m"]),
                                                      float(rw["length_m"])))
@@ -471,4 +475,4 @@ def tracker_for_run(run, precision=None, record_turns: int = 4096) -> Tracker:
                    seed=run.seed, resonators=run.resonators, nbins=run.nbins,
                    half_width_sigmas=run.half_width_sigmas, buckets=run.buckets, currents_A=run.currents_A,
                    n_mp=run.n_mp, record_turns=record_turns, wake_tables=run.wake_tables,
-                   resistive_wall=run.resistive_wall)
+                   resistive_wall=run.resistive_wall, harmonic_cavities=run.harmonic_cavities)

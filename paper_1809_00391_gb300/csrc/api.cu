@@ -114,6 +114,8 @@ struct mbt_ctx {
   // tabulated short-range wakes (t, W) and resistive-wall pipes (b, sigma, L)
   std::vector<std::vector<double>> wt_t, wt_w;
   std::vector<std::array<double, 3>> rwalls;
+  // active harmonic cavities (n, V, phi)
+  std::vector<std::array<double, 3>> harm;
   RunDev rundev{};
   PlanStore own;
   int tile = kMixedTile;       // particles per push CTA (mixed precision)
@@ -210,7 +212,9 @@ void derive(mbt_ctx *c) {
   const double U0 = sr ? r.U0_eV : 0.0;
   c->T_rf = r.T0_s / (double)r.h;
   c->omega_rf = 2.0 * kPi * (double)r.h / r.T0_s;
-  c->sin_phi_s = U0 / r.V_rf_V;
+  double Uh = 0.0;   // harmonic cavities' voltage at the synchronous particle
+  for (auto &hc : c->harm) Uh += hc[1] * std::sin(hc[2]);
+  c->sin_phi_s = (U0 - Uh) / r.V_rf_V;
   c->phi_s = std::asin(c->sin_phi_s);
   if (r.alpha_c < 0.0) c->phi_s = kPi - c->phi_s;
   c->cos_phi_s = std::cos(c->phi_s);
@@ -325,9 +329,11 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
   pl.njobs = (int)st.jobs.size();
   pl.max_nbins = 0;
   pl.max_nlong = 0;
+  pl.max_nharm = 0;
   for (auto &r : st.runs) {
     pl.max_nbins = std::max(pl.max_nbins, r.nbins);
     pl.max_nlong = std::max(pl.max_nlong, r.nlong);
+    pl.max_nharm = std::max(pl.max_nharm, r.nharm);
   }
   st.bytes += pb + 16;
   st.plan = pl;
@@ -503,6 +509,18 @@ mbt_status mbt_add_resonator(mbt_ctx *c, double Rs, double fr, double Q, int ran
   return MBT_OK;
 }
 
+mbt_status mbt_add_harmonic_cavity(mbt_ctx *c, int n, double V, double phi) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "harmonic cavities must be added before mbt_set_fill");
+  if (n < 1 || n > 16 || !(V >= 0) || !std::isfinite(V) || !std::isfinite(phi))
+    return fail(c, MBT_ERR_ARG, "a harmonic cavity needs 1 <= n <= 16, V >= 0 and a finite phase");
+  if ((int)c->harm.size() >= kMaxHarm) return fail(c, MBT_ERR_UNSUPPORTED, "at most %d harmonic cavities", kMaxHarm);
+  c->harm.push_back({(double)n, V, phi});
+  derive(c);
+  return MBT_OK;
+}
+
 mbt_status mbt_add_wake_table(mbt_ctx *c, int n, const double *t, const double *w) {
   if (!c) return MBT_ERR_ARG;
   c->err.clear();
@@ -567,6 +585,9 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     if (!(current[m] >= 0) || nmp[m] < 1 || nmp[m] > nmax)
       return fail(c, MBT_ERR_ARG, "bunch %d: current >= 0 and 1 <= n_mp <= %lld required", m, (long long)nmax);
   }
+  derive(c);
+  if (!(std::fabs(c->sin_phi_s) <= 1.0) || !(c->sigma_tau0 > 0.0))
+    return fail(c, MBT_ERR_ARG, "no stable synchronous phase: the main cavity cannot balance U0 and the harmonic cavities");
   cudaError_t ce = cudaFree(0);
   if (ce != cudaSuccess) return cuda_fail(c, ce, "CUDA initialisation");
   c->nb = nb;
@@ -773,6 +794,15 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   for (int li = 0; li < kMaxLong; ++li) {
     rd.f_la[li] = li < c->nlong ? (float)(-rd.lr_s[li].x) : 0.f;
     rd.f_lw[li] = li < c->nlong ? (float)rd.lr_s[li].y : 0.f;
+  }
+  rd.nharm = (int)c->harm.size();
+  for (int k = 0; k < rd.nharm; ++k) {
+    const double n = c->harm[k][0], V = c->harm[k][1], ph = c->harm[k][2];
+    rd.harm_VoE0[k] = V / c->ring.E0_eV;
+    rd.harm_phi[k] = ph;
+    rd.harm_nw[k] = n * c->omega_rf;
+    rd.f_harm[k] = make_float4((float)(2.0 * V / c->ring.E0_eV * rd.one_minus_D), (float)std::cos(ph),
+                               (float)std::sin(ph), (float)(0.5 * n * c->omega_rf));
   }
 
   PlanStore &ps = c->own;
@@ -1155,7 +1185,7 @@ mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
   for (int64_t done = 0; done < nturns; done += chunk) {
     a.nturns = (int)std::min<int64_t>(chunk, nturns - done);
     cudaError_t e = cudaMemsetAsync(c->d_gbar, 0, 16, s);
-    if (e == cudaSuccess) e = launch_resident(a, c->nlong, c->nb, s);
+    if (e == cudaSuccess) e = launch_resident(a, c->nlong, c->rundev.nharm, c->nb, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "resident launch");
   }
   return MBT_OK;

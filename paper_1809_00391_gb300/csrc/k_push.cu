@@ -49,11 +49,12 @@ __device__ __forceinline__ void issue_chunk(const TileDev &t, const float *tau, 
   bulk_g2s(stage + kChunk * sizeof(float), del + (size_t)c * kChunk, db, bar);
 }
 
-template <int NLONG_MAX>
+template <int NLONG_MAX, bool HARM>
 __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixed(const Plan p) {
   extern __shared__ __align__(128) uint8_t sm_push[];
   __shared__ float s_red[kPushThreads / 32][5];
   __shared__ float2 s_phi[kMaxLong];
+  __shared__ float4 s_hc[kMaxHarm];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ int s_abort;
 
@@ -80,6 +81,8 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
     s_abort = 0;
     for (int ch = 0; ch < min(kStages, nchunks); ++ch) issue_chunk(t, tau, del, stages + ch * kStageBytes, &full[ch], ch);
   }
+  const int nharm = R->nharm;
+  if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
   grid_dependents_launch();
   grid_dependency_wait();   // the previous post kernel's wake, phasors and turn counter are complete
   const long long turn = *R->turn;
@@ -145,8 +148,12 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
       float tt[4] = {tv.x, tv.y, tv.z, tv.w};
       double dd[4] = {da.x, da.y, db.x, db.y};
       const int nvalid = min(4, t.count - q);
-      if (ngp) quad_push<NLONG_MAX, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, tt, dd, rr, nvalid, st, st2, sd, sd2, nout);
-      else quad_push<NLONG_MAX, false>(c, sVd, sH, nlong, la, lw, phi, omD_d, tt, dd, rr, nvalid, st, st2, sd, sd2, nout);
+      if (ngp)
+        quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
+                                   sd, sd2, nout);
+      else
+        quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
+                                    sd, sd2, nout);
       *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
       *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
       *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
@@ -277,7 +284,9 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
         v += ea * (s_phi[r].x * cs - s_phi[r].y * sn);
       }
       d = d - v * invE0;
-      d = d + VoE0 * sin(phis - wrf * tp) - U0oE0;
+      d = d + VoE0 * sin(phis - wrf * tp);
+      for (int k = 0; k < R->nharm; ++k) d = d + R->harm_VoE0[k] * sin(R->harm_phi[k] - R->harm_nw[k] * tp);
+      d = d - U0oE0;
       d = d * omD + qe * rr[e];
       tp = tp + aT0 * d;
       tt[e] = tp;
@@ -366,11 +375,14 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   const int max_nbins = p.max_nbins;
   if (precision == kMixed) {
     const size_t smem = (size_t)kStages * kStageBytes + (size_t)max_nbins * (sizeof(float2) + sizeof(int));
+    const bool harm = p.max_nharm > 0;
     switch (p.max_nlong) {
-      case 0: return launch_ex(k_push_mixed<0>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 1: return launch_ex(k_push_mixed<1>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 2: return launch_ex(k_push_mixed<2>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      default: return launch_ex(k_push_mixed<kMaxLong>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 0: return launch_ex(harm ? k_push_mixed<0, true> : k_push_mixed<0, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 1: return launch_ex(harm ? k_push_mixed<1, true> : k_push_mixed<1, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 2: return launch_ex(harm ? k_push_mixed<2, true> : k_push_mixed<2, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      default:
+        return launch_ex(harm ? k_push_mixed<kMaxLong, true> : k_push_mixed<kMaxLong, false>, p.ntiles, kPushThreads,
+                         smem, s, pdl, p);
     }
   }
   const size_t smem = (size_t)max_nbins * (sizeof(double) + sizeof(int));
@@ -382,7 +394,7 @@ cudaError_t push_resident_slots(int *slots) {
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1>, kPushThreads, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1, false>, kPushThreads, smem);
   *slots = per * nsm;
   return e;
 }
@@ -390,7 +402,8 @@ cudaError_t push_resident_slots(int *slots) {
 cudaError_t configure_push_kernels() {
   const int bytes = (int)((size_t)kStages * kStageBytes + 1024 * (sizeof(float2) + sizeof(int)));
   cudaError_t e = cudaSuccess;
-  for (auto k : {k_push_mixed<0>, k_push_mixed<1>, k_push_mixed<2>, k_push_mixed<kMaxLong>})
+  for (auto k : {k_push_mixed<0, false>, k_push_mixed<1, false>, k_push_mixed<2, false>, k_push_mixed<kMaxLong, false>,
+                 k_push_mixed<0, true>, k_push_mixed<1, true>, k_push_mixed<2, true>, k_push_mixed<kMaxLong, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }

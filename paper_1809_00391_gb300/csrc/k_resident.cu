@@ -61,12 +61,13 @@ __host__ __device__ inline size_t resident_layout(int per, int nbins, ResidentSm
 
 size_t resident_smem_bytes(int per, int nbins) { return resident_layout(per, nbins, nullptr, nullptr); }
 
-template <int NLONG_MAX>
+template <int NLONG_MAX, bool HARM>
 __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const ResidentArgs a) {
   extern __shared__ __align__(16) uint8_t sm_res[];
   __shared__ float s_red[kResidentThreads / 32][5];
   __shared__ double s_mom[5];
   __shared__ float2 s_phi[kMaxLong];
+  __shared__ float4 s_hc[kMaxHarm];
   __shared__ double2 s_phid[kMaxLong];
   __shared__ double2 s_carry[kMaxLong];
   __shared__ int s_fail;
@@ -111,6 +112,8 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     s_carry[tid] = R->carry[tid];
   }
   if (tid == 0) s_fail = 0;
+  const int nharm = R->nharm;
+  if (tid < nharm) s_hc[tid] = R->f_harm[tid];
   const long long turn0 = *R->turn;
 
   PushConstF c;
@@ -162,8 +165,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
       float tt[4] = {tv.x, tv.y, tv.z, tv.w};
       double dd[4] = {da.x, da.y, db.x, db.y};
       const int nvalid = min(4, ns - q);
-      if (ngp) quad_push<NLONG_MAX, true>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, tt, dd, rr, nvalid, st, st2, sd, sd2, nout);
-      else quad_push<NLONG_MAX, false>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, tt, dd, rr, nvalid, st, st2, sd, sd2, nout);
+      if (ngp)
+        quad_push<NLONG_MAX, true, HARM>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st,
+                                   st2, sd, sd2, nout);
+      else
+        quad_push<NLONG_MAX, false, HARM>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st,
+                                    st2, sd, sd2, nout);
       *reinterpret_cast<float4 *>(S.sT + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
       *reinterpret_cast<double2 *>(S.sD + q) = make_double2(dd[0], dd[1]);
       *reinterpret_cast<double2 *>(S.sD + q + 2) = make_double2(dd[2], dd[3]);
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
   cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nb, cudaStream_t s) {
+cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nharm, int nb, cudaStream_t s) {
   const int nbins = a.plan.max_nbins;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(nb * a.cluster));
@@ -346,11 +353,12 @@ cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nb, cudaStream
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, kern, a);
   };
+  const bool harm = nharm > 0;
   switch (nlong) {
-    case 0: return run(k_resident<0>);
-    case 1: return run(k_resident<1>);
-    case 2: return run(k_resident<2>);
-    default: return run(k_resident<kMaxLong>);
+    case 0: return harm ? run(k_resident<0, true>) : run(k_resident<0, false>);
+    case 1: return harm ? run(k_resident<1, true>) : run(k_resident<1, false>);
+    case 2: return harm ? run(k_resident<2, true>) : run(k_resident<2, false>);
+    default: return harm ? run(k_resident<kMaxLong, true>) : run(k_resident<kMaxLong, false>);
   }
 }
 
@@ -366,10 +374,10 @@ cudaError_t resident_max_clusters(int cluster, size_t smem, int *max_clusters) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaFuncSetAttribute(k_resident<kMaxLong>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident<kMaxLong>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaFuncSetAttribute(k_resident<kMaxLong, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident<kMaxLong, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveClusters(max_clusters, (void *)k_resident<kMaxLong>, &cfg);
+  return cudaOccupancyMaxActiveClusters(max_clusters, (void *)k_resident<kMaxLong, true>, &cfg);
 }
 
 }  // namespace mbt

@@ -11,6 +11,7 @@ namespace mbt {
 
 constexpr int kMaxRes = 8;           // resonators per run
 constexpr int kMaxLong = 4;          // resonators with the long-range bit
+constexpr int kMaxHarm = 2;          // active harmonic RF cavities
 constexpr int kBunchTile = 32;       // bunches per post-kernel tile (one lane per bunch)
 constexpr int kMaxBunches = 1024;    // one warp scans the tile aggregates
 constexpr int kPushThreads = 256;
@@ -62,6 +63,10 @@ struct RunDev {
   const float *q_mp_f;      // [nb] macro-particle charge (float)
   const double *inv_n;      // [nb] 1 / n_mp
   const float *lag_f;       // [nbins] summed short-range wake per lag, FP32 (resident mode)
+  // active harmonic cavities: (V_h/E0) sin(phi_h - n omega_rf tau) each
+  int nharm;
+  double harm_VoE0[kMaxHarm], harm_phi[kMaxHarm], harm_nw[kMaxHarm];
+  float4 f_harm[kMaxHarm];  // (2 V_h/E0 (1 - D), cos phi_h, sin phi_h, n omega_rf / 2), mixed path
 };
 
 
@@ -94,6 +99,7 @@ struct Plan {
   int nruns, nbunches, ntiles, njobs;
   int max_nbins;              // largest mesh of the plan's runs (shared-memory sizing)
   int max_nlong;              // most long-range resonators of any run of the plan
+  int max_nharm;              // most harmonic cavities of any run of the plan
   unsigned long long *trace;  // null, or [njobs][3] post-kernel CTA timestamps (start, job done, exit) [ns]
 };
 
@@ -115,7 +121,7 @@ struct ResidentArgs {
   int grid_sync;          // 1 if clusters must meet every turn (long-range coupling of several bunches)
 };
 size_t resident_smem_bytes(int per, int nbins);
-cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nb, cudaStream_t s);
+cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nharm, int nb, cudaStream_t s);
 cudaError_t resident_max_clusters(int cluster, size_t smem, int *max_clusters);
 
 // Kernel launchers (one translation unit each).

@@ -12,12 +12,16 @@ struct PushConstF {
   int nbins;
 };
 
-// One particle: kick with the previous turn's wake, RF, damping + excitation,
-// drift.  Returns the new tau; delta is updated in place.
-template <int NLONG_MAX, bool NGP>
+// One particle: kick with the previous turn's wake, RF (main and harmonic
+// cavities), damping + excitation, drift.  Returns the new tau; delta is
+// updated in place.  hc: nharm harmonic cavities (2 V_h/E0 (1 - D), cos phi_h,
+// sin phi_h, n omega_rf / 2), in shared memory.  HARM: compiled in only for
+// plans with harmonic cavities, so that the particle code of the others stays
+// one straight block in which the four particles of a quad overlap.
+template <int NLONG_MAX, bool NGP, bool HARM>
 __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd, int nlong,
                                           const float *la, const float *lw, const float2 *phi, double omD_d,
-                                          float t0, double &d, float r, float &df) {
+                                          const float4 *hc, int nharm, float t0, double &d, float r, float &df) {
   const float x = fmaf(t0, c.invD, c.HinvD);
   float v;
   if (NGP) {
@@ -44,7 +48,14 @@ __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd
   float sh, ch;
   __sincosf(c.halfw * t0, &sh, &ch);
   // c.twoVoE0 and c.invE0 carry the damping factor (1 - D) already
-  const float rf = -c.twoVoE0 * sh * fmaf(ch, c.cphi, sh * c.sphi);
+  float rf = -c.twoVoE0 * sh * fmaf(ch, c.cphi, sh * c.sphi);
+  // harmonic cavities, the same form: (V_h/E0)[sin(phi_h - n w t) - sin(phi_h)]
+  for (int k = 0; HARM && k < nharm; ++k) {
+    const float4 h = hc[k];
+    float sk, ck;
+    __sincosf(h.w * t0, &sk, &ck);
+    rf = fmaf(-h.x * sk, fmaf(ck, h.y, sk * h.z), rf);
+  }
   const float inc = fmaf(-v, c.invE0, fmaf(c.qe, r, rf));
   d = fma(d, omD_d, f32_to_f64_bits(inc));
   df = f64_to_f32_trunc(d);
@@ -53,17 +64,17 @@ __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd
 
 // Four consecutive particles: push, deposit, moment partials.  Full quads
 // (nvalid == 4, all but a bunch's last) take no per-particle validity tests.
-template <int NLONG_MAX, bool NGP>
+template <int NLONG_MAX, bool NGP, bool HARM>
 __device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd, int *sH, int nlong, const float *la,
-                                          const float *lw, const float2 *phi, double omD_d, float (&tt)[4],
-                                          double (&dd)[4], const float (&rr)[4], int nvalid, float &st, float &st2,
-                                          float &sd, float &sd2, int &nout) {
+                                          const float *lw, const float2 *phi, double omD_d, const float4 *hc,
+                                          int nharm, float (&tt)[4], double (&dd)[4], const float (&rr)[4],
+                                          int nvalid, float &st, float &st2, float &sd, float &sd2, int &nout) {
   const bool full = nvalid == 4;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (full || e < nvalid) {
       float df;
-      const float t1 = push_one<NLONG_MAX, NGP>(c, sVd, nlong, la, lw, phi, omD_d, tt[e], dd[e], rr[e], df);
+      const float t1 = push_one<NLONG_MAX, NGP, HARM>(c, sVd, nlong, la, lw, phi, omD_d, hc, nharm, tt[e], dd[e], rr[e], df);
       tt[e] = t1;
       const float xb = fmaf(t1, c.invD, c.HinvD);
       if (xb >= 0.f && xb < c.fnb) atomicAdd(&sH[(int)xb], 1);

@@ -604,18 +604,8 @@ def test_wake_table_of_a_resonator_differs_by_the_cell_curvature(oracle_mod):
 
 
 # ----------------------------------------------------------------------------- harmonic cavities
-def _flat_potential(ring, n=3):
-    """Textbook flat-potential setting of an n-th harmonic cavity: the energy
-    change of a turn and its first two derivatives vanish at tau = 0:
-      V sin(phi_s) + k V sin(phi_h) = U0,  cos(phi_s) + n k cos(phi_h) = 0,
-      sin(phi_s) + n^2 k sin(phi_h) = 0
-    => sin(phi_s) = n^2/(n^2-1) U0/V, k = sqrt(1/n^2 - (U0/V)^2/(n^2-1))."""
-    u = ring["U0_eV"] / ring["V_rf_V"]
-    sphi = n * n / (n * n - 1) * u
-    cphi = math.sqrt(1 - sphi * sphi)
-    k = math.sqrt(1 / n ** 2 - u * u / (n * n - 1))
-    phih = math.atan2(-sphi / (n * n * k), -cphi / (n * k))
-    return dict(n=n, V_V=k * ring["V_rf_V"], phi_rad=phih), sphi, cphi, k
+from physics_helpers import double_rf_equilibrium as _double_rf_equilibrium  # noqa: E402
+from physics_helpers import flat_potential as _flat_potential  # noqa: E402
 
 
 def test_flat_potential_phase_and_cubic_energy_change(oracle_mod):
@@ -637,24 +627,6 @@ def test_flat_potential_phase_and_cubic_energy_change(oracle_mod):
     K = VoE * w * cphi * 1e-12                 # main cavity alone: first-order change per ps
     assert abs(c[1]) < 1e-7 * K and abs(c[2]) < 1e-7 * K
     assert c[3] == pytest.approx(VoE * w ** 3 * cphi * (1 - 9) / 6 * 1e-36, rel=1e-3)
-
-
-def _double_rf_equilibrium(ring, hcs, L):
-    """Stationary line density exp(-Phi / (alpha_c T0 sigma_E^2)) with Phi the
-    exact potential of the main and harmonic cavities and the mean loss."""
-    E0, T0, V, ac, sd = ring["E0_eV"], ring["T0_s"], ring["V_rf_V"], ring["alpha_c"], ring["sigma_delta"]
-    w = 2 * math.pi * ring["h"] / T0
-    Uh = sum(hc["V_V"] * math.sin(hc["phi_rad"]) for hc in hcs)
-    phis = math.asin((ring["U0_eV"] - Uh) / V)
-    tau = np.linspace(-L, L, 20001)
-    Phi = -((V / w) * (np.cos(phis - w * tau) - math.cos(phis)) - ring["U0_eV"] * tau)
-    for hc in hcs:
-        nw = hc["n"] * w
-        Phi -= (hc["V_V"] / nw) * (np.cos(hc["phi_rad"] - nw * tau) - math.cos(hc["phi_rad"]))
-    Phi /= E0
-    lam = np.exp(-(Phi - Phi.min()) / (ac * T0 * sd * sd))
-    lam /= np.trapezoid(lam, tau)
-    return tau, lam
 
 
 def test_flat_potential_equilibrium_is_stationary(oracle_mod):
