@@ -87,6 +87,27 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over the ranks of the process group (x itself alone)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_run(rank: int) -> W.Run:
+    """The fill a rank tracks: every rank its own 390-bunch fill (independent
+    replicas, weak scaling; no data-path collective)."""
+    return W.fill_390(seed=1 + rank, precision=W.PREC_MIXED)
+
+
+def weak_scaling_value(units_per_rank: int, steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job throughput: all ranks' units x steps over the slowest rank's time."""
+    return units_per_rank * steps * world / (t_max_ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -518,7 +539,7 @@ def main():
     import paper_1809_00391_gb300 as pkg
     pkg.build()
 
-    run = W.fill_390(seed=1 + rank, precision=W.PREC_MIXED)
+    run = replica_run(rank)
     K, Wm = args.steps, args.warmup
     G = max(1, min(GRAPH_TURNS, K))
     stream = torch.cuda.current_stream()
@@ -552,13 +573,9 @@ def main():
     tr.sync()
     clocks = clk.summary()
 
-    t_max = elapsed_ms
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(elapsed_ms, dist)
     n_part = run.n_particles
-    value = n_part * K * world / (t_max * 1e-3)
+    value = weak_scaling_value(n_part, K, world, t_max)
 
     # ---- roofline of the dominant kernel (push): a second timed region of KR
     # turns with CUDA events around every launch (ordinary launches)
@@ -597,11 +614,7 @@ def main():
         mom = tr2.moments(0, K)
         torch.cuda.synchronize()
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
         h2d = run.n_particles * (4 + 8)
         d2h = mom.nbytes
         e2e = {"value": n_part * K * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
