@@ -112,6 +112,17 @@ def _load():
             lib.orc_turn.restype = _i64
             lib.orc_add_wake_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
             lib.orc_add_wake_table.restype = ctypes.c_int
+            lib.orc_twake.argtypes = [_P(Resonator), _d]
+            lib.orc_twake.restype = _d
+            lib.orc_set_transverse.argtypes = [ctypes.c_void_p, _d, _d, _d, _d, _d, ctypes.c_int, _P(Resonator)]
+            lib.orc_set_transverse.restype = ctypes.c_int
+            lib.orc_track2.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_d)]
+            lib.orc_set_tparticles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+            lib.orc_get_tparticles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+            lib.orc_get_dip.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_get_vt.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_get_atlr.argtypes = [ctypes.c_void_p, _P(_d)]
+            lib.orc_vt_direct.argtypes = [ctypes.c_void_p, _P(_d), _d, _P(_d)]
             _lib = lib
     return _lib
 
@@ -186,6 +197,12 @@ def derive_h(ring: dict, harmonic_cavities=(), flags: int = 0) -> dict:
     return {k: out[i] for i, k in enumerate(keys)}
 
 
+def twake(res: dict, t: float) -> float:
+    """Transverse resonator wake W(t) [V/(C m)] (Rs_ohm in Ohm/m)."""
+    r = make_resonator(res)
+    return _load().orc_twake(ctypes.byref(r), float(t))
+
+
 def wake(res: dict, t: float) -> float:
     r = make_resonator(res)
     return _load().orc_wake(ctypes.byref(r), float(t))
@@ -239,7 +256,7 @@ class OracleSim:
 
     def __init__(self, ring: dict, resonators: list, nbins: int, half_width_sigmas: float,
                  buckets, currents_A, n_mp, seed: int, flags: int = 0, wake_tables=(), resistive_wall=(),
-                 harmonic_cavities=()):
+                 harmonic_cavities=(), transverse=None):
         self._lib = _load()
         self.nb = len(buckets)
         self.nbins = int(nbins)
@@ -269,6 +286,17 @@ class OracleSim:
             w = np.ascontiguousarray(w, np.float64)
             if self._lib.orc_add_wake_table(self._h, len(t), _ptr(t, _d), _ptr(w, _d)) != 0:
                 raise ValueError("wake table needs t[0] = 0 and increasing samples")
+        self.transverse = transverse
+        self.ntres = 0
+        if transverse is not None:
+            tres = list(transverse.get("resonators", ()))
+            self.ntres = len(tres)
+            self.tresonators = tres
+            ta = (Resonator * max(1, len(tres)))(*[make_resonator(r) for r in tres])
+            if self._lib.orc_set_transverse(self._h, float(transverse["beta_m"]), float(transverse.get("alpha", 0.0)),
+                                            float(transverse["tune"]), float(transverse.get("chromaticity", 0.0)),
+                                            float(transverse["emittance_m"]), len(tres), ta) != 0:
+                raise ValueError("oracle rejected the transverse plane")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -359,6 +387,46 @@ class OracleSim:
 
     def wake_voltage_at(self, m: int, tau: float) -> float:
         return self._lib.orc_wake_voltage_at(self._h, int(m), float(tau))
+
+    def track2(self, nturns: int):
+        """Track nturns; returns (moments [n][nb][6], transverse moments [n][nb][4])."""
+        rec = np.empty((int(nturns), self.nb, 6), np.float64)
+        trec = np.empty((int(nturns), self.nb, 4), np.float64)
+        self._lib.orc_track2(self._h, int(nturns), _ptr(rec, _d), _ptr(trec, _d))
+        return rec, trec
+
+    def set_tparticles(self, m: int, x, xp):
+        x = np.ascontiguousarray(x, np.float64)
+        xp = np.ascontiguousarray(xp, np.float64)
+        assert x.size == self.n_mp[m] and xp.size == self.n_mp[m]
+        self._lib.orc_set_tparticles(self._h, int(m), _ptr(x, _d), _ptr(xp, _d))
+
+    def tparticles(self, m: int):
+        x = np.empty(int(self.n_mp[m]), np.float64)
+        xp = np.empty(int(self.n_mp[m]), np.float64)
+        self._lib.orc_get_tparticles(self._h, int(m), _ptr(x, _d), _ptr(xp, _d))
+        return x, xp
+
+    def dipoles(self):
+        d = np.empty((self.nb, self.nbins), np.float64)
+        self._lib.orc_get_dip(self._h, _ptr(d, _d))
+        return d
+
+    def vt(self):
+        v = np.empty((self.nb, self.nbins), np.float64)
+        self._lib.orc_get_vt(self._h, _ptr(v, _d))
+        return v
+
+    def atlr(self):
+        a = np.empty((max(1, self.ntres), self.nb, 2), np.float64)
+        self._lib.orc_get_atlr(self._h, _ptr(a, _d))
+        return a[..., 0] + 1j * a[..., 1]
+
+    def vt_direct(self, dip, q: float):
+        d = np.ascontiguousarray(dip, np.float64)
+        v = np.empty(self.nbins, np.float64)
+        self._lib.orc_vt_direct(self._h, _ptr(d, _d), float(q), _ptr(v, _d))
+        return v
 
     @property
     def turn(self) -> int:

@@ -49,7 +49,11 @@
  *   R11 a tabulated short-range wake (e.g. the resistive wall) acts through
  *      its average over each lag cell (see orc_add_wake_table);
  *   R14 harmonic cavities add (V_h/E0) sin(phi_h - n_h omega_rf tau) each;
- *      the main cavity's phase balances U0 (see orc_derive_h).
+ *      the main cavity's phase balances U0 (see orc_derive_h);
+ *   R15 the transverse plane (see orc_set_transverse): one plane per run,
+ *      no dispersion at the tracking point, kicks with the previous turn's
+ *      wake before the RF, momentum ratio across the cavity, chromatic
+ *      rotation with the new delta, excitation, dipole sums per cell.
  */
 #include <complex.h>
 #include <math.h>
@@ -224,6 +228,21 @@ double orc_wake(const orc_resonator *q, double t)
     return 2.0 * a * q->Rs_ohm * exp(-a * t) * (cos(wb * t) - (a / wb) * sin(wb * t));
 }
 
+/* Transverse resonator wake [V/(C m)]:
+ * W(t > 0) = (wr^2 Rs / (Q wb)) e^{-a t} sin(wb t) = Im(c e^{s t}),
+ * c = wr^2 Rs / (Q wb), s = -a + i wb;  W(t <= 0) = 0 (it also vanishes at
+ * t = 0+).  Its transform i int W e^{-i w t} dt is the transverse resonator
+ * impedance (wr / w) Rs / (1 + i Q (w / wr - wr / w)), Rs in Ohm/m. */
+double orc_twake(const orc_resonator *q, double t)
+{
+    double a, wb;
+    res_consts(q, &a, &wb);
+    if (t <= 0.0)
+        return 0.0;
+    const double wr = 2.0 * 3.14159265358979323846264338327950 * q->fr_Hz;
+    return wr * wr * q->Rs_ohm / (q->Q * wb) * exp(-a * t) * sin(wb * t);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Simulation state                                                           */
 /* ------------------------------------------------------------------------- */
@@ -255,6 +274,19 @@ typedef struct orc_sim {
     double complex *Ehist;
     int64_t turn;          /* turns completed                                */
     double *moments;       /* [nb][6]: <tau>, sig_tau, <delta>, sig_delta, n_in, n_out */
+    /* transverse plane (reading R15), allocated by orc_set_transverse */
+    int trans;
+    double tb_beta, tb_alpha, tb_gamma, tb_mu0, tb_xi, tb_sx, tb_sxp, tb_Dx;
+    int ntres;
+    orc_resonator tres[ORC_MAX_RES];
+    double **x, **xp;
+    double *dip;           /* [nb][nbins] sum of x over the cell's particles, this turn */
+    double *Vt;            /* [nb][nbins] transverse short-range voltage [V] for the kick */
+    double *Wtlag;         /* [nbins] summed transverse wake at lag l*Delta [V/(C m)] */
+    double complex *Atlr;  /* [ntres][nb] long-range transverse amplitude */
+    int nthist;
+    double complex *Ethist;/* [ntres][nthist][nb] transverse emission history */
+    double *tmoments;      /* [nb][4]: <x>, sig_x, <x'>, sig_x' */
 } orc_sim;
 
 /* e^{-a dt} below this is dropped from the direct history sum. */
@@ -391,7 +423,75 @@ void orc_destroy(orc_sim *s)
     }
     free(s->tau); free(s->delta); free(s->bucket); free(s->current); free(s->n_mp); free(s->q_mp);
     free(s->hist); free(s->out_count); free(s->Vsr); free(s->Alr); free(s->moments);
-    free(s->Wlag); free(s->Ehist); free(s);
+    free(s->Wlag); free(s->Ehist);
+    if (s->trans) {
+        for (int m = 0; m < s->nb; ++m) {
+            free(s->x[m]);
+            free(s->xp[m]);
+        }
+        free(s->x); free(s->xp); free(s->dip); free(s->Vt); free(s->Wtlag); free(s->Atlr); free(s->Ethist);
+        free(s->tmoments);
+    }
+    free(s);
+}
+
+/* Transverse plane (reading R15): Twiss beta_m, alpha at the tracking point
+ * (no dispersion there), betatron tune nu0 with phase advance
+ * 2 pi nu0 (1 + xi delta) (Eq. 3), equilibrium emittance emit_m; transverse
+ * resonators (Eq. 6, second line) with Rs in Ohm/m and the range bits of the
+ * longitudinal ones.  Radiation: x' scales with the momentum ratio across the
+ * RF cavity, (1 + delta_before)/(1 + delta_after_gain) (Eq. 5, x' line), and
+ * the noise amplitudes sqrt(beta emit) sqrt(Dx), sqrt(gamma emit) sqrt(Dx)
+ * with Dx = U0/E0, the damping that the momentum ratio produces on average,
+ * so that emit_m is the equilibrium.  Returns 0, or -1 on bad input. */
+int orc_set_transverse(orc_sim *s, double beta_m, double alpha, double nu0, double xi, double emit_m,
+                       int ntres, const orc_resonator *tres)
+{
+    if (s->trans || !(beta_m > 0.0) || !(emit_m >= 0.0) || ntres < 0 || ntres > ORC_MAX_RES)
+        return -1;
+    const double pi = 3.14159265358979323846264338327950;
+    s->trans = 1;
+    s->tb_beta = beta_m;
+    s->tb_alpha = alpha;
+    s->tb_gamma = (1.0 + alpha * alpha) / beta_m;
+    s->tb_mu0 = 2.0 * pi * nu0;
+    s->tb_xi = xi;
+    int sr = !(s->flags & ORC_NO_SR), qe = sr && !(s->flags & ORC_NO_QE);
+    s->tb_Dx = qe ? s->dv.U0_over_E0 : 0.0;
+    s->tb_sx = sqrt(beta_m * emit_m);
+    s->tb_sxp = sqrt(s->tb_gamma * emit_m);
+    s->ntres = ntres;
+    for (int r = 0; r < ntres; ++r)
+        s->tres[r] = tres[r];
+    s->x = (double **)calloc(s->nb, sizeof(double *));
+    s->xp = (double **)calloc(s->nb, sizeof(double *));
+    for (int m = 0; m < s->nb; ++m) {
+        s->x[m] = (double *)calloc(s->n_mp[m] > 0 ? s->n_mp[m] : 1, sizeof(double));
+        s->xp[m] = (double *)calloc(s->n_mp[m] > 0 ? s->n_mp[m] : 1, sizeof(double));
+    }
+    s->dip = (double *)calloc((size_t)s->nb * s->nbins, sizeof(double));
+    s->Vt = (double *)calloc((size_t)s->nb * s->nbins, sizeof(double));
+    s->Wtlag = (double *)calloc(s->nbins, sizeof(double));
+    for (int l = 0; l < s->nbins; ++l)
+        for (int r = 0; r < ntres; ++r)
+            if (tres[r].range & ORC_RANGE_SHORT)
+                s->Wtlag[l] += orc_twake(&tres[r], (double)l * s->Delta);
+    double amin = 0.0;
+    int any_long = 0;
+    for (int r = 0; r < ntres; ++r) {
+        if (!(tres[r].range & ORC_RANGE_LONG))
+            continue;
+        double a, wb;
+        res_consts(&tres[r], &a, &wb);
+        if (!any_long || a < amin)
+            amin = a;
+        any_long = 1;
+    }
+    s->nthist = any_long ? (int)ceil(-log(ORC_HISTORY_CUTOFF) / (amin * s->ring.T0_s)) + 2 : 1;
+    s->Atlr = (double complex *)calloc((size_t)(ntres > 0 ? ntres : 1) * s->nb, sizeof(double complex));
+    s->Ethist = (double complex *)calloc((size_t)(ntres > 0 ? ntres : 1) * s->nthist * s->nb, sizeof(double complex));
+    s->tmoments = (double *)calloc((size_t)s->nb * 4, sizeof(double));
+    return 0;
 }
 
 void orc_get_derived(const orc_sim *s, double out[12])
@@ -414,6 +514,17 @@ void orc_init_particles(orc_sim *s)
             for (int e = 0; e < 4 && i + e < n; ++e) {
                 s->tau[m][i + e] = s->dv.sigma_tau0 * a[e];
                 s->delta[m][i + e] = s->ring.sigma_delta * b[e];
+            }
+            if (s->trans) {
+                /* matched Gaussian: x = sqrt(beta emit) a, x' = sqrt(emit / beta) (b - alpha a) */
+                double c[4], d[4];
+                orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, 0u, 5u, c);
+                orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, 0u, 6u, d);
+                const double emit = s->tb_sx * s->tb_sx / s->tb_beta;
+                for (int e = 0; e < 4 && i + e < n; ++e) {
+                    s->x[m][i + e] = s->tb_sx * c[e];
+                    s->xp[m][i + e] = sqrt(emit / s->tb_beta) * (d[e] - s->tb_alpha * c[e]);
+                }
             }
         }
     }
@@ -556,6 +667,99 @@ static double complex history_sum(const orc_sim *s, int r, int m)
     return acc;
 }
 
+/* Transverse short-range voltage at cell coordinate x of bunch m, linear
+ * between cell centres like the longitudinal one (zero outside the mesh). */
+static double vt_at(const orc_sim *s, int m, double xc)
+{
+    const int nb = s->nbins;
+    if (!(xc >= 0.0 && xc < (double)nb))
+        return 0.0;
+    const double *V = s->Vt + (size_t)m * nb;
+    if (s->flags & ORC_KICK_NGP)
+        return V[(int)floor(xc)];
+    double u = xc - 0.5;
+    if (u <= 0.0)
+        return V[0];
+    if (u >= (double)(nb - 1))
+        return V[nb - 1];
+    double j0 = floor(u);
+    double f = u - j0;
+    int j = (int)j0;
+    return (1.0 - f) * V[j] + f * V[j + 1];
+}
+
+/* Transverse long-range voltage: sum over transverse long-range resonators of
+ * Im(A e^{s tau}). */
+static double vtlr_at(const orc_sim *s, int m, double tau)
+{
+    double v = 0.0;
+    for (int r = 0; r < s->ntres; ++r) {
+        if (!(s->tres[r].range & ORC_RANGE_LONG))
+            continue;
+        double a, wb;
+        res_consts(&s->tres[r], &a, &wb);
+        v += cimag(s->Atlr[(size_t)r * s->nb + m] * cexp((-a + I * wb) * tau));
+    }
+    return v;
+}
+
+/* Transverse short-range voltage of one bunch from its dipole sums (sum of x
+ * per cell): V[j] = q * sum_{k<=j} dip[k] * Wt((j-k) Delta), Eq. 6 second line. */
+void orc_vt_direct(const orc_sim *s, const double *dip, double q, double *V)
+{
+    for (int j = 0; j < s->nbins; ++j) {
+        double v = 0.0;
+        for (int k = 0; k <= j; ++k)
+            v += dip[k] * s->Wtlag[j - k];
+        V[j] = q * v;
+    }
+}
+
+/* Transverse emission of one passage: c q sum_k dip[k] e^{-s tau_k},
+ * c = wr^2 Rs / (Q wb) (so that the wake is Im(c e^{s t})). */
+static double complex temission(const orc_sim *s, int r, const double *dip, double q)
+{
+    double a, wb;
+    res_consts(&s->tres[r], &a, &wb);
+    const double wr = 2.0 * 3.14159265358979323846264338327950 * s->tres[r].fr_Hz;
+    double complex sr = -a + I * wb;
+    double complex acc = 0.0;
+    for (int k = 0; k < s->nbins; ++k) {
+        if (dip[k] == 0.0)
+            continue;
+        double tk = -s->H + ((double)k + 0.5) * s->Delta;
+        acc += dip[k] * cexp(-sr * tk);
+    }
+    return wr * wr * s->tres[r].Rs_ohm / (s->tres[r].Q * wb) * q * acc;
+}
+
+/* Direct history sum of the transverse emissions (as history_sum). */
+static double complex thistory_sum(const orc_sim *s, int r, int m)
+{
+    double a, wb;
+    res_consts(&s->tres[r], &a, &wb);
+    double complex sr = -a + I * wb;
+    const int64_t n = s->turn;
+    const int h = s->ring.h;
+    double complex acc = 0.0;
+    for (int64_t back = 0; back < s->nthist; ++back) {
+        int64_t np = n - back;
+        if (np < 0)
+            break;
+        const double complex *E = s->Ethist + ((size_t)r * s->nthist + (size_t)(np % s->nthist)) * s->nb;
+        for (int mp = 0; mp < s->nb; ++mp) {
+            int64_t D = back * (int64_t)h + (int64_t)s->bucket[m] - (int64_t)s->bucket[mp];
+            if (D <= 0)
+                continue;
+            double dt = (double)D * s->dv.T_rf;
+            if (exp(-a * dt) < ORC_HISTORY_CUTOFF)
+                continue;
+            acc += cexp(sr * dt) * E[mp];
+        }
+    }
+    return acc;
+}
+
 /* One turn for every bunch in fill order, then the wakes for the next turn. */
 static void one_turn(orc_sim *s)
 {
@@ -566,28 +770,60 @@ static void one_turn(orc_sim *s)
         memset(hist, 0, sizeof(int32_t) * s->nbins);
         int64_t out = 0;
         double *tau = s->tau[m], *delta = s->delta[m];
+        double *dip = s->trans ? s->dip + (size_t)m * s->nbins : NULL;
+        if (dip)
+            memset(dip, 0, sizeof(double) * s->nbins);
         for (int64_t i = 0; i < n; i += 4) {
-            double r[4] = {0.0, 0.0, 0.0, 0.0};
+            double r[4] = {0.0, 0.0, 0.0, 0.0}, rx[4] = {0.0, 0.0, 0.0, 0.0}, rxp[4] = {0.0, 0.0, 0.0, 0.0};
             if (s->dv.qe_amp != 0.0)
                 orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, turn32, 0u, r);
+            if (s->trans && s->tb_Dx != 0.0) {
+                orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, turn32, 3u, rx);
+                orc_normal_quad(s->seed, (uint32_t)(i / 4), (uint32_t)m, turn32, 4u, rxp);
+            }
             for (int e = 0; e < 4 && i + e < n; ++e) {
                 double t = tau[i + e], d = delta[i + e];
                 /* wake kick with the previous turn's wake (zero on turn 0) */
                 double V = vsr_at(s, m, orc_cell_coord(s, t)) + vlr_at(s, m, t);
                 d = d - V / s->ring.E0_eV;
+                const double d_before = d;
                 /* Eq. 1: RF gain (main and harmonic cavities) minus mean radiation loss */
                 d = d + s->dv.V_over_E0 * sin(s->dv.phi_s - s->dv.omega_rf * t);
                 for (int k = 0; k < s->nharm; ++k)
                     d = d + s->harm_VoE0[k] * sin(s->harm[k].phi_rad - s->harm_nw[k] * t);
+                const double d_gain = d;
                 d = d - s->dv.U0_over_E0;
                 /* Eq. 5, delta line: damping and quantum excitation */
                 d = d * (1.0 - s->dv.D) + s->dv.qe_amp * r[e];
+                if (s->trans) {
+                    double x = s->x[m][i + e], xp = s->xp[m][i + e];
+                    /* transverse wake kick (Eq. 6, second line), previous turn's wake */
+                    double Vt = vt_at(s, m, orc_cell_coord(s, t)) + vtlr_at(s, m, t);
+                    xp = xp + Vt / s->ring.E0_eV;
+                    /* Eq. 5, x' line: momentum ratio across the cavity */
+                    xp = xp * (1.0 + d_before) / (1.0 + d_gain);
+                    /* Eqs. 3-4: betatron rotation with the chromatic phase of the new delta */
+                    double psi = s->tb_mu0 * (1.0 + s->tb_xi * d);
+                    double c = cos(psi), sn = sin(psi);
+                    double xn = (c + s->tb_alpha * sn) * x + s->tb_beta * sn * xp;
+                    double xpn = -s->tb_gamma * sn * x + (c - s->tb_alpha * sn) * xp;
+                    /* Eq. 5, x and x' lines: excitation */
+                    xn = xn + s->tb_sx * sqrt(s->tb_Dx) * rx[e];
+                    xpn = xpn + s->tb_sxp * sqrt(s->tb_Dx) * rxp[e];
+                    s->x[m][i + e] = xn;
+                    s->xp[m][i + e] = xpn;
+                }
                 /* Eq. 2 with the new energy deviation (reading R1) */
                 t = t + s->ring.alpha_c * s->ring.T0_s * d;
                 tau[i + e] = t;
                 delta[i + e] = d;
-                /* binning (Sec. 2.3) */
+                /* binning (Sec. 2.3); dipole sums of the same cells */
                 out += bin_one(s, t, hist);
+                if (dip) {
+                    double xc = orc_cell_coord(s, t);
+                    if (xc >= 0.0 && xc < (double)s->nbins)
+                        dip[(int)xc] += s->x[m][i + e];
+                }
             }
         }
         s->out_count[m] = out;
@@ -610,6 +846,24 @@ static void one_turn(orc_sim *s)
         mo[3] = n > 0 ? sqrt(vd / (double)n) : 0.0;
         mo[4] = (double)(n - out);
         mo[5] = (double)out;
+        if (s->trans) {
+            double sx = 0.0, sxp = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                sx += s->x[m][i];
+                sxp += s->xp[m][i];
+            }
+            double mx = n > 0 ? sx / (double)n : 0.0, mxp = n > 0 ? sxp / (double)n : 0.0;
+            double vx = 0.0, vxp = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                vx += (s->x[m][i] - mx) * (s->x[m][i] - mx);
+                vxp += (s->xp[m][i] - mxp) * (s->xp[m][i] - mxp);
+            }
+            double *tm = s->tmoments + (size_t)m * 4;
+            tm[0] = mx;
+            tm[1] = n > 0 ? sqrt(vx / (double)n) : 0.0;
+            tm[2] = mxp;
+            tm[3] = n > 0 ? sqrt(vxp / (double)n) : 0.0;
+        }
     }
     /* wakes from this turn's histograms, applied at the start of the next */
     for (int m = 0; m < s->nb; ++m)
@@ -623,16 +877,68 @@ static void one_turn(orc_sim *s)
         for (int m = 0; m < s->nb; ++m)
             s->Alr[(size_t)r * s->nb + m] = history_sum(s, r, m);
     }
+    if (s->trans) {
+        for (int m = 0; m < s->nb; ++m)
+            orc_vt_direct(s, s->dip + (size_t)m * s->nbins, s->q_mp[m], s->Vt + (size_t)m * s->nbins);
+        for (int r = 0; r < s->ntres; ++r) {
+            if (!(s->tres[r].range & ORC_RANGE_LONG))
+                continue;
+            double complex *E = s->Ethist + ((size_t)r * s->nthist + (size_t)(s->turn % s->nthist)) * s->nb;
+            for (int m = 0; m < s->nb; ++m)
+                E[m] = temission(s, r, s->dip + (size_t)m * s->nbins, s->q_mp[m]);
+            for (int m = 0; m < s->nb; ++m)
+                s->Atlr[(size_t)r * s->nb + m] = thistory_sum(s, r, m);
+        }
+    }
     s->turn += 1;
 }
 
-/* Track nturns; if rec is non-null it receives [nturns][nb][6] moments. */
-void orc_track(orc_sim *s, int64_t nturns, double *rec)
+/* Track nturns; if rec is non-null it receives [nturns][nb][6] moments, if
+ * trec is non-null (transverse plane set) [nturns][nb][4]: <x>, sig_x, <x'>, sig_x'. */
+void orc_track2(orc_sim *s, int64_t nturns, double *rec, double *trec)
 {
     for (int64_t t = 0; t < nturns; ++t) {
         one_turn(s);
         if (rec)
             memcpy(rec + (size_t)t * s->nb * 6, s->moments, sizeof(double) * s->nb * 6);
+        if (trec && s->trans)
+            memcpy(trec + (size_t)t * s->nb * 4, s->tmoments, sizeof(double) * s->nb * 4);
+    }
+}
+
+void orc_track(orc_sim *s, int64_t nturns, double *rec)
+{
+    orc_track2(s, nturns, rec, NULL);
+}
+
+void orc_set_tparticles(orc_sim *s, int m, const double *x, const double *xp)
+{
+    memcpy(s->x[m], x, sizeof(double) * s->n_mp[m]);
+    memcpy(s->xp[m], xp, sizeof(double) * s->n_mp[m]);
+}
+
+void orc_get_tparticles(const orc_sim *s, int m, double *x, double *xp)
+{
+    memcpy(x, s->x[m], sizeof(double) * s->n_mp[m]);
+    memcpy(xp, s->xp[m], sizeof(double) * s->n_mp[m]);
+}
+
+void orc_get_dip(const orc_sim *s, double *dip)
+{
+    memcpy(dip, s->dip, sizeof(double) * (size_t)s->nb * s->nbins);
+}
+
+void orc_get_vt(const orc_sim *s, double *V)
+{
+    memcpy(V, s->Vt, sizeof(double) * (size_t)s->nb * s->nbins);
+}
+
+/* Transverse long-range amplitudes [ntres][nb] as interleaved (re, im). */
+void orc_get_atlr(const orc_sim *s, double *A)
+{
+    for (size_t i = 0; i < (size_t)s->ntres * s->nb; ++i) {
+        A[2 * i] = creal(s->Atlr[i]);
+        A[2 * i + 1] = cimag(s->Atlr[i]);
     }
 }
 

@@ -651,3 +651,135 @@ def test_flat_potential_equilibrium_is_stationary(oracle_mod):
     rec = s.track(3000)
     assert rec[1000:, 0, 1].mean() == pytest.approx(sig, rel=0.025)
     assert abs(rec[1000:, 0, 0].mean() - mean) < 0.03 * sig
+
+
+# ----------------------------------------------------------------------------- transverse plane
+TRES = dict(Rs_ohm=2e5, fr_Hz=1.5e9, Q=2e4, range=W.RANGE_BOTH)   # Ohm/m
+
+
+def _tplane(**kw):
+    t = dict(beta_m=10.0, alpha=0.0, tune=0.3, chromaticity=0.0, emittance_m=1e-9, resonators=[])
+    t.update(kw)
+    return t
+
+
+def test_transverse_wake_transforms_to_resonator_impedance(oracle_mod):
+    """i int W(t) e^{-i w t} dt = (wr/w) Rs / (1 + i Q (w/wr - wr/w)) for a
+    low-Q transverse resonator, at three frequencies."""
+    res = dict(Rs_ohm=1e6, fr_Hz=2e9, Q=3.0, range=W.RANGE_SHORT)
+    wr = 2 * math.pi * res["fr_Hz"]
+    t = np.linspace(0.0, 60e-9 * 3 / 2e9 * 1e9 / 60 * 40, 400001)
+    w_t = np.array([oracle_mod.twake(res, ti) for ti in t])
+    for f in (0.5, 1.0, 1.7):
+        w = f * wr
+        z = 1j * np.trapezoid(w_t * np.exp(-1j * w * t), t)
+        ref = (wr / w) * res["Rs_ohm"] / (1 + 1j * res["Q"] * (w / wr - wr / w))
+        assert abs(z - ref) < 2e-4 * abs(ref)
+    assert oracle_mod.twake(res, 0.0) == 0.0 and oracle_mod.twake(res, -1e-12) == 0.0
+
+
+def test_transverse_short_range_is_causal_and_linear(oracle_mod):
+    s = oracle_mod.OracleSim(W.ring_r0(), [], 128, 5.0, [0], [1e-3], [4], 1, 0,
+                             transverse=_tplane(resonators=[dict(TRES, range=W.RANGE_SHORT)]))
+    D = s.derived["Delta"]
+    dip = np.zeros(128)
+    dip[40] = 3e-4
+    v = s.vt_direct(dip, 2e-12)
+    lags = np.arange(128) - 40
+    ref = np.array([2e-12 * 3e-4 * oracle_mod.twake(dict(TRES), l * D) if l > 0 else 0.0 for l in lags])
+    assert np.allclose(v, ref, rtol=1e-12, atol=0.0)
+    dip2 = dip.copy()
+    dip2[70] = -1e-4
+    v2 = s.vt_direct(dip2, 2e-12)
+    one = np.zeros(128)
+    one[70] = -1e-4
+    assert np.allclose(v2, v + s.vt_direct(one, 2e-12), rtol=1e-12, atol=1e-30)
+
+
+@pytest.mark.parametrize("alpha,xi,d0", [(0.0, 0.0, 0.0), (0.7, 0.0, 0.0), (0.0, 2.5, 1e-3), (-0.4, -1.5, -2e-3)])
+def test_betatron_map_is_the_twiss_rotation(oracle_mod, alpha, xi, d0):
+    """One turn of particles at tau = 0 (no radiation: delta stays) maps (x,
+    x') by the Twiss matrix of phase 2 pi nu0 (1 + xi delta): det 1, the
+    elements of Eq. 4."""
+    beta, nu = 12.0, 0.27
+    s = oracle_mod.OracleSim(W.ring_r0(), [], 64, 5.0, [0], [0.0], [4], 1, W.NO_SR,
+                             transverse=_tplane(beta_m=beta, alpha=alpha, tune=nu, chromaticity=xi))
+    s.set_particles(0, np.zeros(4), np.full(4, d0))
+    s.set_tparticles(0, np.array([1e-4, 0.0, 0.0, 0.0]), np.array([0.0, 1e-5, 0.0, 0.0]))
+    s.track(1, record=False)
+    x, xp = s.tparticles(0)
+    M = np.array([[x[0] / 1e-4, x[1] / 1e-5], [xp[0] / 1e-4, xp[1] / 1e-5]])
+    psi = 2 * math.pi * nu * (1 + xi * d0)
+    g = (1 + alpha * alpha) / beta
+    ref = np.array([[math.cos(psi) + alpha * math.sin(psi), beta * math.sin(psi)],
+                    [-g * math.sin(psi), math.cos(psi) - alpha * math.sin(psi)]])
+    assert np.allclose(M, ref, rtol=0, atol=1e-12)
+    assert np.linalg.det(M) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_transverse_radiation_damping_rate(oracle_mod):
+    """A coherent betatron oscillation damps through the momentum ratio across
+    the cavity at the rate U0 / (2 E0 T0) (J_x = 1), without excitation."""
+    ring = W.ring_r0()
+    s = oracle_mod.OracleSim(ring, [], 64, 5.0, [0], [0.0], [400], 2, W.NO_QE, transverse=_tplane())
+    s.init_particles()
+    x, xp = s.tparticles(0)
+    s.set_tparticles(0, x + 5e-4, xp)
+    _, trec = s.track2(3000)
+    beta = 10.0
+    z = trec[:, 0, 0] / math.sqrt(beta) - 1j * math.sqrt(beta) * trec[:, 0, 2]
+    n = np.arange(3000)
+    rate = np.polyfit(n, np.log(np.abs(z)), 1)[0] / ring["T0_s"]
+    assert rate == pytest.approx(-ring["U0_eV"] / (2 * ring["E0_eV"] * ring["T0_s"]), rel=0.02)
+
+
+def test_transverse_equilibrium_emittance_is_kept(oracle_mod):
+    """From the matched start the emittance stays at its equilibrium value
+    (damping through the cavity balanced by the excitation of Eq. 5)."""
+    ring = W.ring_r0()
+    emit = 2e-9
+    s = oracle_mod.OracleSim(ring, [], 64, 5.0, [0], [0.0], [4000], 3, 0,
+                             transverse=_tplane(emittance_m=emit, alpha=0.3, beta_m=8.0))
+    s.init_particles()
+    _, trec = s.track2(3000)
+    g = (1 + 0.09) / 8.0
+    assert np.mean(trec[1000:, 0, 1] ** 2) == pytest.approx(8.0 * emit, rel=0.04)
+    assert np.mean(trec[1000:, 0, 3] ** 2) == pytest.approx(g * emit, rel=0.04)
+
+
+def test_transverse_coupled_bunch_growth_rate(oracle_mod):
+    """Four point-like bunches, a narrow long-range transverse resonator on
+    the negative-frequency line of mode 3: the mode grows at
+    -(I_b M beta / (2 E0 T0)) sum_p Re Z((pM + mu) w0 + w_beta), the result of
+    the turn-by-turn kick model summed over lines (Poisson summation)."""
+    ring = W.ring_r0()
+    T0, h = ring["T0_s"], ring["h"]
+    M, nu, beta, Ib, Rs, Q = 4, 0.3, 20.0, 5e-3, 1.2e7, 2e4
+    w0 = 2 * math.pi / T0
+    fr = (1441 - nu) / T0
+    tres = dict(Rs_ohm=Rs, fr_Hz=fr, Q=Q, range=W.RANGE_LONG)
+    buckets = [m * (h // M) for m in range(M)]
+    n_mp, turns = 200, 3000
+    s = oracle_mod.OracleSim(ring, [], 64, 5.0, buckets, [Ib] * M, [n_mp] * M, 4, W.NO_SR,
+                             transverse=_tplane(beta_m=beta, tune=nu, resonators=[tres]))
+    g = np.random.default_rng(8)
+    for m in range(M):
+        s.set_particles(m, g.normal(0, 3e-12, n_mp), np.zeros(n_mp))
+        ph = g.uniform(0, 2 * math.pi)
+        s.set_tparticles(m, np.full(n_mp, 1e-6 * math.cos(ph)), np.full(n_mp, -1e-6 / beta * math.sin(ph)))
+    _, trec = s.track2(turns)
+    z = trec[:, :, 0] / math.sqrt(beta) - 1j * math.sqrt(beta) * trec[:, :, 2]
+    # mode mu: phase (2 pi nu + 2 pi mu) / M from one bunch to the next
+    th = (2 * math.pi * nu + 2 * math.pi * 3) / M
+    X3 = (z * np.exp(-1j * th * np.arange(M))[None, :]).sum(axis=1)
+    rate = np.polyfit(np.arange(1000, turns), np.log(np.abs(X3[1000:])), 1)[0] / T0
+    wr = 2 * math.pi * fr
+
+    def re_z(w):
+        return ((wr / w) * Rs / (1 + 1j * Q * (w / wr - wr / w))).real
+
+    p = np.arange(-2000, 2000)
+    lines = (p * M + 3) * w0 + nu * w0
+    pred = -(Ib * M * beta / (2 * ring["E0_eV"] * T0)) * np.sum(re_z(lines[lines != 0]))
+    assert pred > 500
+    assert rate == pytest.approx(pred, rel=0.02)
