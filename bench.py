@@ -37,6 +37,12 @@ Harmonic-cavity scan: python bench.py --workload hcscan tracks a single 1 mA
 bunch of ring R0 with the broadband wake and an active third-harmonic
 cavity at fractions 0 ... 1.2 of the flat-potential voltage (one batch) and
 prints the equilibrium bunch length per setting.
+
+Transverse plane: python bench.py --workload fill390t tracks the 390-bunch
+fill with a horizontal plane (beta 10 m, tune 0.31, chromaticity 1.5,
+1 nm) and a transverse HOM (200 kOhm/m, 1.5 GHz, Q 2e4, short and long
+range) besides the longitudinal wakes, and prints its throughput and the
+push roofline (40 B per macro-particle-turn: tau, delta, x, x').
 """
 from __future__ import annotations
 
@@ -79,7 +85,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
-    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan"], default="fill390")
+    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t"],
+                    default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests tracked together")
@@ -515,6 +522,61 @@ def hcscan_bench(args, rank, local):
     return 0
 
 
+def fill390t_bench(args, rank, local):
+    """The 390-bunch fill with a transverse plane: throughput and push roofline."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    base = W.fill_390(precision=W.PREC_MIXED)
+    tplane = dict(beta_m=10.0, alpha=0.0, tune=0.31, chromaticity=1.5, emittance_m=1e-9,
+                  resonators=[dict(Rs_ohm=2e5, fr_Hz=1.5e9, Q=2e4, range=W.RANGE_BOTH)])
+    run = W.Run(**{**base.__dict__, "transverse": tplane, "name": base.name + " + transverse plane"})
+    K, Wm = min(args.steps, 5000), max(args.warmup, 3)
+    stream = torch.cuda.current_stream()
+    tr = pkg.tracker_for_run(run, record_turns=K + Wm + GRAPH_TURNS + 600)
+    tr.init_particles(stream)
+    tr.set_graph(GRAPH_TURNS)
+    tr.track(max(Wm, GRAPH_TURNS), stream)
+    tr.sync()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        tr.track(K, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    tr.sync()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    KR = 500
+    tr.set_timing(True)
+    tr.track(KR, stream)
+    tr.sync()
+    push_ms, post_ms, launches = tr.timing()
+    tr.set_timing(False)
+    n = run.n_particles
+    bpp = 40
+    push_s = push_ms / max(1, launches) * 1e-3
+    peak, kind = measured_peak_hbm()
+    achieved = bpp * n / push_s / 1e9
+    line = {"metric": "macro-particle-turns/s (390-bunch fill with a transverse plane)", "value": n * K / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": run.name, "transverse": {k: v for k, v in tplane.items() if k != "resonators"},
+                       "transverse_resonator": tplane["resonators"][0], "turns_timed": K},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": kind, "kernel": "k_push_mixed_t",
+                         "bytes_per_unit": bpp, "unit_count": n, "push_us": push_s * 1e6,
+                         "post_us": post_ms / max(1, launches) * 1e3},
+            "gpu_launches": 2 * K, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    tr.close()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -528,6 +590,8 @@ def main():
         return rwscan_bench(args, rank, local)
     if args.workload == "hcscan":
         return hcscan_bench(args, rank, local)
+    if args.workload == "fill390t":
+        return fill390t_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)

@@ -147,6 +147,47 @@ mbt_status mbt_add_resonator(mbt_ctx *ctx, double Rs_ohm, double fr_Hz, double Q
  * is a resonator near n f_rf with the long-range bit instead. */
 mbt_status mbt_add_harmonic_cavity(mbt_ctx *ctx, int n, double V_V, double phi_rad);
 
+/* Transverse plane (Eqs. 3-5, x lines; Eq. 6, second line).  One plane per
+ * run (x or y: the paper treats them alike, and they couple to each other
+ * through nothing but the longitudinal motion, which they do not change, so
+ * two runs with the same seed give both planes of one run).  Twiss beta_m,
+ * alpha at the tracking point, where the dispersion is taken as zero;
+ * betatron phase advance per turn 2 pi tune (1 + chromaticity delta) (Eq. 3);
+ * equilibrium emittance emittance_m.  Per turn, after the previous turn's
+ * transverse wake kick x' += V_x(tau) / E0: x' scales by the momentum ratio
+ * across the RF cavity (1 + delta) / (1 + delta + eps) (Eq. 5), the Twiss
+ * rotation (Eq. 4) uses the updated delta, then the excitation
+ * sqrt(beta emit D_x) r, sqrt(gamma emit D_x) r' with D_x = U0 / E0 (the
+ * damping the momentum ratio produces on average, so emittance_m is the
+ * equilibrium; none with MBT_NO_SR / MBT_NO_QE).  Only before mbt_set_fill.
+ * Checkpoints include it; mbt_track_resident refuses it (MBT_ERR_UNSUPPORTED). */
+mbt_status mbt_set_transverse(mbt_ctx *ctx, double beta_m, double alpha, double tune, double chromaticity,
+                              double emittance_m);
+
+/* Add a transverse resonator (shunt impedance Rs in Ohm/m): wake
+ * W(t > 0) = (wr^2 Rs / (Q wb)) e^{-a t} sin(wb t), a = wr / 2Q,
+ * wb = sqrt(wr^2 - a^2); the kick of a particle is the sum over earlier
+ * cells and passages of charge x dipole moment x W (Eq. 6, second line).
+ * range MBT_RANGE_* as for mbt_add_resonator; long-range entries count
+ * towards the limit of 4 shared with the longitudinal ones.  Needs
+ * mbt_set_transverse first; only before mbt_set_fill. */
+mbt_status mbt_add_transverse_resonator(mbt_ctx *ctx, double Rs_ohm_per_m, double fr_Hz, double Q, int range);
+
+/* Copy one bunch's transverse coordinates from host arrays of n_mp[bunch]
+ * doubles (MBT_PREC_MIXED rounds to FP32) / to host arrays.  Synchronous. */
+mbt_status mbt_set_transverse_particles(mbt_ctx *ctx, int bunch, const double *x_m, const double *xp);
+mbt_status mbt_get_transverse_particles(mbt_ctx *ctx, int bunch, double *x_m, double *xp);
+
+/* Per-turn transverse moments of turns [turn0, turn0 + nturns) into
+ * out[nturns][nb][4]: <x>, rms x, <x'>, rms x' (after the turn's map, like
+ * mbt_read_moments).  Synchronous. */
+mbt_status mbt_read_transverse_moments(mbt_ctx *ctx, int64_t turn0, int64_t nturns, double *out);
+
+/* Dipole sums (sum of x over each cell's particles, [nb][nbins]) of the last
+ * completed turn and the transverse short-range voltage [V] built from them
+ * for the next kick ([nb][nbins]); either may be NULL.  Synchronous. */
+mbt_status mbt_read_transverse_wake(mbt_ctx *ctx, double *dipoles, double *V);
+
 /* Add a tabulated short-range wake (Sec. 2.3: other wakes, such as the
  * resistive wall, are added to the same wake).  W_V_per_C[i] is W(t_s[i]) in
  * V/C (positive = energy loss), t_s[0] = 0 (W(0+)) and t_s strictly

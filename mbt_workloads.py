@@ -69,6 +69,7 @@ class Run:
     wake_tables: list = field(default_factory=list)      # [(t [s], W [V/C])] short range
     resistive_wall: list = field(default_factory=list)   # [dict(radius_m, conductivity_S_per_m, length_m)]
     harmonic_cavities: list = field(default_factory=list)  # [dict(n, V_V, phi_rad)] active harmonic RF
+    transverse: dict = None   # dict(beta_m, alpha, tune, chromaticity, emittance_m, resonators=[...]) or None
 
     @property
     def nb(self) -> int:

@@ -29,7 +29,9 @@ NO_SR, NO_QE, KICK_NGP = 1, 2, 4
 # every entry point declared in include/mbt.h
 EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt_last_error",
            "mbt_add_resonator", "mbt_add_wake_table", "mbt_add_resistive_wall",
-           "mbt_add_harmonic_cavity", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
+           "mbt_add_harmonic_cavity", "mbt_set_transverse", "mbt_add_transverse_resonator",
+           "mbt_set_transverse_particles", "mbt_get_transverse_particles", "mbt_read_transverse_moments",
+           "mbt_read_transverse_wake", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
            "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
@@ -113,6 +115,12 @@ def lib() -> ctypes.CDLL:
                 "mbt_add_wake_table": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_add_resistive_wall": ([_vp, _d, _d, _d], _i),
                 "mbt_add_harmonic_cavity": ([_vp, _i, _d, _d], _i),
+                "mbt_set_transverse": ([_vp, _d, _d, _d, _d, _d], _i),
+                "mbt_add_transverse_resonator": ([_vp, _d, _d, _d, _i], _i),
+                "mbt_set_transverse_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
+                "mbt_get_transverse_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
+                "mbt_read_transverse_moments": ([_vp, _i64, _i64, _P(_d)], _i),
+                "mbt_read_transverse_wake": ([_vp, _P(_d), _P(_d)], _i),
                 "mbt_set_fill": ([_vp, _i, _P(_i32), _P(_d), _P(_i64)], _i),
                 "mbt_set_record": ([_vp, _i64], _i), "mbt_init_particles": ([_vp, _vp], _i),
                 "mbt_set_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
@@ -168,7 +176,7 @@ class Tracker:
     def __init__(self, ring: dict, precision: int = PREC_MIXED, flags: int = 0, seed: int = 1,
                  resonators=(), nbins: int = 256, half_width_sigmas: float = 5.0,
                  buckets=(0,), currents_A=(1e-3,), n_mp=(10_000,), record_turns: int = 4096,
-                 wake_tables=(), resistive_wall=(), harmonic_cavities=()):
+                 wake_tables=(), resistive_wall=(), harmonic_cavities=(), transverse=None):
         self._L = lib()
         self._h = ctypes.c_void_p()
         r = Ring(E0_eV=ring["E0_eV"], T0_s=ring["T0_s"], h=int(ring["h"]), reserved=0, V_rf_V=ring["V_rf_V"],
@@ -187,6 +195,14 @@ class Tracker:
             if t.shape != w.shape:
                 raise ValueError("wake table: t and W differ in length")
             self._chk(self._L.mbt_add_wake_table(self._h, len(t), _ptr(t, _d), _ptr(w, _d)))
+        self.transverse = transverse
+        if transverse is not None:
+            self._chk(self._L.mbt_set_transverse(self._h, float(transverse["beta_m"]), float(transverse.get("alpha", 0.0)),
+                                                 float(transverse["tune"]), float(transverse.get("chromaticity", 0.0)),
+                                                 float(transverse["emittance_m"])))
+            for res in transverse.get("resonators", ()):
+                self._chk(self._L.mbt_add_transverse_resonator(self._h, res["Rs_ohm"], res["fr_Hz"], res["Q"],
+                                                               int(res["range"])))
         for hc in harmonic_cavities:
             self._chk(self._L.mbt_add_harmonic_cavity(self._h, int(hc["n"]), float(hc["V_V"]), float(hc["phi_rad"])))
         for rw in resistive_wall:
@@ -277,6 +293,32 @@ class Tracker:
         i = Info()
         self._chk(self._L.mbt_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def set_transverse_particles(self, bunch: int, x, xp):
+        x = np.ascontiguousarray(x, np.float64)
+        xp = np.ascontiguousarray(xp, np.float64)
+        if x.size != self.n_mp[bunch] or xp.size != self.n_mp[bunch]:
+            raise ValueError("need n_mp[bunch] coordinates")
+        self._chk(self._L.mbt_set_transverse_particles(self._h, int(bunch), _ptr(x, _d), _ptr(xp, _d)))
+
+    def transverse_particles(self, bunch: int):
+        n = int(self.n_mp[bunch])
+        x = np.empty(n, np.float64)
+        xp = np.empty(n, np.float64)
+        self._chk(self._L.mbt_get_transverse_particles(self._h, int(bunch), _ptr(x, _d), _ptr(xp, _d)))
+        return x, xp
+
+    def transverse_moments(self, turn0: int, nturns: int) -> np.ndarray:
+        out = np.empty((int(nturns), self.nb, 4), np.float64)
+        self._chk(self._L.mbt_read_transverse_moments(self._h, int(turn0), int(nturns), _ptr(out, _d)))
+        return out
+
+    def transverse_wake(self):
+        """(dipole sums [nb][nbins] of the last turn, transverse voltage [nb][nbins] for the next kick)."""
+        dip = np.empty((self.nb, self.nbins), np.float64)
+        v = np.empty((self.nb, self.nbins), np.float64)
+        self._chk(self._L.mbt_read_transverse_wake(self._h, _ptr(dip, _d), _ptr(v, _d)))
+        return dip, v
 
     def set_graph(self, turns_per_graph: int):
         self._chk(self._L.mbt_set_graph(self._h, int(turns_per_graph)))
@@ -475,4 +517,5 @@ def tracker_for_run(run, precision=None, record_turns: int = 4096) -> Tracker:
                    seed=run.seed, resonators=run.resonators, nbins=run.nbins,
                    half_width_sigmas=run.half_width_sigmas, buckets=run.buckets, currents_A=run.currents_A,
                    n_mp=run.n_mp, record_turns=record_turns, wake_tables=run.wake_tables,
-                   resistive_wall=run.resistive_wall, harmonic_cavities=run.harmonic_cavities)
+                   resistive_wall=run.resistive_wall, harmonic_cavities=run.harmonic_cavities,
+                   transverse=run.transverse)

@@ -90,7 +90,15 @@ struct mbt_ctx {
   std::vector<double> current;
   std::vector<int64_t> nmp, off;
   int64_t n_particles = 0, n_alloc = 0;
-  std::vector<int> long_idx;   // indices into res of long-range resonators
+  std::vector<int> long_idx;   // long-range entries: index into res (plane 0) or tres (plane 1)
+  std::vector<int> long_plane;
+  // transverse plane
+  bool trans = false;
+  double t_beta = 0, t_alpha = 0, t_tune = 0, t_xi = 0, t_emit = 0;
+  std::vector<Resonator> tres;
+  void *d_x = nullptr, *d_xp = nullptr, *d_dip = nullptr, *d_vt = nullptr;
+  double *d_trec = nullptr, *d_tlag = nullptr;
+  float *d_tlag_f = nullptr;
   // device state
   std::vector<DevBuf> bufs;
   void *d_tau = nullptr;
@@ -242,6 +250,16 @@ double wake(const Resonator &q, double t) {
   return 2.0 * a * q.Rs * std::exp(-a * t) * (std::cos(wb * t) - (a / wb) * std::sin(wb * t));
 }
 
+// Transverse resonator wake [V/(C m)]: (wr^2 Rs / (Q wb)) e^{-a t} sin(wb t)
+// for t > 0, zero at and before t = 0 (Rs in Ohm/m).
+double twake(const Resonator &q, double t) {
+  if (!(t > 0.0)) return 0.0;
+  double a, wb;
+  res_consts(q, a, wb);
+  const double wr = 2.0 * kPi * q.fr;
+  return wr * wr * q.Rs / (q.Q * wb) * std::exp(-a * t) * std::sin(wb * t);
+}
+
 // Integral over [lo, hi] of the piecewise linear wake through (t[i], w[i]),
 // zero beyond the last sample.
 double table_integral(const std::vector<double> &t, const std::vector<double> &w, double lo, double hi) {
@@ -330,10 +348,12 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
   pl.max_nbins = 0;
   pl.max_nlong = 0;
   pl.max_nharm = 0;
+  pl.max_trans = 0;
   for (auto &r : st.runs) {
     pl.max_nbins = std::max(pl.max_nbins, r.nbins);
     pl.max_nlong = std::max(pl.max_nlong, r.nlong);
     pl.max_nharm = std::max(pl.max_nharm, r.nharm);
+    pl.max_trans = std::max(pl.max_trans, r.trans);
   }
   st.bytes += pb + 16;
   st.plan = pl;
@@ -379,7 +399,13 @@ void append_run(PlanStore &st, mbt_ctx *c, int mixed_tile) {
   if (c->precision == MBT_PREC_F64) {
     const int nchunk = (c->nbins + kF64RowChunk - 1) / kF64RowChunk;
     for (int m = 0; m < c->nb; ++m)
-      for (int ch = 0; ch < nchunk; ++ch) st.jobs.push_back(PostJob{ri, kJobWake, m, ch});
+      for (int ch = 0; ch < nchunk; ++ch) {
+        st.jobs.push_back(PostJob{ri, kJobWake, m, ch});
+        if (c->trans) st.jobs.push_back(PostJob{ri, kJobTrans, m, ch});
+      }
+  } else if (c->trans) {
+    for (int bt = 0; bt < c->ntile_b; ++bt)
+      for (int ch = 0; ch < c->nbins / kTransRows; ++ch) st.jobs.push_back(PostJob{ri, kJobTrans, bt, ch});
   }
 }
 
@@ -509,6 +535,40 @@ mbt_status mbt_add_resonator(mbt_ctx *c, double Rs, double fr, double Q, int ran
   return MBT_OK;
 }
 
+mbt_status mbt_set_transverse(mbt_ctx *c, double beta, double alpha, double tune, double xi, double emit) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "the transverse plane must be set before mbt_set_fill");
+  if (c->trans) return fail(c, MBT_ERR_STATE, "the transverse plane is already set");
+  if (!(beta > 0) || !std::isfinite(beta) || !std::isfinite(alpha) || !std::isfinite(tune) || !std::isfinite(xi) ||
+      !(emit >= 0) || !std::isfinite(emit))
+    return fail(c, MBT_ERR_ARG, "transverse plane needs beta > 0, emittance >= 0 and finite alpha, tune, chromaticity");
+  c->trans = true;
+  c->t_beta = beta;
+  c->t_alpha = alpha;
+  c->t_tune = tune;
+  c->t_xi = xi;
+  c->t_emit = emit;
+  return MBT_OK;
+}
+
+mbt_status mbt_add_transverse_resonator(mbt_ctx *c, double Rs, double fr, double Q, int range) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "resonators must be added before mbt_set_fill");
+  if (!c->trans) return fail(c, MBT_ERR_STATE, "set the transverse plane first");
+  if (!(Rs > 0) || !(fr > 0) || !(Q > 0.5) || range < 1 || range > 3)
+    return fail(c, MBT_ERR_ARG, "resonator needs Rs > 0, fr > 0, Q > 0.5, range 1..3");
+  if ((int)c->tres.size() >= kMaxRes) return fail(c, MBT_ERR_UNSUPPORTED, "at most %d transverse resonators", kMaxRes);
+  int nl = 0;
+  for (auto &r : c->res) nl += (r.range & MBT_RANGE_LONG) ? 1 : 0;
+  for (auto &r : c->tres) nl += (r.range & MBT_RANGE_LONG) ? 1 : 0;
+  if ((range & MBT_RANGE_LONG) && nl >= kMaxLong)
+    return fail(c, MBT_ERR_UNSUPPORTED, "at most %d long-range resonators (both planes)", kMaxLong);
+  c->tres.push_back(Resonator{Rs, fr, Q, range});
+  return MBT_OK;
+}
+
 mbt_status mbt_add_harmonic_cavity(mbt_ctx *c, int n, double V, double phi) {
   if (!c) return MBT_ERR_ARG;
   c->err.clear();
@@ -605,8 +665,17 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   c->n_alloc = o + 4;
   c->ntile_b = (nb + kBunchTile - 1) / kBunchTile;
   c->long_idx.clear();
+  c->long_plane.clear();
   for (int i = 0; i < (int)c->res.size(); ++i)
-    if (c->res[i].range & MBT_RANGE_LONG) c->long_idx.push_back(i);
+    if (c->res[i].range & MBT_RANGE_LONG) {
+      c->long_idx.push_back(i);
+      c->long_plane.push_back(0);
+    }
+  for (int i = 0; i < (int)c->tres.size(); ++i)
+    if (c->tres[i].range & MBT_RANGE_LONG) {
+      c->long_idx.push_back(i);
+      c->long_plane.push_back(1);
+    }
   c->nlong = (int)c->long_idx.size();
   const int nl = std::max(1, c->nlong);
   const bool mixed = c->precision == MBT_PREC_MIXED;
@@ -641,6 +710,16 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     for (int mt = 0; mt < nbins / 128; ++mt) toep_bytes += (size_t)512 * std::min(nbins, 128 * (mt + 1));
   }
   ALLOC(c->d_toep, toep_bytes);
+  if (c->trans) {
+    const size_t fs = mixed ? sizeof(float) : sizeof(double);
+    ALLOC(c->d_x, (size_t)c->n_alloc * fs);
+    ALLOC(c->d_xp, (size_t)c->n_alloc * fs);
+    ALLOC(c->d_dip, (size_t)2 * nb * nbins * fs);
+    ALLOC(c->d_vt, (size_t)nb * nbins * fs);
+    ALLOC(c->d_trec, (size_t)c->cap * nb * kTRecord * sizeof(double));
+    ALLOC(c->d_tlag, (size_t)nbins * sizeof(double));
+    ALLOC(c->d_tlag_f, (size_t)nbins * sizeof(float));
+  }
 #undef ALLOC
 
   // macro-particle charge
@@ -712,11 +791,15 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     std::vector<float2> emis_f((size_t)nl * nbins, make_float2(0, 0));
     std::vector<double2> step((size_t)nl * nb, make_double2(1, 0));
     for (int li = 0; li < c->nlong; ++li) {
-      const Resonator &r = c->res[c->long_idx[li]];
+      const bool tr = c->long_plane[li] == 1;
+      const Resonator &r = tr ? c->tres[c->long_idx[li]] : c->res[c->long_idx[li]];
       double a, wb;
       res_consts(r, a, wb);
       const cplx s(-a, wb);
-      const cplx cc = 2.0 * a * r.Rs * cplx(1.0, a / wb);
+      // longitudinal: W = Re(c e^{st}), c = 2 a Rs (1 + i a / wb); transverse: W = Im(c e^{st}), c = wr^2 Rs / (Q wb)
+      const double wr = 2.0 * kPi * r.fr;
+      const cplx cc = tr ? cplx(wr * wr * r.Rs / (r.Q * wb), 0.0) : 2.0 * a * r.Rs * cplx(1.0, a / wb);
+      rd.lr_plane[li] = tr ? 1 : 0;
       rd.lr_s[li] = make_double2(s.real(), s.imag());
       rd.lr_c[li] = make_double2(cc.real(), cc.imag());
       for (int k = 0; k < nbins; ++k) {
@@ -795,6 +878,46 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     rd.f_la[li] = li < c->nlong ? (float)(-rd.lr_s[li].x) : 0.f;
     rd.f_lw[li] = li < c->nlong ? (float)rd.lr_s[li].y : 0.f;
   }
+  if (c->trans) {
+    std::vector<double> tl(nbins, 0.0);
+    std::vector<float> tlf(nbins);
+    for (int l = 0; l < nbins; ++l) {
+      for (auto &r : c->tres)
+        if (r.range & MBT_RANGE_SHORT) tl[l] += twake(r, (double)l * c->Delta);
+      tlf[l] = (float)tl[l];
+    }
+    cudaMemcpy(c->d_tlag, tl.data(), nbins * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_tlag_f, tlf.data(), nbins * sizeof(float), cudaMemcpyHostToDevice);
+    const bool sr = !(c->flags & MBT_NO_SR), qe = sr && !(c->flags & MBT_NO_QE);
+    const double Dx = qe ? c->ring.U0_eV / c->ring.E0_eV : 0.0;
+    rd.trans = 1;
+    rd.x = c->d_x;
+    rd.xp = c->d_xp;
+    rd.dip = c->d_dip;
+    rd.vt = c->d_vt;
+    rd.trec = c->d_trec;
+    rd.tlag = c->d_tlag;
+    rd.tlag_f = c->d_tlag_f;
+    rd.t_beta = c->t_beta;
+    rd.t_alpha = c->t_alpha;
+    rd.t_gamma = (1.0 + c->t_alpha * c->t_alpha) / c->t_beta;
+    rd.t_mu0 = 2.0 * kPi * c->t_tune;
+    rd.t_xi = c->t_xi;
+    rd.t_emit = c->t_emit;
+    rd.t_nx = std::sqrt(c->t_beta * c->t_emit) * std::sqrt(Dx);
+    rd.t_nxp = std::sqrt(rd.t_gamma * c->t_emit) * std::sqrt(Dx);
+    // FP32 phase: the fractional tune (|2 pi frac| <= pi keeps the special-function unit accurate)
+    // plus the chromatic term of the full tune
+    rd.f_tmu0 = (float)(2.0 * kPi * (c->t_tune - std::nearbyint(c->t_tune)));
+    rd.f_tmu0xi = (float)(2.0 * kPi * c->t_tune * c->t_xi);
+    rd.f_tbeta = (float)rd.t_beta;
+    rd.f_talpha = (float)rd.t_alpha;
+    rd.f_tgamma = (float)rd.t_gamma;
+    rd.f_tnx = (float)rd.t_nx;
+    rd.f_tnxp = (float)rd.t_nxp;
+  }
+  rd.f_inv_omD = (float)(1.0 / rd.one_minus_D);
+  rd.f_U0oE0 = (float)rd.U0_over_E0;
   rd.nharm = (int)c->harm.size();
   for (int k = 0; k < rd.nharm; ++k) {
     const double n = c->harm[k][0], V = c->harm[k][1], ph = c->harm[k][2];
@@ -845,6 +968,11 @@ mbt_status mbt_init_particles(mbt_ctx *c, void *stream) {
   cudaMemsetAsync(c->d_agg, 0, (size_t)nl * c->ntile_b * 2 * sizeof(double2), s);
   cudaMemsetAsync(c->d_carry, 0, (size_t)nl * sizeof(double2), s);
   cudaMemsetAsync(c->d_turn, 0, 16, s);
+  if (c->trans) {
+    const size_t fs = c->precision == MBT_PREC_MIXED ? sizeof(float) : sizeof(double);
+    cudaMemsetAsync(c->d_dip, 0, (size_t)2 * c->nb * c->nbins * fs, s);
+    cudaMemsetAsync(c->d_vt, 0, (size_t)c->nb * c->nbins * fs, s);
+  }
   cudaError_t e = launch_init(c->own.plan, c->precision, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "init launch");
   return MBT_OK;
@@ -900,6 +1028,59 @@ mbt_status mbt_get_particles(mbt_ctx *c, int bunch, double *tau, double *delta) 
   }
   std::memcpy(delta, h + tb, (size_t)n * sizeof(double));
   return MBT_OK;
+}
+
+// Transverse coordinates of one bunch, host doubles <-> device (float for kMixed).
+static mbt_status transverse_copy(mbt_ctx *c, int bunch, double *x, double *xp, bool to_device) {
+  if (!c || !x || !xp) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (!c->trans) return fail(c, MBT_ERR_STATE, "no transverse plane");
+  if (bunch < 0 || bunch >= c->nb) return fail(c, MBT_ERR_ARG, "bunch out of range");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+  const int64_t n = c->nmp[bunch];
+  const bool mixed = c->precision == MBT_PREC_MIXED;
+  const size_t fs = mixed ? sizeof(float) : sizeof(double);
+  char *h = static_cast<char *>(stage(c, 2 * (size_t)n * fs));
+  if (!h) return fail(c, MBT_ERR_NOMEM, "pinned staging buffer");
+  char *dx = static_cast<char *>(c->d_x) + (size_t)c->off[bunch] * fs;
+  char *dxp = static_cast<char *>(c->d_xp) + (size_t)c->off[bunch] * fs;
+  double *arrs[2] = {x, xp};
+  if (to_device) {
+    for (int a = 0; a < 2; ++a) {
+      if (mixed) {
+        float *f = reinterpret_cast<float *>(h + a * n * fs);
+        for (int64_t i = 0; i < n; ++i) f[i] = (float)arrs[a][i];
+      } else {
+        std::memcpy(h + a * n * fs, arrs[a], (size_t)n * fs);
+      }
+    }
+    e = cudaMemcpy(dx, h, (size_t)n * fs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dxp, h + n * fs, (size_t)n * fs, cudaMemcpyHostToDevice);
+  } else {
+    e = cudaMemcpy(h, dx, (size_t)n * fs, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h + n * fs, dxp, (size_t)n * fs, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      for (int a = 0; a < 2; ++a) {
+        if (mixed) {
+          const float *f = reinterpret_cast<const float *>(h + a * n * fs);
+          for (int64_t i = 0; i < n; ++i) arrs[a][i] = f[i];
+        } else {
+          std::memcpy(arrs[a], h + a * n * fs, (size_t)n * fs);
+        }
+      }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "transverse particles");
+  return MBT_OK;
+}
+
+mbt_status mbt_set_transverse_particles(mbt_ctx *c, int bunch, const double *x, const double *xp) {
+  return transverse_copy(c, bunch, const_cast<double *>(x), const_cast<double *>(xp), true);
+}
+
+mbt_status mbt_get_transverse_particles(mbt_ctx *c, int bunch, double *x, double *xp) {
+  return transverse_copy(c, bunch, x, xp, false);
 }
 
 mbt_status mbt_set_graph(mbt_ctx *c, int turns) {
@@ -1161,6 +1342,7 @@ mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
   if (nturns == 0) return MBT_OK;
   if (c->precision != MBT_PREC_MIXED)
     return fail(c, MBT_ERR_UNSUPPORTED, "resident tracking is implemented for the mixed precision path");
+  if (c->trans) return fail(c, MBT_ERR_UNSUPPORTED, "resident tracking has no transverse plane");
   if (c->nb > kResidentMaxBunches)
     return fail(c, MBT_ERR_UNSUPPORTED, "resident tracking holds at most %d bunches", kResidentMaxBunches);
   int C = 0, per = 0;
@@ -1288,6 +1470,58 @@ mbt_status mbt_read_wake(mbt_ctx *c, double *Vsr, double *Phi) {
   return MBT_OK;
 }
 
+mbt_status mbt_read_transverse_moments(mbt_ctx *c, int64_t turn0, int64_t nturns, double *out) {
+  if (!c || !out) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (!c->trans) return fail(c, MBT_ERR_STATE, "no transverse plane");
+  long long turn;
+  mbt_status st = current_turn(c, &turn);
+  if (st != MBT_OK) return st;
+  if (turn0 < 0 || nturns < 0 || turn0 + nturns > turn || turn0 < turn - c->cap)
+    return fail(c, MBT_ERR_ARG, "turns [%lld, %lld) not in the record", (long long)turn0, (long long)(turn0 + nturns));
+  const size_t per = (size_t)c->nb * kTRecord;
+  int64_t t = 0;
+  while (t < nturns) {
+    const int64_t slot = (turn0 + t) % c->cap;
+    const int64_t len = std::min<int64_t>(nturns - t, c->cap - slot);
+    cudaError_t e = cudaMemcpy(out + (size_t)t * per, c->d_trec + (size_t)slot * per,
+                               (size_t)len * per * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read transverse moments");
+    t += len;
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_read_transverse_wake(mbt_ctx *c, double *dip, double *V) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  if (!c->trans) return fail(c, MBT_ERR_STATE, "no transverse plane");
+  long long turn;
+  mbt_status st = current_turn(c, &turn);
+  if (st != MBT_OK) return st;
+  if (turn < 1) return fail(c, MBT_ERR_STATE, "no turn tracked yet");
+  const size_t n = (size_t)c->nb * c->nbins;
+  const int par = (int)((turn - 1) & 1);
+  const bool mixed = c->precision == MBT_PREC_MIXED;
+  double *outs[2] = {dip, V};
+  const void *srcs[2] = {static_cast<const char *>(c->d_dip) + (size_t)par * n * (mixed ? 4 : 8), c->d_vt};
+  for (int a = 0; a < 2; ++a) {
+    if (!outs[a]) continue;
+    cudaError_t e;
+    if (mixed) {
+      std::vector<float> v(n);
+      e = cudaMemcpy(v.data(), srcs[a], n * sizeof(float), cudaMemcpyDeviceToHost);
+      for (size_t i = 0; i < n; ++i) outs[a][i] = v[i];
+    } else {
+      e = cudaMemcpy(outs[a], srcs[a], n * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "read transverse wake");
+  }
+  return MBT_OK;
+}
+
 mbt_status mbt_get_info(mbt_ctx *c, mbt_info *info) {
   if (!c || !info) return MBT_ERR_ARG;
   c->err.clear();
@@ -1330,7 +1564,7 @@ struct Section {
 std::vector<Section> state_sections(mbt_ctx *c) {
   const bool mixed = c->precision == MBT_PREC_MIXED;
   const int nl = std::max(1, c->nlong);
-  return {
+  std::vector<Section> out = {
       {c->d_tau, (size_t)c->n_alloc * (mixed ? sizeof(float) : sizeof(double))},
       {c->d_delta, (size_t)c->n_alloc * sizeof(double)},
       {c->d_hist, (size_t)2 * c->nb * c->nbins * sizeof(int32_t)},
@@ -1341,6 +1575,14 @@ std::vector<Section> state_sections(mbt_ctx *c) {
       {c->d_carry, (size_t)nl * sizeof(double2)},
       {c->d_turn, 16},
   };
+  if (c->trans) {
+    const size_t fs = mixed ? sizeof(float) : sizeof(double);
+    out.push_back({c->d_x, (size_t)c->n_alloc * fs});
+    out.push_back({c->d_xp, (size_t)c->n_alloc * fs});
+    out.push_back({c->d_dip, (size_t)2 * c->nb * c->nbins * fs});
+    out.push_back({c->d_vt, (size_t)c->nb * c->nbins * fs});
+  }
+  return out;
 }
 }  // namespace
 

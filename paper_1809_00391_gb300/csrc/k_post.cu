@@ -64,7 +64,7 @@ __device__ void post_stage(const Plan &p, const RunDev *__restrict__ R, const Po
     }
     if (tid < kBunchTile) st->q[tid] = tid < nbt ? R->q_mp[m0 + tid] : 0.0;
     if (tid == 32) prefetch_l2(R->carry);   // read by whichever CTA finishes last
-  } else if (tid < kBunchTile) {
+  } else if (job.type == kJobWake && tid < kBunchTile) {
     st->qf[tid] = tid < nbt ? R->q_mp_f[m0 + tid] : 0.f;
     if (job.sub == 0 && tid < nbt) {
       const BunchDev bd = p.bunches[R->bunch_base + m0 + tid];
@@ -91,9 +91,11 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
                             double (*s_sum)[kBunchTile], const PostStage *st) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = R->nb, nbins = R->nbins;
-  {
-    const int b = threadIdx.x & 31, cidx = threadIdx.x >> 5;
-    if (cidx < 5 && b < nbt) {
+  // columns: 0-4 longitudinal, and with a transverse plane 6-9 (slots 5-8)
+  const int ncol = R->trans ? 9 : 5;
+  for (int ci = threadIdx.x >> 5; ci < ncol; ci += kPostThreads / 32) {
+    const int b = threadIdx.x & 31, cidx = ci < 5 ? ci : ci + 1;
+    if (b < nbt) {
       int tile0, ntiles;
       if (st) {
         tile0 = st->tile0[b];
@@ -113,11 +115,19 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
         a3 += pp[(size_t)(i + 3) * kPartials];
       }
       for (; i < ntiles; ++i) a0 += pp[(size_t)i * kPartials];
-      s_sum[cidx][b] = (a0 + a1) + (a2 + a3);
+      s_sum[ci][b] = (a0 + a1) + (a2 + a3);
     }
   }
   int32_t *hz = R->hist + ((size_t)(par ^ 1) * nb + m0) * nbins;
   for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) hz[i] = 0;
+  if (R->trans) {
+    // the other dipole buffer too (float for kMixed, double for kF64)
+    const size_t off = ((size_t)(par ^ 1) * nb + m0) * nbins;
+    if (R->precision == kMixed)
+      for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) static_cast<float *>(R->dip)[off + i] = 0.f;
+    else
+      for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) static_cast<double *>(R->dip)[off + i] = 0.0;
+  }
   __syncthreads();
   if (warp == 0 && lane < nbt) {
     const double inv_n = st ? st->inv_n[lane] : R->inv_n[m0 + lane];
@@ -133,7 +143,63 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
     rec[3] = sqrt(vd);
     rec[4] = (double)(st ? st->n[lane] : p.bunches[R->bunch_base + m0 + lane].n) - s4;
     rec[5] = s4;
+    if (R->trans) {
+      const double mx = s_sum[5][lane] * inv_n, mp = s_sum[7][lane] * inv_n;
+      const double vx = fmax(fma(s_sum[6][lane], inv_n, -mx * mx), 0.0);
+      const double vp = fmax(fma(s_sum[8][lane], inv_n, -mp * mp), 0.0);
+      double *tr = R->trec + ((size_t)(turn % R->cap) * nb + m0 + lane) * kTRecord;
+      tr[0] = mx;
+      tr[1] = sqrt(vx);
+      tr[2] = mp;
+      tr[3] = sqrt(vp);
+    }
   }
+}
+
+// Transverse short-range voltage (Eq. 6, second line) of the tile's bunches,
+// rows [64 sub, 64 sub + 64): V[j] = q sum_{k<=j} dip[k] Wx((j - k) Delta)
+// from this turn's dipole sums, FP32 on the CUDA cores (kMixed; the
+// contraction is small: 64 rows x 32 bunches x <= 256 lags per job).
+__device__ void trans_job_f32(const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem) {
+  const int nbins = R->nbins, nb = R->nb;
+  const int m0 = job.bt * kBunchTile, nbt = min(kBunchTile, nb - m0);
+  float *sW = reinterpret_cast<float *>(smem);
+  float *sD = sW + nbins;   // [nbt][nbins]
+  const float *dg = static_cast<const float *>(R->dip) + ((size_t)par * nb + m0) * nbins;
+  for (int k = threadIdx.x; k < nbins; k += kPostThreads) sW[k] = R->tlag_f[k];
+  for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) sD[i] = dg[i];
+  __syncthreads();
+  const int r = threadIdx.x % kTransRows, j = job.sub * kTransRows + r;
+  float *vt = static_cast<float *>(R->vt);
+  for (int b = threadIdx.x / kTransRows; b < nbt; b += kPostThreads / kTransRows) {
+    const float *d = sD + (size_t)b * nbins;
+    float acc = 0.f;
+    for (int k = 0; k <= j; ++k) acc = fmaf(d[k], sW[j - k], acc);
+    vt[(size_t)(m0 + b) * nbins + j] = R->q_mp_f[m0 + b] * acc;
+  }
+}
+
+// The same in FP64 for bunch job.bt, rows [32 sub, 32 sub + 32), 8 threads per row (kF64).
+__device__ void trans_job_f64(const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem) {
+  const int nbins = R->nbins;
+  const int m = job.bt, chunk = job.sub;
+  double *sW = reinterpret_cast<double *>(smem);
+  double *sD = sW + nbins;
+  const double *dg = static_cast<const double *>(R->dip) + ((size_t)par * R->nb + m) * nbins;
+  for (int k = threadIdx.x; k < nbins; k += kPostThreads) {
+    sW[k] = R->tlag[k];
+    sD[k] = dg[k];
+  }
+  __syncthreads();
+  const int row = threadIdx.x >> 3, sub = threadIdx.x & 7;
+  const int j = chunk * kF64RowChunk + row;
+  double acc = 0.0;
+  if (j < nbins)
+    for (int k = sub; k <= j; k += 8) acc = fma(sD[k], sW[j - k], acc);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+  if (sub == 0 && j < nbins) static_cast<double *>(R->vt)[(size_t)m * nbins + j] = R->q_mp[m] * acc;
 }
 
 // Long-range emission and the tile's affine scan, per long-range resonator.
@@ -151,14 +217,17 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
   const int32_t *hcur = R->hist + ((size_t)par * nb + m0) * nbins;
   const int b = threadIdx.x >> 3, sub = threadIdx.x & 7;   // kPostThreads / 8 == kBunchTile
   for (int r = 0; r < R->nlong; ++r) {
+    // source of the emission: the cell counts, or for a transverse entry the dipole sums
+    const bool tplane = R->lr_plane[r] != 0;
     if (PREC == kMixed) {
       float ax = 0.f, ay = 0.f;
       if (b < nbt) {
         const int32_t *hrow = hcur + (size_t)b * nbins;
+        const float *drow = tplane ? static_cast<const float *>(R->dip) + ((size_t)par * nb + m0 + b) * nbins : nullptr;
         const float2 *tab = (tabf ? tabf : R->emis_f) + (size_t)r * nbins;
 #pragma unroll 8
         for (int k = sub; k < nbins; k += 8) {
-          const float cnt = (float)hrow[k];
+          const float cnt = tplane ? drow[k] : (float)hrow[k];
           const float2 e = tab[k];
           ax = fmaf(cnt, e.x, ax);
           ay = fmaf(cnt, e.y, ay);
@@ -174,9 +243,10 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
       double ax = 0.0, ay = 0.0;
       if (b < nbt) {
         const int32_t *hrow = hcur + (size_t)b * nbins;
+        const double *drow = tplane ? static_cast<const double *>(R->dip) + ((size_t)par * nb + m0 + b) * nbins : nullptr;
         const double2 *tab = R->emis + (size_t)r * nbins;
         for (int k = sub; k < nbins; k += 8) {
-          const double cnt = (double)hrow[k];
+          const double cnt = tplane ? drow[k] : (double)hrow[k];
           ax = fma(cnt, tab[k].x, ax);
           ay = fma(cnt, tab[k].y, ay);
         }
@@ -417,7 +487,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   __shared__ int s_flag;
   __shared__ double2 sE[kBunchTile];
   __shared__ float2 sEf[kBunchTile];
-  __shared__ double s_sum[5][kBunchTile];
+  __shared__ double s_sum[9][kBunchTile];
   __shared__ PostStage st;
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
@@ -433,7 +503,10 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   const int par = (int)(turn & 1);
   if (job.type == kJobWake)
     wake_job_tc(p, R, job, par, turn, sm_post, bars, &tmem_slot, &s_flag, s_sum, st.qf, &st);
-  else tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
+  else if (job.type == kJobTile)
+    tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
+  else
+    trans_job_f32(R, job, par, sm_post);
   trace_mark(p, 1);
   finish_turn(p);
   trace_mark(p, 2);
@@ -469,7 +542,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
   extern __shared__ __align__(16) uint8_t sm_post64[];
   __shared__ double2 sE[kBunchTile];
   __shared__ float2 sEf[kBunchTile];
-  __shared__ double s_sum[5][kBunchTile];
+  __shared__ double s_sum[9][kBunchTile];
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   trace_mark(p, 0);
@@ -479,6 +552,8 @@ __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
   const int par = (int)(turn & 1);
   if (job.type == kJobWake) {
     wake_job_f64(R, job, par, sm_post64);
+  } else if (job.type == kJobTrans) {
+    trans_job_f64(R, job, par, sm_post64);
   } else {
     const int m0 = job.bt * kBunchTile;
     moments_job(p, R, m0, min(kBunchTile, R->nb - m0), par, turn, s_sum, nullptr);
@@ -495,7 +570,7 @@ size_t post_smem_bytes(int precision, int max_nbins) {
   // form from these descriptors (even with the K and M/N strides exchanged)
   // stays inside the allocation
   if (precision == kMixed) return (size_t)max_nbins * 512u + (size_t)max_nbins * 2u * kWakeN + 24576u;
-  return (size_t)max_nbins * (sizeof(double) + sizeof(int));
+  return (size_t)max_nbins * 2 * sizeof(double);   // lag table + counts, or (transverse) lag table + dipole sums
 }
 
 cudaError_t configure_kernels() {
@@ -529,7 +604,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) 
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_flag;
-  __shared__ double s_sum[5][kBunchTile];
+  __shared__ double s_sum[9][kBunchTile];
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   wake_prologue(R, job, sm_wna, bars, &tmem_slot, &s_flag);

@@ -198,6 +198,165 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
 }
 
 // ---------------------------------------------------------------------------
+// Mixed precision with a transverse plane (plans where some run has one):
+// tau, delta, x, x' read and written with coalesced vector accesses, one
+// quad of consecutive particles per thread and step; runs of the plan without
+// a transverse plane take the longitudinal quad step.  Harmonic cavities are
+// a runtime loop here.
+// ---------------------------------------------------------------------------
+template <int NLONG_MAX>
+__global__ void __launch_bounds__(kPushThreads, 3) k_push_mixed_t(const Plan p) {
+  extern __shared__ __align__(16) uint8_t sm_pt[];
+  __shared__ float s_red[kPushThreads / 32][9];
+  __shared__ float2 s_phi[kMaxLong];
+  __shared__ int s_plane[kMaxLong];
+  __shared__ float4 s_hc[kMaxHarm];
+
+  const TileDev t = p.tiles[blockIdx.x];
+  const RunDev *__restrict__ R = p.runs + t.run;
+  const BunchDev bd = p.bunches[t.bunch];
+  PushConstF c;
+  c.nbins = R->nbins;
+  const int nbins = c.nbins;
+  const int nlong = R->nlong;
+  const bool tr = R->trans != 0;
+  float2 *sVd = reinterpret_cast<float2 *>(sm_pt);
+  int *sH = reinterpret_cast<int *>(sVd + nbins);
+  float2 *sVt = reinterpret_cast<float2 *>(sH + nbins);
+  float *sDip = reinterpret_cast<float *>(sVt + nbins);
+  float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
+  double *del = R->delta + bd.off + t.start;
+  float *xg = tr ? static_cast<float *>(R->x) + bd.off + t.start : nullptr;
+  float *pg = tr ? static_cast<float *>(R->xp) + bd.off + t.start : nullptr;
+  const int nharm = R->nharm;
+  if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
+  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+    sH[k] = 0;
+    sDip[k] = 0.f;
+  }
+  grid_dependents_launch();
+  grid_dependency_wait();   // the previous post kernel's wakes, phasors and turn counter are complete
+  const long long turn = *R->turn;
+  const int par = (int)(turn & 1);
+  const float *vsr = static_cast<const float *>(R->vsr) + (size_t)t.m * nbins;
+  const float *vtg = tr ? static_cast<const float *>(R->vt) + (size_t)t.m * nbins : nullptr;
+  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+    const float v0 = vsr[k];
+    const float v1 = k + 1 < nbins ? vsr[k + 1] : v0;
+    sVd[k] = make_float2(v0, v1 - v0);
+    if (tr) {
+      const float w0 = vtg[k];
+      const float w1 = k + 1 < nbins ? vtg[k + 1] : w0;
+      sVt[k] = make_float2(w0, w1 - w0);
+    }
+  }
+  if (threadIdx.x < nlong) {
+    const int r = threadIdx.x;
+    const double2 P = R->pq[((size_t)r * R->nb + t.m) * 2];
+    const double2 Q = R->pq[((size_t)r * R->nb + t.m) * 2 + 1];
+    const double2 y = R->y[(size_t)r * R->ntile_b + t.m / kBunchTile];
+    const double2 phi = cfma(P, y, Q);
+    s_phi[r] = make_float2((float)phi.x, (float)phi.y);
+    s_plane[r] = R->lr_plane[r];
+  }
+  c.invD = R->f_invD;
+  c.HinvD = R->f_HinvD;
+  c.fnb = R->f_nbins;
+  c.invE0 = R->f_invE0 * R->f_omD;
+  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
+  c.cphi = R->f_cphi;
+  c.sphi = R->f_sphi;
+  c.halfw = R->f_halfw;
+  c.omD = R->f_omD;
+  c.qe = R->f_qe;
+  c.aT0 = R->f_aT0;
+  const TransConstF tc = trans_consts(R);
+  const double omD_d = R->one_minus_D;
+  const bool ngp = (R->flags & kKickNGP) != 0;
+  float la[NLONG_MAX > 0 ? NLONG_MAX : 1], lw[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  float2 phi[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  int plane[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < NLONG_MAX; ++r) {
+    la[r] = R->f_la[r];
+    lw[r] = R->f_lw[r];
+    phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
+    plane[r] = r < nlong ? s_plane[r] : 0;
+  }
+  const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
+  const bool texc = tc.nx != 0.f || tc.nxp != 0.f;
+
+  float mom[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int nout = 0;
+#pragma unroll 1
+  for (int q = 4 * (int)threadIdx.x; q < t.count; q += 4 * kPushThreads) {
+    const uint32_t quad = (uint32_t)((t.start + q) >> 2);
+    const float4 tv = *reinterpret_cast<const float4 *>(tau + q);
+    const double2 da = *reinterpret_cast<const double2 *>(del + q);
+    const double2 db = *reinterpret_cast<const double2 *>(del + q + 2);
+    float rr[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c.qe != 0.f) normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 0u, k0, k1), rr);
+    float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+    double dd[4] = {da.x, da.y, db.x, db.y};
+    const int nvalid = min(4, t.count - q);
+    if (tr) {
+      const float4 xv = *reinterpret_cast<const float4 *>(xg + q);
+      const float4 pv = *reinterpret_cast<const float4 *>(pg + q);
+      float xx[4] = {xv.x, xv.y, xv.z, xv.w}, pp[4] = {pv.x, pv.y, pv.z, pv.w};
+      float rx[4] = {0.f, 0.f, 0.f, 0.f}, rp[4] = {0.f, 0.f, 0.f, 0.f};
+      if (texc) {
+        normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 3u, k0, k1), rx);
+        normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
+      }
+      quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, tt, dd, xx,
+                             pp, rr, rx, rp, nvalid, mom, nout);
+      *reinterpret_cast<float4 *>(xg + q) = make_float4(xx[0], xx[1], xx[2], xx[3]);
+      *reinterpret_cast<float4 *>(pg + q) = make_float4(pp[0], pp[1], pp[2], pp[3]);
+    } else if (ngp) {
+      quad_push<NLONG_MAX, true, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, mom[0],
+                                       mom[1], mom[2], mom[3], nout);
+    } else {
+      quad_push<NLONG_MAX, false, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, mom[0],
+                                        mom[1], mom[2], mom[3], nout);
+    }
+    *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+    *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
+    *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+  }
+
+  // moment partials (columns 0-4 longitudinal, 6-9 transverse)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) mom[k] = warp_sum_f(mom[k]);
+  const int no = __reduce_add_sync(0xFFFFFFFFu, nout);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_red[warp][k] = mom[k];
+    s_red[warp][4] = (float)no;
+#pragma unroll
+    for (int k = 4; k < 8; ++k) s_red[warp][k + 1] = mom[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
+    const int col = threadIdx.x < 5 ? threadIdx.x : threadIdx.x + 1;
+    p.partial[(size_t)blockIdx.x * kPartials + col] = acc;
+  }
+  int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
+  float *dg = tr ? static_cast<float *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
+  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+    const int cnt = sH[k];
+    if (cnt) {
+      atomicAdd(hg + k, cnt);
+      if (tr) atomicAdd(dg + k, sDip[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64: the oracle's arithmetic step for step.  Each thread handles quads of
 // consecutive particles (one Philox block per quad).  The cell index is formed
 // with explicitly rounded operations so it cannot be contracted into an FMA.
@@ -216,8 +375,9 @@ __device__ __forceinline__ double vsr_at_f64(const double *sV, double x, int nbi
 
 __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   extern __shared__ __align__(16) double sm_push64[];
-  __shared__ double s_red[kPushThreads / 32][5];
+  __shared__ double s_red[kPushThreads / 32][9];
   __shared__ double2 s_phi[kMaxLong];
+  __shared__ int s_plane[kMaxLong];
 
   const TileDev t = p.tiles[blockIdx.x];
   const RunDev *__restrict__ R = p.runs + t.run;
@@ -228,6 +388,10 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   grid_dependency_wait();
   double *sV = sm_push64;
   int *sH = reinterpret_cast<int *>(sm_push64 + nbins);
+  // transverse plane: voltage and dipole sums of the bunch (plans with one reserve the room)
+  const bool tr = R->trans != 0;
+  double *sVt = sm_push64 + nbins + (nbins + 1) / 2;
+  double *sDip = sVt + nbins;
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
 
@@ -235,6 +399,10 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
     sV[k] = vsr[k];
     sH[k] = 0;
+    if (tr) {
+      sVt[k] = static_cast<const double *>(R->vt)[(size_t)t.m * nbins + k];
+      sDip[k] = 0.0;
+    }
   }
   if (threadIdx.x < nlong) {
     const int r = threadIdx.x;
@@ -242,6 +410,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
     const double2 Q = R->pq[((size_t)r * R->nb + t.m) * 2 + 1];
     const double2 y = R->y[(size_t)r * R->ntile_b + t.m / kBunchTile];
     s_phi[r] = cfma(P, y, Q);
+    s_plane[r] = R->lr_plane[r];
   }
   __syncthreads();
 
@@ -253,7 +422,10 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
 
   double *tau = static_cast<double *>(R->tau) + bd.off + t.start;
   double *del = R->delta + bd.off + t.start;
-  double st = 0.0, st2 = 0.0, sd = 0.0, sd2 = 0.0;
+  double *xg = tr ? static_cast<double *>(R->x) + bd.off + t.start : nullptr;
+  double *pg = tr ? static_cast<double *>(R->xp) + bd.off + t.start : nullptr;
+  const bool texc = tr && (R->t_nx != 0.0 || R->t_nxp != 0.0);
+  double st = 0.0, st2 = 0.0, sd = 0.0, sd2 = 0.0, sx = 0.0, sx2 = 0.0, sp = 0.0, sp2 = 0.0;
   int nout = 0;
 
 #pragma unroll 1
@@ -269,35 +441,78 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
       tt[0] = t0.x; tt[1] = t0.y; tt[2] = t1.x; tt[3] = t1.y;
       dd[0] = d0.x; dd[1] = d0.y; dd[2] = d1.x; dd[3] = d1.y;
     }
-    double rr[4] = {0.0, 0.0, 0.0, 0.0};
+    double rr[4] = {0.0, 0.0, 0.0, 0.0}, rx[4] = {0.0, 0.0, 0.0, 0.0}, rp[4] = {0.0, 0.0, 0.0, 0.0};
     if (qe != 0.0) normal_quad_f64(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
+    if (texc) {
+      normal_quad_f64(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 3u, k0, k1), rx);
+      normal_quad_f64(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 4u, k0, k1), rp);
+    }
+    double xx[4] = {0.0, 0.0, 0.0, 0.0}, pp[4] = {0.0, 0.0, 0.0, 0.0};
+    if (tr) {
+      const double2 x0 = *reinterpret_cast<const double2 *>(xg + q), x1 = *reinterpret_cast<const double2 *>(xg + q + 2);
+      const double2 p0 = *reinterpret_cast<const double2 *>(pg + q), p1 = *reinterpret_cast<const double2 *>(pg + q + 2);
+      xx[0] = x0.x; xx[1] = x0.y; xx[2] = x1.x; xx[3] = x1.y;
+      pp[0] = p0.x; pp[1] = p0.y; pp[2] = p1.x; pp[3] = p1.y;
+    }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (q + e >= t.count) continue;
       double tp = tt[e], d = dd[e];
-      double v = vsr_at_f64(sV, __dmul_rn(__dadd_rn(tp, H), invD), nbins, ngp);
+      const double xc = __dmul_rn(__dadd_rn(tp, H), invD);
+      double v = vsr_at_f64(sV, xc, nbins, ngp);
+      double vt = tr ? vsr_at_f64(sVt, xc, nbins, ngp) : 0.0;
       for (int r = 0; r < nlong; ++r) {
         const double2 s = R->lr_s[r];
         double sn, cs;
         sincos(s.y * tp, &sn, &cs);
         const double ea = exp(s.x * tp);
-        v += ea * (s_phi[r].x * cs - s_phi[r].y * sn);
+        if (s_plane[r]) vt += ea * (s_phi[r].x * sn + s_phi[r].y * cs);   // Im(Phi e^{s tau})
+        else v += ea * (s_phi[r].x * cs - s_phi[r].y * sn);                // Re(Phi e^{s tau})
       }
       d = d - v * invE0;
+      const double d_before = d;
       d = d + VoE0 * sin(phis - wrf * tp);
       for (int k = 0; k < R->nharm; ++k) d = d + R->harm_VoE0[k] * sin(R->harm_phi[k] - R->harm_nw[k] * tp);
+      const double d_gain = d;
       d = d - U0oE0;
       d = d * omD + qe * rr[e];
+      if (tr) {
+        // transverse: wake kick, momentum ratio across the cavity, rotation with the new delta, excitation
+        double p = pp[e] + vt * invE0;
+        p = p * (1.0 + d_before) / (1.0 + d_gain);
+        const double psi = R->t_mu0 * (1.0 + R->t_xi * d);
+        double sn, cs;
+        sincos(psi, &sn, &cs);
+        const double x = xx[e];
+        double xn = (cs + R->t_alpha * sn) * x + R->t_beta * sn * p;
+        double pn = -R->t_gamma * sn * x + (cs - R->t_alpha * sn) * p;
+        xx[e] = xn + R->t_nx * rx[e];
+        pp[e] = pn + R->t_nxp * rp[e];
+        sx += xx[e];
+        sx2 += xx[e] * xx[e];
+        sp += pp[e];
+        sp2 += pp[e] * pp[e];
+      }
       tp = tp + aT0 * d;
       tt[e] = tp;
       dd[e] = d;
       const double xb = __dmul_rn(__dadd_rn(tp, H), invD);
-      if (xb >= 0.0 && xb < (double)nbins) atomicAdd(&sH[(int)xb], 1);
-      else ++nout;
+      if (xb >= 0.0 && xb < (double)nbins) {
+        atomicAdd(&sH[(int)xb], 1);
+        if (tr) atomicAdd(&sDip[(int)xb], xx[e]);
+      } else {
+        ++nout;
+      }
       st += tp;
       st2 += tp * tp;
       sd += d;
       sd2 += d * d;
+    }
+    if (tr) {
+      *reinterpret_cast<double2 *>(xg + q) = make_double2(xx[0], xx[1]);
+      *reinterpret_cast<double2 *>(xg + q + 2) = make_double2(xx[2], xx[3]);
+      *reinterpret_cast<double2 *>(pg + q) = make_double2(pp[0], pp[1]);
+      *reinterpret_cast<double2 *>(pg + q + 2) = make_double2(pp[2], pp[3]);
     }
     *reinterpret_cast<double2 *>(tau + q) = make_double2(tt[0], tt[1]);
     *reinterpret_cast<double2 *>(tau + q + 2) = make_double2(tt[2], tt[3]);
@@ -310,6 +525,10 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   st2 = warp_sum_d(st2);
   sd = warp_sum_d(sd);
   sd2 = warp_sum_d(sd2);
+  sx = warp_sum_d(sx);
+  sx2 = warp_sum_d(sx2);
+  sp = warp_sum_d(sp);
+  sp2 = warp_sum_d(sp2);
   const int no = __reduce_add_sync(0xFFFFFFFFu, nout);
   if (lane == 0) {
     s_red[warp][0] = st;
@@ -317,17 +536,26 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
     s_red[warp][2] = sd;
     s_red[warp][3] = sd2;
     s_red[warp][4] = (double)no;
+    s_red[warp][5] = sx;
+    s_red[warp][6] = sx2;
+    s_red[warp][7] = sp;
+    s_red[warp][8] = sp2;
   }
   __syncthreads();
-  if (threadIdx.x < 5) {
+  if (threadIdx.x < 9) {
     double acc = 0.0;
     for (int w = 0; w < kPushThreads / 32; ++w) acc += s_red[w][threadIdx.x];
-    p.partial[(size_t)blockIdx.x * kPartials + threadIdx.x] = acc;
+    const int col = threadIdx.x < 5 ? threadIdx.x : threadIdx.x + 1;   // columns 0-4, 6-9
+    p.partial[(size_t)blockIdx.x * kPartials + col] = acc;
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
+  double *dg = tr ? static_cast<double *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
     const int c = sH[k];
-    if (c) atomicAdd(hg + k, c);
+    if (c) {
+      atomicAdd(hg + k, c);
+      if (tr) atomicAdd(dg + k, sDip[k]);
+    }
   }
 }
 
@@ -351,6 +579,25 @@ __global__ void __launch_bounds__(kPushThreads) k_init(const Plan p, int precisi
       else static_cast<double *>(R->tau)[i + e] = R->sigma_tau0 * a[e];
       R->delta[i + e] = R->sigma_E * b[e];
     }
+    if (R->trans) {
+      // matched Gaussian of the transverse plane, tags 5 (x) and 6 (x'):
+      // x = sqrt(beta emit) c, x' = sqrt(emit / beta) (d - alpha c)
+      double cx[4], dx[4];
+      normal_quad_f64(philox4x32_10(quad, (uint32_t)t.m, 0u, 5u, R->key0, R->key1), cx);
+      normal_quad_f64(philox4x32_10(quad, (uint32_t)t.m, 0u, 6u, R->key0, R->key1), dx);
+      const double sx = sqrt(R->t_beta * R->t_emit);
+      const double emit = sx * sx / R->t_beta;
+      for (int e = 0; e < nv; ++e) {
+        const double x = sx * cx[e], xp = sqrt(emit / R->t_beta) * (dx[e] - R->t_alpha * cx[e]);
+        if (precision == kMixed) {
+          static_cast<float *>(R->x)[i + e] = (float)x;
+          static_cast<float *>(R->xp)[i + e] = (float)xp;
+        } else {
+          static_cast<double *>(R->x)[i + e] = x;
+          static_cast<double *>(R->xp)[i + e] = xp;
+        }
+      }
+    }
   }
 }
 
@@ -373,6 +620,15 @@ static cudaError_t launch_ex(void (*kern)(Args...), int grid, int block, size_t 
 cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) {
   if (p.ntiles == 0) return cudaSuccess;
   const int max_nbins = p.max_nbins;
+  if (precision == kMixed && p.max_trans) {
+    const size_t smem = (size_t)max_nbins * (2 * sizeof(float2) + sizeof(int) + sizeof(float));
+    switch (p.max_nlong) {
+      case 0: return launch_ex(k_push_mixed_t<0>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 1: return launch_ex(k_push_mixed_t<1>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 2: return launch_ex(k_push_mixed_t<2>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      default: return launch_ex(k_push_mixed_t<kMaxLong>, p.ntiles, kPushThreads, smem, s, pdl, p);
+    }
+  }
   if (precision == kMixed) {
     const size_t smem = (size_t)kStages * kStageBytes + (size_t)max_nbins * (sizeof(float2) + sizeof(int));
     const bool harm = p.max_nharm > 0;
@@ -385,7 +641,9 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
                          smem, s, pdl, p);
     }
   }
-  const size_t smem = (size_t)max_nbins * (sizeof(double) + sizeof(int));
+  // sV, sH (rounded up to doubles), and with a transverse plane sVt, sDip
+  const size_t smem = ((size_t)max_nbins + (size_t)(max_nbins + 1) / 2 + (p.max_trans ? 2 * (size_t)max_nbins : 0)) *
+                      sizeof(double);
   return launch_ex(k_push_f64, p.ntiles, kPushThreads, smem, s, pdl, p);
 }
 

@@ -19,14 +19,16 @@ constexpr int kMixedQuadsPerThread = 8;                                    // 4 
 constexpr int kMixedTile = kPushThreads * 4 * kMixedQuadsPerThread;        // 8192 particles
 constexpr int kF64QuadsPerThread = 2;                                      // 4 particles per quad
 constexpr int kF64Tile = kPushThreads * 4 * kF64QuadsPerThread;            // 2048 particles
-constexpr int kPartials = 6;         // sum tau, sum tau^2, sum delta, sum delta^2, n_out, pad
+constexpr int kPartials = 10;        // sums of tau, tau^2, delta, delta^2, n_out, pad, x, x^2, x', x'^2
+constexpr int kTRecord = 4;          // transverse record: <x>, rms x, <x'>, rms x'
+constexpr int kTransRows = 64;       // transverse short-range rows per post job (kMixed)
 constexpr int kRecord = 6;           // <tau>, rms tau, <delta>, rms delta, n_in, n_out
 constexpr int kPostThreads = 256;
 constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
 
 enum Precision { kF64 = 0, kMixed = 1 };
 enum Flags { kNoSR = 1, kNoQE = 2, kKickNGP = 4 };
-enum JobType { kJobWake = 0, kJobTile = 1 };
+enum JobType { kJobWake = 0, kJobTile = 1, kJobTrans = 2 };
 enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2 };
 
 // One run's device state and constants.
@@ -67,6 +69,21 @@ struct RunDev {
   int nharm;
   double harm_VoE0[kMaxHarm], harm_phi[kMaxHarm], harm_nw[kMaxHarm];
   float4 f_harm[kMaxHarm];  // (2 V_h/E0 (1 - D), cos phi_h, sin phi_h, n omega_rf / 2), mixed path
+  // long-range entries: 0 = longitudinal (Re(Phi e^{s tau}) kicks delta),
+  // 1 = transverse (emission from the dipole sums, Im(Phi e^{s tau}) kicks x')
+  int lr_plane[kMaxLong];
+  // transverse plane (one per run): x [m], x' (float for kMixed, double for kF64)
+  int trans;
+  void *x, *xp;
+  void *dip;                // [2][nb][nbins] sum of x over each cell's particles; turn parity selects
+  void *vt;                 // [nb][nbins] transverse short-range voltage [V] for the next kick
+  double *trec;             // [cap][nb][kTRecord]
+  const double *tlag;       // [nbins] transverse wake per lag [V/(C m)]
+  const float *tlag_f;
+  double t_beta, t_alpha, t_gamma, t_mu0, t_xi, t_nx, t_nxp;   // t_nx = sqrt(beta emit Dx), t_nxp = sqrt(gamma emit Dx)
+  double t_emit;
+  // float copies: 2 pi frac(nu), 2 pi nu xi, beta, alpha, gamma, nx, nxp, 1/(1 - D)
+  float f_tmu0, f_tmu0xi, f_tbeta, f_talpha, f_tgamma, f_tnx, f_tnxp, f_inv_omD, f_U0oE0;
 };
 
 
@@ -100,6 +117,7 @@ struct Plan {
   int max_nbins;              // largest mesh of the plan's runs (shared-memory sizing)
   int max_nlong;              // most long-range resonators of any run of the plan
   int max_nharm;              // most harmonic cavities of any run of the plan
+  int max_trans;              // 1 if any run of the plan has a transverse plane
   unsigned long long *trace;  // null, or [njobs][3] post-kernel CTA timestamps (start, job done, exit) [ns]
 };
 

@@ -87,4 +87,129 @@ __device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd
   }
 }
 
+// ---------------------------------------------------------------------------
+// Runs with a transverse plane (Eqs. 3-5 x lines, Eq. 6 second line, FP32).
+// ---------------------------------------------------------------------------
+struct TransConstF {
+  float mu0, mu0xi;            // 2 pi frac(nu), 2 pi nu xi: phase = mu0 + mu0xi delta
+  float beta, alpha, gamma;
+  float nx, nxp;               // excitation amplitudes sqrt(beta emit Dx), sqrt(gamma emit Dx)
+  float invE0, inv_omD, U0oE0; // 1/E0 (no damping factor), 1/(1 - D), U0/E0
+};
+
+// One particle with a transverse plane: the longitudinal map of push_one
+// (its long-range sum over the plane-0 entries only) and, with the same
+// previous-turn wake, x' += V_x / E0, the momentum ratio across the cavity,
+// the rotation with the new delta's phase, the excitation.  vtd: (V_x[j],
+// V_x[j+1] - V_x[j]) of the bunch; plane: long-range entry planes.
+template <int NLONG_MAX>
+__device__ __forceinline__ float push_one_t(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
+                                            const float2 *sVt, int nlong, const int *plane, const float *la,
+                                            const float *lw, const float2 *phi, double omD_d, const float4 *hc,
+                                            int nharm, bool ngp, float t0, double &d, float r, float &df, float &x,
+                                            float &xp, float rx, float rxp) {
+  const float x0 = fmaf(t0, c.invD, c.HinvD);
+  const bool inside = x0 >= 0.f && x0 < c.fnb;
+  float v, vt;
+  if (ngp) {
+    const int k = min(max((int)x0, 0), c.nbins - 1);
+    v = sVd[k].x;
+    vt = sVt[k].x;
+  } else {
+    const float u = fminf(fmaxf(x0 - 0.5f, 0.f), c.fnb - 1.f);
+    const int j = min((int)u, c.nbins - 2);
+    const float2 vd = sVd[j], vtd = sVt[j];
+    v = fmaf(u - (float)j, vd.y, vd.x);
+    vt = fmaf(u - (float)j, vtd.y, vtd.x);
+  }
+  v = inside ? v : 0.f;
+  vt = inside ? vt : 0.f;
+#pragma unroll
+  for (int r2 = 0; r2 < NLONG_MAX; ++r2) {
+    if (r2 < nlong) {
+      float sn, cs;
+      __sincosf(lw[r2] * t0, &sn, &cs);
+      const float ea = __expf(-la[r2] * t0);
+      if (plane[r2]) vt = fmaf(ea, fmaf(phi[r2].x, sn, phi[r2].y * cs), vt);   // Im(Phi e^{s t})
+      else v = fmaf(ea, fmaf(phi[r2].x, cs, -phi[r2].y * sn), v);             // Re(Phi e^{s t})
+    }
+  }
+  float sh, ch;
+  __sincosf(c.halfw * t0, &sh, &ch);
+  float rf = -c.twoVoE0 * sh * fmaf(ch, c.cphi, sh * c.sphi);
+  for (int k = 0; k < nharm; ++k) {
+    const float4 h = hc[k];
+    float sk, ck;
+    __sincosf(h.w * t0, &sk, &ck);
+    rf = fmaf(-h.x * sk, fmaf(ck, h.y, sk * h.z), rf);
+  }
+  const float inc = fmaf(-v, c.invE0, fmaf(c.qe, r, rf));
+  // momentum ratio across the cavity: (1 + d_b) / (1 + d_b + g), d_b after the
+  // wake kick, g the RF gain (the damping factor taken out of rf)
+  const float db = fmaf(-v, tc.invE0, f64_to_f32_trunc(d));
+  const float g = fmaf(rf, tc.inv_omD, tc.U0oE0);
+  d = fma(d, omD_d, f32_to_f64_bits(inc));
+  df = f64_to_f32_trunc(d);
+  float p = fmaf(vt, tc.invE0, xp);
+  p = fmaf(-p, __fdividef(g, 1.f + db + g), p);
+  float sp, cp;
+  __sincosf(fmaf(tc.mu0xi, df, tc.mu0), &sp, &cp);
+  const float xn = fmaf(fmaf(tc.alpha, sp, cp), x, tc.beta * sp * p);
+  const float pn = fmaf(-tc.gamma * sp, x, fmaf(-tc.alpha, sp, cp) * p);
+  x = fmaf(tc.nx, rx, xn);
+  xp = fmaf(tc.nxp, rxp, pn);
+  return fmaf(c.aT0, df, t0);
+}
+
+// Four consecutive particles with a transverse plane: push, deposit of the
+// count and of x into the cell, moment partials of both planes.
+template <int NLONG_MAX>
+__device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
+                                            const float2 *sVt, int *sH, float *sDip, int nlong, const int *plane,
+                                            const float *la, const float *lw, const float2 *phi, double omD_d,
+                                            const float4 *hc, int nharm, bool ngp, float (&tt)[4], double (&dd)[4],
+                                            float (&xx)[4], float (&pp)[4], const float (&rr)[4],
+                                            const float (&rx)[4], const float (&rp)[4], int nvalid, float (&mom)[8],
+                                            int &nout) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (e < nvalid) {
+      float df;
+      const float t1 = push_one_t<NLONG_MAX>(c, tc, sVd, sVt, nlong, plane, la, lw, phi, omD_d, hc, nharm, ngp,
+                                             tt[e], dd[e], rr[e], df, xx[e], pp[e], rx[e], rp[e]);
+      tt[e] = t1;
+      const float xb = fmaf(t1, c.invD, c.HinvD);
+      if (xb >= 0.f && xb < c.fnb) {
+        atomicAdd(&sH[(int)xb], 1);
+        atomicAdd(&sDip[(int)xb], xx[e]);
+      } else {
+        ++nout;
+      }
+      mom[0] += t1;
+      mom[1] = fmaf(t1, t1, mom[1]);
+      mom[2] += df;
+      mom[3] = fmaf(df, df, mom[3]);
+      mom[4] += xx[e];
+      mom[5] = fmaf(xx[e], xx[e], mom[5]);
+      mom[6] += pp[e];
+      mom[7] = fmaf(pp[e], pp[e], mom[7]);
+    }
+  }
+}
+
+__device__ __forceinline__ TransConstF trans_consts(const RunDev *__restrict__ R) {
+  TransConstF t;
+  t.mu0 = R->f_tmu0;
+  t.mu0xi = R->f_tmu0xi;
+  t.beta = R->f_tbeta;
+  t.alpha = R->f_talpha;
+  t.gamma = R->f_tgamma;
+  t.nx = R->f_tnx;
+  t.nxp = R->f_tnxp;
+  t.invE0 = R->f_invE0;
+  t.inv_omD = R->f_inv_omD;
+  t.U0oE0 = R->f_U0oE0;
+  return t;
+}
+
 }  // namespace mbt

@@ -1,0 +1,171 @@
+"""Transverse plane (Eqs. 3-5 x lines, Eq. 6 second line) on the GPU, through
+the C ABI, against the FP64 oracle and the transverse coupled-bunch growth
+rate -(I_b M beta / (2 E0 T0)) sum_p Re Z((pM + mu) w0 + w_beta)."""
+import math
+
+import numpy as np
+import pytest
+
+import mbt_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TRES = dict(Rs_ohm=2e5, fr_Hz=1.5e9, Q=2e4, range=W.RANGE_BOTH)
+BBT = dict(Rs_ohm=5e5, fr_Hz=8e9, Q=1.0, range=W.RANGE_SHORT)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1809_00391_gb300 as p
+    p.build()
+    return p
+
+
+def _plane(**kw):
+    t = dict(beta_m=10.0, alpha=0.4, tune=0.31, chromaticity=1.5, emittance_m=1e-9, resonators=[])
+    t.update(kw)
+    return t
+
+
+def _run(precision, buckets, n_mp, turns, I=1e-3, tplane=None, res=(W.BROADBAND,), flags=0, seed=5):
+    b, c, n = W._fill(buckets, I, n_mp)
+    return W.Run(W.ring_r0(), [dict(r) for r in res], b, c, n, seed=seed, turns=turns, precision=precision,
+                 flags=flags, transverse=tplane or _plane(), name="transverse")
+
+
+def _oracle(oracle_mod, run):
+    return oracle_mod.OracleSim(run.ring, run.resonators, run.nbins, run.half_width_sigmas, run.buckets,
+                                run.currents_A, run.n_mp, run.seed, run.flags, transverse=run.transverse)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.mark.parametrize("wakes", [False, True], ids=["no_wake", "wakes"])
+def test_f64_transverse_matches_oracle(pkg, oracle_mod, wakes):
+    tplane = _plane(resonators=[dict(TRES), dict(BBT)] if wakes else [])
+    run = _run(W.PREC_F64, [0, 1, 7] if wakes else [0], 4000, 150, I=2e-3, tplane=tplane)
+    tr = pkg.tracker_for_run(run, record_turns=run.turns)
+    orc = _oracle(oracle_mod, run)
+    tr.init_particles()
+    orc.init_particles()
+    for m in range(run.nb):   # the same start on both sides
+        assert _rel(tr.transverse_particles(m)[0], orc.tparticles(m)[0]) < 1e-15
+    tr.track(run.turns)
+    rec_o, trec_o = orc.track2(run.turns)
+    trec_g = tr.transverse_moments(0, run.turns)
+    h_g, _ = tr.histograms()
+    h_o, _ = orc.histograms()
+    assert np.array_equal(h_g, h_o)
+    for m in range(run.nb):
+        xg, pg = tr.transverse_particles(m)
+        xo, po = orc.tparticles(m)
+        assert _rel(xg, xo) < 1e-9 and _rel(pg, po) < 1e-9, m
+    for col in range(4):
+        assert _rel(trec_g[:, :, col], trec_o[:, :, col]) < 1e-9, col
+    if wakes:
+        dip, v = tr.transverse_wake()
+        assert _rel(dip, orc.dipoles()) < 1e-12
+        q = run.currents_A[0] * run.ring["T0_s"] / run.n_mp[0]
+        for m in range(run.nb):
+            assert _rel(v[m], orc.vt_direct(dip[m], q)) < 1e-12
+    tr.close()
+
+
+def test_mixed_transverse_matches_oracle(pkg, oracle_mod):
+    run = _run(W.PREC_MIXED, [0, 1, 7], 20_000, 300, I=2e-3, tplane=_plane(resonators=[dict(TRES), dict(BBT)]))
+    tr = pkg.tracker_for_run(run, record_turns=run.turns)
+    orc = _oracle(oracle_mod, run)
+    tr.init_particles()
+    orc.init_particles()
+    tr.track(run.turns)
+    rec_o, trec_o = orc.track2(run.turns)
+    rec_g = tr.moments(0, run.turns)
+    trec_g = tr.transverse_moments(0, run.turns)
+    st, sd = rec_o[:, :, 1], rec_o[:, :, 3]
+    for col, scale in ((0, st), (1, st), (2, sd), (3, sd)):
+        assert np.max(np.abs(rec_g[:, :, col] - rec_o[:, :, col]) / scale) <= 1e-3, col
+    sx, sp = trec_o[:, :, 1], trec_o[:, :, 3]
+    for col, scale in ((0, sx), (1, sx), (2, sp), (3, sp)):
+        assert np.max(np.abs(trec_g[:, :, col] - trec_o[:, :, col]) / scale) <= 1e-3, col
+    # the transverse voltage of the GPU's own dipole sums
+    dip, v = tr.transverse_wake()
+    q = run.currents_A[0] * run.ring["T0_s"] / run.n_mp[0]
+    for m in range(run.nb):
+        ref = orc.vt_direct(dip[m], q)
+        assert np.max(np.abs(v[m] - ref)) <= 1e-5 * np.max(np.abs(ref))
+    tr.close()
+
+
+@pytest.mark.parametrize("prec", [W.PREC_MIXED, W.PREC_F64], ids=["mixed", "f64"])
+def test_transverse_coupled_bunch_growth_rate(pkg, prec):
+    ring = W.ring_r0()
+    T0, h = ring["T0_s"], ring["h"]
+    M, nu, beta, Ib, Rs, Q = 4, 0.3, 20.0, 5e-3, 1.2e7, 2e4
+    w0 = 2 * math.pi / T0
+    fr = (1441 - nu) / T0
+    tplane = dict(beta_m=beta, alpha=0.0, tune=nu, chromaticity=0.0, emittance_m=0.0,
+                  resonators=[dict(Rs_ohm=Rs, fr_Hz=fr, Q=Q, range=W.RANGE_LONG)])
+    n_mp, turns = 400, 3000
+    b, c, n = W._fill([m * (h // M) for m in range(M)], Ib, n_mp)
+    run = W.Run(ring, [], b, c, n, seed=4, turns=turns, precision=prec, flags=W.NO_SR, transverse=tplane)
+    tr = pkg.tracker_for_run(run, record_turns=turns)
+    g = np.random.default_rng(8)
+    for m in range(M):
+        tr.set_particles(m, g.normal(0, 3e-12, n_mp), np.zeros(n_mp))
+        ph = g.uniform(0, 2 * math.pi)
+        tr.set_transverse_particles(m, np.full(n_mp, 1e-6 * math.cos(ph)), np.full(n_mp, -1e-6 / beta * math.sin(ph)))
+    tr.track(turns)
+    trec = tr.transverse_moments(0, turns)
+    z = trec[:, :, 0] / math.sqrt(beta) - 1j * math.sqrt(beta) * trec[:, :, 2]
+    th = (2 * math.pi * nu + 2 * math.pi * 3) / M
+    X3 = (z * np.exp(-1j * th * np.arange(M))[None, :]).sum(axis=1)
+    rate = np.polyfit(np.arange(1000, turns), np.log(np.abs(X3[1000:])), 1)[0] / T0
+    wr = 2 * math.pi * fr
+    p = np.arange(-2000, 2000)
+    lines = (p * M + 3 + nu) * w0
+    re_z = ((wr / lines) * Rs / (1 + 1j * Q * (lines / wr - wr / lines))).real
+    pred = -(Ib * M * beta / (2 * ring["E0_eV"] * T0)) * np.sum(re_z)
+    assert rate == pytest.approx(pred, rel=0.02)
+    tr.close()
+
+
+def test_transverse_checkpoint_resume_is_bit_identical(pkg):
+    run = _run(W.PREC_F64, [0, 3], 3000, 40, tplane=_plane(resonators=[dict(TRES)]))
+    a = pkg.tracker_for_run(run, record_turns=run.turns)
+    a.init_particles()
+    a.track(20)
+    blob = a.save_state()
+    a.track(20)
+    b = pkg.tracker_for_run(run, record_turns=run.turns)
+    b.load_state(blob)
+    b.track(20)
+    for m in range(run.nb):
+        xa, pa = a.transverse_particles(m)
+        xb, pb = b.transverse_particles(m)
+        assert np.array_equal(xa, xb) and np.array_equal(pa, pb)
+    a.close()
+    b.close()
+
+
+def test_transverse_batch_equals_alone_and_resident_refuses(pkg):
+    tr_run = _run(W.PREC_MIXED, [0, 5], 8000, 30, tplane=_plane(resonators=[dict(TRES)]))
+    lo_run = W.single_bunch(seed=2).scaled(turns=30)
+    lo_run = W.Run(**{**lo_run.__dict__, "precision": W.PREC_MIXED})
+    alone = pkg.tracker_for_run(tr_run, record_turns=30)
+    alone.init_particles()
+    alone.track(30)
+    t1 = pkg.tracker_for_run(tr_run, record_turns=30)
+    t2 = pkg.tracker_for_run(lo_run, record_turns=30)
+    t1.init_particles()
+    t2.init_particles()
+    bt = pkg.Batch([t1, t2])
+    bt.track(30)
+    bt.sync()
+    assert np.array_equal(t1.transverse_moments(0, 30), alone.transverse_moments(0, 30))
+    with pytest.raises(pkg.MBTError):
+        alone.track_resident(1)
+    bt.close()
+    for t in (alone, t1, t2):
+        t.close()
