@@ -116,8 +116,10 @@ const char *mbt_status_string(mbt_status s);
 /* Create a context for one run.  precision: MBT_PREC_*; flags: MBT_NO_SR |
  * MBT_NO_QE | MBT_KICK_NGP; seed: 64-bit key of the Philox4x32-10 streams
  * (Salmon et al., SC'11) that draw the initial distribution and the quantum
- * excitation (counter = pair index, bunch, turn, tag).  Errors: MBT_ERR_ARG on
- * a null pointer or an invalid ring. */
+ * excitation: one block per quad of consecutive particles, counter = (quad,
+ * bunch, turn, tag), tag 0 the delta excitation of a turn, 1 / 2 the initial
+ * tau / delta, 3 / 4 the x / x' excitation, 5 / 6 the initial x / x'.
+ * Errors: MBT_ERR_ARG on a null pointer or an invalid ring. */
 mbt_status mbt_create(const mbt_ring *ring, int precision, int flags, uint64_t seed, mbt_ctx **out);
 
 /* Destroy a context and free its device memory (synchronises its stream).

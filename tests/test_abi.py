@@ -102,3 +102,63 @@ def test_binding_fails_loudly_without_library(pkg, monkeypatch, tmp_path):
     monkeypatch.setattr(p, "_LIB_PATH", tmp_path / "missing.so")
     with pytest.raises(RuntimeError, match="not built"):
         p.lib()
+
+
+def test_new_entry_points_validate_their_arguments(pkg):
+    import ctypes
+    L = pkg.lib()
+    D = ctypes.c_double
+    st, h = _create(pkg, W.ring_r0(), prec=0)
+    assert st == 0
+
+    def arr(v):
+        a = (D * len(v))(*v)
+        return a
+
+    # tabulated wakes: at least 2 samples from t = 0, strictly increasing, finite
+    assert L.mbt_add_wake_table(h, 1, arr([0.0]), arr([1.0])) == 1
+    assert L.mbt_add_wake_table(h, 2, arr([1e-12, 2e-12]), arr([1.0, 0.5])) == 1
+    assert L.mbt_add_wake_table(h, 3, arr([0.0, 2e-12, 1e-12]), arr([1.0, 0.5, 0.2])) == 1
+    assert L.mbt_add_wake_table(h, 2, arr([0.0, 1e-12]), arr([float("nan"), 0.5])) == 1
+    assert L.mbt_add_wake_table(h, 2, arr([0.0, 1e-12]), arr([1.0, 0.5])) == 0
+    # resistive wall: every argument positive
+    for bad in ((0.0, 5.8e7, 100.0), (0.01, -1.0, 100.0), (0.01, 5.8e7, 0.0)):
+        assert L.mbt_add_resistive_wall(h, *bad) == 1
+    assert L.mbt_add_resistive_wall(h, 0.01, 5.8e7, 100.0) == 0
+    # harmonic cavities: 1 <= n <= 16, V >= 0, at most two
+    assert L.mbt_add_harmonic_cavity(h, 0, 1e5, 0.0) == 1
+    assert L.mbt_add_harmonic_cavity(h, 17, 1e5, 0.0) == 1
+    assert L.mbt_add_harmonic_cavity(h, 3, -1.0, 0.0) == 1
+    assert L.mbt_add_harmonic_cavity(h, 3, 1e5, 0.3) == 0
+    assert L.mbt_add_harmonic_cavity(h, 4, 1e4, 0.1) == 0
+    assert L.mbt_add_harmonic_cavity(h, 5, 1e4, 0.1) == 6
+    # transverse: resonators need the plane first; the long-range limit is shared
+    assert L.mbt_add_transverse_resonator(h, 1e5, 1e9, 1e3, 3) == 2
+    assert L.mbt_set_transverse(h, -1.0, 0.0, 0.3, 0.0, 1e-9) == 1
+    assert L.mbt_set_transverse(h, 10.0, 0.0, 0.3, 0.0, -1e-9) == 1
+    assert L.mbt_set_transverse(h, 10.0, 0.0, 0.3, 0.0, 1e-9) == 0
+    assert L.mbt_set_transverse(h, 10.0, 0.0, 0.3, 0.0, 1e-9) == 2   # already set
+    for _ in range(3):
+        assert L.mbt_add_resonator(h, 1e3, 1e9, 2.0, 3) == 0
+    assert L.mbt_add_transverse_resonator(h, 1e5, 1e9, 1e3, 2) == 0
+    assert L.mbt_add_transverse_resonator(h, 1e5, 1e9, 1e3, 2) == 6   # fifth long-range entry
+    assert L.mbt_add_transverse_resonator(h, 1e5, 1e9, 1e3, 1) == 0   # short range only is fine
+    assert L.mbt_add_transverse_resonator(h, 1e5, 1e9, 0.2, 1) == 1   # Q <= 1/2
+    L.mbt_destroy(h)
+
+
+def test_harmonic_cavity_derivation_matches_the_oracle(pkg, oracle_mod):
+    import ctypes
+    ring = W.ring_r0()
+    hcs = [dict(n=3, V_V=4e5, phi_rad=-2.9), dict(n=4, V_V=5e4, phi_rad=0.4)]
+    st, h = _create(pkg, ring, prec=0)
+    L = pkg.lib()
+    for hc in hcs:
+        assert L.mbt_add_harmonic_cavity(h, hc["n"], hc["V_V"], hc["phi_rad"]) == 0
+    assert L.mbt_set_grid(h, 256, 5.0) == 0
+    info = pkg.Info()
+    assert L.mbt_get_info(h, ctypes.byref(info)) == 0
+    d = oracle_mod.derive_h(ring, hcs)
+    assert info.phi_s == pytest.approx(math.asin(d["sin_phi_s"]), rel=1e-15)
+    assert info.sigma_tau0_s == pytest.approx(d["sigma_tau0"], rel=1e-14)
+    L.mbt_destroy(h)
