@@ -536,8 +536,9 @@ def fill390t_bench(args, rank, local):
     run = W.Run(**{**base.__dict__, "transverse": tplane, "name": base.name + " + transverse plane"})
     K, Wm = min(args.steps, 5000), max(args.warmup, 3)
     stream = torch.cuda.current_stream()
-    tr = pkg.tracker_for_run(run, record_turns=K + Wm + GRAPH_TURNS + 600)
+    tr = pkg.tracker_for_run(run, record_turns=K + Wm + GRAPH_TURNS + 17 * (AUTOTUNE_TURNS + 2) + 600)
     tr.init_particles(stream)
+    tile = tr.autotune(AUTOTUNE_TURNS)
     tr.set_graph(GRAPH_TURNS)
     tr.track(max(Wm, GRAPH_TURNS), stream)
     tr.sync()
@@ -566,7 +567,7 @@ def fill390t_bench(args, rank, local):
             "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": run.name, "transverse": {k: v for k, v in tplane.items() if k != "resonators"},
-                       "transverse_resonator": tplane["resonators"][0], "turns_timed": K},
+                       "transverse_resonator": tplane["resonators"][0], "turns_timed": K, "push_tile": tile},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": kind, "kernel": "k_push_mixed_t",
                          "bytes_per_unit": bpp, "unit_count": n, "push_us": push_s * 1e6,

@@ -198,19 +198,40 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
 }
 
 // ---------------------------------------------------------------------------
-// Mixed precision with a transverse plane (plans where some run has one):
-// tau, delta, x, x' read and written with coalesced vector accesses, one
-// quad of consecutive particles per thread and step; runs of the plan without
-// a transverse plane take the longitudinal quad step.  Harmonic cavities are
-// a runtime loop here.
+// Mixed precision with a transverse plane (plans where some run has one).
+// The same bulk-copy ring as k_push_mixed, a stage holding tau, delta, x and
+// x' of kChunk particles (20 KB); one quad of consecutive particles per
+// thread and chunk.  Runs of the plan without a transverse plane stage and
+// push only tau and delta.  Harmonic cavities are a runtime loop here.
 // ---------------------------------------------------------------------------
+constexpr int kStageBytesT = kChunk * (int)(3 * sizeof(float) + sizeof(double));
+#ifndef MBT_PUSH_T_MIN_BLOCKS
+#define MBT_PUSH_T_MIN_BLOCKS 4
+#endif
+
+__device__ __forceinline__ void issue_chunk_t(const TileDev &t, const float *tau, const double *del, const float *x,
+                                              const float *xp, uint8_t *stage, uint64_t *bar, int c, bool tr) {
+  const int n = min(kChunk, t.count - c * kChunk);
+  const int n4 = (n + 3) & ~3;   // segments are padded to 4 particles: 16-byte multiples
+  const uint32_t fb = (uint32_t)n4 * 4u, db = (uint32_t)n4 * 8u;
+  mbar_arrive_expect_tx(bar, fb + db + (tr ? 2u * fb : 0u));
+  bulk_g2s(stage, tau + (size_t)c * kChunk, fb, bar);
+  bulk_g2s(stage + kChunk * 4, del + (size_t)c * kChunk, db, bar);
+  if (tr) {
+    bulk_g2s(stage + kChunk * 12, x + (size_t)c * kChunk, fb, bar);
+    bulk_g2s(stage + kChunk * 16, xp + (size_t)c * kChunk, fb, bar);
+  }
+}
+
 template <int NLONG_MAX>
-__global__ void __launch_bounds__(kPushThreads, 3) k_push_mixed_t(const Plan p) {
-  extern __shared__ __align__(16) uint8_t sm_pt[];
+__global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed_t(const Plan p) {
+  extern __shared__ __align__(128) uint8_t sm_pt[];
   __shared__ float s_red[kPushThreads / 32][9];
   __shared__ float2 s_phi[kMaxLong];
   __shared__ int s_plane[kMaxLong];
   __shared__ float4 s_hc[kMaxHarm];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int s_abort;
 
   const TileDev t = p.tiles[blockIdx.x];
   const RunDev *__restrict__ R = p.runs + t.run;
@@ -220,7 +241,8 @@ __global__ void __launch_bounds__(kPushThreads, 3) k_push_mixed_t(const Plan p) 
   const int nbins = c.nbins;
   const int nlong = R->nlong;
   const bool tr = R->trans != 0;
-  float2 *sVd = reinterpret_cast<float2 *>(sm_pt);
+  uint8_t *stages = sm_pt;
+  float2 *sVd = reinterpret_cast<float2 *>(sm_pt + kStages * kStageBytesT);
   int *sH = reinterpret_cast<int *>(sVd + nbins);
   float2 *sVt = reinterpret_cast<float2 *>(sH + nbins);
   float *sDip = reinterpret_cast<float *>(sVt + nbins);
@@ -228,6 +250,15 @@ __global__ void __launch_bounds__(kPushThreads, 3) k_push_mixed_t(const Plan p) 
   double *del = R->delta + bd.off + t.start;
   float *xg = tr ? static_cast<float *>(R->x) + bd.off + t.start : nullptr;
   float *pg = tr ? static_cast<float *>(R->xp) + bd.off + t.start : nullptr;
+  const int nchunks = (t.count + kChunk - 1) / kChunk;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&full[st], 1);
+    fence_mbar_init();
+    s_abort = 0;
+    for (int ch = 0; ch < min(kStages, nchunks); ++ch)
+      issue_chunk_t(t, tau, del, xg, pg, stages + ch * kStageBytesT, &full[ch], ch, tr);
+  }
   const int nharm = R->nharm;
   if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
@@ -290,39 +321,56 @@ __global__ void __launch_bounds__(kPushThreads, 3) k_push_mixed_t(const Plan p) 
   float mom[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int nout = 0;
 #pragma unroll 1
-  for (int q = 4 * (int)threadIdx.x; q < t.count; q += 4 * kPushThreads) {
-    const uint32_t quad = (uint32_t)((t.start + q) >> 2);
-    const float4 tv = *reinterpret_cast<const float4 *>(tau + q);
-    const double2 da = *reinterpret_cast<const double2 *>(del + q);
-    const double2 db = *reinterpret_cast<const double2 *>(del + q + 2);
-    float rr[4] = {0.f, 0.f, 0.f, 0.f};
-    if (c.qe != 0.f) normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 0u, k0, k1), rr);
-    float tt[4] = {tv.x, tv.y, tv.z, tv.w};
-    double dd[4] = {da.x, da.y, db.x, db.y};
-    const int nvalid = min(4, t.count - q);
-    if (tr) {
-      const float4 xv = *reinterpret_cast<const float4 *>(xg + q);
-      const float4 pv = *reinterpret_cast<const float4 *>(pg + q);
-      float xx[4] = {xv.x, xv.y, xv.z, xv.w}, pp[4] = {pv.x, pv.y, pv.z, pv.w};
-      float rx[4] = {0.f, 0.f, 0.f, 0.f}, rp[4] = {0.f, 0.f, 0.f, 0.f};
-      if (texc) {
-        normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 3u, k0, k1), rx);
-        normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
-      }
-      quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, tt, dd, xx,
-                             pp, rr, rx, rp, nvalid, mom, nout);
-      *reinterpret_cast<float4 *>(xg + q) = make_float4(xx[0], xx[1], xx[2], xx[3]);
-      *reinterpret_cast<float4 *>(pg + q) = make_float4(pp[0], pp[1], pp[2], pp[3]);
-    } else if (ngp) {
-      quad_push<NLONG_MAX, true, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, mom[0],
-                                       mom[1], mom[2], mom[3], nout);
-    } else {
-      quad_push<NLONG_MAX, false, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, mom[0],
-                                        mom[1], mom[2], mom[3], nout);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int slot = ch % kStages;
+    uint8_t *sg = stages + slot * kStageBytesT;
+    if (!mbar_wait_bounded(&full[slot], (uint32_t)((ch / kStages) & 1), kPushWaitNs)) {
+      atomicExch(p.error, kErrTimeout);
+      s_abort = 1;
     }
-    *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
-    *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
-    *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+    const int q = ch * kChunk + 4 * (int)threadIdx.x;
+    if (!s_abort && q < t.count) {
+      const uint32_t quad = (uint32_t)((t.start + q) >> 2);
+      const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
+      const double2 da = reinterpret_cast<const double2 *>(sg + kChunk * 4)[2 * threadIdx.x];
+      const double2 db = reinterpret_cast<const double2 *>(sg + kChunk * 4)[2 * threadIdx.x + 1];
+      float rr[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c.qe != 0.f) normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 0u, k0, k1), rr);
+      float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+      double dd[4] = {da.x, da.y, db.x, db.y};
+      const int nvalid = min(4, t.count - q);
+      if (tr) {
+        const float4 xv = reinterpret_cast<const float4 *>(sg + kChunk * 12)[threadIdx.x];
+        const float4 pv = reinterpret_cast<const float4 *>(sg + kChunk * 16)[threadIdx.x];
+        float xx[4] = {xv.x, xv.y, xv.z, xv.w}, pp[4] = {pv.x, pv.y, pv.z, pv.w};
+        float rx[4] = {0.f, 0.f, 0.f, 0.f}, rp[4] = {0.f, 0.f, 0.f, 0.f};
+        if (texc) {
+          normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 3u, k0, k1), rx);
+          normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
+        }
+        quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, tt, dd,
+                               xx, pp, rr, rx, rp, nvalid, mom, nout);
+        *reinterpret_cast<float4 *>(xg + q) = make_float4(xx[0], xx[1], xx[2], xx[3]);
+        *reinterpret_cast<float4 *>(pg + q) = make_float4(pp[0], pp[1], pp[2], pp[3]);
+      } else if (ngp) {
+        quad_push<NLONG_MAX, true, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid,
+                                         mom[0], mom[1], mom[2], mom[3], nout);
+      } else {
+        quad_push<NLONG_MAX, false, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid,
+                                          mom[0], mom[1], mom[2], mom[3], nout);
+      }
+      *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+      *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
+      *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+    }
+    __syncthreads();   // stage `slot` consumed by every thread
+    if (threadIdx.x == 0 && !s_abort && ch + kStages < nchunks) {
+      fence_proxy_async_smem();
+      issue_chunk_t(t, tau, del, xg, pg, sg, &full[slot], ch + kStages, tr);
+    }
+  }
+  if (s_abort && threadIdx.x == 0) {
+    for (int ch = 0; ch < nchunks; ++ch) mbar_wait_bounded(&full[ch % kStages], (uint32_t)((ch / kStages) & 1), kPushWaitNs);
   }
 
   // moment partials (columns 0-4 longitudinal, 6-9 transverse)
@@ -621,7 +669,7 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   if (p.ntiles == 0) return cudaSuccess;
   const int max_nbins = p.max_nbins;
   if (precision == kMixed && p.max_trans) {
-    const size_t smem = (size_t)max_nbins * (2 * sizeof(float2) + sizeof(int) + sizeof(float));
+    const size_t smem = (size_t)kStages * kStageBytesT + (size_t)max_nbins * (2 * sizeof(float2) + sizeof(int) + sizeof(float));
     switch (p.max_nlong) {
       case 0: return launch_ex(k_push_mixed_t<0>, p.ntiles, kPushThreads, smem, s, pdl, p);
       case 1: return launch_ex(k_push_mixed_t<1>, p.ntiles, kPushThreads, smem, s, pdl, p);
@@ -663,6 +711,9 @@ cudaError_t configure_push_kernels() {
   for (auto k : {k_push_mixed<0, false>, k_push_mixed<1, false>, k_push_mixed<2, false>, k_push_mixed<kMaxLong, false>,
                  k_push_mixed<0, true>, k_push_mixed<1, true>, k_push_mixed<2, true>, k_push_mixed<kMaxLong, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const int bytes_t = (int)((size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float)));
+  for (auto k : {k_push_mixed_t<0>, k_push_mixed_t<1>, k_push_mixed_t<2>, k_push_mixed_t<kMaxLong>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_t);
   return e;
 }
 
