@@ -123,6 +123,10 @@ def _load():
             lib.orc_get_vt.argtypes = [ctypes.c_void_p, _P(_d)]
             lib.orc_get_atlr.argtypes = [ctypes.c_void_p, _P(_d)]
             lib.orc_vt_direct.argtypes = [ctypes.c_void_p, _P(_d), _d, _P(_d)]
+            lib.orc_add_transverse_rw.argtypes = [ctypes.c_void_p, _d, _d, _d, ctypes.c_int]
+            lib.orc_add_transverse_rw.restype = ctypes.c_int
+            lib.orc_transverse_rw_wake.argtypes = [ctypes.c_void_p, _d]
+            lib.orc_transverse_rw_wake.restype = _d
             _lib = lib
     return _lib
 
@@ -297,6 +301,10 @@ class OracleSim:
                                             float(transverse["tune"]), float(transverse.get("chromaticity", 0.0)),
                                             float(transverse["emittance_m"]), len(tres), ta) != 0:
                 raise ValueError("oracle rejected the transverse plane")
+            for rw in transverse.get("resistive_wall", ()):
+                if self._lib.orc_add_transverse_rw(self._h, float(rw["radius_m"]), float(rw["conductivity_S_per_m"]),
+                                                   float(rw["length_m"]), int(rw["history_turns"])) != 0:
+                    raise ValueError("oracle rejected the transverse resistive wall")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -387,6 +395,9 @@ class OracleSim:
 
     def wake_voltage_at(self, m: int, tau: float) -> float:
         return self._lib.orc_wake_voltage_at(self._h, int(m), float(tau))
+
+    def transverse_rw_wake(self, t: float) -> float:
+        return self._lib.orc_transverse_rw_wake(self._h, float(t))
 
     def track2(self, nturns: int):
         """Track nturns; returns (moments [n][nb][6], transverse moments [n][nb][4])."""

@@ -53,7 +53,9 @@
  *   R15 the transverse plane (see orc_set_transverse): one plane per run,
  *      no dispersion at the tracking point, kicks with the previous turn's
  *      wake before the RF, momentum ratio across the cavity, chromatic
- *      rotation with the new delta, excitation, dipole sums per cell.
+ *      rotation with the new delta, excitation, dipole sums per cell;
+ *   R16 the long-range transverse resistive wall acts through bunch
+ *      centroids over a finite history (see orc_add_transverse_rw).
  */
 #include <complex.h>
 #include <math.h>
@@ -287,6 +289,11 @@ typedef struct orc_sim {
     int nthist;
     double complex *Ethist;/* [ntres][nthist][nb] transverse emission history */
     double *tmoments;      /* [nb][4]: <x>, sig_x, <x'>, sig_x' */
+    /* long-range transverse resistive wall on bunch centroids (reading R16) */
+    double rw_A;           /* W(t) = rw_A / sqrt(t) [V/(C m)], t in s        */
+    int rw_nh;             /* turns of history                               */
+    double *rw_cent;       /* [rw_nh + 1][nb] charge x centroid, by turn     */
+    double *Vrw;           /* [nb] kick voltage of each bunch for the next turn */
 } orc_sim;
 
 /* e^{-a dt} below this is dropped from the direct history sum. */
@@ -430,7 +437,7 @@ void orc_destroy(orc_sim *s)
             free(s->xp[m]);
         }
         free(s->x); free(s->xp); free(s->dip); free(s->Vt); free(s->Wtlag); free(s->Atlr); free(s->Ethist);
-        free(s->tmoments);
+        free(s->tmoments); free(s->rw_cent); free(s->Vrw);
     }
     free(s);
 }
@@ -667,6 +674,36 @@ static double complex history_sum(const orc_sim *s, int r, int m)
     return acc;
 }
 
+/* Long-range transverse resistive wall of a round pipe (radius b,
+ * conductivity sigma, length L), reading R16: far from the wake's head the
+ * dipole wake is W(t) = (c L / (pi b^3)) sqrt(Z0 / (pi sigma)) / sqrt(c t)
+ * [V/(C m)] (positive: the trailing charge is deflected towards the source
+ * offset, the sign of the transverse resonator's wake).  It acts between
+ * bunch passages through the bunch centroids: every particle of bunch m gets
+ * x' += (1/E0) sum Q_p <x>_p W(t_m - t_p) over the passages of the last
+ * history_turns turns before it (the bunch's own earlier turns included).
+ * Several pipes add their coefficients; the history is the longest asked. */
+int orc_add_transverse_rw(orc_sim *s, double radius_m, double sigma, double length_m, int history_turns)
+{
+    if (!s->trans || !(radius_m > 0.0) || !(sigma > 0.0) || !(length_m > 0.0) || history_turns < 1)
+        return -1;
+    const double pi = 3.14159265358979323846264338327950, c = 299792458.0, Z0 = 376.730313668;
+    s->rw_A += c * length_m / (pi * radius_m * radius_m * radius_m) * sqrt(Z0 / (pi * sigma)) / sqrt(c);
+    if (history_turns > s->rw_nh) {
+        free(s->rw_cent);
+        s->rw_nh = history_turns;
+        s->rw_cent = (double *)calloc((size_t)(s->rw_nh + 1) * s->nb, sizeof(double));
+    }
+    if (!s->Vrw)
+        s->Vrw = (double *)calloc(s->nb, sizeof(double));
+    return 0;
+}
+
+double orc_transverse_rw_wake(const orc_sim *s, double t)
+{
+    return t > 0.0 ? s->rw_A / sqrt(t) : 0.0;
+}
+
 /* Transverse short-range voltage at cell coordinate x of bunch m, linear
  * between cell centres like the longitudinal one (zero outside the mesh). */
 static double vt_at(const orc_sim *s, int m, double xc)
@@ -798,7 +835,7 @@ static void one_turn(orc_sim *s)
                 if (s->trans) {
                     double x = s->x[m][i + e], xp = s->xp[m][i + e];
                     /* transverse wake kick (Eq. 6, second line), previous turn's wake */
-                    double Vt = vt_at(s, m, orc_cell_coord(s, t)) + vtlr_at(s, m, t);
+                    double Vt = vt_at(s, m, orc_cell_coord(s, t)) + vtlr_at(s, m, t) + (s->Vrw ? s->Vrw[m] : 0.0);
                     xp = xp + Vt / s->ring.E0_eV;
                     /* Eq. 5, x' line: momentum ratio across the cavity */
                     xp = xp * (1.0 + d_before) / (1.0 + d_gain);
@@ -876,6 +913,27 @@ static void one_turn(orc_sim *s)
             E[m] = orc_emission(s, r, s->hist + (size_t)m * s->nbins, s->q_mp[m]);
         for (int m = 0; m < s->nb; ++m)
             s->Alr[(size_t)r * s->nb + m] = history_sum(s, r, m);
+    }
+    if (s->trans && s->rw_cent) {
+        /* charge x centroid of every bunch (all its particles) for this turn's slot */
+        double *cur = s->rw_cent + (size_t)(s->turn % (s->rw_nh + 1)) * s->nb;
+        for (int m = 0; m < s->nb; ++m)
+            cur[m] = s->current[m] * s->ring.T0_s * s->tmoments[(size_t)m * 4];
+        for (int m = 0; m < s->nb; ++m) {
+            double v = 0.0;
+            for (int back = 0; back <= s->rw_nh; ++back) {
+                if (s->turn - back < 0)
+                    break;
+                const double *src = s->rw_cent + (size_t)((s->turn - back) % (s->rw_nh + 1)) * s->nb;
+                for (int mp = 0; mp < s->nb; ++mp) {
+                    int64_t D = (int64_t)back * s->ring.h + (int64_t)s->bucket[m] - (int64_t)s->bucket[mp];
+                    if (D <= 0)
+                        continue;
+                    v += src[mp] * orc_transverse_rw_wake(s, (double)D * s->dv.T_rf);
+                }
+            }
+            s->Vrw[m] = v;
+        }
     }
     if (s->trans) {
         for (int m = 0; m < s->nb; ++m)

@@ -658,7 +658,7 @@ TRES = dict(Rs_ohm=2e5, fr_Hz=1.5e9, Q=2e4, range=W.RANGE_BOTH)   # Ohm/m
 
 
 def _tplane(**kw):
-    t = dict(beta_m=10.0, alpha=0.0, tune=0.3, chromaticity=0.0, emittance_m=1e-9, resonators=[])
+    t = dict(beta_m=10.0, alpha=0.0, tune=0.3, chromaticity=0.0, emittance_m=1e-9, resonators=[], resistive_wall=[])
     t.update(kw)
     return t
 
@@ -783,3 +783,43 @@ def test_transverse_coupled_bunch_growth_rate(oracle_mod):
     pred = -(Ib * M * beta / (2 * ring["E0_eV"] * T0)) * np.sum(re_z(lines[lines != 0]))
     assert pred > 500
     assert rate == pytest.approx(pred, rel=0.02)
+
+
+def test_transverse_rw_wake_is_the_integral_of_the_longitudinal_one(oracle_mod):
+    """Round pipe: Z_x = (2c / (b^2 w)) Z_parallel, i.e. W_x(t) = (2c/b^2) int_0^t
+    W_parallel; far behind the head the transverse resistive-wall wake equals
+    that integral of the (pinned) longitudinal Bane-Sands wake."""
+    b, sig, L, Z0, c, s0, tail = _rw_consts()
+    s = oracle_mod.OracleSim(W.ring_r0(), [], 64, 5.0, [0], [0.0], [4], 1, 0,
+                             transverse=_tplane(resistive_wall=[dict(radius_m=b, conductivity_S_per_m=sig,
+                                                                     length_m=L, history_turns=2)]))
+    for u in (2000.0, 8000.0):
+        T = u * s0 / c
+        t, w = oracle_mod.resistive_wall_table(b, sig, L, T)
+        integral = np.trapezoid(w, t)
+        assert s.transverse_rw_wake(T) == pytest.approx(2 * c / (b * b) * integral, rel=2e-3)
+
+
+def test_transverse_rw_kicks_follow_the_centroid_history(oracle_mod):
+    """A single offset bunch at integer tune (x frozen, no radiation, no other
+    wake): x' grows turn by turn by (Q X0 / E0) sum_k W(k T0) over its earlier
+    passages within the history, W(t) = (cL/(pi b^3)) sqrt(Z0/(pi sigma)) / sqrt(c t)."""
+    ring = W.ring_r0()
+    T0 = ring["T0_s"]
+    b, sig, L, nh = 0.01, 5.8e7, 290.4, 3
+    Z0, c = 376.730313668, 299792458.0
+    A = c * L / (math.pi * b ** 3) * math.sqrt(Z0 / (math.pi * sig)) / math.sqrt(c)
+    I, N, X0 = 2e-3, 8, 1e-4
+    tp = _tplane(tune=1.0, emittance_m=0.0,
+                 resistive_wall=[dict(radius_m=b, conductivity_S_per_m=sig, length_m=L, history_turns=nh)])
+    s = oracle_mod.OracleSim(ring, [], 64, 5.0, [0], [I], [N], 1, W.NO_SR, transverse=tp)
+    s.set_particles(0, np.zeros(N), np.zeros(N))
+    s.set_tparticles(0, np.full(N, X0), np.zeros(N))
+    turns = 7
+    _, trec = s.track2(turns)
+    Q = I * T0
+    xp = 0.0
+    for n in range(turns):
+        # the kick of turn n uses the passages of turns n-1-k, k = 1 .. nh (k = 0 is this passage)
+        xp += Q * X0 / ring["E0_eV"] * sum(A / math.sqrt(k * T0) for k in range(1, nh + 1) if n - 1 - k >= 0)
+        assert trec[n, 0, 2] == pytest.approx(xp, rel=1e-9, abs=1e-18)   # sin(2 pi) residue ~1e-21
