@@ -175,6 +175,18 @@ mbt_status mbt_set_transverse(mbt_ctx *ctx, double beta_m, double alpha, double 
  * mbt_set_transverse first; only before mbt_set_fill. */
 mbt_status mbt_add_transverse_resonator(mbt_ctx *ctx, double Rs_ohm_per_m, double fr_Hz, double Q, int range);
 
+/* Add the long-range transverse resistive wall of a round pipe (radius_m,
+ * conductivity_S_per_m, length_m; the paper applies it to the transverse
+ * planes from the statistics of earlier bunches): far from the head the
+ * dipole wake is W(t) = (c L / (pi b^3)) sqrt(Z0 / (pi sigma)) / sqrt(c t)
+ * [V/(C m)], and every particle of a bunch gets x' += (1/E0) sum Q_p <x>_p
+ * W(t_m - t_p) over the passages of the last history_turns turns before its
+ * own (1 <= history_turns <= 1000; the bunch's own earlier turns count).
+ * Several pipes add up; the longest history is kept.  Needs
+ * mbt_set_transverse; only before mbt_set_fill. */
+mbt_status mbt_add_transverse_resistive_wall(mbt_ctx *ctx, double radius_m, double conductivity_S_per_m,
+                                             double length_m, int history_turns);
+
 /* Copy one bunch's transverse coordinates from host arrays of n_mp[bunch]
  * doubles (MBT_PREC_MIXED rounds to FP32) / to host arrays.  Synchronous. */
 mbt_status mbt_set_transverse_particles(mbt_ctx *ctx, int bunch, const double *x_m, const double *xp);

@@ -30,6 +30,7 @@ NO_SR, NO_QE, KICK_NGP = 1, 2, 4
 EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt_last_error",
            "mbt_add_resonator", "mbt_add_wake_table", "mbt_add_resistive_wall",
            "mbt_add_harmonic_cavity", "mbt_set_transverse", "mbt_add_transverse_resonator",
+           "mbt_add_transverse_resistive_wall",
            "mbt_set_transverse_particles", "mbt_get_transverse_particles", "mbt_read_transverse_moments",
            "mbt_read_transverse_wake", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
            "mbt_set_particles", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
@@ -117,6 +118,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_add_harmonic_cavity": ([_vp, _i, _d, _d], _i),
                 "mbt_set_transverse": ([_vp, _d, _d, _d, _d, _d], _i),
                 "mbt_add_transverse_resonator": ([_vp, _d, _d, _d, _i], _i),
+                "mbt_add_transverse_resistive_wall": ([_vp, _d, _d, _d, _i], _i),
                 "mbt_set_transverse_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_get_transverse_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_read_transverse_moments": ([_vp, _i64, _i64, _P(_d)], _i),
@@ -203,6 +205,10 @@ class Tracker:
             for res in transverse.get("resonators", ()):
                 self._chk(self._L.mbt_add_transverse_resonator(self._h, res["Rs_ohm"], res["fr_Hz"], res["Q"],
                                                                int(res["range"])))
+            for rw in transverse.get("resistive_wall", ()):
+                self._chk(self._L.mbt_add_transverse_resistive_wall(
+                    self._h, float(rw["radius_m"]), float(rw["conductivity_S_per_m"]), float(rw["length_m"]),
+                    int(rw["history_turns"])))
         for hc in harmonic_cavities:
             self._chk(self._L.mbt_add_harmonic_cavity(self._h, int(hc["n"]), float(hc["V_V"]), float(hc["phi_rad"])))
         for rw in resistive_wall:

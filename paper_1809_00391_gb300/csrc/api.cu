@@ -96,6 +96,11 @@ struct mbt_ctx {
   bool trans = false;
   double t_beta = 0, t_alpha = 0, t_tune = 0, t_xi = 0, t_emit = 0;
   std::vector<Resonator> tres;
+  double rw_A = 0.0;   // long-range transverse resistive wall: W = rw_A / sqrt(t)
+  int rw_nh = 0;
+  double *d_rwtab = nullptr, *d_rwcent = nullptr;
+  float *d_rwtab_f = nullptr;
+  int32_t *d_bucket = nullptr;
   void *d_x = nullptr, *d_xp = nullptr, *d_dip = nullptr, *d_vt = nullptr;
   double *d_trec = nullptr, *d_tlag = nullptr;
   float *d_tlag_f = nullptr;
@@ -569,6 +574,20 @@ mbt_status mbt_add_transverse_resonator(mbt_ctx *c, double Rs, double fr, double
   return MBT_OK;
 }
 
+mbt_status mbt_add_transverse_resistive_wall(mbt_ctx *c, double b, double sigma, double L, int nh) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (c->filled) return fail(c, MBT_ERR_STATE, "resistive walls must be added before mbt_set_fill");
+  if (!c->trans) return fail(c, MBT_ERR_STATE, "set the transverse plane first");
+  if (!(b > 0) || !(sigma > 0) || !(L > 0) || !std::isfinite(b) || !std::isfinite(sigma) || !std::isfinite(L) ||
+      nh < 1 || nh > 1000)
+    return fail(c, MBT_ERR_ARG, "a transverse resistive wall needs radius, conductivity, length > 0 and 1..1000 turns");
+  constexpr double kZ0 = 376.730313668, kC = 299792458.0;
+  c->rw_A += kC * L / (kPi * b * b * b) * std::sqrt(kZ0 / (kPi * sigma)) / std::sqrt(kC);
+  c->rw_nh = std::max(c->rw_nh, nh);
+  return MBT_OK;
+}
+
 mbt_status mbt_add_harmonic_cavity(mbt_ctx *c, int n, double V, double phi) {
   if (!c) return MBT_ERR_ARG;
   c->err.clear();
@@ -719,6 +738,12 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     ALLOC(c->d_trec, (size_t)c->cap * nb * kTRecord * sizeof(double));
     ALLOC(c->d_tlag, (size_t)nbins * sizeof(double));
     ALLOC(c->d_tlag_f, (size_t)nbins * sizeof(float));
+    if (c->rw_nh > 0) {
+      ALLOC(c->d_rwtab, (size_t)(c->rw_nh + 1) * c->ring.h * sizeof(double));
+      ALLOC(c->d_rwtab_f, (size_t)(c->rw_nh + 1) * c->ring.h * sizeof(float));
+      ALLOC(c->d_rwcent, (size_t)(c->rw_nh + 1) * nb * sizeof(double));
+      ALLOC(c->d_bucket, (size_t)nb * sizeof(int32_t));
+    }
   }
 #undef ALLOC
 
@@ -915,6 +940,24 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     rd.f_tgamma = (float)rd.t_gamma;
     rd.f_tnx = (float)rd.t_nx;
     rd.f_tnxp = (float)rd.t_nxp;
+    if (c->rw_nh > 0) {
+      const size_t nt = (size_t)(c->rw_nh + 1) * c->ring.h;
+      std::vector<double> tab(nt, 0.0);
+      std::vector<float> tabf(nt, 0.f);
+      for (size_t D = 1; D < nt; ++D) {
+        tab[D] = c->rw_A / std::sqrt((double)D * c->T_rf);
+        tabf[D] = (float)tab[D];
+      }
+      cudaMemcpy(c->d_rwtab, tab.data(), nt * sizeof(double), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->d_rwtab_f, tabf.data(), nt * sizeof(float), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->d_bucket, c->bucket.data(), (size_t)nb * sizeof(int32_t), cudaMemcpyHostToDevice);
+      rd.rw_nh = c->rw_nh;
+      rd.h_rf = c->ring.h;
+      rd.rw_tab = c->d_rwtab;
+      rd.rw_tab_f = c->d_rwtab_f;
+      rd.rw_cent = c->d_rwcent;
+      rd.bucket = c->d_bucket;
+    }
   }
   rd.f_inv_omD = (float)(1.0 / rd.one_minus_D);
   rd.f_U0oE0 = (float)rd.U0_over_E0;
@@ -972,6 +1015,7 @@ mbt_status mbt_init_particles(mbt_ctx *c, void *stream) {
     const size_t fs = c->precision == MBT_PREC_MIXED ? sizeof(float) : sizeof(double);
     cudaMemsetAsync(c->d_dip, 0, (size_t)2 * c->nb * c->nbins * fs, s);
     cudaMemsetAsync(c->d_vt, 0, (size_t)c->nb * c->nbins * fs, s);
+    if (c->rw_nh > 0) cudaMemsetAsync(c->d_rwcent, 0, (size_t)(c->rw_nh + 1) * c->nb * sizeof(double), s);
   }
   cudaError_t e = launch_init(c->own.plan, c->precision, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "init launch");
@@ -1581,6 +1625,7 @@ std::vector<Section> state_sections(mbt_ctx *c) {
     out.push_back({c->d_xp, (size_t)c->n_alloc * fs});
     out.push_back({c->d_dip, (size_t)2 * c->nb * c->nbins * fs});
     out.push_back({c->d_vt, (size_t)c->nb * c->nbins * fs});
+    if (c->rw_nh > 0) out.push_back({c->d_rwcent, (size_t)(c->rw_nh + 1) * c->nb * sizeof(double)});
   }
   return out;
 }

@@ -152,6 +152,8 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
       tr[1] = sqrt(vx);
       tr[2] = mp;
       tr[3] = sqrt(vp);
+      // charge x centroid of the bunch for the long-range resistive wall
+      if (R->rw_nh > 0) R->rw_cent[(size_t)(turn % (R->rw_nh + 1)) * nb + m0 + lane] = R->q_mp[m0 + lane] * s_sum[5][lane];
     }
   }
 }

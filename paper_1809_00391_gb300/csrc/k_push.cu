@@ -223,6 +223,53 @@ __device__ __forceinline__ void issue_chunk_t(const TileDev &t, const float *tau
   }
 }
 
+// Long-range transverse resistive-wall voltage on bunch m for the turn
+// `turn`: sum over the passages of the last rw_nh turns before it (earlier
+// bunches of the same passage included) of charge x centroid x W(D T_rf), D
+// the bucket distance; every thread of the CTA returns the sum.  red: 8
+// floats / doubles of shared scratch.  0 without a resistive wall.
+__device__ float rw_voltage_f32(const RunDev *__restrict__ R, int m, long long turn, float *red) {
+  if (R->rw_nh <= 0) return 0.f;
+  const int nh1 = R->rw_nh + 1, nb = R->nb, h = R->h_rf, bm = R->bucket[m];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < nh1 * nb; i += kPushThreads) {
+    const int back = i / nb, mp = i - back * nb;
+    const long long src = turn - 1 - back;
+    const int D = back * h + bm - R->bucket[mp];
+    if (src >= 0 && D > 0) acc = fmaf((float)R->rw_cent[(size_t)(src % nh1) * nb + mp], R->rw_tab_f[D], acc);
+  }
+  acc = warp_sum_f(acc);
+  __syncthreads();   // red may hold other data until every thread is here
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  float v = 0.f;
+#pragma unroll
+  for (int w = 0; w < kPushThreads / 32; ++w) v += red[w];
+  __syncthreads();
+  return v;
+}
+
+__device__ double rw_voltage_f64(const RunDev *__restrict__ R, int m, long long turn, double *red) {
+  if (R->rw_nh <= 0) return 0.0;
+  const int nh1 = R->rw_nh + 1, nb = R->nb, h = R->h_rf, bm = R->bucket[m];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nh1 * nb; i += kPushThreads) {
+    const int back = i / nb, mp = i - back * nb;
+    const long long src = turn - 1 - back;
+    const int D = back * h + bm - R->bucket[mp];
+    if (src >= 0 && D > 0) acc = fma(R->rw_cent[(size_t)(src % nh1) * nb + mp], R->rw_tab[D], acc);
+  }
+  acc = warp_sum_d(acc);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double v = 0.0;
+#pragma unroll
+  for (int w = 0; w < kPushThreads / 32; ++w) v += red[w];
+  __syncthreads();
+  return v;
+}
+
 template <int NLONG_MAX>
 __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed_t(const Plan p) {
   extern __shared__ __align__(128) uint8_t sm_pt[];
@@ -317,6 +364,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   }
   const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
   const bool texc = tc.nx != 0.f || tc.nxp != 0.f;
+  const float vrw = tr ? rw_voltage_f32(R, t.m, turn, s_red[0]) : 0.f;
 
   float mom[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int nout = 0;
@@ -348,8 +396,8 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
           normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 3u, k0, k1), rx);
           normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
         }
-        quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, tt, dd,
-                               xx, pp, rr, rx, rp, nvalid, mom, nout);
+        quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, vrw, tt,
+                               dd, xx, pp, rr, rx, rp, nvalid, mom, nout);
         *reinterpret_cast<float4 *>(xg + q) = make_float4(xx[0], xx[1], xx[2], xx[3]);
         *reinterpret_cast<float4 *>(pg + q) = make_float4(pp[0], pp[1], pp[2], pp[3]);
       } else if (ngp) {
@@ -475,6 +523,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   const bool texc = tr && (R->t_nx != 0.0 || R->t_nxp != 0.0);
   double st = 0.0, st2 = 0.0, sd = 0.0, sd2 = 0.0, sx = 0.0, sx2 = 0.0, sp = 0.0, sp2 = 0.0;
   int nout = 0;
+  const double vrw = tr ? rw_voltage_f64(R, t.m, turn, s_red[0]) : 0.0;
 
 #pragma unroll 1
   for (int it = 0; it < kF64QuadsPerThread; ++it) {
@@ -508,7 +557,7 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
       double tp = tt[e], d = dd[e];
       const double xc = __dmul_rn(__dadd_rn(tp, H), invD);
       double v = vsr_at_f64(sV, xc, nbins, ngp);
-      double vt = tr ? vsr_at_f64(sVt, xc, nbins, ngp) : 0.0;
+      double vt = tr ? vsr_at_f64(sVt, xc, nbins, ngp) + vrw : 0.0;
       for (int r = 0; r < nlong; ++r) {
         const double2 s = R->lr_s[r];
         double sn, cs;

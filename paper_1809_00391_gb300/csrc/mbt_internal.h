@@ -82,6 +82,13 @@ struct RunDev {
   const float *tlag_f;
   double t_beta, t_alpha, t_gamma, t_mu0, t_xi, t_nx, t_nxp;   // t_nx = sqrt(beta emit Dx), t_nxp = sqrt(gamma emit Dx)
   double t_emit;
+  // long-range transverse resistive wall on bunch centroids
+  int rw_nh;                // turns of history (0: none)
+  const double *rw_tab;     // [(rw_nh + 1) h] W(D T_rf) by bucket distance D (0 at D = 0)
+  const float *rw_tab_f;
+  double *rw_cent;          // [rw_nh + 1][nb] charge x centroid, by turn
+  const int32_t *bucket;    // [nb]
+  int h_rf;                 // harmonic number
   // float copies: 2 pi frac(nu), 2 pi nu xi, beta, alpha, gamma, nx, nxp, 1/(1 - D)
   float f_tmu0, f_tmu0xi, f_tbeta, f_talpha, f_tgamma, f_tnx, f_tnxp, f_inv_omD, f_U0oE0;
 };

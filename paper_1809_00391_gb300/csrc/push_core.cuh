@@ -106,8 +106,8 @@ template <int NLONG_MAX>
 __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
                                             const float2 *sVt, int nlong, const int *plane, const float *la,
                                             const float *lw, const float2 *phi, double omD_d, const float4 *hc,
-                                            int nharm, bool ngp, float t0, double &d, float r, float &df, float &x,
-                                            float &xp, float rx, float rxp) {
+                                            int nharm, bool ngp, float vrw, float t0, double &d, float r, float &df,
+                                            float &x, float &xp, float rx, float rxp) {
   const float x0 = fmaf(t0, c.invD, c.HinvD);
   const bool inside = x0 >= 0.f && x0 < c.fnb;
   float v, vt;
@@ -123,7 +123,7 @@ __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransCons
     vt = fmaf(u - (float)j, vtd.y, vtd.x);
   }
   v = inside ? v : 0.f;
-  vt = inside ? vt : 0.f;
+  vt = (inside ? vt : 0.f) + vrw;   // the long-range resistive wall acts on every particle of the bunch
 #pragma unroll
   for (int r2 = 0; r2 < NLONG_MAX; ++r2) {
     if (r2 < nlong) {
@@ -167,7 +167,8 @@ template <int NLONG_MAX>
 __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
                                             const float2 *sVt, int *sH, float *sDip, int nlong, const int *plane,
                                             const float *la, const float *lw, const float2 *phi, double omD_d,
-                                            const float4 *hc, int nharm, bool ngp, float (&tt)[4], double (&dd)[4],
+                                            const float4 *hc, int nharm, bool ngp, float vrw, float (&tt)[4],
+                                            double (&dd)[4],
                                             float (&xx)[4], float (&pp)[4], const float (&rr)[4],
                                             const float (&rx)[4], const float (&rp)[4], int nvalid, float (&mom)[8],
                                             int &nout) {
@@ -175,7 +176,7 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
   for (int e = 0; e < 4; ++e) {
     if (e < nvalid) {
       float df;
-      const float t1 = push_one_t<NLONG_MAX>(c, tc, sVd, sVt, nlong, plane, la, lw, phi, omD_d, hc, nharm, ngp,
+      const float t1 = push_one_t<NLONG_MAX>(c, tc, sVd, sVt, nlong, plane, la, lw, phi, omD_d, hc, nharm, ngp, vrw,
                                              tt[e], dd[e], rr[e], df, xx[e], pp[e], rx[e], rp[e]);
       tt[e] = t1;
       const float xb = fmaf(t1, c.invD, c.HinvD);
