@@ -538,7 +538,11 @@ def fill390t_bench(args, rank, local):
     stream = torch.cuda.current_stream()
     tr = pkg.tracker_for_run(run, record_turns=K + Wm + GRAPH_TURNS + 17 * (AUTOTUNE_TURNS + 2) + 600)
     tr.init_particles(stream)
-    tile = tr.autotune(AUTOTUNE_TURNS)
+    if args.tile > 0:
+        tr.set_tile(args.tile)
+        tile = args.tile
+    else:
+        tile = tr.autotune(AUTOTUNE_TURNS)
     tr.set_graph(GRAPH_TURNS)
     tr.track(max(Wm, GRAPH_TURNS), stream)
     tr.sync()

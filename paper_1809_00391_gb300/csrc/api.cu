@@ -332,9 +332,137 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
     *dst = static_cast<T *>(p);
     return true;
   };
+  // Streaming push (mixed precision, no transverse plane): each run's
+  // particle sequence (its bunches in order, each padded to 4 particles) is
+  // cut into one equal share per SM at multiples of 4, each share into tiles
+  // at bunch boundaries, and CTA g takes share g of every run.  A run's tiles
+  // (and so the order of its moment sums) are the same alone and in a batch.
+  // p.tiles stays in bunch order (the post kernel sums each bunch's partials
+  // over its consecutive tiles); p.stiles lists each CTA's tiles together.
+  bool streaming = !st.runs.empty();
+  for (const RunDev &r : st.runs) streaming = streaming && r.precision == kMixed && !r.trans;
+  std::vector<int> first, owner;
+  std::vector<int> sorder;   // tile indices in CTA order
+  if (streaming) {
+    int slots = 0;
+    if (push_resident_slots(&slots) != cudaSuccess || slots <= 0) {
+      cudaGetLastError();
+      return fail(c, MBT_ERR_CUDA, "streaming push occupancy");
+    }
+    const int G = slots;
+    constexpr int64_t kMaxCount = int64_t(1) << 28;
+    std::vector<TileDev> tiles;
+    size_t b0 = 0;
+    for (size_t ri = 0; ri < st.runs.size(); ++ri) {
+      size_t b1 = b0;
+      int64_t P = 0;
+      while (b1 < st.bunches.size() && st.bunches[b1].run == (int)ri) P += (st.bunches[b1++].n + 3) / 4 * 4;
+      size_t m = b0;
+      int64_t B = 0;   // padded start of bunch m within the run
+      for (int g = 0; g < G; ++g) {
+        const int64_t a = (P / 4) * g / G * 4, e = g + 1 == G ? P : (P / 4) * (g + 1) / G * 4;
+        while (m < b1 && B + (st.bunches[m].n + 3) / 4 * 4 <= a) B += (st.bunches[m++].n + 3) / 4 * 4;
+        int64_t Bm = B;
+        for (size_t mm = m; mm < b1 && Bm < e; ++mm) {
+          const BunchDev &bd = st.bunches[mm];
+          const int64_t pm = (bd.n + 3) / 4 * 4;
+          const int64_t s0 = std::max(a, Bm) - Bm, s1 = std::min<int64_t>(std::min(e, Bm + pm) - Bm, bd.n);
+          for (int64_t s = s0; s < s1; s += kMaxCount) {
+            TileDev t{};
+            t.bunch = (int)mm;
+            t.run = bd.run;
+            t.m = bd.m;
+            t.start = s;
+            t.count = (int)std::min<int64_t>(kMaxCount, s1 - s);
+            tiles.push_back(t);
+            owner.push_back(g);
+          }
+          Bm += pm;
+        }
+      }
+      b0 = b1;
+    }
+    st.tiles.swap(tiles);
+    for (BunchDev &bd : st.bunches) bd.tile0 = bd.ntiles = 0;
+    for (size_t i = 0; i < st.tiles.size(); ++i) {
+      BunchDev &bd = st.bunches[(size_t)st.tiles[i].bunch];
+      if (bd.ntiles == 0) bd.tile0 = (int)i;
+      ++bd.ntiles;
+    }
+    first.assign((size_t)G + 1, 0);
+    for (int g : owner) ++first[(size_t)g + 1];
+    for (int g = 0; g < G; ++g) first[(size_t)g + 1] += first[(size_t)g];
+    sorder.assign(st.tiles.size(), 0);
+    std::vector<int> fill(first.begin(), first.end() - 1);
+    for (size_t i = 0; i < st.tiles.size(); ++i) sorder[(size_t)fill[(size_t)owner[i]]++] = (int)i;
+  }
   Plan pl{};
   if (!up(st.runs, &pl.runs) || !up(st.bunches, &pl.bunches) || !up(st.tiles, &pl.tiles) || !up(st.jobs, &pl.jobs))
     return fail(c, MBT_ERR_NOMEM, "plan upload failed");
+  if (streaming) {
+    if (!up(first, &pl.stream_first)) return fail(c, MBT_ERR_NOMEM, "plan upload failed");
+    pl.stream_ctas = (int)first.size() - 1;
+  }
+  // streaming-push copies of the run constants and tile descriptors
+  std::vector<StreamRun> sr(st.runs.size());
+  for (size_t i = 0; i < st.runs.size(); ++i) {
+    const RunDev &r = st.runs[i];
+    StreamRun &x = sr[i];
+    x = StreamRun{};
+    x.invD = r.f_invD;
+    x.HinvD = r.f_HinvD;
+    x.fnb = r.f_nbins;
+    x.invE0 = r.f_invE0 * r.f_omD;
+    x.twoVoE0 = r.f_twoVoE0 * r.f_omD;
+    x.cphi = r.f_cphi;
+    x.sphi = r.f_sphi;
+    x.halfw = r.f_halfw;
+    x.qe = r.f_qe;
+    x.aT0 = r.f_aT0;
+    x.nbins = r.nbins;
+    x.nlong = r.nlong;
+    x.nharm = r.nharm;
+    x.flags = r.flags;
+    x.key0 = r.key0;
+    x.key1 = r.key1;
+    x.omD = r.one_minus_D;
+    for (int k = 0; k < kMaxLong; ++k) {
+      x.la[k] = r.f_la[k];
+      x.lw[k] = r.f_lw[k];
+    }
+    for (int k = 0; k < kMaxHarm; ++k) x.harm[k] = r.f_harm[k];
+  }
+  if (!up(sr, &pl.sruns)) return fail(c, MBT_ERR_NOMEM, "plan upload failed");
+  std::vector<StreamTile> stl(st.tiles.size());
+  for (size_t o = 0; o < st.tiles.size(); ++o) {
+    const size_t i = streaming ? (size_t)sorder[o] : o;
+    const TileDev &t = st.tiles[i];
+    const RunDev &r = st.runs[t.run];
+    const BunchDev &b = st.bunches[t.bunch];
+    StreamTile &x = stl[o];
+    x = StreamTile{};
+    x.start = t.start;
+    x.count = t.count;
+    x.index = (int)i;
+    x.m = t.m;
+    x.nlong = r.nlong;
+    x.nbins = r.nbins;
+    if (r.precision != kMixed) continue;
+    x.tau = static_cast<float *>(r.tau) + b.off + t.start;
+    x.del = r.delta + b.off + t.start;
+    x.hist = r.hist + (size_t)t.m * r.nbins;
+    x.hist_par = (long long)r.nb * r.nbins;
+    x.vrow = static_cast<const float *>(r.vsr) + (size_t)t.m * r.nbins;
+    x.turn = r.turn;
+    x.rc = pl.sruns + t.run;
+    if (r.nlong > 0) {
+      x.pq = r.pq + (size_t)t.m * 2;
+      x.pq_stride = r.nb * 2;
+      x.y = r.y + t.m / kBunchTile;
+      x.y_stride = r.ntile_b;
+    }
+  }
+  if (!up(stl, &pl.stiles)) return fail(c, MBT_ERR_NOMEM, "plan upload failed");
   void *p = nullptr;
   size_t pb = std::max<size_t>(st.tiles.size() * kPartials * sizeof(double), 16);
   if (cudaMalloc(&p, pb) != cudaSuccess) return fail(c, MBT_ERR_NOMEM, "plan partials");
@@ -1256,13 +1384,14 @@ mbt_status mbt_set_tile(mbt_ctx *c, int particles) {
   return rebuild_own_plan(c);
 }
 
-// Candidate push tiles for the autotuner: fixed sizes, plus "wave-aligned"
-// sizes for which the runs' tile count is a whole multiple of the push
-// kernel's resident CTA slots (no partly filled last wave).
+// Candidate push tiles for the autotuner (runs with a transverse plane, one
+// CTA per tile): fixed sizes, plus "wave-aligned" sizes for which the runs'
+// tile count is a whole multiple of that push kernel's resident CTA slots (no
+// partly filled last wave).
 static std::vector<int> tile_candidates(const std::vector<mbt_ctx *> &ctxs) {
   std::vector<int> cand = {2048, 4096, 8192, 16384, 32768};
   int slots = 0;
-  if (push_resident_slots(&slots) != cudaSuccess || slots <= 0) {
+  if (push_t_resident_slots(&slots) != cudaSuccess || slots <= 0) {
     cudaGetLastError();
     return cand;
   }
@@ -1316,6 +1445,10 @@ mbt_status mbt_autotune(mbt_ctx *c, int turns_per_trial, int *chosen_tile) {
   if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
   if (c->precision != MBT_PREC_MIXED) {
     if (chosen_tile) *chosen_tile = kF64Tile;
+    return MBT_OK;
+  }
+  if (!c->trans) {   // the streaming push splits the particles by SM: no tile to choose
+    if (chosen_tile) *chosen_tile = c->tile;
     return MBT_OK;
   }
   float best = 1e30f;
@@ -1832,6 +1965,12 @@ mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_til
   if (!b || turns_per_trial < 1) return MBT_ERR_ARG;
   if (b->precision != MBT_PREC_MIXED) {
     if (chosen_tile) *chosen_tile = kF64Tile;
+    return MBT_OK;
+  }
+  bool any_trans = false;
+  for (mbt_ctx *c : b->ctx) any_trans = any_trans || c->trans;
+  if (!any_trans) {   // the streaming push splits the particles by SM: no tile to choose
+    if (chosen_tile) *chosen_tile = b->tile;
     return MBT_OK;
   }
   float best = 1e30f;

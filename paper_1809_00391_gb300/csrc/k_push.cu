@@ -8,6 +8,10 @@
 //   deposit into a shared-memory histogram, moment partial sums (Sec. 2.4).
 // The histogram is flushed to global memory with one atomic per non-empty
 // cell; the moment partials go to a per-tile slot (deterministic sums).
+#include <algorithm>
+#include <climits>
+#include <mutex>
+
 #include "push_core.cuh"
 
 namespace mbt {
@@ -19,15 +23,12 @@ namespace mbt {
 // quad.  NLONG_MAX bounds the number of long-range resonators of any run in
 // the plan.
 // ---------------------------------------------------------------------------
-// The particle stream of a tile is staged through shared memory by the TMA
-// bulk-copy engine: chunks of kChunk particles (tau 4 KB + delta 8 KB) in a
+// The particle stream is staged through shared memory by the TMA bulk-copy
+// engine: chunks of kChunk particles (tau 4 KB + delta 8 KB) in a
 // kStages-deep ring, refilled by one thread as soon as the CTA has consumed a
-// stage, so the bytes in flight do not depend on registers or occupancy.
-// Thread t handles the quad of particles 4t .. 4t+3 of each chunk (one
-// Philox block, two Box-Muller pairs); results are stored straight to global
-// memory with 16-byte stores.
-// 2 stages x 12 KB with 6 CTAs (40 registers) per SM measured fastest on
-// GB300 among {4, 5, 6, 8} CTAs x {2, 3} stages for the 390-bunch fill
+// stage.  Thread t handles the quad of particles 4t .. 4t+3 of each chunk
+// (one Philox block, two Box-Muller pairs); results are stored straight to
+// global memory with 16-byte stores.
 #ifndef MBT_PUSH_STAGES
 #define MBT_PUSH_STAGES 2
 #endif
@@ -36,170 +37,344 @@ namespace mbt {
 #endif
 constexpr int kChunk = 1024;
 constexpr int kStages = MBT_PUSH_STAGES;
+static_assert(kStages >= 2, "the stage being refilled must differ from the next one read");
 constexpr int kStageBytes = kChunk * (int)(sizeof(float) + sizeof(double));
 constexpr unsigned long long kPushWaitNs = 2000000000ull;
 
-__device__ __forceinline__ void issue_chunk(const TileDev &t, const float *tau, const double *del, uint8_t *stage,
-                                            uint64_t *bar, int c) {
-  const int n = min(kChunk, t.count - c * kChunk);
-  const int n4 = (n + 3) & ~3;   // segments are padded to 4 particles: 16-byte multiples
-  const uint32_t tb = (uint32_t)n4 * 4u, db = (uint32_t)n4 * 8u;
-  mbar_arrive_expect_tx(bar, tb + db);
-  bulk_g2s(stage, tau + (size_t)c * kChunk, tb, bar);
-  bulk_g2s(stage + kChunk * sizeof(float), del + (size_t)c * kChunk, db, bar);
+// ---------------------------------------------------------------------------
+// Streaming push (runs without a transverse plane): one persistent CTA of
+// kStreamThreads threads per SM, so that no CTA is launched, set up and
+// retired per tile, and no CTA of the push competes with another for an SM's
+// issue slots (with several resident CTAs the warp schedulers starve some of
+// them for the whole launch).  The plan cuts each run's particle sequence
+// into one equal share per SM (tiles at bunch boundaries) and CTA g takes
+// share g of every run; the SMs run at the same rate, so the shares end
+// together.
+//
+// Warp specialised: the last warp feeds a ring of kStreamStages stages of
+// kStreamChunk particles with bulk copies (full barriers), and requests each
+// tile's descriptor, kick table, phasor inputs and turn counter a tile ahead
+// (slot barriers) with an L1 prefetch of the run constants; the other warps
+// consume.  A consumer warp hands its part of a stage back (empty barrier) as
+// soon as it has read it, so the warps are not held together chunk by chunk;
+// they meet (named barrier) only at tile boundaries, to hand in the tile's
+// histogram and partial sums and build the next tile's tables.  The run
+// constants are read with read-only loads that the compiler may repeat
+// instead of holding them in registers.  Every tile keeps its own
+// partial-sum slot, so the moments do not depend on the split.
+// ---------------------------------------------------------------------------
+constexpr int kStreamThreads = 1024;
+constexpr int kConsumerWarps = kStreamThreads / 32 - 1;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kStreamChunk = kConsumers * 4;   // particles per stage: one quad per consumer thread
+constexpr int kStreamStageBytes = kStreamChunk * (int)(sizeof(float) + sizeof(double));
+#ifndef MBT_STREAM_STAGES
+#define MBT_STREAM_STAGES 3
+#endif
+constexpr int kStreamStages = MBT_STREAM_STAGES;
+constexpr int kStreamMaxBins = 256;   // kMixed meshes have 128 or 256 cells
+constexpr int kSlots = 3;             // tile slots: the consumers' tile and two ahead
+constexpr int kProducerTid = kConsumers;
+
+struct alignas(16) StreamSlot {
+  StreamTile td;                 // descriptor (bulk copy, barrier tdb)
+  long long turn[2];             // turn counter  } barrier thb
+  double2 pq[kMaxLong][2];       // P_m, Q_m      }
+  double2 y[kMaxLong];           // y of the tile }
+  float vrow[kStreamMaxBins];    // short-range voltage of the bunch
+};
+constexpr size_t kStreamSmem = (size_t)kStreamStages * kStreamStageBytes + kSlots * sizeof(StreamSlot) +
+                               kStreamMaxBins * (sizeof(float2) + sizeof(int));
+
+struct StreamSmem {
+  uint64_t full[kStreamStages], empty[kStreamStages];   // stage loaded / handed back by every consumer warp
+  uint64_t tdb[kSlots], thb[kSlots], freed[kSlots];      // slot descriptor / data arrived, slot set up by the consumers
+  int issued_full[kStreamStages], issued_tdb[kSlots], issued_thb[kSlots];   // phases issued (producer, for draining)
+  float red[kConsumerWarps][5];
+  float2 phi[kMaxLong];
+};
+
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory");
+}
+
+// Producer: a tile's kick data (written by the previous post kernel, so only
+// after the grid dependency wait), and an L1 prefetch of its run constants.
+__device__ __forceinline__ void stream_issue_data(StreamSmem &S, StreamSlot &D, int sl) {
+  const StreamTile &td = D.td;
+  const int nl = min(td.nlong, kMaxLong), nbins = min(td.nbins, kStreamMaxBins);
+  mbar_arrive_expect_tx(&S.thb[sl], (uint32_t)(16 + nl * 48 + nbins * 4));
+  bulk_g2s(D.turn, td.turn, 16u, &S.thb[sl]);
+  for (int r = 0; r < nl; ++r) {
+    bulk_g2s(D.pq[r], td.pq + (size_t)r * td.pq_stride, 32u, &S.thb[sl]);
+    bulk_g2s(&D.y[r], td.y + (size_t)r * td.y_stride, 16u, &S.thb[sl]);
+  }
+  bulk_g2s(D.vrow, td.vrow, (uint32_t)nbins * 4u, &S.thb[sl]);
+  ++S.issued_thb[sl];
+  const char *rc = reinterpret_cast<const char *>(td.rc);
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(rc));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(rc + sizeof(StreamRun) - 1));
+}
+
+__device__ __forceinline__ void stream_issue_desc(const Plan &p, StreamSmem &S, StreamSlot *slots, int idx, int j) {
+  const int sl = j % kSlots;
+  mbar_arrive_expect_tx(&S.tdb[sl], (uint32_t)sizeof(StreamTile));
+  bulk_g2s(&slots[sl].td, p.stiles + idx, (uint32_t)sizeof(StreamTile), &S.tdb[sl]);
+  ++S.issued_tdb[sl];
+}
+
+// The producer thread's whole job: tiles 0 .. last of the CTA (p.stiles
+// first + j), chunk by chunk.  False if a wait gave up (it then stops
+// issuing; the consumers' own bounded waits end their loops).
+__device__ bool stream_producer(const Plan &p, StreamSmem &S, StreamSlot *slots, uint8_t *stages, int first, int last) {
+  // descriptors of the first tiles (free slots), chunks of tile 0 before the
+  // wait for the previous post kernel; then the kick data
+  for (int j = 0; j <= min(last, kSlots - 1); ++j) stream_issue_desc(p, S, slots, first + j, j);
+  int K = 0;   // chunks issued
+  bool data_ok = false;
+  for (int j = 0; j <= last; ++j) {
+    const int sl = j % kSlots;
+    if (!mbar_wait_bounded(&S.tdb[sl], (uint32_t)((j / kSlots) & 1), kPushWaitNs)) return false;
+    if (j == 0) {
+      // tile 0's first chunks do not depend on the previous post kernel
+      const StreamTile &td = slots[0].td;
+      const int nc0 = (td.count + kStreamChunk - 1) / kStreamChunk;
+      for (; K < min(kStreamStages, nc0); ++K) {
+        const int n = min(kStreamChunk, td.count - K * kStreamChunk), n4 = (n + 3) & ~3;
+        mbar_arrive_expect_tx(&S.full[K], (uint32_t)n4 * 12u);
+        bulk_g2s(stages + K * kStreamStageBytes, td.tau + (size_t)K * kStreamChunk, (uint32_t)n4 * 4u, &S.full[K]);
+        bulk_g2s(stages + K * kStreamStageBytes + kStreamChunk * sizeof(float), td.del + (size_t)K * kStreamChunk,
+                 (uint32_t)n4 * 8u, &S.full[K]);
+        ++S.issued_full[K];
+      }
+      grid_dependency_wait();
+      data_ok = true;
+      for (int q = 0; q <= min(last, kSlots - 1); ++q) {
+        if (q > 0 && !mbar_wait_bounded(&S.tdb[q], 0u, kPushWaitNs)) return false;
+        stream_issue_data(S, slots[q], q);
+      }
+    } else if (j >= kSlots) {
+      // tile j reuses the slot of tile j - kSlots: its data only now
+      stream_issue_data(S, slots[sl], sl);
+    }
+    // the descriptor of tile j + kSlots - 1 into the slot of tile j - 1, once the consumers have set that one up
+    const int jn = j + kSlots - 1;
+    if (j >= 1 && jn <= last) {
+      const int sp = jn % kSlots;   // == (j - 1) % kSlots
+      if (!mbar_wait_bounded(&S.freed[sp], (uint32_t)(((j - 1) / kSlots) & 1), kPushWaitNs)) return false;
+      fence_proxy_async_smem();
+      stream_issue_desc(p, S, slots, first + jn, jn);
+    }
+    // the tile's chunks
+    const StreamTile &td = slots[sl].td;
+    const int nc = (td.count + kStreamChunk - 1) / kStreamChunk;
+    const int ci0 = j == 0 ? K : 0;
+    for (int ci = ci0; ci < nc; ++ci, ++K) {
+      const int stg = K % kStreamStages;
+      if (K >= kStreamStages) {
+        if (!mbar_wait_bounded(&S.empty[stg], (uint32_t)((K / kStreamStages - 1) & 1), kPushWaitNs)) return false;
+        fence_proxy_async_smem();   // the consumers' reads of the stage before its refill
+      }
+      const int n = min(kStreamChunk, td.count - ci * kStreamChunk), n4 = (n + 3) & ~3;
+      uint8_t *stage = stages + stg * kStreamStageBytes;
+      mbar_arrive_expect_tx(&S.full[stg], (uint32_t)n4 * 12u);
+      bulk_g2s(stage, td.tau + (size_t)ci * kStreamChunk, (uint32_t)n4 * 4u, &S.full[stg]);
+      bulk_g2s(stage + kStreamChunk * sizeof(float), td.del + (size_t)ci * kStreamChunk, (uint32_t)n4 * 8u, &S.full[stg]);
+      ++S.issued_full[stg];
+    }
+  }
+  (void)data_ok;
+  return true;
 }
 
 template <int NLONG_MAX, bool HARM>
-__global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixed(const Plan p) {
+__global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p) {
   extern __shared__ __align__(128) uint8_t sm_push[];
-  __shared__ float s_red[kPushThreads / 32][5];
-  __shared__ float2 s_phi[kMaxLong];
-  __shared__ float4 s_hc[kMaxHarm];
-  __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ int s_abort;
-
-  // Prologue that reads only the plan and the particle state: with
-  // programmatic dependent launch it overlaps the previous post kernel, which
-  // signals its dependents only after the previous push has completed.
-  const TileDev t = p.tiles[blockIdx.x];
-  const RunDev *__restrict__ R = p.runs + t.run;
-  const BunchDev bd = p.bunches[t.bunch];
-  PushConstF c;
-  c.nbins = R->nbins;
-  const int nbins = c.nbins;
-  const int nlong = R->nlong;
+  __shared__ StreamSmem S;
   uint8_t *stages = sm_push;
-  float2 *sVd = reinterpret_cast<float2 *>(sm_push + kStages * kStageBytes);   // (V[j], V[j+1] - V[j])
-  int *sH = reinterpret_cast<int *>(sVd + nbins);
-  float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
-  double *del = R->delta + bd.off + t.start;
-  const int nchunks = (t.count + kChunk - 1) / kChunk;
+  StreamSlot *slots = reinterpret_cast<StreamSlot *>(sm_push + kStreamStages * kStreamStageBytes);
+  float2 *sVd = reinterpret_cast<float2 *>(slots + kSlots);   // (V[j], V[j+1] - V[j]) of the current tile's bunch
+  int *sH = reinterpret_cast<int *>(sVd + kStreamMaxBins);
+  const int tid = threadIdx.x;
+  const int first = p.stream_first[blockIdx.x];
+  const int last = p.stream_first[blockIdx.x + 1] - first - 1;   // the CTA's tiles are first .. first + last
 
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(&full[st], 1);
+  if (tid == kProducerTid) {
+    for (int s = 0; s < kStreamStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], kConsumerWarps);
+      S.issued_full[s] = 0;
+    }
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&S.tdb[s], 1);
+      mbar_init(&S.thb[s], 1);
+      mbar_init(&S.freed[s], 1);
+      S.issued_tdb[s] = S.issued_thb[s] = 0;
+    }
     fence_mbar_init();
-    s_abort = 0;
-    for (int ch = 0; ch < min(kStages, nchunks); ++ch) issue_chunk(t, tau, del, stages + ch * kStageBytes, &full[ch], ch);
   }
-  const int nharm = R->nharm;
-  if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
+  for (int b = tid; b < kStreamMaxBins; b += kStreamThreads) sH[b] = 0;
+  __syncthreads();   // barriers initialised, histogram zeroed
   grid_dependents_launch();
-  grid_dependency_wait();   // the previous post kernel's wake, phasors and turn counter are complete
-  const long long turn = *R->turn;
-  const int par = (int)(turn & 1);
-  const float *vsr = static_cast<const float *>(R->vsr) + (size_t)t.m * nbins;
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
-    const float v0 = vsr[k];
-    const float v1 = k + 1 < nbins ? vsr[k + 1] : v0;
-    sVd[k] = make_float2(v0, v1 - v0);
-    sH[k] = 0;
-  }
-  if (threadIdx.x < nlong) {
-    // Phi_m = P_m y_tile + Q_m of this bunch, narrowed to FP32
-    const int r = threadIdx.x;
-    const double2 P = R->pq[((size_t)r * R->nb + t.m) * 2];
-    const double2 Q = R->pq[((size_t)r * R->nb + t.m) * 2 + 1];
-    const double2 y = R->y[(size_t)r * R->ntile_b + t.m / kBunchTile];
-    const double2 phi = cfma(P, y, Q);
-    s_phi[r] = make_float2((float)phi.x, (float)phi.y);
-  }
-  c.invD = R->f_invD;
-  c.HinvD = R->f_HinvD;
-  c.fnb = R->f_nbins;
-  c.invE0 = R->f_invE0 * R->f_omD;
-  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
-  c.cphi = R->f_cphi;
-  c.sphi = R->f_sphi;
-  c.halfw = R->f_halfw;
-  c.omD = R->f_omD;
-  c.qe = R->f_qe;
-  c.aT0 = R->f_aT0;
-  const double omD_d = R->one_minus_D;
-  const bool ngp = (R->flags & kKickNGP) != 0;
-  float la[NLONG_MAX > 0 ? NLONG_MAX : 1], lw[NLONG_MAX > 0 ? NLONG_MAX : 1];
-  float2 phi[NLONG_MAX > 0 ? NLONG_MAX : 1];
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < NLONG_MAX; ++r) {
-    la[r] = R->f_la[r];
-    lw[r] = R->f_lw[r];
-    phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
-  }
-  const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
 
+  if (tid >= kConsumers) {
+    // ---------------- producer warp ----------------
+    if (tid == kProducerTid && last >= 0) {
+      if (!stream_producer(p, S, slots, stages, first, last)) {
+        atomicExch(p.error, kErrTimeout);
+      }
+      // let every copy still in flight land before the CTA exits
+      for (int s = 0; s < kStreamStages; ++s)
+        if (S.issued_full[s]) mbar_wait_bounded(&S.full[s], (uint32_t)((S.issued_full[s] - 1) & 1), kPushWaitNs);
+      for (int s = 0; s < kSlots; ++s) {
+        if (S.issued_tdb[s]) mbar_wait_bounded(&S.tdb[s], (uint32_t)((S.issued_tdb[s] - 1) & 1), kPushWaitNs);
+        if (S.issued_thb[s]) mbar_wait_bounded(&S.thb[s], (uint32_t)((S.issued_thb[s] - 1) & 1), kPushWaitNs);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumer warps ----------------
+  grid_dependency_wait();   // the previous post kernel zeroed this turn's histograms
+  const int warp = tid >> 5, lane = tid & 31;
+  bool failed = false;   // a wait of this thread gave up: it skips every further wait and all processing
   float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;
   int nout = 0;
+  int k = 0;   // chunks consumed (chunk k is in stage k % kStreamStages)
 
 #pragma unroll 1
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int slot = ch % kStages;
-    uint8_t *sg = stages + slot * kStageBytes;
-    if (!mbar_wait_bounded(&full[slot], (uint32_t)((ch / kStages) & 1), kPushWaitNs)) {
+  for (int J = 0; J <= last; ++J) {
+    // ---- set up tile J ----
+    const int sl = J % kSlots;
+    const StreamSlot &D = slots[sl];
+    if (!failed && !mbar_wait_bounded(&S.thb[sl], (uint32_t)((J / kSlots) & 1), kPushWaitNs)) {
+      failed = true;
       atomicExch(p.error, kErrTimeout);
-      s_abort = 1;
     }
-    const int q = ch * kChunk + 4 * (int)threadIdx.x;   // first particle of this thread's quad in the tile
-    if (!s_abort && q < t.count) {
-      const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
-      const double2 da = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x];
-      const double2 db = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x + 1];
-      float rr[4] = {0.f, 0.f, 0.f, 0.f};
-      if (c.qe != 0.f) normal_quad_f32(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
-      float tt[4] = {tv.x, tv.y, tv.z, tv.w};
-      double dd[4] = {da.x, da.y, db.x, db.y};
-      const int nvalid = min(4, t.count - q);
-      if (ngp)
-        quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
-                                   sd, sd2, nout);
-      else
-        quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
-                                    sd, sd2, nout);
-      *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
-      *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
-      *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+    const int nbins = max(2, min(D.td.nbins, kStreamMaxBins));
+    for (int b = tid; b < nbins; b += kConsumers) {
+      const float v0 = D.vrow[b];
+      const float v1 = b + 1 < nbins ? D.vrow[b + 1] : v0;
+      sVd[b] = make_float2(v0, v1 - v0);
     }
-    __syncthreads();   // stage `slot` consumed by every thread
-    if (threadIdx.x == 0 && !s_abort && ch + kStages < nchunks) {
-      fence_proxy_async_smem();   // order the generic-proxy reads of the stage before its refill
-      issue_chunk(t, tau, del, sg, &full[slot], ch + kStages);
+    const int nl = max(0, min(D.td.nlong, NLONG_MAX));
+    if (tid >= 64 && tid < 64 + nl) {
+      // Phi_m = P_m y_tile + Q_m of this bunch, narrowed to FP32
+      const int r = tid - 64;
+      const double2 ph = cfma(D.pq[r][0], D.y[r], D.pq[r][1]);
+      S.phi[r] = make_float2((float)ph.x, (float)ph.y);
     }
-  }
-  if (s_abort && threadIdx.x == 0) {
-    // let the copies still in flight land before the CTA exits
-    for (int ch = 0; ch < nchunks; ++ch) mbar_wait_bounded(&full[ch % kStages], (uint32_t)((ch / kStages) & 1), kPushWaitNs);
-  }
-
-  // moment partials: FP32 within a warp, FP64 across the CTA's warps
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  st = warp_sum_f(st);
-  st2 = warp_sum_f(st2);
-  sd = warp_sum_f(sd);
-  sd2 = warp_sum_f(sd2);
-  const int no = __reduce_add_sync(0xFFFFFFFFu, nout);
-  if (lane == 0) {
-    s_red[warp][0] = st;
-    s_red[warp][1] = st2;
-    s_red[warp][2] = sd;
-    s_red[warp][3] = sd2;
-    s_red[warp][4] = (float)no;
-  }
-  __syncthreads();
-  if (threadIdx.x < 5) {
-    double acc = 0.0;
+    const StreamRun *__restrict__ RC = D.td.rc;
+    const long long turn = D.turn[0];
+    int32_t *const hg = D.td.hist + (turn & 1) * D.td.hist_par;
+    const int pslot = D.td.index;
+    float *const tau = D.td.tau;
+    double *const del = D.td.del;
+    const long long start = D.td.start;
+    const int count = D.td.count;
+    const uint32_t turn32 = (uint32_t)turn, bunch32 = (uint32_t)D.td.m;
+    consumers_sync();   // tables built, slot read
+    if (tid == 0) mbar_arrive(&S.freed[sl]);
+    PushConstF c;
+    c.nbins = nbins;
+    c.invD = __ldg(&RC->invD);
+    c.HinvD = __ldg(&RC->HinvD);
+    c.fnb = __ldg(&RC->fnb);
+    c.invE0 = __ldg(&RC->invE0);
+    c.twoVoE0 = __ldg(&RC->twoVoE0);
+    c.cphi = __ldg(&RC->cphi);
+    c.sphi = __ldg(&RC->sphi);
+    c.halfw = __ldg(&RC->halfw);
+    c.omD = 0.f;
+    c.qe = __ldg(&RC->qe);
+    c.aT0 = __ldg(&RC->aT0);
+    const double omD_d = __ldg(&RC->omD);
+    const bool ngp = (__ldg(&RC->flags) & kKickNGP) != 0;
+    const int nharm = HARM ? max(0, min(__ldg(&RC->nharm), kMaxHarm)) : 0;
+    float la[NLONG_MAX > 0 ? NLONG_MAX : 1], lw[NLONG_MAX > 0 ? NLONG_MAX : 1];
+    float2 phi[NLONG_MAX > 0 ? NLONG_MAX : 1];
 #pragma unroll
-    for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
-    p.partial[(size_t)blockIdx.x * kPartials + threadIdx.x] = acc;
-  }
-  int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
-    const int cnt = sH[k];
-    if (cnt) atomicAdd(hg + k, cnt);
+    for (int r = 0; r < NLONG_MAX; ++r) {
+      la[r] = __ldg(&RC->la[r]);
+      lw[r] = __ldg(&RC->lw[r]);
+      phi[r] = r < nl ? S.phi[r] : make_float2(0.f, 0.f);
+    }
+    const uint32_t k0 = __ldg(&RC->key0), k1 = __ldg(&RC->key1);
+    const int nc = (count + kStreamChunk - 1) / kStreamChunk;
+
+    // ---- the tile's chunks ----
+#pragma unroll 1
+    for (int ci = 0; ci < nc; ++ci, ++k) {
+      const int stg = k % kStreamStages;
+      if (!failed && !mbar_wait_bounded(&S.full[stg], (uint32_t)((k / kStreamStages) & 1), kPushWaitNs)) {
+        failed = true;
+        atomicExch(p.error, kErrTimeout);
+      }
+      const uint8_t *sg = stages + stg * kStreamStageBytes;
+      const float4 tv = reinterpret_cast<const float4 *>(sg)[tid];
+      const double2 da = reinterpret_cast<const double2 *>(sg + kStreamChunk * sizeof(float))[2 * tid];
+      const double2 db = reinterpret_cast<const double2 *>(sg + kStreamChunk * sizeof(float))[2 * tid + 1];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[stg]);   // this warp's part of the stage is read
+      const int q = ci * kStreamChunk + 4 * tid;   // first particle of this thread's quad in the tile
+      if (!failed && q < count) {
+        float rr[4] = {0.f, 0.f, 0.f, 0.f};
+        if (c.qe != 0.f) normal_quad_f32(philox4x32_10((uint32_t)((start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
+        float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+        double dd[4] = {da.x, da.y, db.x, db.y};
+        const int nvalid = min(4, count - q);
+        const float4 *hc = RC->harm;
+        if (ngp)
+          quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nl, la, lw, phi, omD_d, hc, nharm, tt, dd, rr, nvalid, st, st2,
+                                           sd, sd2, nout);
+        else
+          quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nl, la, lw, phi, omD_d, hc, nharm, tt, dd, rr, nvalid, st,
+                                            st2, sd, sd2, nout);
+        *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+        *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
+        *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+      }
+    }
+
+    // ---- hand in tile J ----
+    st = warp_sum_f(st);
+    st2 = warp_sum_f(st2);
+    sd = warp_sum_f(sd);
+    sd2 = warp_sum_f(sd2);
+    const int no = __reduce_add_sync(0xFFFFFFFFu, nout);
+    if (lane == 0) {
+      float *r = S.red[warp];
+      r[0] = st;
+      r[1] = st2;
+      r[2] = sd;
+      r[3] = sd2;
+      r[4] = (float)no;
+    }
+    st = st2 = sd = sd2 = 0.f;
+    nout = 0;
+    consumers_sync();   // every deposit of the tile made, S.red complete
+    for (int b = tid; b < nbins; b += kConsumers) {
+      const int cnt = sH[b];
+      if (cnt) {
+        if (!failed) atomicAdd(hg + b, cnt);
+        sH[b] = 0;
+      }
+    }
+    if (tid >= 32 && tid < 37 && !failed) {
+      // the tile's sums over the warps, in a fixed order
+      const int col = tid - 32;
+      float acc = S.red[0][col];
+      for (int w = 1; w < kConsumerWarps; ++w) acc += S.red[w][col];
+      p.partial[(size_t)pslot * kPartials + col] = (double)acc;
+    }
+    // the next tile's set-up rewrites sVd and S.phi only after its own wait
+    // and before its barrier; S.red and sH are rewritten only after it
   }
 }
 
 // ---------------------------------------------------------------------------
 // Mixed precision with a transverse plane (plans where some run has one).
-// The same bulk-copy ring as k_push_mixed, a stage holding tau, delta, x and
+// A bulk-copy ring like the streaming push's, a stage holding tau, delta, x and
 // x' of kChunk particles (20 KB); one quad of consecutive particles per
 // thread and chunk.  Runs of the plan without a transverse plane stage and
 // push only tau and delta.  Harmonic cavities are a runtime loop here.
@@ -727,15 +902,16 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
     }
   }
   if (precision == kMixed) {
-    const size_t smem = (size_t)kStages * kStageBytes + (size_t)max_nbins * (sizeof(float2) + sizeof(int));
+    if (p.stream_ctas <= 0 || !p.stream_first) return cudaErrorInvalidValue;   // the plan was not split for it
     const bool harm = p.max_nharm > 0;
+    const int grid = p.stream_ctas;
     switch (p.max_nlong) {
-      case 0: return launch_ex(harm ? k_push_mixed<0, true> : k_push_mixed<0, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 1: return launch_ex(harm ? k_push_mixed<1, true> : k_push_mixed<1, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 2: return launch_ex(harm ? k_push_mixed<2, true> : k_push_mixed<2, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 0: return launch_ex(harm ? k_push_stream<0, true> : k_push_stream<0, false>, grid, kStreamThreads, kStreamSmem, s, pdl, p);
+      case 1: return launch_ex(harm ? k_push_stream<1, true> : k_push_stream<1, false>, grid, kStreamThreads, kStreamSmem, s, pdl, p);
+      case 2: return launch_ex(harm ? k_push_stream<2, true> : k_push_stream<2, false>, grid, kStreamThreads, kStreamSmem, s, pdl, p);
       default:
-        return launch_ex(harm ? k_push_mixed<kMaxLong, true> : k_push_mixed<kMaxLong, false>, p.ntiles, kPushThreads,
-                         smem, s, pdl, p);
+        return launch_ex(harm ? k_push_stream<kMaxLong, true> : k_push_stream<kMaxLong, false>, grid, kStreamThreads,
+                         kStreamSmem, s, pdl, p);
     }
   }
   // sV, sH (rounded up to doubles), and with a transverse plane sVt, sDip
@@ -744,22 +920,47 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   return launch_ex(k_push_f64, p.ntiles, kPushThreads, smem, s, pdl, p);
 }
 
+// Streaming-push CTAs resident at once on the current device, one per SM
+// (cached per device: every variant has the same launch bounds and shared
+// memory).
 cudaError_t push_resident_slots(int *slots) {
-  const size_t smem = (size_t)kStages * kStageBytes + 256 * (sizeof(float2) + sizeof(int));
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (cache[dev] == 0) {
+    int nsm = 0, per = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_push_stream<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_stream<1, false>, kStreamThreads, kStreamSmem);
+    if (e != cudaSuccess) return e;
+    cache[dev] = std::max(1, per) * nsm;
+  }
+  *slots = cache[dev];
+  return cudaSuccess;
+}
+
+cudaError_t push_t_resident_slots(int *slots) {
+  const size_t smem = (size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float));
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1, false>, kPushThreads, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed_t<1>, kPushThreads, smem);
   *slots = per * nsm;
   return e;
 }
 
 cudaError_t configure_push_kernels() {
-  const int bytes = (int)((size_t)kStages * kStageBytes + 1024 * (sizeof(float2) + sizeof(int)));
   cudaError_t e = cudaSuccess;
-  for (auto k : {k_push_mixed<0, false>, k_push_mixed<1, false>, k_push_mixed<2, false>, k_push_mixed<kMaxLong, false>,
-                 k_push_mixed<0, true>, k_push_mixed<1, true>, k_push_mixed<2, true>, k_push_mixed<kMaxLong, true>})
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for (auto k : {k_push_stream<0, false>, k_push_stream<1, false>, k_push_stream<2, false>, k_push_stream<kMaxLong, false>,
+                 k_push_stream<0, true>, k_push_stream<1, true>, k_push_stream<2, true>, k_push_stream<kMaxLong, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
+  int slots = 0;
+  if (e == cudaSuccess) e = push_resident_slots(&slots);
   const int bytes_t = (int)((size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float)));
   for (auto k : {k_push_mixed_t<0>, k_push_mixed_t<1>, k_push_mixed_t<2>, k_push_mixed_t<kMaxLong>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_t);

@@ -107,6 +107,36 @@ struct TileDev {
   long long start;            // first particle of the tile within its bunch (multiple of 4)
 };
 
+// Streaming push (kMixed, no transverse plane): run constants and tile
+// descriptors laid out for bulk copies into shared memory, so that a
+// persistent CTA moves from tile to tile without a dependent global load.
+struct alignas(16) StreamRun {
+  float invD, HinvD, fnb, invE0, twoVoE0, cphi, sphi, halfw, qe, aT0;   // invE0, twoVoE0 carry (1 - D)
+  int nbins, nlong, nharm, flags;
+  uint32_t key0, key1;
+  double omD;                   // 1 - D
+  float la[kMaxLong], lw[kMaxLong];
+  float4 harm[kMaxHarm];        // as RunDev::f_harm
+};
+static_assert(sizeof(StreamRun) % 16 == 0, "bulk-copy size");
+
+struct alignas(16) StreamTile {
+  float *tau;                   // first particle of the tile
+  double *del;
+  int32_t *hist;                // bunch's row in histogram buffer 0 (buffer 1 at + hist_par)
+  const float *vrow;            // bunch's row of the short-range voltage
+  const long long *turn;        // run's turn counter (a 16-byte block)
+  const StreamRun *rc;
+  const double2 *pq;            // P_m of resonator 0 (Q_m follows); resonator r at + r * pq_stride
+  const double2 *y;             // value entering the bunch's post tile, resonator 0; r at + r * y_stride
+  long long start;              // first particle of the tile within its bunch
+  long long hist_par;
+  int count, index, m, nlong;   // index: the tile's partial-sum slot
+  int pq_stride, y_stride, nbins, pad0;
+  int pad1[4];
+};
+static_assert(sizeof(StreamTile) == 128, "bulk-copy size");
+
 struct PostJob {
   int run, type, bt, sub;     // kJobWake: sub = M-tile (kMixed) or (bunch, row chunk) (kF64)
 };
@@ -126,6 +156,10 @@ struct Plan {
   int max_nharm;              // most harmonic cavities of any run of the plan
   int max_trans;              // 1 if any run of the plan has a transverse plane
   unsigned long long *trace;  // null, or [njobs][3] post-kernel CTA timestamps (start, job done, exit) [ns]
+  StreamTile *stiles;         // [ntiles] the tiles for the streaming push
+  StreamRun *sruns;           // [nruns]
+  int *stream_first;          // [stream_ctas + 1]: CTA b of the streaming push takes tiles stream_first[b] .. [b + 1] - 1
+  int stream_ctas;            // 0 if the plan is not split for the streaming push
 };
 
 // Cluster-resident tracking of one run: one thread-block cluster per bunch,
@@ -164,6 +198,7 @@ cudaError_t configure_kernels();
 cudaError_t wake_noalloc_launch(const RunDev &proto, const void *img, size_t img_bytes, const float *q_f, int nb,
                                 int nbins, const int32_t *hist, float *V, cudaStream_t s, int *device_error_out);
 cudaError_t configure_push_kernels();
-cudaError_t push_resident_slots(int *slots);   // push CTAs resident at once on this device (256 cells)
+cudaError_t push_resident_slots(int *slots);     // streaming-push CTAs resident at once on this device
+cudaError_t push_t_resident_slots(int *slots);   // the same for the push with a transverse plane (256 cells)
 
 }  // namespace mbt
