@@ -69,7 +69,7 @@ BYTES_PER_MP_TURN = 24          # tau f32 + delta f64, read + written once per t
 FALLBACK_HBM_GBS = 6800.0
 PUSH_SOURCES = ["paper_1809_00391_gb300/csrc/k_push.cu", "paper_1809_00391_gb300/csrc/push_core.cuh",
                 "paper_1809_00391_gb300/csrc/device_common.cuh", "paper_1809_00391_gb300/csrc/mbt_internal.h"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_mixed_fill390_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_stream_fill390_traffic.json")
 GRAPH_TURNS = 100      # turns per captured CUDA graph
 AUTOTUNE_TURNS = 20    # timed turns per push-tile candidate
 ROOFLINE_TURNS = 4000  # turns of the event-timed roofline region
@@ -661,7 +661,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "k_push_mixed", "bytes_per_unit": BYTES_PER_MP_TURN, "unit_count": n_part,
+                "kernel": "k_push_stream", "bytes_per_unit": BYTES_PER_MP_TURN, "unit_count": n_part,
                 "timed_launches": launches, "push_us": push_avg_s * 1e6,
                 "post_us": post_ms / max(1, launches) * 1e3,
                 "region": f"{KR} turns after the headline region, CUDA events around each push launch"}
@@ -703,7 +703,7 @@ def main():
                            "turns_timed": K, "precision": "tau f32, delta f64-accumulated, wake bf16x2 on tcgen05 "
                            "(fp32 accumulate), phasor scan + moments f64",
                            "l2": "state 468 MB > 129 MB L2 (no flush needed)",
-                           "push_tile": tile,
+                           "push": "persistent, one 1024-thread CTA per SM, equal per-SM shares of each run",
                            "parallelism": f"{world} independent fill(s), one per GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K,
                 "launch_mode": f"CUDA graph of {G} turns, programmatic dependent launch between kernels",

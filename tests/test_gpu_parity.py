@@ -174,6 +174,30 @@ def test_mixed_three_bunches_moments(pkg, oracle_mod):
     tr.close()
 
 
+def test_mixed_tiny_ragged_bunches(pkg, oracle_mod):
+    """Streaming push with fewer particles than one quad per SM share and bunch
+    sizes that are not multiples of 4 (one bunch of a single particle): most
+    CTAs get no tile, shares cut bunches at multiples of 4, and every particle
+    is pushed and deposited exactly once per turn."""
+    run = W.Run(W.ring_r0(), [dict(W.BROADBAND), dict(W.HOM)], np.array([0, 3, 7], np.int32), np.full(3, 1e-3),
+                np.array([37, 1, 510], np.int64), seed=41, turns=50, precision=W.PREC_MIXED)
+    tr, orc = _pair(pkg, oracle_mod, run, precision=W.PREC_MIXED)
+    tr.init_particles()
+    orc.init_particles()
+    tr.track(run.turns)
+    orc.track(run.turns)
+    h, out = tr.histograms()
+    assert np.array_equal(h.sum(axis=1) + out, run.n_mp)
+    sig = tr.info["sigma_tau0_s"]
+    dsig = np.std(np.concatenate([orc.particles(m)[1] for m in range(run.nb)]))   # energy spread of the fill
+    for m in range(run.nb):
+        tg, dg = tr.particles(m)
+        to, do = orc.particles(m)
+        assert np.median(np.abs(tg - to)) <= 1e-4 * sig and np.max(np.abs(tg - to)) <= 1e-2 * sig, f"bunch {m}"
+        assert np.median(np.abs(dg - do)) <= 1e-4 * dsig and np.max(np.abs(dg - do)) <= 1e-2 * dsig, f"bunch {m}"
+    tr.close()
+
+
 @pytest.mark.parametrize("nbins", [128, 256])
 def test_tensor_core_wake_matches_direct_convolution(pkg, oracle_mod, nbins):
     """The tcgen05 Toeplitz contraction against the exact FP64 double sum of the
