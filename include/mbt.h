@@ -304,24 +304,26 @@ mbt_status mbt_get_info(mbt_ctx *ctx, mbt_info *info);
  * (0 disables; default 0).  The first mbt_track after a change captures. */
 mbt_status mbt_set_graph(mbt_ctx *ctx, int turns_per_graph);
 
-/* Push tile of runs with a transverse plane: at most this many
- * macro-particles per CTA of their mixed-precision push kernel, a multiple of
- * 4 in [1024, 65536] (default 8192); each bunch is split into ceil(n / tile)
- * tiles of equal size.  Changing it rebuilds the work lists (and drops a
- * captured graph); results do not depend on it except for the summation order
- * of the moment sums.  Mixed-precision plans without a transverse plane use
- * the streaming push, which cuts each run into one equal share per SM whatever
- * the tile (stored, no effect). */
+/* Push tile: at most this many macro-particles per CTA of the per-tile
+ * mixed-precision push, a multiple of 4 in [1024, 65536] (default 8192); each
+ * bunch is split into ceil(n / tile) tiles of equal size.  Changing it
+ * rebuilds the work lists (and drops a captured graph); results do not depend
+ * on it except for the summation order of the moment sums.  A plan whose runs
+ * are all large (no transverse plane; every run at least 4 stages of 3968
+ * particles per SM, bunches of at least 2 stages on average) uses the
+ * streaming push instead, which cuts each run into one equal share per SM
+ * whatever the tile (stored, no effect); a run's moments are then the same
+ * alone and in any such batch. */
 mbt_status mbt_set_tile(mbt_ctx *ctx, int particles);
 
-/* Autotuner (runs with a transverse plane): times turns_per_trial turns for
+/* Autotuner (plans on the per-tile push): times turns_per_trial turns for
  * each candidate push tile (2048 .. 32768 particles, plus tiles that make the
  * tile count a whole multiple of the push CTAs the GPU holds at once) and
  * keeps the fastest (written to *chosen_tile, may be NULL).  The trial turns
  * are real tracking turns: the run advances by (turns_per_trial + 2) turns
  * per candidate (at most 17).  Synchronous.  No-op (the current tile is
- * reported, no turn is tracked) for MBT_PREC_F64 and for runs on the
- * streaming push (mixed precision, no transverse plane). */
+ * reported, no turn is tracked) for MBT_PREC_F64 and for plans on the
+ * streaming push (see mbt_set_tile). */
 mbt_status mbt_autotune(mbt_ctx *ctx, int turns_per_trial, int *chosen_tile);
 
 /* Kernel timing: when enabled, mbt_track records CUDA events around every

@@ -332,23 +332,34 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
     *dst = static_cast<T *>(p);
     return true;
   };
-  // Streaming push (mixed precision, no transverse plane): each run's
+  // Streaming push (mixed precision, no transverse plane, runs large enough:
+  // plan_streams): each run's
   // particle sequence (its bunches in order, each padded to 4 particles) is
   // cut into one equal share per SM at multiples of 4, each share into tiles
   // at bunch boundaries, and CTA g takes share g of every run.  A run's tiles
   // (and so the order of its moment sums) are the same alone and in a batch.
   // p.tiles stays in bunch order (the post kernel sums each bunch's partials
   // over its consecutive tiles); p.stiles lists each CTA's tiles together.
-  bool streaming = !st.runs.empty();
-  for (const RunDev &r : st.runs) streaming = streaming && r.precision == kMixed && !r.trans;
+  bool mixed = !st.runs.empty(), any_trans = false;
+  std::vector<int64_t> run_n(st.runs.size(), 0);
+  std::vector<int> run_nb(st.runs.size(), 0);
+  for (const RunDev &r : st.runs) {
+    mixed = mixed && r.precision == kMixed;
+    any_trans = any_trans || r.trans;
+  }
+  for (const BunchDev &b : st.bunches) {
+    run_n[(size_t)b.run] += b.n;
+    ++run_nb[(size_t)b.run];
+  }
+  int slots = 0;
+  if (mixed && (push_resident_slots(&slots) != cudaSuccess || slots <= 0)) {
+    cudaGetLastError();
+    return fail(c, MBT_ERR_CUDA, "streaming push occupancy");
+  }
+  const bool streaming = mixed && plan_streams(run_n, run_nb, any_trans, slots);
   std::vector<int> first, owner;
   std::vector<int> sorder;   // tile indices in CTA order
   if (streaming) {
-    int slots = 0;
-    if (push_resident_slots(&slots) != cudaSuccess || slots <= 0) {
-      cudaGetLastError();
-      return fail(c, MBT_ERR_CUDA, "streaming push occupancy");
-    }
     const int G = slots;
     constexpr int64_t kMaxCount = int64_t(1) << 28;
     std::vector<TileDev> tiles;
@@ -1384,14 +1395,16 @@ mbt_status mbt_set_tile(mbt_ctx *c, int particles) {
   return rebuild_own_plan(c);
 }
 
-// Candidate push tiles for the autotuner (runs with a transverse plane, one
-// CTA per tile): fixed sizes, plus "wave-aligned" sizes for which the runs'
-// tile count is a whole multiple of that push kernel's resident CTA slots (no
+// Candidate push tiles for the autotuner (plans on a per-tile push, one CTA
+// per tile): fixed sizes, plus "wave-aligned" sizes for which the runs' tile
+// count is a whole multiple of that push kernel's resident CTA slots (no
 // partly filled last wave).
 static std::vector<int> tile_candidates(const std::vector<mbt_ctx *> &ctxs) {
   std::vector<int> cand = {2048, 4096, 8192, 16384, 32768};
   int slots = 0;
-  if (push_t_resident_slots(&slots) != cudaSuccess || slots <= 0) {
+  bool trans = false;
+  for (mbt_ctx *c : ctxs) trans = trans || c->trans;
+  if (push_tile_resident_slots(trans, &slots) != cudaSuccess || slots <= 0) {
     cudaGetLastError();
     return cand;
   }
@@ -1447,10 +1460,13 @@ mbt_status mbt_autotune(mbt_ctx *c, int turns_per_trial, int *chosen_tile) {
     if (chosen_tile) *chosen_tile = kF64Tile;
     return MBT_OK;
   }
-  if (!c->trans) {   // the streaming push splits the particles by SM: no tile to choose
+  int slots = 0;
+  if (push_resident_slots(&slots) == cudaSuccess &&
+      plan_streams({c->n_particles}, {c->nb}, c->trans != 0, slots)) {   // split by SM: no tile to choose
     if (chosen_tile) *chosen_tile = c->tile;
     return MBT_OK;
   }
+  cudaGetLastError();
   float best = 1e30f;
   int best_tile = c->tile;
   for (int tile : tile_candidates({c})) {
@@ -1968,11 +1984,19 @@ mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_til
     return MBT_OK;
   }
   bool any_trans = false;
-  for (mbt_ctx *c : b->ctx) any_trans = any_trans || c->trans;
-  if (!any_trans) {   // the streaming push splits the particles by SM: no tile to choose
-    if (chosen_tile) *chosen_tile = b->tile;
+  std::vector<int64_t> n;
+  std::vector<int> nb;
+  for (mbt_ctx *c : b->ctx) {
+    any_trans = any_trans || c->trans;
+    n.push_back(c->n_particles);
+    nb.push_back(c->nb);
+  }
+  int slots = 0;
+  if (push_resident_slots(&slots) == cudaSuccess && plan_streams(n, nb, any_trans, slots)) {
+    if (chosen_tile) *chosen_tile = b->tile;   // split by SM: no tile to choose
     return MBT_OK;
   }
+  cudaGetLastError();
   float best = 1e30f;
   int best_tile = b->tile;
   for (int tile : tile_candidates(b->ctx)) {

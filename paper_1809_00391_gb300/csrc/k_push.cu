@@ -41,6 +41,168 @@ static_assert(kStages >= 2, "the stage being refilled must differ from the next 
 constexpr int kStageBytes = kChunk * (int)(sizeof(float) + sizeof(double));
 constexpr unsigned long long kPushWaitNs = 2000000000ull;
 
+// Per-tile push (plans with small runs or small bunches: the streaming push
+// below needs a share of several stages per SM to fill its lanes): one CTA
+// per tile of one bunch, six CTAs per SM; the hardware hands a finished CTA's
+// slot to the next tile.
+__device__ __forceinline__ void issue_chunk(const TileDev &t, const float *tau, const double *del, uint8_t *stage,
+                                            uint64_t *bar, int c) {
+  const int n = min(kChunk, t.count - c * kChunk);
+  const int n4 = (n + 3) & ~3;   // segments are padded to 4 particles: 16-byte multiples
+  const uint32_t tb = (uint32_t)n4 * 4u, db = (uint32_t)n4 * 8u;
+  mbar_arrive_expect_tx(bar, tb + db);
+  bulk_g2s(stage, tau + (size_t)c * kChunk, tb, bar);
+  bulk_g2s(stage + kChunk * sizeof(float), del + (size_t)c * kChunk, db, bar);
+}
+
+template <int NLONG_MAX, bool HARM>
+__global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixed(const Plan p) {
+  extern __shared__ __align__(128) uint8_t sm_push[];
+  __shared__ float s_red[kPushThreads / 32][5];
+  __shared__ float2 s_phi[kMaxLong];
+  __shared__ float4 s_hc[kMaxHarm];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ int s_abort;
+
+  // Prologue that reads only the plan and the particle state: with
+  // programmatic dependent launch it overlaps the previous post kernel, which
+  // signals its dependents only after the previous push has completed.
+  const TileDev t = p.tiles[blockIdx.x];
+  const RunDev *__restrict__ R = p.runs + t.run;
+  const BunchDev bd = p.bunches[t.bunch];
+  PushConstF c;
+  c.nbins = R->nbins;
+  const int nbins = c.nbins;
+  const int nlong = R->nlong;
+  uint8_t *stages = sm_push;
+  float2 *sVd = reinterpret_cast<float2 *>(sm_push + kStages * kStageBytes);   // (V[j], V[j+1] - V[j])
+  int *sH = reinterpret_cast<int *>(sVd + nbins);
+  float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
+  double *del = R->delta + bd.off + t.start;
+  const int nchunks = (t.count + kChunk - 1) / kChunk;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&full[st], 1);
+    fence_mbar_init();
+    s_abort = 0;
+    for (int ch = 0; ch < min(kStages, nchunks); ++ch) issue_chunk(t, tau, del, stages + ch * kStageBytes, &full[ch], ch);
+  }
+  const int nharm = R->nharm;
+  if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
+  grid_dependents_launch();
+  grid_dependency_wait();   // the previous post kernel's wake, phasors and turn counter are complete
+  const long long turn = *R->turn;
+  const int par = (int)(turn & 1);
+  const float *vsr = static_cast<const float *>(R->vsr) + (size_t)t.m * nbins;
+  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+    const float v0 = vsr[k];
+    const float v1 = k + 1 < nbins ? vsr[k + 1] : v0;
+    sVd[k] = make_float2(v0, v1 - v0);
+    sH[k] = 0;
+  }
+  if (threadIdx.x < nlong) {
+    // Phi_m = P_m y_tile + Q_m of this bunch, narrowed to FP32
+    const int r = threadIdx.x;
+    const double2 P = R->pq[((size_t)r * R->nb + t.m) * 2];
+    const double2 Q = R->pq[((size_t)r * R->nb + t.m) * 2 + 1];
+    const double2 y = R->y[(size_t)r * R->ntile_b + t.m / kBunchTile];
+    const double2 phi = cfma(P, y, Q);
+    s_phi[r] = make_float2((float)phi.x, (float)phi.y);
+  }
+  c.invD = R->f_invD;
+  c.HinvD = R->f_HinvD;
+  c.fnb = R->f_nbins;
+  c.invE0 = R->f_invE0 * R->f_omD;
+  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
+  c.cphi = R->f_cphi;
+  c.sphi = R->f_sphi;
+  c.halfw = R->f_halfw;
+  c.omD = R->f_omD;
+  c.qe = R->f_qe;
+  c.aT0 = R->f_aT0;
+  const double omD_d = R->one_minus_D;
+  const bool ngp = (R->flags & kKickNGP) != 0;
+  float la[NLONG_MAX > 0 ? NLONG_MAX : 1], lw[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  float2 phi[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < NLONG_MAX; ++r) {
+    la[r] = R->f_la[r];
+    lw[r] = R->f_lw[r];
+    phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
+  }
+  const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
+
+  float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;
+  int nout = 0;
+
+#pragma unroll 1
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int slot = ch % kStages;
+    uint8_t *sg = stages + slot * kStageBytes;
+    if (!mbar_wait_bounded(&full[slot], (uint32_t)((ch / kStages) & 1), kPushWaitNs)) {
+      atomicExch(p.error, kErrTimeout);
+      s_abort = 1;
+    }
+    const int q = ch * kChunk + 4 * (int)threadIdx.x;   // first particle of this thread's quad in the tile
+    if (!s_abort && q < t.count) {
+      const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
+      const double2 da = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x];
+      const double2 db = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x + 1];
+      float rr[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c.qe != 0.f) normal_quad_f32(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
+      float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+      double dd[4] = {da.x, da.y, db.x, db.y};
+      const int nvalid = min(4, t.count - q);
+      if (ngp)
+        quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
+                                   sd, sd2, nout);
+      else
+        quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
+                                    sd, sd2, nout);
+      *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+      *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
+      *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
+    }
+    __syncthreads();   // stage `slot` consumed by every thread
+    if (threadIdx.x == 0 && !s_abort && ch + kStages < nchunks) {
+      fence_proxy_async_smem();   // order the generic-proxy reads of the stage before its refill
+      issue_chunk(t, tau, del, sg, &full[slot], ch + kStages);
+    }
+  }
+  if (s_abort && threadIdx.x == 0) {
+    // let the copies still in flight land before the CTA exits
+    for (int ch = 0; ch < nchunks; ++ch) mbar_wait_bounded(&full[ch % kStages], (uint32_t)((ch / kStages) & 1), kPushWaitNs);
+  }
+
+  // moment partials: FP32 within a warp, FP64 across the CTA's warps
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  st = warp_sum_f(st);
+  st2 = warp_sum_f(st2);
+  sd = warp_sum_f(sd);
+  sd2 = warp_sum_f(sd2);
+  const int no = __reduce_add_sync(0xFFFFFFFFu, nout);
+  if (lane == 0) {
+    s_red[warp][0] = st;
+    s_red[warp][1] = st2;
+    s_red[warp][2] = sd;
+    s_red[warp][3] = sd2;
+    s_red[warp][4] = (float)no;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
+    p.partial[(size_t)blockIdx.x * kPartials + threadIdx.x] = acc;
+  }
+  int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
+  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+    const int cnt = sH[k];
+    if (cnt) atomicAdd(hg + k, cnt);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Streaming push (runs without a transverse plane): one persistent CTA of
 // kStreamThreads threads per SM, so that no CTA is launched, set up and
@@ -901,8 +1063,21 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
       default: return launch_ex(k_push_mixed_t<kMaxLong>, p.ntiles, kPushThreads, smem, s, pdl, p);
     }
   }
+  if (precision == kMixed && p.stream_ctas <= 0) {
+    // per-tile push
+    const size_t smem = (size_t)kStages * kStageBytes + (size_t)max_nbins * (sizeof(float2) + sizeof(int));
+    const bool harm = p.max_nharm > 0;
+    switch (p.max_nlong) {
+      case 0: return launch_ex(harm ? k_push_mixed<0, true> : k_push_mixed<0, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 1: return launch_ex(harm ? k_push_mixed<1, true> : k_push_mixed<1, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 2: return launch_ex(harm ? k_push_mixed<2, true> : k_push_mixed<2, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      default:
+        return launch_ex(harm ? k_push_mixed<kMaxLong, true> : k_push_mixed<kMaxLong, false>, p.ntiles, kPushThreads,
+                         smem, s, pdl, p);
+    }
+  }
   if (precision == kMixed) {
-    if (p.stream_ctas <= 0 || !p.stream_first) return cudaErrorInvalidValue;   // the plan was not split for it
+    if (!p.stream_first) return cudaErrorInvalidValue;
     const bool harm = p.max_nharm > 0;
     const int grid = p.stream_ctas;
     switch (p.max_nlong) {
@@ -944,12 +1119,26 @@ cudaError_t push_resident_slots(int *slots) {
   return cudaSuccess;
 }
 
-cudaError_t push_t_resident_slots(int *slots) {
-  const size_t smem = (size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float));
+bool plan_streams(const std::vector<int64_t> &n, const std::vector<int> &nb, bool any_trans, int sms) {
+  if (any_trans || n.empty() || sms <= 0) return false;
+  for (size_t i = 0; i < n.size(); ++i) {
+    if (n[i] < (int64_t)sms * 4 * kStreamChunk) return false;           // a share of >= 4 stages per SM
+    if (nb[i] <= 0 || n[i] / nb[i] < 2 * kStreamChunk) return false;    // bunches of >= 2 stages on average
+  }
+  return true;
+}
+
+// CTAs of a per-tile push (with or without a transverse plane) resident at
+// once on the current device (256 cells).
+cudaError_t push_tile_resident_slots(bool trans, int *slots) {
+  const size_t smem = trans ? (size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float))
+                            : (size_t)kStages * kStageBytes + 256 * (sizeof(float2) + sizeof(int));
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed_t<1>, kPushThreads, smem);
+  if (e == cudaSuccess)
+    e = trans ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed_t<1>, kPushThreads, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1, false>, kPushThreads, smem);
   *slots = per * nsm;
   return e;
 }
@@ -961,6 +1150,10 @@ cudaError_t configure_push_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
   int slots = 0;
   if (e == cudaSuccess) e = push_resident_slots(&slots);
+  const int bytes = (int)((size_t)kStages * kStageBytes + 1024 * (sizeof(float2) + sizeof(int)));
+  for (auto k : {k_push_mixed<0, false>, k_push_mixed<1, false>, k_push_mixed<2, false>, k_push_mixed<kMaxLong, false>,
+                 k_push_mixed<0, true>, k_push_mixed<1, true>, k_push_mixed<2, true>, k_push_mixed<kMaxLong, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   const int bytes_t = (int)((size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float)));
   for (auto k : {k_push_mixed_t<0>, k_push_mixed_t<1>, k_push_mixed_t<2>, k_push_mixed_t<kMaxLong>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_t);

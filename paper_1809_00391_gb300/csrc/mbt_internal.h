@@ -5,6 +5,7 @@
 // plain data: pointers into device memory plus constants derived on the host.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace mbt {
@@ -199,6 +200,10 @@ cudaError_t wake_noalloc_launch(const RunDev &proto, const void *img, size_t img
                                 int nbins, const int32_t *hist, float *V, cudaStream_t s, int *device_error_out);
 cudaError_t configure_push_kernels();
 cudaError_t push_resident_slots(int *slots);     // streaming-push CTAs resident at once on this device
-cudaError_t push_t_resident_slots(int *slots);   // the same for the push with a transverse plane (256 cells)
+cudaError_t push_tile_resident_slots(bool trans, int *slots);   // the same for a per-tile push (256 cells)
+// Whether a mixed-precision plan of these runs (their particle counts and
+// bunch counts) uses the streaming push: no transverse plane, and every run
+// gives each SM a share of several stages in bunches of at least two stages.
+bool plan_streams(const std::vector<int64_t> &n, const std::vector<int> &nb, bool any_trans, int sms);
 
 }  // namespace mbt
