@@ -1028,7 +1028,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   rd.inv_n = c->d_inv_n;
   rd.lag_f = c->d_lagf;
   rd.f_invD = (float)rd.invDelta;
-  rd.f_HinvD = (float)(rd.H * rd.invDelta);
+  rd.f_HinvD = (float)(rd.H * rd.invDelta - 0.5);   // cell coordinate from the cell centres
   rd.f_nbins = (float)nbins;
   rd.f_invE0 = (float)rd.inv_E0;
   rd.f_twoVoE0 = (float)(2.0 * rd.V_over_E0);
@@ -1039,7 +1039,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   rd.f_qe = (float)rd.qe_amp;
   rd.f_aT0 = (float)rd.aT0;
   for (int li = 0; li < kMaxLong; ++li) {
-    rd.f_la[li] = li < c->nlong ? (float)(-rd.lr_s[li].x) : 0.f;
+    rd.f_la[li] = li < c->nlong ? (float)(-rd.lr_s[li].x * 1.4426950408889634) : 0.f;   // x log2(e): ex2
     rd.f_lw[li] = li < c->nlong ? (float)rd.lr_s[li].y : 0.f;
   }
   if (c->trans) {

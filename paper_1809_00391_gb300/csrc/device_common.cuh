@@ -79,10 +79,19 @@ __device__ __forceinline__ void normal_quad_f32(const Words4 &w, float (&r)[4]) 
 // Widening of a float by exponent rebias (exact for normal floats).  Zero and
 // subnormals map to +-2^-127 and non-finite values to +-2^128: both far
 // outside anything a particle increment can be, and harmless there.
+// (sign kept by the arithmetic shift and the mask; equal to
+// (u & 0x80000000) | (((u & 0x7FFFFFFF) >> 3) + (896 << 20)) for every u.)
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  const uint32_t hi = (uint32_t)(((int)u >> 3) & (int)0x8FFFFFFF) + (896u << 20);
   return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// 2^x on the special-function unit (subnormal results flushed to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Narrowing by truncation of the significand (error below one float ulp),

@@ -61,6 +61,7 @@ struct RunDev {
   double2 lr_c[kMaxLong];   // c = 2 a Rs (1 + i a / wb)
   // FP32 copies for the mixed-precision push (GB300 issues FP64 and its
   // conversions at ~1.6 lanes per clock per SM: none of them per thread)
+  // (f_HinvD = H/Delta - 1/2: cells from the cell centres; f_la = decay rate x log2(e))
   float f_invD, f_HinvD, f_nbins, f_invE0, f_twoVoE0, f_cphi, f_sphi, f_halfw, f_omD, f_qe, f_aT0;
   float f_la[kMaxLong], f_lw[kMaxLong];
   const float *q_mp_f;      // [nb] macro-particle charge (float)

@@ -8,6 +8,9 @@
 namespace mbt {
 
 struct PushConstF {
+  // invD = 1/Delta, HinvD = H/Delta - 1/2: x = tau invD + HinvD is the
+  // position in cells relative to the cell centres (cell k holds
+  // -1/2 <= x - k < 1/2); la: decay rates times log2(e)
   float invD, HinvD, fnb, invE0, twoVoE0, cphi, sphi, halfw, omD, qe, aT0;
   int nbins;
 };
@@ -22,25 +25,25 @@ template <int NLONG_MAX, bool NGP, bool HARM>
 __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd, int nlong,
                                           const float *la, const float *lw, const float2 *phi, double omD_d,
                                           const float4 *hc, int nharm, float t0, double &d, float r, float &df) {
-  const float x = fmaf(t0, c.invD, c.HinvD);
+  const float x = fmaf(t0, c.invD, c.HinvD);   // cells, from the cell centres
   float v;
   if (NGP) {
-    const int k = min(max((int)x, 0), c.nbins - 1);
+    const int k = min(max(__float2int_rn(x), 0), c.nbins - 1);
     v = sVd[k].x;
   } else {
     // linear interpolation between cell centres, clamped to the end cells
-    const float u = fminf(fmaxf(x - 0.5f, 0.f), c.fnb - 1.f);
+    const float u = fminf(fmaxf(x, 0.f), c.fnb - 1.f);
     const int j = min((int)u, c.nbins - 2);
     const float2 vd = sVd[j];
     v = fmaf(u - (float)j, vd.y, vd.x);
   }
-  v = (x >= 0.f && x < c.fnb) ? v : 0.f;
+  v = (x >= -0.5f && x < c.fnb - 0.5f) ? v : 0.f;
 #pragma unroll
   for (int r2 = 0; r2 < NLONG_MAX; ++r2) {
     if (r2 < nlong) {
       float sn, cs;
       __sincosf(lw[r2] * t0, &sn, &cs);
-      const float ea = __expf(-la[r2] * t0);
+      const float ea = ex2_approx(-la[r2] * t0);
       v = fmaf(ea, fmaf(phi[r2].x, cs, -phi[r2].y * sn), v);
     }
   }
@@ -77,7 +80,7 @@ __device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd
       const float t1 = push_one<NLONG_MAX, NGP, HARM>(c, sVd, nlong, la, lw, phi, omD_d, hc, nharm, tt[e], dd[e], rr[e], df);
       tt[e] = t1;
       const float xb = fmaf(t1, c.invD, c.HinvD);
-      if (xb >= 0.f && xb < c.fnb) atomicAdd(&sH[(int)xb], 1);
+      if (xb >= -0.5f && xb < c.fnb - 0.5f) atomicAdd(&sH[__float2int_rn(xb)], 1);
       else ++nout;
       st += t1;
       st2 = fmaf(t1, t1, st2);
@@ -108,15 +111,15 @@ __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransCons
                                             const float *lw, const float2 *phi, double omD_d, const float4 *hc,
                                             int nharm, bool ngp, float vrw, float t0, double &d, float r, float &df,
                                             float &x, float &xp, float rx, float rxp) {
-  const float x0 = fmaf(t0, c.invD, c.HinvD);
-  const bool inside = x0 >= 0.f && x0 < c.fnb;
+  const float x0 = fmaf(t0, c.invD, c.HinvD);   // cells, from the cell centres
+  const bool inside = x0 >= -0.5f && x0 < c.fnb - 0.5f;
   float v, vt;
   if (ngp) {
-    const int k = min(max((int)x0, 0), c.nbins - 1);
+    const int k = min(max(__float2int_rn(x0), 0), c.nbins - 1);
     v = sVd[k].x;
     vt = sVt[k].x;
   } else {
-    const float u = fminf(fmaxf(x0 - 0.5f, 0.f), c.fnb - 1.f);
+    const float u = fminf(fmaxf(x0, 0.f), c.fnb - 1.f);
     const int j = min((int)u, c.nbins - 2);
     const float2 vd = sVd[j], vtd = sVt[j];
     v = fmaf(u - (float)j, vd.y, vd.x);
@@ -129,7 +132,7 @@ __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransCons
     if (r2 < nlong) {
       float sn, cs;
       __sincosf(lw[r2] * t0, &sn, &cs);
-      const float ea = __expf(-la[r2] * t0);
+      const float ea = ex2_approx(-la[r2] * t0);
       if (plane[r2]) vt = fmaf(ea, fmaf(phi[r2].x, sn, phi[r2].y * cs), vt);   // Im(Phi e^{s t})
       else v = fmaf(ea, fmaf(phi[r2].x, cs, -phi[r2].y * sn), v);             // Re(Phi e^{s t})
     }
@@ -180,9 +183,10 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
                                              tt[e], dd[e], rr[e], df, xx[e], pp[e], rx[e], rp[e]);
       tt[e] = t1;
       const float xb = fmaf(t1, c.invD, c.HinvD);
-      if (xb >= 0.f && xb < c.fnb) {
-        atomicAdd(&sH[(int)xb], 1);
-        atomicAdd(&sDip[(int)xb], xx[e]);
+      if (xb >= -0.5f && xb < c.fnb - 0.5f) {
+        const int kb = __float2int_rn(xb);
+        atomicAdd(&sH[kb], 1);
+        atomicAdd(&sDip[kb], xx[e]);
       } else {
         ++nout;
       }
