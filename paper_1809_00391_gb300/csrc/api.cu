@@ -424,10 +424,9 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
     x.HinvD = r.f_HinvD;
     x.fnb = r.f_nbins;
     x.invE0 = r.f_invE0 * r.f_omD;
-    x.twoVoE0 = r.f_twoVoE0 * r.f_omD;
-    x.cphi = r.f_cphi;
-    x.sphi = r.f_sphi;
-    x.halfw = r.f_halfw;
+    x.rfA = r.f_rfA;
+    x.rfB = r.f_rfB;
+    x.w = r.f_w;
     x.qe = r.f_qe;
     x.aT0 = r.f_aT0;
     x.nbins = r.nbins;
@@ -1031,10 +1030,9 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   rd.f_HinvD = (float)(rd.H * rd.invDelta - 0.5);   // cell coordinate from the cell centres
   rd.f_nbins = (float)nbins;
   rd.f_invE0 = (float)rd.inv_E0;
-  rd.f_twoVoE0 = (float)(2.0 * rd.V_over_E0);
-  rd.f_cphi = (float)rd.cos_phi_s;
-  rd.f_sphi = (float)rd.sin_phi_s;
-  rd.f_halfw = (float)(0.5 * rd.omega_rf);
+  rd.f_rfA = (float)(rd.V_over_E0 * rd.one_minus_D * rd.sin_phi_s);
+  rd.f_rfB = (float)(rd.V_over_E0 * rd.one_minus_D * rd.cos_phi_s);
+  rd.f_w = (float)rd.omega_rf;
   rd.f_omD = (float)rd.one_minus_D;
   rd.f_qe = (float)rd.qe_amp;
   rd.f_aT0 = (float)rd.aT0;

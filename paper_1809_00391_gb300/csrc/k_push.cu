@@ -113,10 +113,9 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
   c.HinvD = R->f_HinvD;
   c.fnb = R->f_nbins;
   c.invE0 = R->f_invE0 * R->f_omD;
-  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
-  c.cphi = R->f_cphi;
-  c.sphi = R->f_sphi;
-  c.halfw = R->f_halfw;
+  c.rfA = R->f_rfA;
+  c.rfB = R->f_rfB;
+  c.w = R->f_w;
   c.omD = R->f_omD;
   c.qe = R->f_qe;
   c.aT0 = R->f_aT0;
@@ -443,10 +442,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
     c.HinvD = __ldg(&RC->HinvD);
     c.fnb = __ldg(&RC->fnb);
     c.invE0 = __ldg(&RC->invE0);
-    c.twoVoE0 = __ldg(&RC->twoVoE0);
-    c.cphi = __ldg(&RC->cphi);
-    c.sphi = __ldg(&RC->sphi);
-    c.halfw = __ldg(&RC->halfw);
+    c.rfA = __ldg(&RC->rfA);
+    c.rfB = __ldg(&RC->rfB);
+    c.w = __ldg(&RC->w);
     c.omD = 0.f;
     c.qe = __ldg(&RC->qe);
     c.aT0 = __ldg(&RC->aT0);
@@ -678,10 +676,9 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   c.HinvD = R->f_HinvD;
   c.fnb = R->f_nbins;
   c.invE0 = R->f_invE0 * R->f_omD;
-  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
-  c.cphi = R->f_cphi;
-  c.sphi = R->f_sphi;
-  c.halfw = R->f_halfw;
+  c.rfA = R->f_rfA;
+  c.rfB = R->f_rfB;
+  c.w = R->f_w;
   c.omD = R->f_omD;
   c.qe = R->f_qe;
   c.aT0 = R->f_aT0;

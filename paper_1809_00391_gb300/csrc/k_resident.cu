@@ -122,10 +122,9 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
   c.HinvD = R->f_HinvD;
   c.fnb = R->f_nbins;
   c.invE0 = R->f_invE0 * R->f_omD;
-  c.twoVoE0 = R->f_twoVoE0 * R->f_omD;
-  c.cphi = R->f_cphi;
-  c.sphi = R->f_sphi;
-  c.halfw = R->f_halfw;
+  c.rfA = R->f_rfA;
+  c.rfB = R->f_rfB;
+  c.w = R->f_w;
   c.omD = R->f_omD;
   c.qe = R->f_qe;
   c.aT0 = R->f_aT0;

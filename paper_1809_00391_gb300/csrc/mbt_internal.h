@@ -62,7 +62,8 @@ struct RunDev {
   // FP32 copies for the mixed-precision push (GB300 issues FP64 and its
   // conversions at ~1.6 lanes per clock per SM: none of them per thread)
   // (f_HinvD = H/Delta - 1/2: cells from the cell centres; f_la = decay rate x log2(e))
-  float f_invD, f_HinvD, f_nbins, f_invE0, f_twoVoE0, f_cphi, f_sphi, f_halfw, f_omD, f_qe, f_aT0;
+  // (f_rfA = (V/E0)(1 - D) sin phi_s, f_rfB = (V/E0)(1 - D) cos phi_s, f_w = omega_rf)
+  float f_invD, f_HinvD, f_nbins, f_invE0, f_rfA, f_rfB, f_w, f_omD, f_qe, f_aT0;
   float f_la[kMaxLong], f_lw[kMaxLong];
   const float *q_mp_f;      // [nb] macro-particle charge (float)
   const double *inv_n;      // [nb] 1 / n_mp
@@ -113,7 +114,7 @@ struct TileDev {
 // descriptors laid out for bulk copies into shared memory, so that a
 // persistent CTA moves from tile to tile without a dependent global load.
 struct alignas(16) StreamRun {
-  float invD, HinvD, fnb, invE0, twoVoE0, cphi, sphi, halfw, qe, aT0;   // invE0, twoVoE0 carry (1 - D)
+  float invD, HinvD, fnb, invE0, rfA, rfB, w, qe, aT0, pad0;   // invE0, rfA, rfB carry (1 - D)
   int nbins, nlong, nharm, flags;
   uint32_t key0, key1;
   double omD;                   // 1 - D

@@ -10,8 +10,10 @@ namespace mbt {
 struct PushConstF {
   // invD = 1/Delta, HinvD = H/Delta - 1/2: x = tau invD + HinvD is the
   // position in cells relative to the cell centres (cell k holds
-  // -1/2 <= x - k < 1/2); la: decay rates times log2(e)
-  float invD, HinvD, fnb, invE0, twoVoE0, cphi, sphi, halfw, omD, qe, aT0;
+  // -1/2 <= x - k < 1/2); la: decay rates times log2(e); RF gain minus the
+  // synchronous one, damped: rfA (cos w tau - 1) - rfB sin w tau with
+  // rfA = (V/E0)(1 - D) sin phi_s, rfB = (V/E0)(1 - D) cos phi_s, w = omega_rf
+  float invD, HinvD, fnb, invE0, rfA, rfB, w, omD, qe, aT0;
   int nbins;
 };
 
@@ -33,7 +35,7 @@ __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd
   } else {
     // linear interpolation between cell centres, clamped to the end cells
     const float u = fminf(fmaxf(x, 0.f), c.fnb - 1.f);
-    const int j = min((int)u, c.nbins - 2);
+    const int j = (int)u;   // <= nbins - 1, where the slope is 0
     const float2 vd = sVd[j];
     v = fmaf(u - (float)j, vd.y, vd.x);
   }
@@ -47,11 +49,11 @@ __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd
       v = fmaf(ea, fmaf(phi[r2].x, cs, -phi[r2].y * sn), v);
     }
   }
-  // (V/E0)[sin(phi_s - w t) - sin(phi_s)] = -2 (V/E0) sin(w t / 2) cos(phi_s - w t / 2)
-  float sh, ch;
-  __sincosf(c.halfw * t0, &sh, &ch);
-  // c.twoVoE0 and c.invE0 carry the damping factor (1 - D) already
-  float rf = -c.twoVoE0 * sh * fmaf(ch, c.cphi, sh * c.sphi);
+  // (V/E0)[sin(phi_s - w t) - sin(phi_s)] (1 - D) = rfA (cos w t - 1) - rfB sin w t
+  // (c.rfA, c.rfB and c.invE0 carry the damping factor already)
+  float sw, cw;
+  __sincosf(c.w * t0, &sw, &cw);
+  float rf = fmaf(-c.rfB, sw, fmaf(c.rfA, cw, -c.rfA));
   // harmonic cavities, the same form: (V_h/E0)[sin(phi_h - n w t) - sin(phi_h)]
   for (int k = 0; HARM && k < nharm; ++k) {
     const float4 h = hc[k];
@@ -120,7 +122,7 @@ __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransCons
     vt = sVt[k].x;
   } else {
     const float u = fminf(fmaxf(x0, 0.f), c.fnb - 1.f);
-    const int j = min((int)u, c.nbins - 2);
+    const int j = (int)u;   // <= nbins - 1, where the slopes are 0
     const float2 vd = sVd[j], vtd = sVt[j];
     v = fmaf(u - (float)j, vd.y, vd.x);
     vt = fmaf(u - (float)j, vtd.y, vtd.x);
@@ -137,9 +139,9 @@ __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransCons
       else v = fmaf(ea, fmaf(phi[r2].x, cs, -phi[r2].y * sn), v);             // Re(Phi e^{s t})
     }
   }
-  float sh, ch;
-  __sincosf(c.halfw * t0, &sh, &ch);
-  float rf = -c.twoVoE0 * sh * fmaf(ch, c.cphi, sh * c.sphi);
+  float sw, cw;
+  __sincosf(c.w * t0, &sw, &cw);
+  float rf = fmaf(-c.rfB, sw, fmaf(c.rfA, cw, -c.rfA));
   for (int k = 0; k < nharm; ++k) {
     const float4 h = hc[k];
     float sk, ck;
