@@ -296,6 +296,9 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
 // ---------------------------------------------------------------------------
 __device__ void finish_turn(const Plan &p) {
   __shared__ int s_last;
+  // the turn counters change only at the end of this function (last CTA):
+  // read them now, so the last CTA does not wait for the read after the scan
+  const long long turn0 = threadIdx.x < p.nruns ? *p.runs[threadIdx.x].turn : 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -328,7 +331,8 @@ __device__ void finish_turn(const Plan &p) {
     }
   }
   __syncthreads();
-  for (int ri = threadIdx.x; ri < p.nruns; ri += kPostThreads) p.runs[ri].turn[0] += 1;
+  if (threadIdx.x < p.nruns) *p.runs[threadIdx.x].turn = turn0 + 1;
+  for (int ri = threadIdx.x + kPostThreads; ri < p.nruns; ri += kPostThreads) p.runs[ri].turn[0] += 1;
   if (threadIdx.x == 0) *p.done = 0u;
 }
 
