@@ -159,25 +159,47 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
 }
 
 // Transverse short-range voltage (Eq. 6, second line) of the tile's bunches,
-// rows [64 sub, 64 sub + 64): V[j] = q sum_{k<=j} dip[k] Wx((j - k) Delta)
+// rows [32 sub, 32 sub + 32): V[j] = q sum_{k<=j} dip[k] Wx((j - k) Delta)
 // from this turn's dipole sums, FP32 on the CUDA cores (kMixed; the
-// contraction is small: 64 rows x 32 bunches x <= 256 lags per job).
+// contraction is small: 32 rows x 32 bunches x <= 256 lags per job).  Thread
+// (row j, warp g) keeps one accumulator for each of the bunches g, g + 8,
+// ... (independent chains, each summed over k in order, as a single chain
+// would); the dipole sums are read four cells at a time, and the lag table
+// is stored behind nbins zeros so that the last group of four needs no test.
 __device__ void trans_job_f32(const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem) {
+  constexpr int kGroups = kPostThreads / kTransRows, kPer = kBunchTile / kGroups;
   const int nbins = R->nbins, nb = R->nb;
   const int m0 = job.bt * kBunchTile, nbt = min(kBunchTile, nb - m0);
-  float *sW = reinterpret_cast<float *>(smem);
-  float *sD = sW + nbins;   // [nbt][nbins]
+  float *sWp = reinterpret_cast<float *>(smem);   // [nbins zeros | Wx[0 .. nbins)]
+  float *sD = sWp + 2 * nbins;                     // [kBunchTile][nbins], rows past nbt zero
   const float *dg = static_cast<const float *>(R->dip) + ((size_t)par * nb + m0) * nbins;
-  for (int k = threadIdx.x; k < nbins; k += kPostThreads) sW[k] = R->tlag_f[k];
-  for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) sD[i] = dg[i];
+  for (int k = threadIdx.x; k < nbins; k += kPostThreads) {
+    sWp[k] = 0.f;
+    sWp[nbins + k] = R->tlag_f[k];
+  }
+  for (int i = threadIdx.x; i < kBunchTile * nbins; i += kPostThreads) sD[i] = i < nbt * nbins ? dg[i] : 0.f;
   __syncthreads();
-  const int r = threadIdx.x % kTransRows, j = job.sub * kTransRows + r;
+  const int r = threadIdx.x % kTransRows, g = threadIdx.x / kTransRows, j = job.sub * kTransRows + r;
+  float acc[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) acc[i] = 0.f;
+  const float *wj = sWp + nbins + j;
+  for (int k = 0; k <= j; k += 4) {
+    const float w0 = wj[-k], w1 = wj[-k - 1], w2 = wj[-k - 2], w3 = wj[-k - 3];   // zero for lags below 0
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const float4 d = *reinterpret_cast<const float4 *>(sD + (size_t)(g + kGroups * i) * nbins + k);
+      acc[i] = fmaf(d.x, w0, acc[i]);
+      acc[i] = fmaf(d.y, w1, acc[i]);
+      acc[i] = fmaf(d.z, w2, acc[i]);
+      acc[i] = fmaf(d.w, w3, acc[i]);
+    }
+  }
   float *vt = static_cast<float *>(R->vt);
-  for (int b = threadIdx.x / kTransRows; b < nbt; b += kPostThreads / kTransRows) {
-    const float *d = sD + (size_t)b * nbins;
-    float acc = 0.f;
-    for (int k = 0; k <= j; ++k) acc = fmaf(d[k], sW[j - k], acc);
-    vt[(size_t)(m0 + b) * nbins + j] = R->q_mp_f[m0 + b] * acc;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int b = g + kGroups * i;
+    if (b < nbt) vt[(size_t)(m0 + b) * nbins + j] = R->q_mp_f[m0 + b] * acc[i];
   }
 }
 

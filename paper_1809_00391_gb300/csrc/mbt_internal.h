@@ -22,7 +22,7 @@ constexpr int kF64QuadsPerThread = 2;                                      // 4 
 constexpr int kF64Tile = kPushThreads * 4 * kF64QuadsPerThread;            // 2048 particles
 constexpr int kPartials = 10;        // sums of tau, tau^2, delta, delta^2, n_out, pad, x, x^2, x', x'^2
 constexpr int kTRecord = 4;          // transverse record: <x>, rms x, <x'>, rms x'
-constexpr int kTransRows = 64;       // transverse short-range rows per post job (kMixed)
+constexpr int kTransRows = 32;       // transverse short-range rows per post job (kMixed)
 constexpr int kRecord = 6;           // <tau>, rms tau, <delta>, rms delta, n_in, n_out
 constexpr int kPostThreads = 256;
 constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
