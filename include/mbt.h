@@ -104,6 +104,9 @@ typedef struct {
     int64_t turn;              /* turns completed                                    */
     int32_t nb, nbins, n_long, precision;
     int64_t device_bytes;      /* device memory held by the context                  */
+    int32_t push_ctas;         /* CTAs of the streaming push tracking the context    */
+                               /* on its own (0: the per-tile or FP64 push)          */
+    int32_t reserved;
 } mbt_info;
 
 typedef struct mbt_ctx mbt_ctx;

@@ -60,7 +60,7 @@ class Info(ctypes.Structure):
                 ("half_width_s", ctypes.c_double), ("bin_width_s", ctypes.c_double),
                 ("n_particles", ctypes.c_int64), ("turn", ctypes.c_int64), ("nb", ctypes.c_int32),
                 ("nbins", ctypes.c_int32), ("n_long", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("push_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):

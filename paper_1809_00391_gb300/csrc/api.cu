@@ -1731,6 +1731,8 @@ mbt_status mbt_get_info(mbt_ctx *c, mbt_info *info) {
   info->n_long = c->nlong;
   info->precision = c->precision;
   info->device_bytes = (int64_t)(c->device_bytes + c->own.bytes);
+  info->push_ctas = c->filled ? c->own.plan.stream_ctas : 0;
+  info->reserved = 0;
   if (c->filled) {
     long long turn = 0;
     mbt_status st = current_turn(c, &turn);

@@ -175,13 +175,35 @@ def test_mixed_three_bunches_moments(pkg, oracle_mod):
 
 
 def test_mixed_tiny_ragged_bunches(pkg, oracle_mod):
-    """Streaming push with fewer particles than one quad per SM share and bunch
-    sizes that are not multiples of 4 (one bunch of a single particle): most
-    CTAs get no tile, shares cut bunches at multiples of 4, and every particle
-    is pushed and deposited exactly once per turn."""
+    """Per-tile push (a run far too small to stream) with bunch sizes that are
+    not multiples of 4, one bunch of a single particle: every particle is pushed
+    and deposited exactly once per turn."""
     run = W.Run(W.ring_r0(), [dict(W.BROADBAND), dict(W.HOM)], np.array([0, 3, 7], np.int32), np.full(3, 1e-3),
                 np.array([37, 1, 510], np.int64), seed=41, turns=50, precision=W.PREC_MIXED)
     tr, orc = _pair(pkg, oracle_mod, run, precision=W.PREC_MIXED)
+    _ragged_vs_oracle(tr, orc, run)
+    assert tr.info["push_ctas"] == 0
+    tr.close()
+
+
+def test_streaming_push_ragged_bunches(pkg, oracle_mod):
+    """Streaming push (one run large enough for equal per-SM shares) on a fill
+    that mixes two bunches of 1.3e6 particles, one not a multiple of 4, with
+    bunches of 37, 1 and 1001 particles: shares cut bunches at multiples of 4,
+    the tiny bunches sit inside one share, and every particle is pushed and
+    deposited exactly once per turn."""
+    n_mp = np.array([1_300_000, 37, 1, 1_300_003, 1001], np.int64)
+    run = W.Run(W.ring_r0(), [dict(W.BROADBAND), dict(W.HOM)], np.array([0, 3, 7, 12, 20], np.int32),
+                np.full(5, 1e-3), n_mp, seed=43, turns=10, precision=W.PREC_MIXED)
+    tr, orc = _pair(pkg, oracle_mod, run, precision=W.PREC_MIXED)
+    _ragged_vs_oracle(tr, orc, run)
+    assert tr.info["push_ctas"] > 0
+    tr.close()
+
+
+def _ragged_vs_oracle(tr, orc, run):
+    """Histogram counts exact; per-particle coordinates against the oracle with
+    tolerances scaled by the fill's own spreads (a one-particle bunch has none)."""
     tr.init_particles()
     orc.init_particles()
     tr.track(run.turns)
@@ -195,7 +217,6 @@ def test_mixed_tiny_ragged_bunches(pkg, oracle_mod):
         to, do = orc.particles(m)
         assert np.median(np.abs(tg - to)) <= 1e-4 * sig and np.max(np.abs(tg - to)) <= 1e-2 * sig, f"bunch {m}"
         assert np.median(np.abs(dg - do)) <= 1e-4 * dsig and np.max(np.abs(dg - do)) <= 1e-2 * dsig, f"bunch {m}"
-    tr.close()
 
 
 @pytest.mark.parametrize("nbins", [128, 256])
