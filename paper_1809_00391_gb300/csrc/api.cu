@@ -537,6 +537,7 @@ void append_run(PlanStore &st, mbt_ctx *c, int mixed_tile) {
     st.jobs.push_back(PostJob{ri, kJobTile, bt, 0});
     if (c->precision == MBT_PREC_MIXED) {
       for (int mt = 0; mt < c->nbins / 128; ++mt) st.jobs.push_back(PostJob{ri, kJobWake, bt, mt});
+      st.jobs.push_back(PostJob{ri, kJobMoments, bt, 0});
     }
   }
   if (c->precision == MBT_PREC_F64) {

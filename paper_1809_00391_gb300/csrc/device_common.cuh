@@ -132,11 +132,15 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // Inclusive warp scan of affine maps x -> A x + B (lane i ends with the
-// composition of lanes 0..i, lane 0 applied first).
-__device__ __forceinline__ void warp_scan_affine(double2 &A, double2 &B) {
+// composition of lanes 0..i, lane 0 applied first), for lanes below `width`
+// (warp-uniform): a level of stride d >= width changes no such lane.  Not
+// unrolled: the post kernel runs it once per turn, after the push has
+// displaced its code from the caches, so its code length counts more than the
+// loop overhead.
+__device__ __forceinline__ void warp_scan_affine(double2 &A, double2 &B, int width = 32) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll 1
+  for (int d = 1; d < width; d <<= 1) {
     const double2 Ap = shfl_up_d2(A, d);
     const double2 Bp = shfl_up_d2(B, d);
     if (lane >= d) {

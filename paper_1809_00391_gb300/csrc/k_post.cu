@@ -41,7 +41,7 @@ struct PostStage {
   double2 step[kMaxLong][kBunchTile];   // a_m of the tile's bunches (tile jobs)
   double q[kBunchTile];                 // macro-particle charge (tile jobs)
   float qf[kBunchTile];                 // same in float (wake jobs)
-  double inv_n[kBunchTile];             // 1 / N_m (wake job of M-tile 0: moments)
+  double inv_n[kBunchTile];             // 1 / N_m (moments jobs)
   long long n[kBunchTile];
   int tile0[kBunchTile], ntiles[kBunchTile];
 };
@@ -66,13 +66,12 @@ __device__ void post_stage(const Plan &p, const RunDev *__restrict__ R, const Po
     if (tid == 32) prefetch_l2(R->carry);   // read by whichever CTA finishes last
   } else if (job.type == kJobWake && tid < kBunchTile) {
     st->qf[tid] = tid < nbt ? R->q_mp_f[m0 + tid] : 0.f;
-    if (job.sub == 0 && tid < nbt) {
-      const BunchDev bd = p.bunches[R->bunch_base + m0 + tid];
-      st->tile0[tid] = bd.tile0;
-      st->ntiles[tid] = bd.ntiles;
-      st->n[tid] = bd.n;
-      st->inv_n[tid] = R->inv_n[m0 + tid];
-    }
+  } else if (job.type == kJobMoments && tid < nbt) {
+    const BunchDev bd = p.bunches[R->bunch_base + m0 + tid];
+    st->tile0[tid] = bd.tile0;
+    st->ntiles[tid] = bd.ntiles;
+    st->n[tid] = bd.n;
+    st->inv_n[tid] = R->inv_n[m0 + tid];
   }
   if (tid == 64) prefetch_l2(R->turn);
 }
@@ -226,6 +225,40 @@ __device__ void trans_job_f64(const RunDev *__restrict__ R, const PostJob &job, 
   if (sub == 0 && j < nbins) static_cast<double *>(R->vt)[(size_t)m * nbins + j] = R->q_mp[m] * acc;
 }
 
+// Warp 0 of a tile job, lane b for bunch m0 + b: E_m = c q_m sum_m, then the
+// affine scan across the tile (lane b holds x -> a_m (x + E_{m-1}); bunch m0
+// maps the tile's entering value).  Writes P_m, Q_m to pq[2 b], pq[2 b + 1]
+// and the tile aggregate to agg[0], agg[1].  The mixed post kernel also runs
+// it on placeholder values into shared scratch before its grid dependency
+// wait, so that this code, which runs once per turn after the push has
+// displaced it from the instruction caches, is cached when the turn's
+// data arrives (tile_scan_warp; the FP64 kernel inlines the body).
+__device__ __forceinline__ void tile_scan_body(double2 c, double2 sum, double q, double2 a, int nbt, double2 *pq,
+                                               double2 *agg) {
+  const int lane = threadIdx.x & 31;
+  double2 E = make_double2(0.0, 0.0);
+  if (lane < nbt) E = cmul(c, make_double2(q * sum.x, q * sum.y));
+  const double2 Eprev = shfl_up_d2(E, 1);
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+  if (lane < nbt) {
+    A = a;
+    if (lane > 0) B = cmul(A, Eprev);
+  }
+  warp_scan_affine(A, B, nbt);
+  if (lane < nbt) {
+    pq[(size_t)lane * 2] = A;
+    pq[(size_t)lane * 2 + 1] = B;
+  }
+  if (lane == nbt - 1) {
+    agg[0] = A;
+    agg[1] = cadd(B, E);
+  }
+}
+__device__ __noinline__ void tile_scan_warp(double2 c, double2 sum, double q, double2 a, int nbt, double2 *pq,
+                                            double2 *agg) {
+  tile_scan_body(c, sum, q, a, nbt, pq, agg);
+}
+
 // Long-range emission and the tile's affine scan, per long-range resonator.
 // Emission sums sum_k count[m,k] e^{-s tau_k}: 8 threads per bunch, all 32
 // bunches of the tile at once.
@@ -244,17 +277,42 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
     // source of the emission: the cell counts, or for a transverse entry the dipole sums
     const bool tplane = R->lr_plane[r] != 0;
     if (PREC == kMixed) {
+      // thread sub takes the 4-cell groups g = sub + 8 i (nbins 128 or 256:
+      // at most kGroups), all of its loads issued before the sums
+      constexpr int kGroups = 256 / 4 / 8;
+      const int ng = nbins / 32;
       float ax = 0.f, ay = 0.f;
       if (b < nbt) {
-        const int32_t *hrow = hcur + (size_t)b * nbins;
-        const float *drow = tplane ? static_cast<const float *>(R->dip) + ((size_t)par * nb + m0 + b) * nbins : nullptr;
-        const float2 *tab = (tabf ? tabf : R->emis_f) + (size_t)r * nbins;
-#pragma unroll 8
-        for (int k = sub; k < nbins; k += 8) {
-          const float cnt = tplane ? drow[k] : (float)hrow[k];
-          const float2 e = tab[k];
-          ax = fmaf(cnt, e.x, ax);
-          ay = fmaf(cnt, e.y, ay);
+        float4 cnt[kGroups];
+        if (tplane) {
+          const float4 *d4 = reinterpret_cast<const float4 *>(static_cast<const float *>(R->dip) +
+                                                              ((size_t)par * nb + m0 + b) * nbins);
+#pragma unroll
+          for (int i = 0; i < kGroups; ++i) cnt[i] = i < ng ? d4[sub + 8 * i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          const int4 *h4 = reinterpret_cast<const int4 *>(hcur + (size_t)b * nbins);
+#pragma unroll
+          for (int i = 0; i < kGroups; ++i) {
+            const int4 v = i < ng ? h4[sub + 8 * i] : make_int4(0, 0, 0, 0);
+            cnt[i] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+          }
+        }
+        // two cells' factors (Re, Im, Re, Im) per float4
+        const float4 *t4 = reinterpret_cast<const float4 *>((tabf ? tabf : R->emis_f) + (size_t)r * nbins);
+#pragma unroll
+        for (int i = 0; i < kGroups; ++i) {
+          if (i < ng) {
+            const int g = sub + 8 * i;
+            const float4 e0 = t4[2 * g], e1 = t4[2 * g + 1];
+            ax = fmaf(cnt[i].x, e0.x, ax);
+            ay = fmaf(cnt[i].x, e0.y, ay);
+            ax = fmaf(cnt[i].y, e0.z, ax);
+            ay = fmaf(cnt[i].y, e0.w, ay);
+            ax = fmaf(cnt[i].z, e1.x, ax);
+            ay = fmaf(cnt[i].z, e1.y, ay);
+            ax = fmaf(cnt[i].w, e1.z, ax);
+            ay = fmaf(cnt[i].w, e1.w, ay);
+          }
         }
       }
 #pragma unroll
@@ -284,30 +342,20 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
     }
     __syncthreads();
     if (warp == 0) {
-      // E_m = c q_m sum (lane-parallel), then the affine scan across the tile:
-      // lane b holds x -> a_m (x + E_{m-1}); bunch m0 maps the tile's entering value
       const int m = m0 + lane;
-      double2 E = make_double2(0.0, 0.0);
+      double2 sum = make_double2(0.0, 0.0), a = make_double2(1.0, 0.0);
+      double q = 0.0;
       if (lane < nbt) {
-        const double2 sum = PREC == kMixed ? make_double2((double)sEf[lane].x, (double)sEf[lane].y) : sE[lane];
-        const double q = st ? st->q[lane] : R->q_mp[m];
-        E = cmul(R->lr_c[r], make_double2(q * sum.x, q * sum.y));
+        sum = PREC == kMixed ? make_double2((double)sEf[lane].x, (double)sEf[lane].y) : sE[lane];
+        q = st ? st->q[lane] : R->q_mp[m];
+        a = st ? st->step[r][lane] : R->step[(size_t)r * nb + m];
       }
-      const double2 Eprev = shfl_up_d2(E, 1);
-      double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
-      if (lane < nbt) {
-        A = st ? st->step[r][lane] : R->step[(size_t)r * nb + m];
-        if (lane > 0) B = cmul(A, Eprev);
-      }
-      warp_scan_affine(A, B);
-      if (lane < nbt) {
-        R->pq[((size_t)r * nb + m) * 2] = A;
-        R->pq[((size_t)r * nb + m) * 2 + 1] = B;
-      }
-      if (lane == nbt - 1) {
-        R->agg[((size_t)r * R->ntile_b + job.bt) * 2] = A;
-        R->agg[((size_t)r * R->ntile_b + job.bt) * 2 + 1] = cadd(B, E);
-      }
+      double2 *const pq = R->pq + ((size_t)r * nb + m0) * 2;
+      double2 *const agg = R->agg + ((size_t)r * R->ntile_b + job.bt) * 2;
+      if (PREC == kMixed)
+        tile_scan_warp(R->lr_c[r], sum, q, a, nbt, pq, agg);
+      else
+        tile_scan_body(R->lr_c[r], sum, q, a, nbt, pq, agg);
     }
     __syncthreads();
   }
@@ -316,44 +364,70 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
 // ---------------------------------------------------------------------------
 // Last CTA: compose tile aggregates with the carry, advance the turns.
 // ---------------------------------------------------------------------------
-__device__ void finish_turn(const Plan &p) {
+// Compose the tile aggregates of pair (run R, long-range resonator r) with
+// the carry K; nt tiles, one lane per tile.
+__device__ __forceinline__ void finish_pair(int nt, double2 K, const double2 *agg, double2 *y, double2 *carry) {
+  const int lane = threadIdx.x & 31;
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+  if (lane < nt) {
+    A = __ldcg(agg + (size_t)lane * 2);
+    B = __ldcg(agg + (size_t)lane * 2 + 1);
+  }
+  warp_scan_affine(A, B, nt);
+  const double2 yn = cfma(A, K, B);   // value leaving tile `lane`
+  if (lane + 1 < nt) y[lane + 1] = yn;
+  if (lane == 0) y[0] = K;
+  __syncwarp();
+  if (lane == nt - 1) *carry = yn;
+}
+
+// own, Rown: the run of this CTA's job and its descriptor (a staged copy).
+__device__ void finish_turn(const Plan &p, int own, const RunDev *Rown) {
   __shared__ int s_last;
-  // the turn counters change only at the end of this function (last CTA):
-  // read them now, so the last CTA does not wait for the read after the scan
-  const long long turn0 = threadIdx.x < p.nruns ? *p.runs[threadIdx.x].turn : 0;
+  const int warp = threadIdx.x >> 5;
+  // Read before the count, so that the last CTA's chain after it is the
+  // aggregate loads, the scan and the stores: the turn counters (they change
+  // only at the end of this function) and, where warp w's first pair (pair w)
+  // belongs to the first run, that pair's layout and carry (written only by
+  // the last CTA of the previous post kernel).
+  long long *const tp =
+      threadIdx.x < p.nruns ? (threadIdx.x == own ? Rown->turn : p.runs[threadIdx.x].turn) : nullptr;
+  const long long turn0 = tp ? *tp : 0;
+  const RunDev *R0 = own == 0 ? Rown : p.runs;
+  const bool pre = p.nruns > 0 && warp < R0->nlong;
+  int nt0 = 0;
+  double2 K0 = make_double2(0.0, 0.0);
+  const double2 *agg0 = nullptr;
+  double2 *y0 = nullptr, *carry0 = nullptr;
+  if (pre) {
+    nt0 = R0->ntile_b;
+    agg0 = R0->agg + (size_t)warp * nt0 * 2;
+    y0 = R0->y + (size_t)warp * nt0;
+    carry0 = R0->carry + warp;
+    K0 = __ldcg(carry0);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    __threadfence();   // this CTA's results before its count (release)
     const unsigned int prev = atomicAdd(p.done, 1u);
     s_last = (prev == gridDim.x - 1) ? 1 : 0;
+    if (s_last) __threadfence();   // acquire: every thread of the CTA reads after the barrier below
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // one warp per (run, long-range resonator)
+  if (pre) finish_pair(nt0, K0, agg0, y0, carry0);
   int pair = 0;
   for (int ri = 0; ri < p.nruns; ++ri) {
     const RunDev *R = p.runs + ri;
     for (int r = 0; r < R->nlong; ++r, ++pair) {
-      if (pair % (kPostThreads / 32) != warp) continue;
+      if (pair % (kPostThreads / 32) != warp || (pre && pair == warp)) continue;
       const int nt = R->ntile_b;
-      const double2 K = __ldcg(R->carry + r);
-      double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
-      if (lane < nt) {
-        A = __ldcg(R->agg + ((size_t)r * nt + lane) * 2);
-        B = __ldcg(R->agg + ((size_t)r * nt + lane) * 2 + 1);
-      }
-      warp_scan_affine(A, B);
-      const double2 yn = cfma(A, K, B);   // value leaving tile `lane`
-      if (lane + 1 < nt) R->y[(size_t)r * nt + lane + 1] = yn;
-      if (lane == 0) R->y[(size_t)r * nt] = K;
-      __syncwarp();
-      if (lane == nt - 1) R->carry[r] = yn;
+      finish_pair(nt, __ldcg(R->carry + r), R->agg + (size_t)r * nt * 2, R->y + (size_t)r * nt, R->carry + r);
     }
   }
   __syncthreads();
-  if (threadIdx.x < p.nruns) *p.runs[threadIdx.x].turn = turn0 + 1;
+  if (tp) *tp = turn0 + 1;
   for (int ri = threadIdx.x + kPostThreads; ri < p.nruns; ri += kPostThreads) p.runs[ri].turn[0] += 1;
   if (threadIdx.x == 0) *p.done = 0u;
 }
@@ -402,14 +476,11 @@ __device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, 
 }
 
 // Main part: B from the turn's counts, the MMAs (issued by one thread, run
-// asynchronously), the moments of the bunch tile while they run (M-tile 0),
-// then the epilogue from tensor memory.
+// asynchronously), then the epilogue from tensor memory.
 // qf: the charges of the tile's 32 bunches (staged, or the run's array at
-// the tile); st: staged descriptors for the moments (or nullptr).
-template <bool WITH_MOMENTS = true>
-__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, long long turn,
-                            uint8_t *smem, uint64_t *bars, uint32_t *tmem_slot, int *s_flag,
-                            double (*s_sum)[kBunchTile], const float *qf, const PostStage *st) {
+// the tile).
+__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem,
+                            uint64_t *bars, uint32_t *tmem_slot, int *s_flag, const float *qf) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbins = R->nbins;
   const int nb = R->nb;
@@ -423,19 +494,29 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
   const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
   const uint32_t tmem = *tmem_slot;
 
-  // B: counts of the 32 bunches split into three exact BF16 byte planes
+  // B: counts of the 32 bunches split into three exact BF16 byte planes.
+  // Item (bunch b, 8-cell group kg) = idx = kg * 32 + b; a thread's items are
+  // idx = tid + i kPostThreads (at most kItems with nbins <= 256), and all of
+  // its loads are issued before the first conversion: one round trip to L2.
   const int32_t *hg = R->hist + ((size_t)par * nb + m0) * nbins;
   const int KG = kmt / 8;
-#pragma unroll 4
-  for (int idx = tid; idx < kBunchTile * KG; idx += kPostThreads) {
-    const int b = idx % kBunchTile, kg = idx / kBunchTile;
-    int c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (b < nbt) {
-      const int4 c0 = *reinterpret_cast<const int4 *>(hg + (size_t)b * nbins + kg * 8);
-      const int4 c1 = *reinterpret_cast<const int4 *>(hg + (size_t)b * nbins + kg * 8 + 4);
-      c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
-      c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+  constexpr int kItems = kBunchTile * 32 / kPostThreads;
+  int4 cv[kItems][2];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int idx = tid + i * kPostThreads, b = idx % kBunchTile, kg = idx / kBunchTile;
+    cv[i][0] = cv[i][1] = make_int4(0, 0, 0, 0);
+    if (kg < KG && b < nbt) {
+      const int4 *src = reinterpret_cast<const int4 *>(hg + (size_t)b * nbins + kg * 8);
+      cv[i][0] = src[0];
+      cv[i][1] = src[1];
     }
+  }
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int idx = tid + i * kPostThreads, b = idx % kBunchTile, kg = idx / kBunchTile;
+    if (kg >= KG) continue;
+    const int c[8] = {cv[i][0].x, cv[i][0].y, cv[i][0].z, cv[i][0].w, cv[i][1].x, cv[i][1].y, cv[i][1].z, cv[i][1].w};
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl) {
       uint32_t w[4];
@@ -471,7 +552,6 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       umma_commit(&bars[1]);
     }
   }
-  if (WITH_MOMENTS && mt == 0) moments_job(p, R, m0, nbt, par, turn, s_sum, st);   // overlaps the MMAs
   __syncthreads();
   const bool aborted = *s_flag != 0;
   if (!aborted && warp < 4) {
@@ -517,26 +597,40 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   __shared__ float2 sEf[kBunchTile];
   __shared__ double s_sum[9][kBunchTile];
   __shared__ PostStage st;
+  __shared__ RunDev sR;
+  __shared__ double2 s_scr[2 * kBunchTile + 2];
   const PostJob job = p.jobs[blockIdx.x];
-  const RunDev *R = p.runs + job.run;
   trace_mark(p, 0);
+  // The run descriptor, copied before the wait: the push streams the particle
+  // state through L2 and evicts it, and after the wait every read of it would
+  // be a miss behind the next push's first bulk copies.
+  static_assert(sizeof(RunDev) % 16 == 0 && sizeof(RunDev) / 16 <= kPostThreads, "run descriptor copy");
+  if (threadIdx.x < sizeof(RunDev) / 16)
+    reinterpret_cast<int4 *>(&sR)[threadIdx.x] = reinterpret_cast<const int4 *>(p.runs + job.run)[threadIdx.x];
+  __syncthreads();
+  const RunDev *R = &sR;
   // tile jobs keep the emission table where wake jobs keep their operands
   float2 *tabf = reinterpret_cast<float2 *>(sm_post);
   if (job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);   // A-image copy first
   post_stage(p, R, job, &st, tabf);
+  if (job.type == kJobTile && threadIdx.x < 32)   // code warm-up, into shared scratch
+    tile_scan_warp(make_double2(0.0, 0.0), make_double2(0.0, 0.0), 0.0, make_double2(1.0, 0.0), kBunchTile, s_scr,
+                   s_scr + 2 * kBunchTile);
   __syncthreads();
   grid_dependency_wait();     // the push of this turn has completed
   grid_dependents_launch();   // the next push may start its prologue (particle prefetch)
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
   if (job.type == kJobWake)
-    wake_job_tc(p, R, job, par, turn, sm_post, bars, &tmem_slot, &s_flag, s_sum, st.qf, &st);
+    wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
   else if (job.type == kJobTile)
     tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
+  else if (job.type == kJobMoments)
+    moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
   else
     trans_job_f32(R, job, par, sm_post);
   trace_mark(p, 1);
-  finish_turn(p);
+  finish_turn(p, job.run, R);
   trace_mark(p, 2);
 }
 
@@ -589,7 +683,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
     tile_job<kF64>(p, R, job, par, sE, sEf, nullptr, nullptr);
   }
   trace_mark(p, 1);
-  finish_turn(p);
+  finish_turn(p, job.run, R);
   trace_mark(p, 2);
 }
 
@@ -636,8 +730,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) 
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   wake_prologue(R, job, sm_wna, bars, &tmem_slot, &s_flag);
-  wake_job_tc<false>(p, R, job, 0, 0, sm_wna, bars, &tmem_slot, &s_flag, s_sum, R->q_mp_f + job.bt * kBunchTile,
-                     nullptr);
+  wake_job_tc(p, R, job, 0, sm_wna, bars, &tmem_slot, &s_flag, R->q_mp_f + job.bt * kBunchTile);
 }
 
 namespace {

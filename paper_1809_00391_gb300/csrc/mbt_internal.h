@@ -29,7 +29,7 @@ constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
 
 enum Precision { kF64 = 0, kMixed = 1 };
 enum Flags { kNoSR = 1, kNoQE = 2, kKickNGP = 4 };
-enum JobType { kJobWake = 0, kJobTile = 1, kJobTrans = 2 };
+enum JobType { kJobWake = 0, kJobTile = 1, kJobTrans = 2, kJobMoments = 3 };
 enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2 };
 
 // One run's device state and constants.
