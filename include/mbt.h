@@ -319,6 +319,29 @@ mbt_status mbt_set_graph(mbt_ctx *ctx, int turns_per_graph);
  * alone and in any such batch. */
 mbt_status mbt_set_tile(mbt_ctx *ctx, int particles);
 
+/* Host-only planning queries (no device, no context): the decisions the
+ * library takes when it builds a mixed-precision plan.
+ * mbt_plan_streams: *streams = 1 if runs of run_n[i] macro-particles in
+ * run_nb[i] bunches (i < nruns) would be tracked by the streaming push on a
+ * device holding `ctas` streaming-push CTAs at once, 0 for the per-tile push
+ * (see mbt_set_tile).  MBT_ERR_ARG for nruns, ctas, a size or a bunch count
+ * below 1 or a NULL pointer.
+ * mbt_plan_stream_split: the streaming push's work split of nb bunches (bunch
+ * i: run[i] >= 0, non-decreasing, n_mp[i] >= 1 macro-particles) over `ctas`
+ * CTAs.  Each run's particle sequence (its bunches in order, each padded to a
+ * multiple of 4) is cut into `ctas` shares at multiples of 4, share g =
+ * [4 floor(P' g / ctas), 4 floor(P' (g + 1) / ctas)) with P' the run's padded
+ * length / 4 (the last share ends at the padded length), and each share into
+ * tiles at bunch boundaries (at most 2^28 particles).  Tile k is written as
+ * out[4k .. 4k+3] = (bunch, first particle within the bunch, count, CTA) for
+ * k < cap, in bunch order; *ntiles receives the number of tiles (call with
+ * cap = 0 to size out; the caller owns out).  MBT_ERR_ARG on invalid input,
+ * nothing written. */
+mbt_status mbt_plan_streams(int nruns, const int64_t *run_n, const int32_t *run_nb, int any_transverse, int ctas,
+                            int *streams);
+mbt_status mbt_plan_stream_split(int nb, const int32_t *run, const int64_t *n_mp, int ctas, int64_t *out,
+                                 int64_t cap, int64_t *ntiles);
+
 /* Autotuner (plans on the per-tile push): times turns_per_trial turns for
  * each candidate push tile (2048 .. 32768 particles, plus tiles that make the
  * tile count a whole multiple of the push CTAs the GPU holds at once) and

@@ -39,7 +39,7 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
            "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy",
            "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
-           "mbt_server_destroy"]
+           "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split"]
 
 
 class MBTError(RuntimeError):
@@ -148,6 +148,8 @@ def lib() -> ctypes.CDLL:
                 "mbt_server_poll": ([_vp, _i64, _P(RequestStatus), _P(_d), _P(_d)], _i),
                 "mbt_server_wait": ([_vp, _i64, _d], _i), "mbt_server_get_stats": ([_vp, _P(ServerStats)], _i),
                 "mbt_server_destroy": ([_vp], None),
+                "mbt_plan_streams": ([_i, _P(_i64), _P(_i32), _i, _i, _P(_i)], _i),
+                "mbt_plan_stream_split": ([_i, _P(_i32), _P(_i64), _i, _P(_i64), _i64, _P(_i64)], _i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -155,6 +157,38 @@ def lib() -> ctypes.CDLL:
                 f.restype = res
             _lib = L
     return _lib
+
+
+def plan_streams(run_n, run_nb, any_transverse: bool, ctas: int) -> bool:
+    """Whether runs of run_n[i] macro-particles in run_nb[i] bunches go to the
+    streaming push on a device holding `ctas` streaming CTAs (host only)."""
+    n = np.ascontiguousarray(run_n, np.int64)
+    nb = np.ascontiguousarray(run_nb, np.int32)
+    out = _i()
+    st = lib().mbt_plan_streams(len(n), _ptr(n, _i64), _ptr(nb, _i32), 1 if any_transverse else 0, ctas,
+                                ctypes.byref(out))
+    if st != 0:
+        raise MBTError(st, "mbt_plan_streams")
+    return bool(out.value)
+
+
+def stream_split(run, n_mp, ctas: int) -> np.ndarray:
+    """The streaming push's tiles for bunches (run[i], n_mp[i]) over `ctas`
+    CTAs: rows (bunch, first particle, count, CTA) in bunch order (host only)."""
+    r = np.ascontiguousarray(run, np.int32)
+    n = np.ascontiguousarray(n_mp, np.int64)
+    cnt = _i64()
+    L = lib()
+    st = L.mbt_plan_stream_split(len(n), _ptr(r, _i32), _ptr(n, _i64), ctas, None, 0, ctypes.byref(cnt))
+    if st != 0:
+        raise MBTError(st, "mbt_plan_stream_split")
+    out = np.zeros((cnt.value, 4), np.int64)
+    if cnt.value:
+        st = L.mbt_plan_stream_split(len(n), _ptr(r, _i32), _ptr(n, _i64), ctas, _ptr(out, _i64), cnt.value,
+                                     ctypes.byref(cnt))
+        if st != 0:
+            raise MBTError(st, "mbt_plan_stream_split")
+    return out
 
 
 def _stream(s) -> ctypes.c_void_p:

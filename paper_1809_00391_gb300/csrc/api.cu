@@ -317,6 +317,51 @@ double rw_integral(double b, double sigma, double L, double ta, double tb) {
   return 4.0 * kZ0 * L * s0 / (kPi * b * b) * ((P(ub) - P(ua)) / 3.0 - std::sqrt(2.0) / kPi * G);
 }
 
+// Streaming-push work split (host only).  bunch_run: the run of each bunch,
+// non-decreasing; bunch_n: its macro-particles (>= 1); G: CTAs.  Each run's
+// particle sequence (its bunches in order, each padded to a multiple of 4) is
+// cut into G shares at multiples of 4, share g = [4 floor(P' g / G),
+// 4 floor(P' (g + 1) / G)) with P' = P / 4 (the last share ends at P), and
+// each share into tiles at bunch boundaries and at most 2^28 particles.  The
+// shares are consecutive ranges of the bunch sequence, so the tiles come out
+// both in bunch order and in CTA order within each run; a run's tiles do not
+// depend on the other runs.
+struct SplitTile {
+  int bunch;
+  int64_t start;   // first particle within the bunch (a multiple of 4)
+  int count;
+  int cta;
+};
+
+std::vector<SplitTile> stream_split(const std::vector<int> &bunch_run, const std::vector<int64_t> &bunch_n, int G) {
+  constexpr int64_t kMaxCount = int64_t(1) << 28;
+  std::vector<SplitTile> out;
+  const size_t nbun = bunch_n.size();
+  auto padded = [&](size_t i) { return (bunch_n[i] + 3) / 4 * 4; };
+  size_t b0 = 0;
+  while (b0 < nbun) {
+    size_t b1 = b0;
+    int64_t P = 0;
+    while (b1 < nbun && bunch_run[b1] == bunch_run[b0]) P += padded(b1++);
+    size_t m = b0;
+    int64_t B = 0;   // padded start of bunch m within the run
+    for (int g = 0; g < G; ++g) {
+      const int64_t a = (P / 4) * g / G * 4, e = g + 1 == G ? P : (P / 4) * (g + 1) / G * 4;
+      while (m < b1 && B + padded(m) <= a) B += padded(m++);
+      int64_t Bm = B;
+      for (size_t mm = m; mm < b1 && Bm < e; ++mm) {
+        const int64_t pm = padded(mm);
+        const int64_t s0 = std::max(a, Bm) - Bm, s1 = std::min<int64_t>(std::min(e, Bm + pm) - Bm, bunch_n[mm]);
+        for (int64_t s = s0; s < s1; s += kMaxCount)
+          out.push_back(SplitTile{(int)mm, s, (int)std::min<int64_t>(kMaxCount, s1 - s), g});
+        Bm += pm;
+      }
+    }
+    b0 = b1;
+  }
+  return out;
+}
+
 // Upload a plan built in st's host vectors.
 mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
   st.release();
@@ -361,37 +406,23 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
   std::vector<int> sorder;   // tile indices in CTA order
   if (streaming) {
     const int G = slots;
-    constexpr int64_t kMaxCount = int64_t(1) << 28;
+    std::vector<int> brun(st.bunches.size());
+    std::vector<int64_t> bn(st.bunches.size());
+    for (size_t i = 0; i < st.bunches.size(); ++i) {
+      brun[i] = st.bunches[i].run;
+      bn[i] = st.bunches[i].n;
+    }
     std::vector<TileDev> tiles;
-    size_t b0 = 0;
-    for (size_t ri = 0; ri < st.runs.size(); ++ri) {
-      size_t b1 = b0;
-      int64_t P = 0;
-      while (b1 < st.bunches.size() && st.bunches[b1].run == (int)ri) P += (st.bunches[b1++].n + 3) / 4 * 4;
-      size_t m = b0;
-      int64_t B = 0;   // padded start of bunch m within the run
-      for (int g = 0; g < G; ++g) {
-        const int64_t a = (P / 4) * g / G * 4, e = g + 1 == G ? P : (P / 4) * (g + 1) / G * 4;
-        while (m < b1 && B + (st.bunches[m].n + 3) / 4 * 4 <= a) B += (st.bunches[m++].n + 3) / 4 * 4;
-        int64_t Bm = B;
-        for (size_t mm = m; mm < b1 && Bm < e; ++mm) {
-          const BunchDev &bd = st.bunches[mm];
-          const int64_t pm = (bd.n + 3) / 4 * 4;
-          const int64_t s0 = std::max(a, Bm) - Bm, s1 = std::min<int64_t>(std::min(e, Bm + pm) - Bm, bd.n);
-          for (int64_t s = s0; s < s1; s += kMaxCount) {
-            TileDev t{};
-            t.bunch = (int)mm;
-            t.run = bd.run;
-            t.m = bd.m;
-            t.start = s;
-            t.count = (int)std::min<int64_t>(kMaxCount, s1 - s);
-            tiles.push_back(t);
-            owner.push_back(g);
-          }
-          Bm += pm;
-        }
-      }
-      b0 = b1;
+    for (const SplitTile &sp : stream_split(brun, bn, G)) {
+      const BunchDev &bd = st.bunches[(size_t)sp.bunch];
+      TileDev t{};
+      t.bunch = sp.bunch;
+      t.run = bd.run;
+      t.m = bd.m;
+      t.start = sp.start;
+      t.count = sp.count;
+      tiles.push_back(t);
+      owner.push_back(sp.cta);
     }
     st.tiles.swap(tiles);
     for (BunchDev &bd : st.bunches) bd.tile0 = bd.ntiles = 0;
@@ -2029,6 +2060,38 @@ void mbt_batch_destroy(mbt_batch *b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   delete b;
+}
+
+mbt_status mbt_plan_streams(int nruns, const int64_t *run_n, const int32_t *run_nb, int any_transverse, int ctas,
+                            int *streams) {
+  if (nruns < 1 || !run_n || !run_nb || ctas < 1 || !streams) return MBT_ERR_ARG;
+  std::vector<int64_t> n(run_n, run_n + nruns);
+  std::vector<int> nb(run_nb, run_nb + nruns);
+  for (int i = 0; i < nruns; ++i)
+    if (n[(size_t)i] < 1 || nb[(size_t)i] < 1) return MBT_ERR_ARG;
+  *streams = plan_streams(n, nb, any_transverse != 0, ctas) ? 1 : 0;
+  return MBT_OK;
+}
+
+mbt_status mbt_plan_stream_split(int nb, const int32_t *run, const int64_t *n_mp, int ctas, int64_t *out,
+                                 int64_t cap, int64_t *ntiles) {
+  if (nb < 1 || !run || !n_mp || ctas < 1 || !ntiles || cap < 0 || (cap > 0 && !out)) return MBT_ERR_ARG;
+  std::vector<int> brun((size_t)nb);
+  std::vector<int64_t> bn((size_t)nb);
+  for (int i = 0; i < nb; ++i) {
+    if (n_mp[i] < 1 || run[i] < 0 || (i > 0 && run[i] < run[i - 1])) return MBT_ERR_ARG;
+    brun[(size_t)i] = run[i];
+    bn[(size_t)i] = n_mp[i];
+  }
+  const std::vector<SplitTile> t = stream_split(brun, bn, ctas);
+  *ntiles = (int64_t)t.size();
+  for (size_t k = 0; k < t.size() && (int64_t)k < cap; ++k) {
+    out[4 * k + 0] = t[k].bunch;
+    out[4 * k + 1] = t[k].start;
+    out[4 * k + 2] = t[k].count;
+    out[4 * k + 3] = t[k].cta;
+  }
+  return MBT_OK;
 }
 
 }  // extern "C"
