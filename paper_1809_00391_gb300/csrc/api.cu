@@ -438,7 +438,24 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
     std::vector<int> fill(first.begin(), first.end() - 1);
     for (size_t i = 0; i < st.tiles.size(); ++i) sorder[(size_t)fill[(size_t)owner[i]]++] = (int)i;
   }
+  // Moments jobs run beside the wake and tile jobs while every post CTA of
+  // the plan fits on the SMs at once (one CTA per SM); in larger plans they
+  // would only add waves, so each tile job sums its bunches' moments first.
+  bool fold = false;
+  if (mixed) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MBT_ERR_CUDA, "device attributes");
+    }
+    if ((int64_t)st.jobs.size() > (int64_t)nsm) {
+      fold = true;
+      st.jobs.erase(std::remove_if(st.jobs.begin(), st.jobs.end(), [](const PostJob &j) { return j.type == kJobMoments; }),
+                    st.jobs.end());
+    }
+  }
   Plan pl{};
+  pl.fold_moments = fold ? 1 : 0;
   if (!up(st.runs, &pl.runs) || !up(st.bunches, &pl.bunches) || !up(st.tiles, &pl.tiles) || !up(st.jobs, &pl.jobs))
     return fail(c, MBT_ERR_NOMEM, "plan upload failed");
   if (streaming) {

@@ -66,7 +66,8 @@ __device__ void post_stage(const Plan &p, const RunDev *__restrict__ R, const Po
     if (tid == 32) prefetch_l2(R->carry);   // read by whichever CTA finishes last
   } else if (job.type == kJobWake && tid < kBunchTile) {
     st->qf[tid] = tid < nbt ? R->q_mp_f[m0 + tid] : 0.f;
-  } else if (job.type == kJobMoments && tid < nbt) {
+  }
+  if ((job.type == kJobMoments || (job.type == kJobTile && p.fold_moments)) && tid < nbt) {
     const BunchDev bd = p.bunches[R->bunch_base + m0 + tid];
     st->tile0[tid] = bd.tile0;
     st->ntiles[tid] = bd.ntiles;
@@ -623,9 +624,13 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   const int par = (int)(turn & 1);
   if (job.type == kJobWake)
     wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
-  else if (job.type == kJobTile)
+  else if (job.type == kJobTile) {
+    if (p.fold_moments) {
+      moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
+      __syncthreads();
+    }
     tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
-  else if (job.type == kJobMoments)
+  } else if (job.type == kJobMoments)
     moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
   else
     trans_job_f32(R, job, par, sm_post);
