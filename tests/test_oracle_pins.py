@@ -290,6 +290,37 @@ def test_short_range_voltage_is_causal_convolution(oracle_mod):
     np.testing.assert_allclose(s.vsr_direct(h1 + h2, q), s.vsr_direct(h1, q) + s.vsr_direct(h2, q), rtol=1e-13, atol=1e-25)
 
 
+@pytest.mark.parametrize("ngp", [False, True])
+def test_kick_voltage_interpolates_between_cell_centres(oracle_mod, ngp):
+    """The short-range voltage a particle is kicked with (Sec. 2.3): the cell
+    voltages taken at the cell centres and interpolated linearly between them
+    (numpy's interp, which holds the end values beyond the outermost
+    centres), or the particle's own cell with the nearest-grid-point option;
+    zero outside the mesh."""
+    bb = dict(W.BROADBAND)
+    s = _sim(oracle_mod, res=[bb], buckets=[0], currents=[1e-3], n_mp=[1000], nbins=32,
+             flags=oracle_mod.KICK_NGP if ngp else 0)
+    rng = np.random.default_rng(9)
+    s.feed_histograms(rng.integers(0, 60, size=(1, 32)).astype(np.int32))
+    V = s.vsr()[0]
+    assert np.max(np.abs(V)) > 0
+    dv = s.derived
+    H, D = dv["H"], dv["Delta"]
+    centres = -H + (np.arange(32) + 0.5) * D
+    taus = np.concatenate([centres, -H + (np.arange(33)) * D * (1 - 1e-12) + 1e-30,
+                           rng.uniform(-H, H, 300)])
+    for tau in taus:
+        x = (tau + H) / D
+        if ngp:
+            expect = V[min(int(np.floor(x)), 31)]
+        else:
+            expect = np.interp(tau, centres, V)
+        got = s.wake_voltage_at(0, float(tau))
+        assert got == pytest.approx(expect, rel=1e-12, abs=1e-12 * np.max(np.abs(V))), tau
+    for tau in (-H - 0.25 * D, -H - 3 * D, H + 1e-3 * D, H + 2 * D):
+        assert s.wake_voltage_at(0, tau) == 0.0
+
+
 def test_long_range_is_the_wake_of_every_earlier_passage(oracle_mod):
     """After feeding histograms for a few turns, the long-range voltage at a
     particle equals the sum over earlier passages of q * count * W(dt + tau -
