@@ -43,6 +43,10 @@ fill with a horizontal plane (beta 10 m, tune 0.31, chromaticity 1.5,
 1 nm) and a transverse HOM (200 kOhm/m, 1.5 GHz, Q 2e4, short and long
 range) besides the longitudinal wakes, and prints its throughput and the
 push roofline (40 B per macro-particle-turn: tau, delta, x, x').
+
+FP64 tracker: python bench.py --workload three_f64 tracks three bunches of
+1e5 macro-particles (broadband + HOM, long and short range) on the FP64 path
+and prints its throughput and the FP64 push's time per launch.
 """
 from __future__ import annotations
 
@@ -85,7 +89,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
-    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t"],
+    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t", "three_f64"],
                     default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
@@ -522,6 +526,54 @@ def hcscan_bench(args, rank, local):
     return 0
 
 
+def three_f64_bench(args, rank, local):
+    """Three bunches x 1e5 macro-particles, broadband + HOM, on the FP64
+    tracker: throughput, and the FP64 push's time per launch.  The FP64 path
+    is bound by the FP64 pipe; its utilisation comes from the ncu counters
+    (sm__inst_executed_pipe_fp64), not from a byte count."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    run = W.three_bunches(seed=1)
+    K, Wm, KR = min(args.steps, 2000), max(args.warmup, 3), 300
+    stream = torch.cuda.current_stream()
+    tr = pkg.tracker_for_run(run, record_turns=K + Wm + 2 * GRAPH_TURNS + KR + 16)
+    tr.init_particles(stream)
+    tr.set_graph(GRAPH_TURNS)
+    tr.track(max(Wm, GRAPH_TURNS), stream)
+    tr.sync()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        tr.track(K, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    tr.sync()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    tr.set_timing(True)
+    tr.track(KR, stream)
+    tr.sync()
+    push_ms, post_ms, launches = tr.timing()
+    tr.set_timing(False)
+    n = run.n_particles
+    line = {"metric": "macro-particle-turns/s (3 bunches, FP64 tracker)", "value": n * K / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": run.name, "turns_timed": K, "l2": "state 4.8 MB: L2-resident (FP64-pipe bound)"},
+            "roofline": {"bound": "fp64 pipe", "kernel": "k_push_f64", "unit_count": n,
+                         "push_us": push_ms / max(1, launches) * 1e3, "post_us": post_ms / max(1, launches) * 1e3,
+                         "utilisation": "ncu sm__inst_executed_pipe_fp64 (profiles/push_f64_three_bunches.md)"},
+            "gpu_launches": 2 * K, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    tr.close()
+    return 0
+
+
 def fill390t_bench(args, rank, local):
     """The 390-bunch fill with a transverse plane: throughput and push roofline."""
     if rank != 0:
@@ -595,6 +647,8 @@ def main():
         return rwscan_bench(args, rank, local)
     if args.workload == "hcscan":
         return hcscan_bench(args, rank, local)
+    if args.workload == "three_f64":
+        return three_f64_bench(args, rank, local)
     if args.workload == "fill390t":
         return fill390t_bench(args, rank, local)
 
