@@ -1,5 +1,5 @@
 // Post-turn kernel: everything that follows the push of a turn, for every run
-// of the plan, in one launch.  Two kinds of CTA (PostJob):
+// of the plan, in one launch, one CTA per job (PostJob):
 //
 //  kJobWake  short-range wake voltage of a tile of bunches (Sec. 2.3, Eq. 6):
 //            V[j, m] = q_m sum_{k<=j} W~((j-k) Delta) count[m, k], a lower
@@ -10,12 +10,18 @@
 //            planes laid side by side along N; FP32 accumulation in tensor
 //            memory; the planes are recombined in the epilogue.  kF64: FP64
 //            on the CUDA cores.
-//  kJobTile  for a tile of up to 32 bunches: per-bunch moments of the turn
-//            into the record ring (Sec. 2.4), zeroing of the other histogram
-//            buffer, and for each long-range resonator the emission
-//            E_m = c q_m sum_k count[m,k] e^{-s tau_k} and the warp-level
-//            prefix scan of the phasor affine maps x -> a_m (x + E_{m-1})
-//            across the tile (long-range wake, Sec. 2.3 last paragraph).
+//  kJobTile  for a tile of up to 32 bunches and each long-range resonator:
+//            the emission E_m = c q_m sum_k count[m,k] e^{-s tau_k} and the
+//            warp-level prefix scan of the phasor affine maps
+//            x -> a_m (x + E_{m-1}) across the tile (long-range wake,
+//            Sec. 2.3 last paragraph).
+//  kJobMoments  (kMixed) per-bunch moments of the turn into the record ring
+//            (Sec. 2.4) and zeroing of the other histogram buffer.  When the
+//            plan's post CTAs would outnumber the SMs there is no moments
+//            job (Plan::fold_moments) and the tile job does this first, as
+//            the kF64 tile job always does.
+//  kJobTrans  transverse short-range voltage of a tile of bunches (rows of
+//            the dipole-sum convolution), for runs with a transverse plane.
 //
 // The last CTA to finish (completion counter) composes the tile aggregates
 // of each (run, resonator) with the carried phasor of the previous turn,
@@ -78,7 +84,8 @@ __device__ void post_stage(const Plan &p, const RunDev *__restrict__ R, const Po
 }
 
 // ---------------------------------------------------------------------------
-// Tile job: moments, histogram reset, long-range emission + local scan.
+// Moments and histogram reset of a bunch tile (moments job, or the first part
+// of a tile job: kF64, and kMixed plans with fold_moments).
 // ---------------------------------------------------------------------------
 // Per-bunch moments of the turn into the record ring (Sec. 2.4): thread
 // (value c, bunch b) sums the push-tile partials of bunch m0+b in a fixed

@@ -141,7 +141,7 @@ struct alignas(16) StreamTile {
 static_assert(sizeof(StreamTile) == 128, "bulk-copy size");
 
 struct PostJob {
-  int run, type, bt, sub;     // kJobWake: sub = M-tile (kMixed) or (bunch, row chunk) (kF64)
+  int run, type, bt, sub;     // kJobWake: sub = M-tile (kMixed) or (bunch, row chunk) (kF64); kJobTrans: row chunk
 };
 
 // A batch of runs tracked by the same launches.
