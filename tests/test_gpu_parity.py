@@ -288,6 +288,46 @@ def test_batch_equals_alone(pkg, prec):
         t.close()
 
 
+def test_streaming_batch_equals_alone(pkg):
+    """Two runs large enough for the streaming push (one with ragged and tiny
+    bunches), tracked alone and as one batch in which every CTA takes one
+    share of each run: particles, histograms, wakes and moments bit for bit."""
+    runs = [W.Run(W.ring_r0(), [dict(W.BROADBAND), dict(W.HOM)], np.arange(30, dtype=np.int32), np.full(30, 0.5e-3),
+                  np.full(30, 90_000, np.int64), seed=51, turns=12, precision=W.PREC_MIXED),
+            W.Run(W.ring_r0(484), [dict(W.BROADBAND), dict(W.HOM, fr_Hz=1.7e9)], np.arange(100, 127, dtype=np.int32),
+                  np.full(27, 0.8e-3), np.array([100_003] * 26 + [37], np.int64), seed=52, turns=12,
+                  precision=W.PREC_MIXED)]
+
+    def state(t, r):
+        h, out = t.histograms()
+        v, phi = t.wake()
+        return [t.particles(m) for m in range(r.nb)], h, out, v, phi, t.moments(0, r.turns)
+
+    alone = []
+    for r in runs:
+        t = pkg.tracker_for_run(r)
+        t.init_particles()
+        t.track(r.turns)
+        assert t.info["push_ctas"] > 0
+        alone.append(state(t, r))
+        t.close()
+    ts = [pkg.tracker_for_run(r) for r in runs]
+    for t in ts:
+        t.init_particles()
+    bt = pkg.Batch(ts)
+    bt.track(12)
+    bt.sync()
+    for t, r, ref in zip(ts, runs, alone):
+        got = state(t, r)
+        for m in range(r.nb):
+            assert np.array_equal(got[0][m][0], ref[0][m][0]) and np.array_equal(got[0][m][1], ref[0][m][1]), m
+        for a, b in zip(got[1:], ref[1:]):
+            assert np.array_equal(a, b)
+    bt.close()
+    for t in ts:
+        t.close()
+
+
 @pytest.mark.parametrize("prec", [W.PREC_F64, W.PREC_MIXED])
 def test_checkpoint_resume_is_bit_identical(pkg, prec):
     run = W.Run(W.ring_r0(), [dict(W.BROADBAND), dict(W.HOM)], np.array([0, 1, 2], np.int32), np.full(3, 1e-3),
