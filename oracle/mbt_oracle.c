@@ -204,6 +204,7 @@ void orc_derive_h(const orc_ring *r, int flags, int nharm, const orc_harmonic *h
     d->sigma_tau0 = fabs(r->alpha_c) * r->sigma_delta * r->T0_s / (2.0 * pi * d->nu_s);
 }
 
+/* orc_derive_h without harmonic cavities. */
 void orc_derive(const orc_ring *r, int flags, orc_derived *d)
 {
     orc_derive_h(r, flags, 0, NULL, d);
@@ -397,6 +398,9 @@ static double table_integral(int n, const double *t, const double *W, double lo,
     return acc;
 }
 
+/* A tabulated short-range wake W(t_i), linear between samples (reading R13):
+ * its average over every lag cell is added to the lag wake.  -1 (nothing
+ * added) unless t_0 = 0 and the times increase. */
 int orc_add_wake_table(orc_sim *s, int n, const double *t, const double *W)
 {
     if (n < 2 || t[0] != 0.0)
@@ -420,6 +424,7 @@ orc_sim *orc_create(const orc_ring *ring, int flags, uint64_t seed,
     return orc_create_h(ring, flags, seed, nres, res, 0, NULL, nbins, half_width_sigmas, nb, bucket, current_A, n_mp);
 }
 
+/* Frees the simulation and everything it owns. */
 void orc_destroy(orc_sim *s)
 {
     if (!s)
@@ -501,6 +506,9 @@ int orc_set_transverse(orc_sim *s, double beta_m, double alpha, double nu0, doub
     return 0;
 }
 
+/* Derived quantities of orc_derive_h and the mesh, as 12 doubles: T_rf,
+ * omega_rf, phi_s, D, excitation amplitude, nu_s, sigma_tau0, H, Delta,
+ * 1/Delta, histogram count, turn. */
 void orc_get_derived(const orc_sim *s, double out[12])
 {
     out[0] = s->dv.T_rf; out[1] = s->dv.omega_rf; out[2] = s->dv.phi_s; out[3] = s->dv.D;
@@ -537,6 +545,7 @@ void orc_init_particles(orc_sim *s)
     }
 }
 
+/* Accessors: tau, delta of bunch m (n_mp[m] each). */
 void orc_set_particles(orc_sim *s, int m, const double *tau, const double *delta)
 {
     memcpy(s->tau[m], tau, sizeof(double) * s->n_mp[m]);
@@ -699,6 +708,8 @@ int orc_add_transverse_rw(orc_sim *s, double radius_m, double sigma, double leng
     return 0;
 }
 
+/* The summed dipole resistive-wall wake of orc_add_transverse_rw at delay t:
+ * rw_A / sqrt(t) for t > 0, zero otherwise (causality). */
 double orc_transverse_rw_wake(const orc_sim *s, double t)
 {
     return t > 0.0 ? s->rw_A / sqrt(t) : 0.0;
@@ -964,11 +975,15 @@ void orc_track2(orc_sim *s, int64_t nturns, double *rec, double *trec)
     }
 }
 
+/* orc_track2 without the transverse record. */
 void orc_track(orc_sim *s, int64_t nturns, double *rec)
 {
     orc_track2(s, nturns, rec, NULL);
 }
 
+/* Accessors (copies in and out of the simulation's arrays): transverse
+ * coordinates of bunch m, dipole sums [nb][nbins], transverse voltage
+ * [nb][nbins]. */
 void orc_set_tparticles(orc_sim *s, int m, const double *x, const double *xp)
 {
     memcpy(s->x[m], x, sizeof(double) * s->n_mp[m]);
@@ -1000,6 +1015,8 @@ void orc_get_atlr(const orc_sim *s, double *A)
     }
 }
 
+/* Accessors: histograms [nb][nbins] and out-of-mesh counts [nb] of the
+ * last turn, short-range voltage [nb][nbins], lag wake [nbins]. */
 void orc_get_hist(const orc_sim *s, int32_t *hist, int64_t *out_count)
 {
     memcpy(hist, s->hist, sizeof(int32_t) * (size_t)s->nb * s->nbins);
