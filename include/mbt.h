@@ -56,7 +56,7 @@ enum {
     MBT_ERR_NOMEM = 3,        /* device or host allocation failed                      */
     MBT_ERR_CUDA = 4,         /* a CUDA runtime call or kernel failed                  */
     MBT_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up                    */
-    MBT_ERR_UNSUPPORTED = 6,  /* configuration outside what this build implements      */
+    MBT_ERR_UNSUPPORTED = 6,  /* configuration outside what the library implements    */
     MBT_ERR_BUDGET = 7        /* request exceeds the memory budget (serving)           */
 };
 
