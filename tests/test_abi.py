@@ -104,6 +104,41 @@ def test_binding_fails_loudly_without_library(pkg, monkeypatch, tmp_path):
         p.lib()
 
 
+def test_fill_is_validated_before_any_device_work(pkg):
+    """mbt_set_fill rejects bad fills on the host (MBT_ERR_ARG, with a message);
+    a valid fill needs the GPU and, without one, fails loudly with
+    MBT_ERR_CUDA: there is no CPU path behind the boundary."""
+    import ctypes
+    L = pkg.lib()
+    st, h = _create(pkg, W.ring_r0(), prec=1)
+    assert st == 0
+
+    def fill(b, c, n):
+        b = np.ascontiguousarray(b, np.int32)
+        c = np.ascontiguousarray(c, np.float64)
+        n = np.ascontiguousarray(n, np.int64)
+        return L.mbt_set_fill(h, len(b), pkg._ptr(b, ctypes.c_int32), pkg._ptr(c, ctypes.c_double),
+                              pkg._ptr(n, ctypes.c_int64))
+
+    bad = [([0, 0], [1e-3, 1e-3], [10, 10]),      # buckets not strictly increasing
+           ([3, 1], [1e-3, 1e-3], [10, 10]),
+           ([480], [1e-3], [10]),                 # bucket outside [0, h)
+           ([-1], [1e-3], [10]),
+           ([0], [-1e-3], [10]),                  # negative current
+           ([0], [float("nan")], [10]),
+           ([0], [1e-3], [0]),                    # empty bunch
+           ([0], [1e-3], [1 << 24])]              # mixed precision: at most 2^24 - 1 per bunch
+    for b, c, n in bad:
+        assert fill(b, c, n) == 1, (b, c, n)
+        assert L.mbt_last_error(h)
+    assert L.mbt_set_fill(h, 0, None, None, None) == 1
+    import torch
+    if not torch.cuda.is_available():
+        assert fill([0, 3], [1e-3, 1e-3], [100, 37]) == 4
+        assert b"CUDA" in L.mbt_last_error(h)
+    L.mbt_destroy(h)
+
+
 def test_new_entry_points_validate_their_arguments(pkg):
     import ctypes
     L = pkg.lib()
