@@ -104,6 +104,17 @@ def test_binding_fails_loudly_without_library(pkg, monkeypatch, tmp_path):
         p.lib()
 
 
+def test_tracker_fails_loudly_without_a_gpu(pkg):
+    """The Python API has no CPU path either: on a machine without a GPU,
+    building a tracker raises MBTError with MBT_ERR_CUDA at mbt_set_fill."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pkg.MBTError) as e:
+        pkg.tracker_for_run(W.single_bunch())
+    assert e.value.status == 4 and "CUDA" in str(e.value)
+
+
 def test_fill_is_validated_before_any_device_work(pkg):
     """mbt_set_fill rejects bad fills on the host (MBT_ERR_ARG, with a message);
     a valid fill needs the GPU and, without one, fails loudly with
