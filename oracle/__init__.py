@@ -33,15 +33,21 @@ NO_QE = 2
 KICK_NGP = 4
 
 
+def compile_source(src: Path, out: Path) -> Path:
+    """gcc -O2 without floating-point contraction: the oracle's build flags."""
+    tmp = Path(out).with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", str(tmp), str(src), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return Path(out)
+
+
 def build(force: bool = False) -> Path:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, no contraction)."""
     _BUILD.mkdir(exist_ok=True)
     if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
-        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", str(tmp), str(_SRC), "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+        compile_source(_SRC, _LIB_PATH)
     return _LIB_PATH
 
 
@@ -73,62 +79,73 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(str(build()))
-            lib.orc_philox4x32_10.argtypes = [_P(_u32), _P(_u32), _P(_u32)]
-            lib.orc_u01.argtypes = [_u32]
-            lib.orc_u01.restype = _d
-            lib.orc_box_muller.argtypes = [_d, _d, _P(_d), _P(_d)]
-            lib.orc_normal_quad.argtypes = [_u64, _u32, _u32, _u32, _u32, _P(_d)]
-            lib.orc_derive.argtypes = [_P(Ring), ctypes.c_int, _P(_d)]
-            lib.orc_wake.argtypes = [_P(Resonator), _d]
-            lib.orc_wake.restype = _d
-            lib.orc_create.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator),
-                                       ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
-            lib.orc_create.restype = ctypes.c_void_p
-            lib.orc_create_h.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator), ctypes.c_int,
-                                         _P(Harmonic), ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
-            lib.orc_create_h.restype = ctypes.c_void_p
-            lib.orc_derive_h.argtypes = [_P(Ring), ctypes.c_int, ctypes.c_int, _P(Harmonic), _P(_d)]
-            lib.orc_destroy.argtypes = [ctypes.c_void_p]
-            lib.orc_get_derived.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_init_particles.argtypes = [ctypes.c_void_p]
-            lib.orc_set_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
-            lib.orc_get_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
-            lib.orc_cell_coord.argtypes = [ctypes.c_void_p, _d]
-            lib.orc_cell_coord.restype = _d
-            lib.orc_bin.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_i32)]
-            lib.orc_bin.restype = _i64
-            lib.orc_vsr_direct.argtypes = [ctypes.c_void_p, _P(_i32), _d, _P(_d)]
-            lib.orc_track.argtypes = [ctypes.c_void_p, _i64, _P(_d)]
-            lib.orc_get_hist.argtypes = [ctypes.c_void_p, _P(_i32), _P(_i64)]
-            lib.orc_get_vsr.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_get_alr.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_get_wlag.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_feed_histograms.argtypes = [ctypes.c_void_p, _P(_i32)]
-            lib.orc_get_last_emission.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d)]
-            lib.orc_wake_voltage_at.argtypes = [ctypes.c_void_p, ctypes.c_int, _d]
-            lib.orc_wake_voltage_at.restype = _d
-            lib.orc_turn.argtypes = [ctypes.c_void_p]
-            lib.orc_turn.restype = _i64
-            lib.orc_add_wake_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
-            lib.orc_add_wake_table.restype = ctypes.c_int
-            lib.orc_twake.argtypes = [_P(Resonator), _d]
-            lib.orc_twake.restype = _d
-            lib.orc_set_transverse.argtypes = [ctypes.c_void_p, _d, _d, _d, _d, _d, ctypes.c_int, _P(Resonator)]
-            lib.orc_set_transverse.restype = ctypes.c_int
-            lib.orc_track2.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_d)]
-            lib.orc_set_tparticles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
-            lib.orc_get_tparticles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
-            lib.orc_get_dip.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_get_vt.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_get_atlr.argtypes = [ctypes.c_void_p, _P(_d)]
-            lib.orc_vt_direct.argtypes = [ctypes.c_void_p, _P(_d), _d, _P(_d)]
-            lib.orc_add_transverse_rw.argtypes = [ctypes.c_void_p, _d, _d, _d, ctypes.c_int]
-            lib.orc_add_transverse_rw.restype = ctypes.c_int
-            lib.orc_transverse_rw_wake.argtypes = [ctypes.c_void_p, _d]
-            lib.orc_transverse_rw_wake.restype = _d
-            _lib = lib
+            _lib = load_library(build())
     return _lib
+
+
+def load_library(path) -> ctypes.CDLL:
+    """A compiled oracle library with its entry points typed (the tests also
+    load deliberately mutated builds of the source to show that a pin fails
+    on them)."""
+    lib = ctypes.CDLL(str(path))
+    lib.orc_philox4x32_10.argtypes = [_P(_u32), _P(_u32), _P(_u32)]
+    lib.orc_u01.argtypes = [_u32]
+    lib.orc_u01.restype = _d
+    lib.orc_box_muller.argtypes = [_d, _d, _P(_d), _P(_d)]
+    lib.orc_normal_quad.argtypes = [_u64, _u32, _u32, _u32, _u32, _P(_d)]
+    lib.orc_derive.argtypes = [_P(Ring), ctypes.c_int, _P(_d)]
+    lib.orc_wake.argtypes = [_P(Resonator), _d]
+    lib.orc_wake.restype = _d
+    lib.orc_create.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator),
+                               ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
+    lib.orc_create.restype = ctypes.c_void_p
+    lib.orc_create_h.argtypes = [_P(Ring), ctypes.c_int, _u64, ctypes.c_int, _P(Resonator), ctypes.c_int,
+                                 _P(Harmonic), ctypes.c_int, _d, ctypes.c_int, _P(_i32), _P(_d), _P(_i64)]
+    lib.orc_create_h.restype = ctypes.c_void_p
+    lib.orc_derive_h.argtypes = [_P(Ring), ctypes.c_int, ctypes.c_int, _P(Harmonic), _P(_d)]
+    lib.orc_destroy.argtypes = [ctypes.c_void_p]
+    lib.orc_get_derived.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_init_particles.argtypes = [ctypes.c_void_p]
+    lib.orc_set_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+    lib.orc_get_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+    lib.orc_cell_coord.argtypes = [ctypes.c_void_p, _d]
+    lib.orc_cell_coord.restype = _d
+    lib.orc_bin.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_i32)]
+    lib.orc_bin.restype = _i64
+    lib.orc_vsr_direct.argtypes = [ctypes.c_void_p, _P(_i32), _d, _P(_d)]
+    lib.orc_track.argtypes = [ctypes.c_void_p, _i64, _P(_d)]
+    lib.orc_get_hist.argtypes = [ctypes.c_void_p, _P(_i32), _P(_i64)]
+    lib.orc_get_vsr.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_get_alr.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_get_wlag.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_feed_histograms.argtypes = [ctypes.c_void_p, _P(_i32)]
+    lib.orc_get_last_emission.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d)]
+    lib.orc_wake_voltage_at.argtypes = [ctypes.c_void_p, ctypes.c_int, _d]
+    lib.orc_wake_voltage_at.restype = _d
+    lib.orc_turn.argtypes = [ctypes.c_void_p]
+    lib.orc_turn.restype = _i64
+    lib.orc_add_wake_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+    lib.orc_add_wake_table.restype = ctypes.c_int
+    lib.orc_twake.argtypes = [_P(Resonator), _d]
+    lib.orc_twake.restype = _d
+    lib.orc_set_transverse.argtypes = [ctypes.c_void_p, _d, _d, _d, _d, _d, ctypes.c_int, _P(Resonator)]
+    lib.orc_set_transverse.restype = ctypes.c_int
+    lib.orc_track2.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_d)]
+    lib.orc_set_tparticles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+    lib.orc_get_tparticles.argtypes = [ctypes.c_void_p, ctypes.c_int, _P(_d), _P(_d)]
+    lib.orc_get_dip.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_get_vt.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_get_atlr.argtypes = [ctypes.c_void_p, _P(_d)]
+    lib.orc_vt_direct.argtypes = [ctypes.c_void_p, _P(_d), _d, _P(_d)]
+    lib.orc_add_transverse_rw.argtypes = [ctypes.c_void_p, _d, _d, _d, ctypes.c_int]
+    lib.orc_add_transverse_rw.restype = ctypes.c_int
+    lib.orc_transverse_rw_wake.argtypes = [ctypes.c_void_p, _d]
+    lib.orc_transverse_rw_wake.restype = _d
+    lib.orc_tvoltage_at.argtypes = [ctypes.c_void_p, ctypes.c_int, _d]
+    lib.orc_tvoltage_at.restype = _d
+    lib.orc_deposit.argtypes = [ctypes.c_void_p, _i64, _P(_d), _P(_d), _P(_i32), _P(_d)]
+    lib.orc_deposit.restype = _i64
+    return lib
 
 
 def _ptr(a: np.ndarray, ct):
@@ -260,8 +277,8 @@ class OracleSim:
 
     def __init__(self, ring: dict, resonators: list, nbins: int, half_width_sigmas: float,
                  buckets, currents_A, n_mp, seed: int, flags: int = 0, wake_tables=(), resistive_wall=(),
-                 harmonic_cavities=(), transverse=None):
-        self._lib = _load()
+                 harmonic_cavities=(), transverse=None, lib=None):
+        self._lib = lib if lib is not None else _load()
         self.nb = len(buckets)
         self.nbins = int(nbins)
         self.nres = len(resonators)
@@ -395,6 +412,21 @@ class OracleSim:
 
     def wake_voltage_at(self, m: int, tau: float) -> float:
         return self._lib.orc_wake_voltage_at(self._h, int(m), float(tau))
+
+    def tvoltage_at(self, m: int, tau: float) -> float:
+        """Transverse kick voltage on a particle of bunch m at tau (short range,
+        long-range resonators and resistive wall of the previous turn)."""
+        return self._lib.orc_tvoltage_at(self._h, int(m), float(tau))
+
+    def deposit(self, tau, x):
+        """(counts, dipole sums, outside count) of particles (tau, x) on the mesh."""
+        t = np.ascontiguousarray(tau, np.float64)
+        xx = np.ascontiguousarray(x, np.float64)
+        assert t.shape == xx.shape
+        h = np.empty(self.nbins, np.int32)
+        d = np.empty(self.nbins, np.float64)
+        out = self._lib.orc_deposit(self._h, t.size, _ptr(t, _d), _ptr(xx, _d), _ptr(h, _i32), _ptr(d, _d))
+        return h, d, int(out)
 
     def transverse_rw_wake(self, t: float) -> float:
         return self._lib.orc_transverse_rw_wake(self._h, float(t))

@@ -751,6 +751,23 @@ static double vtlr_at(const orc_sim *s, int m, double tau)
     return v;
 }
 
+/* The transverse kick voltage on a particle of bunch m at tau (Eq. 6, second
+ * line, with the previous turn's wake): short range at its cell coordinate,
+ * long-range resonators, long-range resistive wall. */
+double orc_tvoltage_at(const orc_sim *s, int m, double tau)
+{
+    return vt_at(s, m, orc_cell_coord(s, tau)) + vtlr_at(s, m, tau) + (s->Vrw ? s->Vrw[m] : 0.0);
+}
+
+/* Dipole deposit of one particle (offset x) at arrival time tau into the
+ * bunch's per-cell sums: the cell that binning gives it, nothing outside. */
+static void deposit_dip(const orc_sim *s, double tau, double x, double *dip)
+{
+    double xc = orc_cell_coord(s, tau);
+    if (xc >= 0.0 && xc < (double)s->nbins)
+        dip[(int)xc] += x;
+}
+
 /* Transverse short-range voltage of one bunch from its dipole sums (sum of x
  * per cell): V[j] = q * sum_{k<=j} dip[k] * Wt((j-k) Delta), Eq. 6 second line. */
 void orc_vt_direct(const orc_sim *s, const double *dip, double q, double *V)
@@ -846,7 +863,7 @@ static void one_turn(orc_sim *s)
                 if (s->trans) {
                     double x = s->x[m][i + e], xp = s->xp[m][i + e];
                     /* transverse wake kick (Eq. 6, second line), previous turn's wake */
-                    double Vt = vt_at(s, m, orc_cell_coord(s, t)) + vtlr_at(s, m, t) + (s->Vrw ? s->Vrw[m] : 0.0);
+                    double Vt = orc_tvoltage_at(s, m, t);
                     xp = xp + Vt / s->ring.E0_eV;
                     /* Eq. 5, x' line: momentum ratio across the cavity */
                     xp = xp * (1.0 + d_before) / (1.0 + d_gain);
@@ -867,11 +884,8 @@ static void one_turn(orc_sim *s)
                 delta[i + e] = d;
                 /* binning (Sec. 2.3); dipole sums of the same cells */
                 out += bin_one(s, t, hist);
-                if (dip) {
-                    double xc = orc_cell_coord(s, t);
-                    if (xc >= 0.0 && xc < (double)s->nbins)
-                        dip[(int)xc] += s->x[m][i + e];
-                }
+                if (dip)
+                    deposit_dip(s, t, s->x[m][i + e], dip);
             }
         }
         s->out_count[m] = out;
@@ -1074,6 +1088,21 @@ void orc_get_last_emission(const orc_sim *s, int r, double *E)
         E[2 * m] = creal(Er[m]);
         E[2 * m + 1] = cimag(Er[m]);
     }
+}
+
+/* Binning and dipole deposit of n given particles (arrival times tau,
+ * offsets x) as a turn does them: hist and dip (nbins each) are overwritten;
+ * returns the number outside the mesh.  For tests. */
+int64_t orc_deposit(const orc_sim *s, int64_t n, const double *tau, const double *x, int32_t *hist, double *dip)
+{
+    memset(hist, 0, sizeof(int32_t) * s->nbins);
+    memset(dip, 0, sizeof(double) * s->nbins);
+    int64_t out = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        out += bin_one(s, tau[i], hist);
+        deposit_dip(s, tau[i], x[i], dip);
+    }
+    return out;
 }
 
 /* Kick-free single-particle evaluation of the wake voltage seen at tau by a

@@ -15,6 +15,7 @@ from scipy import linalg, stats
 import mbt_workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _ring(**kw):
@@ -297,9 +298,13 @@ def test_kick_voltage_interpolates_between_cell_centres(oracle_mod, ngp):
     (numpy's interp, which holds the end values beyond the outermost
     centres), or the particle's own cell with the nearest-grid-point option;
     zero outside the mesh."""
+    check_kick_interpolation(oracle_mod, ngp)
+
+
+def check_kick_interpolation(oracle_mod, ngp, lib=None):
     bb = dict(W.BROADBAND)
-    s = _sim(oracle_mod, res=[bb], buckets=[0], currents=[1e-3], n_mp=[1000], nbins=32,
-             flags=oracle_mod.KICK_NGP if ngp else 0)
+    s = oracle_mod.OracleSim(W.ring_r0(), [bb], 32, 5.0, [0], [1e-3], [1000], 1,
+                             oracle_mod.KICK_NGP if ngp else 0, lib=lib)
     rng = np.random.default_rng(9)
     s.feed_histograms(rng.integers(0, 60, size=(1, 32)).astype(np.int32))
     V = s.vsr()[0]
@@ -319,6 +324,109 @@ def test_kick_voltage_interpolates_between_cell_centres(oracle_mod, ngp):
         assert got == pytest.approx(expect, rel=1e-12, abs=1e-12 * np.max(np.abs(V))), tau
     for tau in (-H - 0.25 * D, -H - 3 * D, H + 1e-3 * D, H + 2 * D):
         assert s.wake_voltage_at(0, tau) == 0.0
+
+
+@pytest.mark.parametrize("ngp", [False, True])
+def test_transverse_kick_voltage_interpolates_between_cell_centres(oracle_mod, ngp):
+    """The transverse short-range voltage a particle is kicked with (Eq. 6,
+    second line): as the longitudinal one, the cell voltages at the cell
+    centres interpolated linearly (numpy's interp, end values held), or the
+    particle's own cell with the nearest-grid-point option; zero outside the
+    mesh.  The cell voltages come from a tracked turn of offset particles, so
+    that the voltage a turn builds is the one the check evaluates."""
+    check_transverse_kick_interpolation(oracle_mod, ngp)
+
+
+def check_transverse_kick_interpolation(oracle_mod, ngp, lib=None):
+    nb, n = 32, 2000
+    s = oracle_mod.OracleSim(W.ring_r0(), [], nb, 5.0, [0], [2e-3], [n], 3,
+                             (oracle_mod.KICK_NGP if ngp else 0) | W.NO_QE, lib=lib,
+                             transverse=_tplane(resonators=[dict(TRES, range=W.RANGE_SHORT)]))
+    rng = np.random.default_rng(21)
+    dv = s.derived
+    H, D = dv["H"], dv["Delta"]
+    s.set_particles(0, rng.normal(0.0, 0.4 * H, n), rng.normal(0.0, 9e-4, n))
+    s.set_tparticles(0, rng.normal(2e-4, 1e-4, n), np.zeros(n))
+    s.track(1, record=False)
+    V = s.vt()[0]
+    assert np.max(np.abs(V)) > 0 and np.count_nonzero(V) > nb // 2
+    centres = -H + (np.arange(nb) + 0.5) * D
+    taus = np.concatenate([centres, -H + (np.arange(nb + 1)) * D * (1 - 1e-12) + 1e-30,
+                           rng.uniform(-H, H, 300)])
+    for tau in taus:
+        x = (tau + H) / D
+        expect = V[min(int(np.floor(x)), nb - 1)] if ngp else np.interp(tau, centres, V)
+        got = s.tvoltage_at(0, float(tau))
+        assert got == pytest.approx(expect, rel=1e-12, abs=1e-12 * np.max(np.abs(V))), tau
+    for tau in (-H - 0.25 * D, -H - 3 * D, H + 1e-3 * D, H + 2 * D):
+        assert s.tvoltage_at(0, tau) == 0.0
+
+
+def test_dipole_deposit_brute_force(oracle_mod):
+    """The dipole sums of the transverse wake (Eq. 6, second line): every
+    particle's offset lands in the cell binning gives it (hand-placed at
+    edges, centres and outside, as in the binning check), nothing outside;
+    and a tracked turn's sums are exactly this deposit of its particles."""
+    check_dipole_deposit(oracle_mod)
+
+
+def check_dipole_deposit(oracle_mod, lib=None):
+    s = oracle_mod.OracleSim(W.ring_r0(), [], 16, 5.0, [0], [1e-3], [64], 5, W.NO_QE, lib=lib,
+                             transverse=_tplane(resonators=[dict(TRES, range=W.RANGE_SHORT)]))
+    H, Dl = s.derived["H"], s.derived["Delta"]
+    e = 1e-3 * Dl
+    placed = [(-H, 0), (-H - e, None), (-2 * H, None), (H + e, None), (3 * H, None), (H - e, 15),
+              (-H + 0.5 * Dl, 0), (-H + 3.5 * Dl, 3), (-H + 3.0 * Dl + e, 3), (-H + 4.0 * Dl - e, 3),
+              (-H + 4.0 * Dl + e, 4), (e, 8), (-e, 7), (-H + 15.25 * Dl, 15), (-H + 7.75 * Dl, 7),
+              (float("nan"), None), (-H + 11.5 * Dl, 11)]
+    taus = np.array([t for t, _ in placed])
+    xs = 1e-4 * (1.0 + np.arange(len(placed))) * (-1.0) ** np.arange(len(placed))
+    hist, dip, out = s.deposit(taus, xs)
+    expect_h = np.zeros(16, np.int32)
+    expect_d = np.zeros(16)
+    for (t, k), x in zip(placed, xs):
+        if k is not None:
+            expect_h[k] += 1
+            expect_d[k] += x
+    assert out == sum(k is None for _, k in placed)
+    assert np.array_equal(hist, expect_h)
+    assert np.array_equal(dip, expect_d)
+    # a tracked turn deposits its particles the same way
+    rng = np.random.default_rng(4)
+    s.set_particles(0, rng.normal(0.0, 0.5 * H, 64), rng.normal(0.0, 9e-4, 64))
+    s.set_tparticles(0, rng.normal(0.0, 1e-4, 64), rng.normal(0.0, 1e-5, 64))
+    s.track(1, record=False)
+    t1, _ = s.particles(0)
+    x1, _ = s.tparticles(0)
+    h1, d1, _ = s.deposit(t1, x1)
+    assert np.array_equal(d1, s.dipoles()[0]) and np.array_equal(h1, s.histograms()[0][0])
+
+
+# Mutants: the source of the oracle with one planted mistake each, compiled
+# on the CPU; the check named beside each must fail on it (so that a
+# half-cell shift or a wrong cell cannot hide behind the pins).
+MUTANTS = [
+    ("longitudinal kick half a cell off", "double u = x - 0.5;", "double u = x;",
+     lambda o, lib: check_kick_interpolation(o, False, lib)),
+    ("transverse kick half a cell off", "double u = xc - 0.5;", "double u = xc;",
+     lambda o, lib: check_transverse_kick_interpolation(o, False, lib)),
+    ("transverse NGP kick from the next cell", "return V[(int)floor(xc)];",
+     "return V[(int)floor(xc) + 1 < nb ? (int)floor(xc) + 1 : nb - 1];",
+     lambda o, lib: check_transverse_kick_interpolation(o, True, lib)),
+    ("dipole deposit into the cell below", "dip[(int)xc] += x;", "dip[(int)xc > 0 ? (int)xc - 1 : 0] += x;",
+     lambda o, lib: check_dipole_deposit(o, lib)),
+]
+
+
+@pytest.mark.parametrize("name,old,new,check", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_fail_on_planted_mistakes(oracle_mod, tmp_path, name, old, new, check):
+    src = open(os.path.join(ROOT, "oracle", "mbt_oracle.c")).read()
+    assert src.count(old) == 1, name
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = oracle_mod.load_library(oracle_mod.compile_source(mutant, tmp_path / "libmutant.so"))
+    with pytest.raises(AssertionError):
+        check(oracle_mod, lib)
 
 
 def test_long_range_is_the_wake_of_every_earlier_passage(oracle_mod):
