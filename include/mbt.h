@@ -256,6 +256,18 @@ mbt_status mbt_init_particles(mbt_ctx *ctx, void *stream);
  * (MBT_PREC_MIXED rounds tau to FP32).  Synchronous. */
 mbt_status mbt_set_particles(mbt_ctx *ctx, int bunch, const double *tau_s, const double *delta);
 
+/* Copy every bunch's coordinates from host arrays of n_particles doubles
+ * each: bunch 0's n_mp[0] values, then bunch 1's, ... (no padding).  When
+ * both arrays are page-locked and device-addressable (cudaHostAlloc /
+ * cudaMallocHost / cudaHostRegister'ed memory; checked with
+ * cudaPointerGetAttributes) one kernel on `stream` reads them across the
+ * host link and writes the device layout; otherwise the call falls back to
+ * mbt_set_particles bunch by bunch.  The result is the same either way
+ * (MBT_PREC_MIXED rounds tau to FP32).  Synchronous: the arrays may be
+ * reused when the call returns.  The caller guarantees that each array holds
+ * n_particles doubles. */
+mbt_status mbt_set_particles_all(mbt_ctx *ctx, const double *tau_s, const double *delta, void *stream);
+
 /* Copy one bunch's coordinates to host arrays of n_mp[bunch] doubles.
  * Synchronous (waits for tracking in flight). */
 mbt_status mbt_get_particles(mbt_ctx *ctx, int bunch, double *tau_s, double *delta);
@@ -389,17 +401,24 @@ mbt_status mbt_load_state(mbt_ctx *ctx, const void *buf, size_t bytes);
  *   nres resonators (Rs_ohm, fr_Hz, Q, range: host arrays; only those with
  *     the short-range bit contribute), at most 8;
  *   nb bunches, 1..1024; charge_per_count[nb]: host, coulombs per count;
- *   hist: DEVICE int32 [nb][nbins] counts (input, caller-owned);
- *   V: DEVICE float [nb][nbins] voltages [V] (output, caller-owned);
+ *   hist: DEVICE int32 [nb][nbins] counts (input, caller-owned), 16-byte
+ *     aligned (the kernel reads it 16 bytes at a time), every count in
+ *     [0, 2^24) (the tensor-core kernel splits a count into three exact
+ *     8-bit planes);
+ *   V: DEVICE float [nb][nbins] voltages [V] (output, caller-owned), 4-byte
+ *     aligned;
  *   stream: cudaStream_t as void*; errbuf/errlen: optional message buffer.
- * Sizes beyond these limits return MBT_ERR_UNSUPPORTED with a message.
- * Working memory is a 256 KB array in the library's static device memory,
- * held by every GPU that loads the library until the process exits.  The
- * first call on a device resolves that array's device address (make it
- * before any stream capture).  The call is synchronous: it returns when V is
- * written.  All calls share the array (host calls are serialised by the
- * library), so calls from another process or kernels that modify hist or V
- * while it runs race. */
+ * Sizes beyond these limits return MBT_ERR_UNSUPPORTED with a message; a
+ * null or misaligned pointer MBT_ERR_ARG before any device work; a count
+ * outside [0, 2^24) MBT_ERR_ARG after the launch (V then holds no valid
+ * result).  Working memory is a 256 KB array in the library's static device
+ * memory, held by every GPU that loads the library until the process exits;
+ * the first call on a device resolves that array's device address.  The call
+ * is synchronous (it waits for the stream and reads an error word back), so
+ * it cannot be captured into a CUDA graph: on a stream that is being
+ * captured it returns MBT_ERR_STATE without doing anything.  All calls share
+ * the array (host calls are serialised by the library), so calls from
+ * another process or kernels that modify hist or V while it runs race. */
 mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const double *Rs_ohm, const double *fr_Hz,
                             const double *Q, const int32_t *range, int nbins, double half_width_sigmas, int nb,
                             const double *charge_per_count, const int32_t *hist, float *V, void *stream,

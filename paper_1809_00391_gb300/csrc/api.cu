@@ -70,6 +70,37 @@ float bf16_to_f32(uint16_t b) {
   return f;
 }
 
+// Tensor-core operand images of the short-range Toeplitz matrix T[j][k] =
+// lag[j - k] (j >= k, else 0), per M-tile mt: rows [128 mt, 128 mt + 128)
+// need only columns k < Kmt = min(nbins, 128 (mt + 1)), so the image holds
+// 128 rows x [T_hi | T_lo] (2 Kmt columns; T_hi = bf16(T), T_lo =
+// bf16(T - T_hi)) of BF16 in K-major 8x8 core matrices, element (row, kk) at
+// byte ((kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2; the
+// images of the M-tiles follow each other (512 Kmt bytes each).  img must
+// hold 512 * sum_mt Kmt bytes; returns that size.  The one layout that the
+// wake kernel reads (wake_img_offset), for tracking and for the
+// allocation-free wake alike.
+size_t pack_toeplitz_images(const double *lag, int nbins, uint16_t *img) {
+  size_t base = 0;
+  for (int mt = 0; mt < nbins / 128; ++mt) {
+    const int kmt = std::min(nbins, 128 * (mt + 1));
+    for (int row = 0; row < 128; ++row)
+      for (int k = 0; k < kmt; ++k) {
+        const int j = mt * 128 + row;
+        const double T = j >= k ? lag[j - k] : 0.0;
+        const uint16_t hi = f32_to_bf16_rne((float)T);
+        const uint16_t lo = f32_to_bf16_rne((float)(T - (double)bf16_to_f32(hi)));
+        for (int half = 0; half < 2; ++half) {
+          const int kk = k + half * kmt;
+          const size_t byte = base + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2;
+          img[byte / 2] = half ? lo : hi;
+        }
+      }
+    base += (size_t)512 * kmt;
+  }
+  return base;
+}
+
 }  // namespace
 
 struct mbt_ctx {
@@ -117,6 +148,7 @@ struct mbt_ctx {
   double2 *d_step = nullptr, *d_emis = nullptr;
   float *d_qf = nullptr;
   double *d_inv_n = nullptr;
+  long long *d_hoff = nullptr;   // [nb] first particle of each bunch in back-to-back host arrays
   float *d_lagf = nullptr;
   // cluster-resident mode (allocated on first use)
   double2 *d_resE = nullptr;
@@ -906,6 +938,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
   ALLOC(c->d_q, (size_t)nb * sizeof(double));
   ALLOC(c->d_qf, (size_t)nb * sizeof(float));
   ALLOC(c->d_inv_n, (size_t)nb * sizeof(double));
+  ALLOC(c->d_hoff, (size_t)nb * sizeof(long long));
   ALLOC(c->d_lagf, (size_t)nbins * sizeof(float));
   ALLOC(c->d_step, (size_t)nl * nb * sizeof(double2));
   ALLOC(c->d_emis, (size_t)nl * nbins * sizeof(double2));
@@ -947,6 +980,13 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     }
     cudaMemcpy(c->d_qf, qf.data(), nb * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_inv_n, inv_n.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<long long> hoff(nb);
+    long long h = 0;
+    for (int m = 0; m < nb; ++m) {
+      hoff[m] = h;
+      h += c->nmp[m];
+    }
+    cudaMemcpy(c->d_hoff, hoff.data(), nb * sizeof(long long), cudaMemcpyHostToDevice);
   }
 
   // summed short-range wake per lag (half of W(0+) at lag 0)
@@ -967,29 +1007,8 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     cudaMemcpy(c->d_lagf, lagf.data(), nbins * sizeof(float), cudaMemcpyHostToDevice);
   }
   if (mixed) {
-    // operand images, per M-tile mt: rows [128 mt, 128 mt + 128) of the lower
-    // triangular Toeplitz matrix need only columns k < Kmt = 128 (mt + 1):
-    // 128 rows x [T_hi | T_lo] (2 Kmt columns) of BF16 in K-major 8x8 core
-    // matrices, byte ((kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2
-    const int nmt = nbins / 128;
     std::vector<uint16_t> img(toep_bytes / 2, 0);
-    size_t base = 0;
-    for (int mt = 0; mt < nmt; ++mt) {
-      const int kmt = std::min(nbins, 128 * (mt + 1));
-      for (int row = 0; row < 128; ++row)
-        for (int k = 0; k < kmt; ++k) {
-          const int j = mt * 128 + row;
-          const double T = j >= k ? lag[j - k] : 0.0;
-          const uint16_t hi = f32_to_bf16_rne((float)T);
-          const uint16_t lo = f32_to_bf16_rne((float)(T - (double)bf16_to_f32(hi)));
-          for (int half = 0; half < 2; ++half) {
-            const int kk = k + half * kmt;
-            const size_t byte = base + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2;
-            img[byte / 2] = half ? lo : hi;
-          }
-        }
-      base += (size_t)512 * kmt;
-    }
+    pack_toeplitz_images(lag.data(), nbins, img.data());
     cudaMemcpy(c->d_toep, img.data(), toep_bytes, cudaMemcpyHostToDevice);
   } else {
     cudaMemcpy(c->d_toep, lag.data(), toep_bytes, cudaMemcpyHostToDevice);
@@ -1231,6 +1250,34 @@ mbt_status mbt_set_particles(mbt_ctx *c, int bunch, const double *tau, const dou
   e = cudaMemcpy(dt, h, tb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_delta + c->off[bunch], h + tb, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "set particles");
+  return MBT_OK;
+}
+
+mbt_status mbt_set_particles_all(mbt_ctx *c, const double *tau, const double *delta, void *stream) {
+  if (!c || !tau || !delta) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // page-locked arrays the device can address: one kernel reads them across
+  // the host link; anything else goes bunch by bunch through the staging buffer
+  cudaPointerAttributes at{}, ad{};
+  const bool pinned = cudaPointerGetAttributes(&at, tau) == cudaSuccess &&
+                      cudaPointerGetAttributes(&ad, delta) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                      ad.type == cudaMemoryTypeHost && at.devicePointer && ad.devicePointer;
+  cudaGetLastError();   // a pageable pointer leaves no error behind
+  if (!pinned) {
+    size_t h = 0;
+    for (int m = 0; m < c->nb; ++m) {
+      const mbt_status st = mbt_set_particles(c, m, tau + h, delta + h);
+      if (st != MBT_OK) return st;
+      h += (size_t)c->nmp[m];
+    }
+    return MBT_OK;
+  }
+  cudaError_t e = launch_load_host(c->own.plan, c->precision, static_cast<const double *>(at.devicePointer),
+                                   static_cast<const double *>(ad.devicePointer), c->d_hoff, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set particles from host");
   return MBT_OK;
 }
 
@@ -1929,6 +1976,20 @@ mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const dou
   for (int i = 0; i < nres; ++i)
     if (!(Rs_ohm[i] > 0) || !(fr_Hz[i] > 0) || !(Q[i] > 0.5) || range[i] < 1 || range[i] > 3)
       return wna_fail(errbuf, errlen, MBT_ERR_ARG, "resonator %d needs Rs > 0, fr > 0, Q > 0.5, range 1..3", i);
+  // the kernel reads the counts 16 bytes at a time and stores V as floats
+  if (reinterpret_cast<uintptr_t>(hist) & 15u)
+    return wna_fail(errbuf, errlen, MBT_ERR_ARG, "hist must be 16-byte aligned (it is read 16 bytes at a time)");
+  if (reinterpret_cast<uintptr_t>(V) & 3u) return wna_fail(errbuf, errlen, MBT_ERR_ARG, "V must be 4-byte aligned");
+  // synchronous (it waits for the stream and reads the error word back), so
+  // it cannot be recorded into a CUDA graph
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(cs, &cap);
+  if (ce != cudaSuccess)
+    return wna_fail(errbuf, errlen, MBT_ERR_CUDA, "allocation-free wake: %s", cudaGetErrorString(ce));
+  if (cap != cudaStreamCaptureStatusNone)
+    return wna_fail(errbuf, errlen, MBT_ERR_STATE, "the stream is being captured: the allocation-free wake is "
+                    "synchronous and cannot be captured");
 
   std::lock_guard<std::mutex> lk(g_wna_host_mutex);
   mbt_ctx g;   // grid constants only: no device state
@@ -1943,29 +2004,15 @@ mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const dou
     for (int i = 0; i < nres; ++i)
       if (range[i] & MBT_RANGE_SHORT) lag[l] += wake(Resonator{Rs_ohm[i], fr_Hz[i], Q[i], range[i]}, (double)l * g.Delta);
   }
-  size_t base = 0;
-  for (int mt = 0; mt < nbins / 128; ++mt) {
-    const int kmt = std::min(nbins, 128 * (mt + 1));
-    for (int row = 0; row < 128; ++row)
-      for (int k = 0; k < kmt; ++k) {
-        const int j = mt * 128 + row;
-        const double T = j >= k ? lag[j - k] : 0.0;
-        const uint16_t hi = f32_to_bf16_rne((float)T);
-        const uint16_t lo = f32_to_bf16_rne((float)(T - (double)bf16_to_f32(hi)));
-        for (int half = 0; half < 2; ++half) {
-          const int kk = k + half * kmt;
-          const size_t byte = base + ((size_t)(kk / 8) * 16 + row / 8) * 128 + (row % 8) * 16 + (kk % 8) * 2;
-          g_wna_img[byte / 2] = half ? lo : hi;
-        }
-      }
-    base += (size_t)512 * kmt;
-  }
+  const size_t base = pack_toeplitz_images(lag, nbins, g_wna_img);
   for (int m = 0; m < nb; ++m) g_wna_q[m] = (float)charge_per_count[m];
   RunDev proto{};
   int derr = 0;
-  cudaError_t e = wake_noalloc_launch(proto, g_wna_img, base, g_wna_q, nb, nbins, hist, V,
-                                      static_cast<cudaStream_t>(stream), &derr);
+  cudaError_t e = wake_noalloc_launch(proto, g_wna_img, base, g_wna_q, nb, nbins, hist, V, cs, &derr);
   if (e != cudaSuccess) return wna_fail(errbuf, errlen, MBT_ERR_CUDA, "allocation-free wake: %s", cudaGetErrorString(e));
+  if (derr == kErrCount)
+    return wna_fail(errbuf, errlen, MBT_ERR_ARG, "a cell count lies outside [0, 2^24): V is not valid");
+  if (derr == kErrTmem) return wna_fail(errbuf, errlen, MBT_ERR_CUDA, "tensor memory could not be allocated");
   if (derr != 0) return wna_fail(errbuf, errlen, MBT_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", derr);
   return MBT_OK;
 }

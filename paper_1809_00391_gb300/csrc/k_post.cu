@@ -486,9 +486,12 @@ __device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, 
 // Main part: B from the turn's counts, the MMAs (issued by one thread, run
 // asynchronously), then the epilogue from tensor memory.
 // qf: the charges of the tile's 32 bunches (staged, or the run's array at
-// the tile).
+// the tile).  check_counts: record kErrCount in the error word if a count
+// lies outside [0, 2^24) (counts from a caller; tracking caps its bunches
+// below 2^24 particles, so its counts never need the test).
 __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem,
-                            uint64_t *bars, uint32_t *tmem_slot, int *s_flag, const float *qf) {
+                            uint64_t *bars, uint32_t *tmem_slot, int *s_flag, const float *qf,
+                            bool check_counts = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbins = R->nbins;
   const int nb = R->nb;
@@ -519,6 +522,14 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       cv[i][0] = src[0];
       cv[i][1] = src[1];
     }
+  }
+  if (check_counts) {
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i)
+      bad |= ((uint32_t)cv[i][0].x | (uint32_t)cv[i][0].y | (uint32_t)cv[i][0].z | (uint32_t)cv[i][0].w |
+              (uint32_t)cv[i][1].x | (uint32_t)cv[i][1].y | (uint32_t)cv[i][1].z | (uint32_t)cv[i][1].w) >= (1u << 24);
+    if (bad) atomicCAS(p.error, kErrNone, kErrCount);
   }
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
@@ -742,7 +753,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) 
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   wake_prologue(R, job, sm_wna, bars, &tmem_slot, &s_flag);
-  wake_job_tc(p, R, job, 0, sm_wna, bars, &tmem_slot, &s_flag, R->q_mp_f + job.bt * kBunchTile);
+  wake_job_tc(p, R, job, 0, sm_wna, bars, &tmem_slot, &s_flag, R->q_mp_f + job.bt * kBunchTile, true);
 }
 
 namespace {

@@ -1032,6 +1032,47 @@ __global__ void __launch_bounds__(kPushThreads) k_init(const Plan p, int precisi
   }
 }
 
+// ---------------------------------------------------------------------------
+// Particle state of every bunch from page-locked host arrays (tau, delta of
+// all bunches back to back, n_mp each), read by the kernel across the host
+// link and written in the device layout (segments padded to 4; tau narrowed
+// to FP32 by rounding for kMixed, as a per-bunch copy does).  hoff[m]: first
+// particle of bunch m in the host arrays.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPushThreads) k_load_host(const Plan p, int precision, const double *tau_h,
+                                                            const double *del_h, const long long *hoff) {
+  const TileDev t = p.tiles[blockIdx.x];
+  const RunDev *__restrict__ R = p.runs + t.run;
+  const BunchDev bd = p.bunches[t.bunch];
+  const long long h0 = hoff[t.m] + t.start, d0 = bd.off + t.start;
+  for (int q = 4 * (int)threadIdx.x; q < t.count; q += 4 * kPushThreads) {
+    const int nv = min(4, t.count - q);
+    double tv[4], dv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (e < nv) {
+        tv[e] = tau_h[h0 + q + e];
+        dv[e] = del_h[h0 + q + e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (e < nv) {
+        if (precision == kMixed) static_cast<float *>(R->tau)[d0 + q + e] = (float)tv[e];
+        else static_cast<double *>(R->tau)[d0 + q + e] = tv[e];
+        R->delta[d0 + q + e] = dv[e];
+      }
+    }
+  }
+}
+
+cudaError_t launch_load_host(const Plan &p, int precision, const double *tau_h, const double *del_h,
+                             const long long *hoff, cudaStream_t s) {
+  if (p.ntiles == 0) return cudaSuccess;
+  k_load_host<<<p.ntiles, kPushThreads, 0, s>>>(p, precision, tau_h, del_h, hoff);
+  return cudaGetLastError();
+}
+
 template <typename... Args>
 static cudaError_t launch_ex(void (*kern)(Args...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
                              Args... args) {

@@ -30,7 +30,9 @@ constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
 enum Precision { kF64 = 0, kMixed = 1 };
 enum Flags { kNoSR = 1, kNoQE = 2, kKickNGP = 4 };
 enum JobType { kJobWake = 0, kJobTile = 1, kJobTrans = 2, kJobMoments = 3 };
-enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2 };
+// kErrCount: a cell count outside [0, 2^24) reached the tensor-core wake,
+// which splits each count into three exact 8-bit planes
+enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2, kErrCount = 3 };
 
 // One run's device state and constants.
 struct RunDev {
@@ -193,6 +195,10 @@ cudaError_t resident_max_clusters(int cluster, size_t smem, int *max_clusters);
 cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl);
 cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s, bool pdl);
 cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s);
+// tau, delta of every bunch from device-accessible (page-locked) host arrays;
+// hoff: device array, first particle of each bunch in the host arrays
+cudaError_t launch_load_host(const Plan &p, int precision, const double *tau_h, const double *del_h,
+                             const long long *hoff, cudaStream_t s);
 size_t post_smem_bytes(int precision, int max_nbins);
 cudaError_t configure_kernels();
 // Allocation-free tensor-core wake of one run (scratch: a static device array

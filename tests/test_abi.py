@@ -208,3 +208,18 @@ def test_harmonic_cavity_derivation_matches_the_oracle(pkg, oracle_mod):
     assert info.phi_s == pytest.approx(math.asin(d["sin_phi_s"]), rel=1e-15)
     assert info.sigma_tau0_s == pytest.approx(d["sigma_tau0"], rel=1e-14)
     L.mbt_destroy(h)
+
+
+def test_wake_noalloc_refuses_misaligned_pointers_before_device_work(pkg):
+    """The allocation-free wake reads the caller's counts 16 bytes at a time
+    and stores the voltages as floats: a misaligned pointer (one row of a
+    larger buffer, an odd offset) is refused with MBT_ERR_ARG and a message
+    before anything reaches the GPU.  The addresses are never dereferenced."""
+    run = W.single_bunch()
+    q = np.full(2, 1e-13)
+    with pytest.raises(pkg.MBTError, match="16-byte aligned") as e:
+        pkg.wake_noalloc(run.ring, run.resonators, 256, 5.0, q, 0x10004, 0x20000)
+    assert e.value.status == 1
+    with pytest.raises(pkg.MBTError, match="4-byte aligned") as e:
+        pkg.wake_noalloc(run.ring, run.resonators, 256, 5.0, q, 0x10000, 0x20002)
+    assert e.value.status == 1
