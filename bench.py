@@ -77,6 +77,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_stream_fill390_traffic.json"
 GRAPH_TURNS = 100      # turns per captured CUDA graph
 AUTOTUNE_TURNS = 20    # timed turns per push-tile candidate
 ROOFLINE_TURNS = 4000  # turns of the event-timed roofline region
+SATURATED_TURNS = 200  # turns of the event-timed region in the saturated instability
 
 
 def parse():
@@ -87,6 +88,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--saturated-turn", type=int, default=1500,
+                    help="also time the push from this turn on (saturated instability); 0 = skip")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
     ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t", "three_f64"],
@@ -156,8 +159,57 @@ def recorded_traffic(n_particles: int):
     return float(t["dram_bytes_per_particle"]) * n_particles
 
 
+# NVML clock-event reason bits reported in the clocks summary
+CLOCK_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+                 0x80: "hw_power_brake_slowdown"}
+
+
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the
+    driver): SM clock, its maximum, power and the active clock-event reasons."""
+
+    SM = 1            # NVML_CLOCK_SM
+
+    def __init__(self, local_index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(local_index)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0".encode()
+            ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            vis = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+            idx = int(vis[local_index]) if local_index < len(vis) and vis[local_index].isdigit() else local_index
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(self.h)) != 0:
+                raise RuntimeError("no NVML handle")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        self.max_mhz = float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(v)) == 0 \
+            else float("nan")
+
+    def sample(self):
+        ct = self.ct
+        c, pw, r = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, ct.byref(c)) != 0:
+            return None
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(pw))
+        self.reasons_fn(self.h, ct.byref(r))
+        return float(c.value), pw.value / 1000.0, int(r.value)
+
+
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """SM clocks and clock-event reasons sampled during the timed region:
+    NVML queried from a host thread every ~0.25 ms (so that a region of a few
+    milliseconds still gets samples), else nvidia-smi every 200 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -167,10 +219,34 @@ class ClockSampler:
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         ids = [x.strip() for x in vis.split(",") if x.strip()]
         self.gpu = ids[local_index] if local_index < len(ids) else str(local_index)
+        self.local = local_index
         self.proc = None
         self.path = None
+        self.nvml = None
+        self.rows = []
+        self.thread = None
+        self.stop = False
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = _Nvml(self.local)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            first = self.nvml.sample()
+            if first is not None:
+                self.rows.append(first)
+
+            def loop():
+                while not self.stop:
+                    x = self.nvml.sample()
+                    if x is not None:
+                        self.rows.append(x)
+                    time.sleep(0.00025)
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return self
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -182,6 +258,9 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop = True
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -190,6 +269,8 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml is not None:
+            return self._summary_nvml()
         rows = []
         try:
             for line in open(self.path):
@@ -217,7 +298,18 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(smax)), "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "source": "nvidia-smi"}
+
+    def _summary_nvml(self):
+        rows = list(self.rows)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.nvml.max_mhz, "reasons": ["no NVML samples"], "samples": 0,
+                    "source": "nvml"}
+        sm = np.array([r[0] for r in rows])
+        pw = np.array([r[1] for r in rows])
+        reasons = sorted({name for r in rows for bit, name in CLOCK_REASONS.items() if r[2] & bit})
+        return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": float(sm.min()), "sm_max_mhz": self.nvml.max_mhz,
+                "power_w_max": float(pw.max()), "reasons": reasons, "samples": len(rows), "source": "nvml"}
 
 
 def cpu_baseline(run: W.Run, turns: int = 2):
@@ -567,7 +659,7 @@ def three_f64_bench(args, rank, local):
             "config": {"workload": run.name, "turns_timed": K, "l2": "state 4.8 MB: L2-resident (FP64-pipe bound)"},
             "roofline": {"bound": "fp64 pipe", "kernel": "k_push_f64", "unit_count": n,
                          "push_us": push_ms / max(1, launches) * 1e3, "post_us": post_ms / max(1, launches) * 1e3,
-                         "utilisation": "ncu sm__inst_executed_pipe_fp64 (profiles/push_f64_three_bunches.md)"},
+                         "utilisation": "ncu counter sm__inst_executed_pipe_fp64"},
             "gpu_launches": 2 * K, "clocks": clocks}
     print(json.dumps(line), flush=True)
     tr.close()
@@ -701,14 +793,19 @@ def main():
     value = weak_scaling_value(n_part, K, world, t_max)
 
     # ---- roofline of the dominant kernel (push): a second timed region of KR
-    # turns with CUDA events around every launch (ordinary launches)
+    # turns with CUDA events around every launch (ordinary launches), right
+    # after the headline region (the same beam state)
+    def timed_push(turns):
+        tr.set_timing(True)
+        tr.track(turns, stream)
+        tr.sync()
+        push_ms, post_ms, launches = tr.timing()
+        tr.set_timing(False)
+        return push_ms / max(1, launches) * 1e-3, post_ms / max(1, launches) * 1e-3, launches
+
     KR = max(1, min(K, ROOFLINE_TURNS))
-    tr.set_timing(True)
-    tr.track(KR, stream)
-    tr.sync()
-    push_ms, post_ms, launches = tr.timing()
-    tr.set_timing(False)
-    push_avg_s = push_ms / max(1, launches) * 1e-3
+    turn_a = tr.info["turn"]
+    push_avg_s, post_avg_s, launches = timed_push(KR)
     achieved = BYTES_PER_MP_TURN * n_part / push_avg_s / 1e9
     peak, peak_kind = measured_peak_hbm()
     traffic = recorded_traffic(n_part)
@@ -716,33 +813,54 @@ def main():
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "kernel": "k_push_stream", "bytes_per_unit": BYTES_PER_MP_TURN, "unit_count": n_part,
-                "timed_launches": launches, "push_us": push_avg_s * 1e6,
-                "post_us": post_ms / max(1, launches) * 1e3,
-                "region": f"{KR} turns after the headline region, CUDA events around each push launch"}
+                "timed_launches": launches, "push_us": push_avg_s * 1e6, "post_us": post_avg_s * 1e6,
+                "region": f"turns {turn_a}..{turn_a + KR - 1}, right after the headline region, CUDA events around "
+                          f"each push launch"}
+    # the same kernel once the coupled-bunch instability has saturated (from
+    # turn ~1000 on most particles lie outside the mesh and skip the deposit)
+    if args.saturated_turn > 0:
+        now = tr.info["turn"]
+        if now < args.saturated_turn:
+            tr.track(args.saturated_turn - now, stream)
+            tr.sync()
+        turn_b = tr.info["turn"]
+        ps, qs, ls = timed_push(SATURATED_TURNS)
+        a_s = BYTES_PER_MP_TURN * n_part / ps / 1e9
+        out_frac = float(np.mean(tr.moments(tr.info["turn"] - 1, 1)[0, :, 5]) / run.n_mp[0])
+        roofline["saturated"] = {"achieved": a_s, "frac": a_s / peak, "push_us": ps * 1e6, "post_us": qs * 1e6,
+                                 "timed_launches": ls, "outside_mesh_fraction": out_frac,
+                                 "region": f"turns {turn_b}..{turn_b + ls - 1}"}
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: a fresh job (new
+    # particle state from page-locked host arrays, K turns, all K turns of
+    # moments back to the host) on a tracker whose turn graph is captured
     e2e = None
     if not args.no_e2e:
         rng = np.random.default_rng(100 + rank)
-        host_tau = [np.ascontiguousarray(rng.normal(0.0, 13.2e-12, n), np.float64) for n in run.n_mp]
-        host_del = [np.ascontiguousarray(rng.normal(0.0, 9e-4, n), np.float64) for n in run.n_mp]
+        n = run.n_particles
+        host_tau = torch.from_numpy(rng.normal(0.0, 13.2e-12, n)).pin_memory()
+        host_del = torch.from_numpy(rng.normal(0.0, 9e-4, n)).pin_memory()
         tr2 = pkg.tracker_for_run(run, record_turns=max(K, 16))
         tr2.set_tile(tile)
         tr2.set_graph(G)
+        tr2.init_particles(stream)
+        tr2.track(G, stream)             # captures the turn graph
+        tr2.init_particles(stream)       # turn counter, wakes and phasors back to zero
+        tr2.sync()
         barrier()
         t0 = time.perf_counter()
-        for m in range(run.nb):
-            tr2.set_particles(m, host_tau[m], host_del[m])
+        tr2.set_particles_all(host_tau, host_del, stream)
         tr2.track(K, stream)
         mom = tr2.moments(0, K)
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-        h2d = run.n_particles * (4 + 8)
+        h2d = n * (8 + 8)
         d2h = mom.nbytes
         e2e = {"value": n_part * K * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
-               "d2h_bytes_per_step": d2h / K,
-               "note": "set particles from host (per bunch), K turns, read all K turns of moments to host"}
+               "d2h_bytes_per_step": d2h / K, "ms": e2e_s * 1e3,
+               "note": "host clock around: tau, delta (FP64) of every bunch from page-locked host memory "
+                       "(mbt_set_particles_all), K turns, all K turns of moments read to the host"}
         tr2.close()
 
     cpu = None

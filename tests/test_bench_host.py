@@ -63,12 +63,35 @@ def test_clock_summary_flags_throttle_reasons(tmp_path):
     cap = "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active"
     hot = "0, 1500, 2070, 1400.0, 0x40, Not Active, Active, Not Active, Not Active"
     s = _summary(tmp_path, [ok, ok, ok])
-    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3, "source": "nvidia-smi"}
     s = _summary(tmp_path, [ok, cap, hot])
     assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
     assert s["sm_mhz"] == 1980.0 and s["samples"] == 3
     s = _summary(tmp_path, [])
     assert s["samples"] == 0 and s["reasons"] == ["no nvidia-smi samples"]
+
+
+class _FakeNvml:
+    """Stands in for the NVML reader: a fixed sequence of (SM MHz, W, reasons)."""
+
+    def __init__(self, rows):
+        self.rows = list(rows)
+        self.max_mhz = 2070.0
+
+    def sample(self):
+        return self.rows.pop(0) if self.rows else None
+
+
+def test_clock_summary_from_nvml_samples(monkeypatch):
+    rows = [(2070.0, 900.0, 0x0), (2055.0, 1390.0, 0x4), (1500.0, 1400.0, 0x40 | 0x4)]
+    monkeypatch.setattr(bench, "_Nvml", lambda local: _FakeNvml(rows))
+    with bench.ClockSampler(0) as c:
+        import time
+        time.sleep(0.05)
+    s = c.summary()
+    assert s["source"] == "nvml" and s["samples"] == 3
+    assert s["sm_mhz"] == 2055.0 and s["sm_min_mhz"] == 1500.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"] and s["power_w_max"] == 1400.0
 
 
 def test_reference_arm_prints_a_complete_line():
