@@ -295,10 +295,34 @@ typedef struct orc_sim {
     int rw_nh;             /* turns of history                               */
     double *rw_cent;       /* [rw_nh + 1][nb] charge x centroid, by turn     */
     double *Vrw;           /* [nb] kick voltage of each bunch for the next turn */
+    /* e^{s D T_rf} by bucket distance D < nhist h for each long-range
+     * resonator, and whether e^{-a D T_rf} clears the history cutoff: the
+     * factors the direct history sums multiply by, computed once */
+    double complex *lr_phase[ORC_MAX_RES], *tr_phase[ORC_MAX_RES];
+    unsigned char *lr_keep[ORC_MAX_RES], *tr_keep[ORC_MAX_RES];
 } orc_sim;
 
 /* e^{-a dt} below this is dropped from the direct history sum. */
 static const double ORC_HISTORY_CUTOFF = 1e-18;
+
+/* The factor e^{s dt}, dt = D T_rf, of every bucket distance 0 <= D < nD for
+ * resonator q, and keep[D] = (D > 0 and e^{-a dt} >= cutoff): exactly the
+ * values the history sums would form term by term. */
+static void phase_table(const orc_resonator *q, double T_rf, int64_t nD, double complex **val, unsigned char **keep)
+{
+    double a, wb;
+    res_consts(q, &a, &wb);
+    double complex sr = -a + I * wb;
+    *val = (double complex *)calloc((size_t)nD, sizeof(double complex));
+    *keep = (unsigned char *)calloc((size_t)nD, 1);
+    for (int64_t D = 1; D < nD; ++D) {
+        double dt = (double)D * T_rf;
+        if (exp(-a * dt) < ORC_HISTORY_CUTOFF)
+            continue;
+        (*keep)[D] = 1;
+        (*val)[D] = cexp(sr * dt);
+    }
+}
 
 orc_sim *orc_create_h(const orc_ring *ring, int flags, uint64_t seed,
                       int nres, const orc_resonator *res, int nharm, const orc_harmonic *harm,
@@ -371,6 +395,9 @@ orc_sim *orc_create_h(const orc_ring *ring, int flags, uint64_t seed,
     }
     s->nhist = any_long ? (int)ceil(-log(ORC_HISTORY_CUTOFF) / (amin * ring->T0_s)) + 2 : 1;
     s->Ehist = (double complex *)calloc((size_t)(nres > 0 ? nres : 1) * s->nhist * nb, sizeof(double complex));
+    for (int r = 0; r < nres; ++r)
+        if (res[r].range & ORC_RANGE_LONG)
+            phase_table(&res[r], s->dv.T_rf, (int64_t)s->nhist * ring->h, &s->lr_phase[r], &s->lr_keep[r]);
     return s;
 }
 
@@ -436,6 +463,10 @@ void orc_destroy(orc_sim *s)
     free(s->tau); free(s->delta); free(s->bucket); free(s->current); free(s->n_mp); free(s->q_mp);
     free(s->hist); free(s->out_count); free(s->Vsr); free(s->Alr); free(s->moments);
     free(s->Wlag); free(s->Ehist);
+    for (int r = 0; r < ORC_MAX_RES; ++r) {
+        free(s->lr_phase[r]); free(s->lr_keep[r]);
+        free(s->tr_phase[r]); free(s->tr_keep[r]);
+    }
     if (s->trans) {
         for (int m = 0; m < s->nb; ++m) {
             free(s->x[m]);
@@ -500,6 +531,9 @@ int orc_set_transverse(orc_sim *s, double beta_m, double alpha, double nu0, doub
         any_long = 1;
     }
     s->nthist = any_long ? (int)ceil(-log(ORC_HISTORY_CUTOFF) / (amin * s->ring.T0_s)) + 2 : 1;
+    for (int r = 0; r < ntres; ++r)
+        if (tres[r].range & ORC_RANGE_LONG)
+            phase_table(&tres[r], s->dv.T_rf, (int64_t)s->nthist * s->ring.h, &s->tr_phase[r], &s->tr_keep[r]);
     s->Atlr = (double complex *)calloc((size_t)(ntres > 0 ? ntres : 1) * s->nb, sizeof(double complex));
     s->Ethist = (double complex *)calloc((size_t)(ntres > 0 ? ntres : 1) * s->nthist * s->nb, sizeof(double complex));
     s->tmoments = (double *)calloc((size_t)s->nb * 4, sizeof(double));
@@ -656,12 +690,12 @@ double complex orc_emission(const orc_sim *s, int r, const int32_t *hist, double
 
 /* Direct history sum for bunch m after turn n has been binned: every passage
  * strictly earlier than (n, m), weighted by e^{s dt}, dt = D T_rf with D the
- * integer bucket distance, truncated at e^{-a dt} < cutoff. */
+ * integer bucket distance, truncated at e^{-a dt} < cutoff (the factors from
+ * the resonator's phase table). */
 static double complex history_sum(const orc_sim *s, int r, int m)
 {
-    double a, wb;
-    res_consts(&s->res[r], &a, &wb);
-    double complex sr = -a + I * wb;
+    const double complex *ph = s->lr_phase[r];
+    const unsigned char *keep = s->lr_keep[r];
     const int64_t n = s->turn; /* the turn just binned */
     const int h = s->ring.h;
     double complex acc = 0.0;
@@ -672,12 +706,9 @@ static double complex history_sum(const orc_sim *s, int r, int m)
         const double complex *E = s->Ehist + ((size_t)r * s->nhist + (size_t)(np % s->nhist)) * s->nb;
         for (int mp = 0; mp < s->nb; ++mp) {
             int64_t D = back * (int64_t)h + (int64_t)s->bucket[m] - (int64_t)s->bucket[mp];
-            if (D <= 0)
-                continue; /* not earlier */
-            double dt = (double)D * s->dv.T_rf;
-            if (exp(-a * dt) < ORC_HISTORY_CUTOFF)
-                continue;
-            acc += cexp(sr * dt) * E[mp];
+            if (D <= 0 || !keep[D])
+                continue; /* not earlier, or below the cutoff */
+            acc += ph[D] * E[mp];
         }
     }
     return acc;
@@ -801,9 +832,8 @@ static double complex temission(const orc_sim *s, int r, const double *dip, doub
 /* Direct history sum of the transverse emissions (as history_sum). */
 static double complex thistory_sum(const orc_sim *s, int r, int m)
 {
-    double a, wb;
-    res_consts(&s->tres[r], &a, &wb);
-    double complex sr = -a + I * wb;
+    const double complex *ph = s->tr_phase[r];
+    const unsigned char *keep = s->tr_keep[r];
     const int64_t n = s->turn;
     const int h = s->ring.h;
     double complex acc = 0.0;
@@ -814,12 +844,9 @@ static double complex thistory_sum(const orc_sim *s, int r, int m)
         const double complex *E = s->Ethist + ((size_t)r * s->nthist + (size_t)(np % s->nthist)) * s->nb;
         for (int mp = 0; mp < s->nb; ++mp) {
             int64_t D = back * (int64_t)h + (int64_t)s->bucket[m] - (int64_t)s->bucket[mp];
-            if (D <= 0)
+            if (D <= 0 || !keep[D])
                 continue;
-            double dt = (double)D * s->dv.T_rf;
-            if (exp(-a * dt) < ORC_HISTORY_CUTOFF)
-                continue;
-            acc += cexp(sr * dt) * E[mp];
+            acc += ph[D] * E[mp];
         }
     }
     return acc;
