@@ -424,6 +424,35 @@ mbt_status mbt_wake_noalloc(const mbt_ring *ring, int flags, int nres, const dou
                             const double *charge_per_count, const int32_t *hist, float *V, void *stream,
                             char *errbuf, size_t errlen);
 
+/* ------------------------------------------------------------------------
+ * Bunch-sharded long-range scan (host side of splitting one fill's bunches
+ * over several GPUs in contiguous ranges; Sec. 2.3, last paragraph: the
+ * long-range wake acts after all bunches).  Bunch m meets the phasor
+ * Phi_m = a_m X_{m-1} and leaves X_m = Phi_m + E_m (E_m its emission,
+ * c q_m sum_k count_k e^{-s tau_k}; a_m = e^{s dt_m}, dt_m the bucket distance
+ * from the bunch before it, for the first bunch of a turn from the last bunch
+ * of the previous turn across the gap).  A rank reduces its bunches to one
+ * map X -> A X + B (mbt_phasor_segment); the ranks allgather the maps (4
+ * doubles per long-range resonator); every rank composes them in rank order
+ * starting from the value carried from the previous turn
+ * (mbt_phasor_compose), which gives the value entering its own range and the
+ * next carry, and applies it to its bunches (mbt_phasor_apply).  Complex
+ * numbers are (re, im) pairs of doubles; arrays are host memory owned by the
+ * caller.  Host only (no GPU); MBT_ERR_ARG on a null pointer or bad size. */
+/* step[2 m], step[2 m + 1] = a_m for bunches in strictly increasing buckets
+ * bucket[0 .. nb-1] of the ring and one resonator (fr_Hz, Q > 1/2). */
+mbt_status mbt_phasor_steps(const mbt_ring *ring, double fr_Hz, double Q, int nb, const int32_t *bucket,
+                            double *step);
+/* map[0..3] = (A, B) of f_{n-1} o ... o f_0, f_m(X) = a_m X + E_m (n >= 0;
+ * n = 0 gives the identity). */
+mbt_status mbt_phasor_segment(int n, const double *step, const double *E, double *map);
+/* maps[4 r .. 4 r + 3]: the maps of nseg consecutive ranges; carry: X after
+ * the last bunch of the previous turn.  entry[2 r] (optional): the value
+ * entering range r; carry_out: X after the last range. */
+mbt_status mbt_phasor_compose(int nseg, const double *maps, const double *carry, double *entry, double *carry_out);
+/* phi[2 m] = Phi_m of a range's n bunches given the value entering it. */
+mbt_status mbt_phasor_apply(int n, const double *step, const double *E, const double *entry, double *phi);
+
 /* Batched tracking: n contexts with the same precision, each with its fill
  * set, tracked together in the same kernel launches (one push and one post
  * launch per turn for all of them).  The contexts stay owned by the caller

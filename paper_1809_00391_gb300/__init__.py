@@ -39,7 +39,8 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
            "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy",
            "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
-           "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split"]
+           "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split", "mbt_phasor_steps",
+           "mbt_phasor_segment", "mbt_phasor_compose", "mbt_phasor_apply"]
 
 
 class MBTError(RuntimeError):
@@ -151,6 +152,10 @@ def lib() -> ctypes.CDLL:
                 "mbt_server_destroy": ([_vp], None),
                 "mbt_plan_streams": ([_i, _P(_i64), _P(_i32), _i, _i, _P(_i)], _i),
                 "mbt_plan_stream_split": ([_i, _P(_i32), _P(_i64), _i, _P(_i64), _i64, _P(_i64)], _i),
+                "mbt_phasor_steps": ([_P(Ring), _d, _d, _i, _P(_i32), _P(_d)], _i),
+                "mbt_phasor_segment": ([_i, _P(_d), _P(_d), _P(_d)], _i),
+                "mbt_phasor_compose": ([_i, _P(_d), _P(_d), _P(_d), _P(_d)], _i),
+                "mbt_phasor_apply": ([_i, _P(_d), _P(_d), _P(_d), _P(_d)], _i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)

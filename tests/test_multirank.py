@@ -55,3 +55,106 @@ def test_two_gloo_ranks():
     assert s0 != s1 and n0 == n1                   # independent fills of the same size
     assert v0 == v1 == pytest.approx(n0 * 100 * 2 / 15e-3)
     assert ref1 == 0                               # the reference arm: rank 0 only
+
+
+# --------------------------------------------------------------------------
+# Bunch-sharded long-range scan (one fill's bunches split over ranks): each
+# rank reduces its contiguous range to an affine phasor map, the ranks
+# allgather the maps, each composes them with the carried phasor.  Checked on
+# gloo ranks against the oracle's direct sum over every earlier passage.
+SHARD_TURNS = 25
+
+
+def _shard_fill():
+    import mbt_workloads as W
+    ring = W.ring_r0()
+    buckets = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 200, 201, 202, 350]    # trains with gaps, and the wrap
+    currents = [0.5e-3 * (1 + (m % 4)) for m in range(len(buckets))]
+    res = [dict(W.HOM), dict(Rs_ohm=3e5, fr_Hz=2.7e9, Q=800.0, range=W.RANGE_LONG)]
+    return ring, buckets, currents, res
+
+
+def _shard_worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch.distributed as dist
+    import oracle
+    from paper_1809_00391_gb300 import sharded
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ring, buckets, currents, res = _shard_fill()
+    nb = len(buckets)
+    lo, hi = sharded.split_bounds(nb, world)[rank:rank + 2]
+    s = oracle.OracleSim(ring, res, 128, 5.0, buckets, currents, [200] * nb, 11, 0)
+    s.init_particles()
+    steps = [sharded.phasor_steps(ring, r, buckets) for r in res]
+    carry = [0j, 0j]
+    worst = 0.0
+    for t in range(SHARD_TURNS):
+        s.track(1, record=False)
+        alr = s.alr()
+        for r in range(len(res)):
+            E = s.last_emission(r)
+            phi, carry[r] = sharded.exchange_turn(steps[r][lo:hi], E[lo:hi], carry[r], dist)
+            ref = alr[r, lo:hi]
+            # both sides round the phase w t of a delay t to about eps w t (FP64):
+            # the scan through its step factors, the direct sum in e^{s t}
+            wr = 2 * np.pi * res[r]["fr_Hz"]
+            bound = np.finfo(np.float64).eps * wr * (t + 1) * ring["T0_s"]
+            err = float(np.max(np.abs(phi - ref)) / np.max(np.abs(alr[r])))
+            worst = max(worst, err / bound)
+    # every rank ends with the same carry
+    import torch
+    c = torch.tensor([carry[0].real, carry[0].imag, carry[1].real, carry[1].imag], dtype=torch.float64)
+    parts = [torch.empty(4, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(parts, c)
+    same = all(bool(torch.equal(p, parts[0])) for p in parts)
+    out.put((rank, worst, same))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_phasor_scan_matches_the_direct_history_sum(world):
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, worst, same in res:
+        assert worst <= 1.0, (rank, worst)   # within the FP64 phase resolution of the longest delay
+        assert same
+
+
+def test_sharded_phasor_scan_is_one_process_scan_on_one_rank():
+    """Splitting changes only the grouping of the same compositions: one range
+    (no exchange) and many small ranges give the same phasors to 1e-13."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from paper_1809_00391_gb300 import sharded
+    ring, buckets, currents, res = _shard_fill()
+    rng = np.random.default_rng(2)
+    nb = len(buckets)
+    step = sharded.phasor_steps(ring, res[0], buckets)
+    E = rng.normal(size=nb) + 1j * rng.normal(size=nb)
+    carry = 0.3 - 0.2j
+    whole, c1 = sharded.exchange_turn(step, E, carry)
+    b = sharded.split_bounds(nb, 5)
+    maps = np.stack([sharded.segment_map(step[b[r]:b[r + 1]], E[b[r]:b[r + 1]]) for r in range(5)])
+    entry, c2 = sharded.compose(maps, carry)
+    parts = np.concatenate([sharded.apply(step[b[r]:b[r + 1]], E[b[r]:b[r + 1]], entry[r]) for r in range(5)])
+    assert np.max(np.abs(parts - whole)) <= 1e-13 * np.max(np.abs(whole))
+    assert abs(c1 - c2) <= 1e-13 * abs(c1)
+    # the definition written out: Phi_m = a_m X_{m-1}, X_m = Phi_m + E_m, X_{-1} = carry
+    X, ref = carry, []
+    for m in range(nb):
+        ref.append(step[m] * X)
+        X = ref[-1] + E[m]
+    assert np.max(np.abs(np.array(ref) - whole)) <= 1e-14 * np.max(np.abs(whole))
+    assert abs(X - c1) <= 1e-14 * abs(X)
