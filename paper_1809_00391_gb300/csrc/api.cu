@@ -170,6 +170,10 @@ struct mbt_ctx {
   cudaStream_t capture_stream = nullptr;
   // timing
   bool timing = false;
+  // failure-detection test hook (mbt_set_wait_test): resident grid-barrier
+  // wait limit (0: the default) and an unreachable barrier count
+  int64_t test_wait_ns = 0;
+  int test_unreachable = 0;
   double push_ms = 0, post_ms = 0;
   int64_t timed_launches = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -640,6 +644,8 @@ mbt_status check_device(mbt_ctx *c, const Plan &pl) {
   if (err != 0) {
     int zero = 0;
     cudaMemcpy(pl.error, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (err == kErrTmem) return fail(c, MBT_ERR_CUDA, "tensor memory could not be allocated");
+    if (err == kErrCount) return fail(c, MBT_ERR_ARG, "a cell count outside [0, 2^24) reached the wake");
     return fail(c, MBT_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", err);
   }
   return MBT_OK;
@@ -1650,6 +1656,8 @@ mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
   a.cluster = C;
   a.per = per;
   a.grid_sync = (c->nlong > 0 && c->nb > 1) ? 1 : 0;
+  a.wait_ns = c->test_wait_ns > 0 ? (unsigned long long)c->test_wait_ns : kResidentWaitNs;
+  a.extra_arrivals = c->test_unreachable ? 1u : 0u;
   const int64_t chunk = 1LL << 20;   // turns per launch (the barrier counter stays far from wrapping)
   for (int64_t done = 0; done < nturns; done += chunk) {
     a.nturns = (int)std::min<int64_t>(chunk, nturns - done);
@@ -1657,6 +1665,17 @@ mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
     if (e == cudaSuccess) e = launch_resident(a, c->nlong, c->rundev.nharm, c->nb, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "resident launch");
   }
+  return MBT_OK;
+}
+
+mbt_status mbt_set_wait_test(mbt_ctx *c, int64_t limit_ns, int unreachable) {
+  if (!c) return MBT_ERR_ARG;
+  c->err.clear();
+  if (limit_ns < 0 || limit_ns > 10000000000LL)
+    return fail(c, MBT_ERR_ARG, "limit_ns must lie in [0, 1e10] (0: the default of 2 s)");
+  if (unreachable != 0 && unreachable != 1) return fail(c, MBT_ERR_ARG, "unreachable must be 0 or 1");
+  c->test_wait_ns = limit_ns;
+  c->test_unreachable = unreachable;
   return MBT_OK;
 }
 

@@ -105,6 +105,14 @@ __device__ __forceinline__ float f64_to_f32_trunc(double d) {
   return __uint_as_float((__funnelshift_l(lo, hi, 3) - (896u << 23)) | (hi & 0x80000000u));
 }
 
+// A float near d for every finite |d| < 2^128 (a reference value for moment
+// sums, not a rounding): 0 for |d| < 2^-100, where the narrowing above does
+// not apply, the truncated value otherwise.  Integer pipe only.
+__device__ __forceinline__ float f64_to_f32_ref(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d);
+  return (hi & 0x7FF00000u) < ((1023u - 100u) << 20) ? 0.f : f64_to_f32_trunc(d);
+}
+
 // ---------------------------------------------------------------------------
 // complex helpers (double2 = re, im)
 // ---------------------------------------------------------------------------

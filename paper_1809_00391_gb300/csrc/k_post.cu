@@ -98,10 +98,12 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
                             double (*s_sum)[kBunchTile], const PostStage *st) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = R->nb, nbins = R->nbins;
-  // columns: 0-4 longitudinal, and with a transverse plane 6-9 (slots 5-8)
-  const int ncol = R->trans ? 9 : 5;
+  // per bunch: 0 the tau plane and 1 the delta plane (mean and variance,
+  // slots 0-1 and 2-3), 2 the outside count (slot 4), and with a transverse
+  // plane the raw sums of partial columns 6-9 (slots 5-8)
+  const int ncol = R->trans ? 7 : 3;
   for (int ci = threadIdx.x >> 5; ci < ncol; ci += kPostThreads / 32) {
-    const int b = threadIdx.x & 31, cidx = ci < 5 ? ci : ci + 1;
+    const int b = threadIdx.x & 31;
     if (b < nbt) {
       int tile0, ntiles;
       if (st) {
@@ -112,17 +114,42 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
         tile0 = bd.tile0;
         ntiles = bd.ntiles;
       }
-      const double *pp = p.partial + (size_t)tile0 * kPartials + cidx;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int i = 0;
-      for (; i + 4 <= ntiles; i += 4) {
-        a0 += pp[(size_t)(i + 0) * kPartials];
-        a1 += pp[(size_t)(i + 1) * kPartials];
-        a2 += pp[(size_t)(i + 2) * kPartials];
-        a3 += pp[(size_t)(i + 3) * kPartials];
+      const double *pp = p.partial + (size_t)tile0 * kPartials;
+      if (ci < 2) {
+        // each tile summed u = x - r_t and u^2 over its n_t particles (r_t
+        // its reference): the mean is sum(S1_t + n_t r_t) / N, the second
+        // moment about it sum(S2_t + 2 e_t S1_t + n_t e_t^2) / N with
+        // e_t = r_t - mean (the pairwise combination of the variance), all
+        // in FP64 in tile order
+        const int c1 = ci == 0 ? 0 : 2, cr = ci == 0 ? 5 : 10;
+        const double inv_n = st ? st->inv_n[b] : R->inv_n[m0 + b];
+        double a = 0.0;
+        for (int i = 0; i < ntiles; ++i) {
+          const double *q = pp + (size_t)i * kPartials;
+          a += fma(q[11], q[cr], q[c1]);
+        }
+        const double mean = a * inv_n;
+        double q2 = 0.0;
+        for (int i = 0; i < ntiles; ++i) {
+          const double *q = pp + (size_t)i * kPartials;
+          const double e = q[cr] - mean;
+          q2 += fma(q[11] * e, e, fma(2.0 * e, q[c1], q[c1 + 1]));
+        }
+        s_sum[2 * ci][b] = mean;
+        s_sum[2 * ci + 1][b] = q2 * inv_n;
+      } else {
+        const int cidx = ci == 2 ? 4 : ci + 3;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int i = 0;
+        for (; i + 4 <= ntiles; i += 4) {
+          a0 += pp[(size_t)(i + 0) * kPartials + cidx];
+          a1 += pp[(size_t)(i + 1) * kPartials + cidx];
+          a2 += pp[(size_t)(i + 2) * kPartials + cidx];
+          a3 += pp[(size_t)(i + 3) * kPartials + cidx];
+        }
+        for (; i < ntiles; ++i) a0 += pp[(size_t)i * kPartials + cidx];
+        s_sum[ci + 2][b] = (a0 + a1) + (a2 + a3);
       }
-      for (; i < ntiles; ++i) a0 += pp[(size_t)i * kPartials];
-      s_sum[ci][b] = (a0 + a1) + (a2 + a3);
     }
   }
   int32_t *hz = R->hist + ((size_t)(par ^ 1) * nb + m0) * nbins;
@@ -138,16 +165,12 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
   __syncthreads();
   if (warp == 0 && lane < nbt) {
     const double inv_n = st ? st->inv_n[lane] : R->inv_n[m0 + lane];
-    const double s0 = s_sum[0][lane], s1 = s_sum[1][lane], s2 = s_sum[2][lane], s3 = s_sum[3][lane];
     const double s4 = s_sum[4][lane];
-    const double mt = s0 * inv_n, md = s2 * inv_n;
-    const double vt = fmax(fma(s1, inv_n, -mt * mt), 0.0);
-    const double vd = fmax(fma(s3, inv_n, -md * md), 0.0);
     double *rec = R->rec + ((size_t)(turn % R->cap) * nb + m0 + lane) * kRecord;
-    rec[0] = mt;
-    rec[1] = sqrt(vt);
-    rec[2] = md;
-    rec[3] = sqrt(vd);
+    rec[0] = s_sum[0][lane];
+    rec[1] = sqrt(fmax(s_sum[1][lane], 0.0));
+    rec[2] = s_sum[2][lane];
+    rec[3] = sqrt(fmax(s_sum[3][lane], 0.0));
     rec[4] = (double)(st ? st->n[lane] : p.bunches[R->bunch_base + m0 + lane].n) - s4;
     rec[5] = s4;
     if (R->trans) {

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
     phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
   }
   const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
+  float tref = 0.f, dref = 0.f;   // moment reference: the tile's first particle before the push
 
   float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;
   int nout = 0;
@@ -143,6 +144,10 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
       atomicExch(p.error, kErrTimeout);
       s_abort = 1;
     }
+    if (ch == 0) {
+      tref = reinterpret_cast<const float *>(sg)[0];
+      dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kChunk * sizeof(float))[0]);
+    }
     const int q = ch * kChunk + 4 * (int)threadIdx.x;   // first particle of this thread's quad in the tile
     if (!s_abort && q < t.count) {
       const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
@@ -154,11 +159,11 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
       double dd[4] = {da.x, da.y, db.x, db.y};
       const int nvalid = min(4, t.count - q);
       if (ngp)
-        quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
-                                   sd, sd2, nout);
+        quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, tref,
+                                         dref, st, st2, sd, sd2, nout);
       else
-        quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st, st2,
-                                    sd, sd2, nout);
+        quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, tref,
+                                          dref, st, st2, sd, sd2, nout);
       *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
       *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
       *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
@@ -194,6 +199,11 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
 #pragma unroll
     for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
     p.partial[(size_t)blockIdx.x * kPartials + threadIdx.x] = acc;
+  } else if (threadIdx.x == 5) {
+    double *pp = p.partial + (size_t)blockIdx.x * kPartials;
+    pp[5] = (double)tref;
+    pp[10] = (double)dref;
+    pp[11] = (double)t.count;
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
@@ -251,9 +261,10 @@ struct StreamSmem {
   uint64_t full[kStreamStages], empty[kStreamStages];   // stage loaded / handed back by every consumer warp
   uint64_t tdb[kSlots], thb[kSlots], freed[kSlots];      // slot descriptor / data arrived, slot set up by the consumers
   int issued_full[kStreamStages], issued_tdb[kSlots], issued_thb[kSlots];   // phases issued (producer, for draining)
-  float red[kConsumerWarps][5];
+  float red[kConsumerWarps][5];      // per-warp sums of a tile
   float2 phi[kMaxLong];
 };
+
 
 __device__ __forceinline__ void consumers_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory");
@@ -436,6 +447,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
     const uint32_t turn32 = (uint32_t)turn, bunch32 = (uint32_t)D.td.m;
     consumers_sync();   // tables built, slot read
     if (tid == 0) mbar_arrive(&S.freed[sl]);
+    // the previous tile's sums over the warps (its per-warp sums are in the
+    // other half of S.red; the next hand-in writes this tile's half)
+
     PushConstF c;
     c.nbins = nbins;
     c.invD = __ldg(&RC->invD);
@@ -460,6 +474,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
       phi[r] = r < nl ? S.phi[r] : make_float2(0.f, 0.f);
     }
     const uint32_t k0 = __ldg(&RC->key0), k1 = __ldg(&RC->key1);
+    float tref = 0.f, dref = 0.f;   // moment reference: the tile's first particle before the push
     const int nc = (count + kStreamChunk - 1) / kStreamChunk;
 
     // ---- the tile's chunks ----
@@ -471,6 +486,10 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
         atomicExch(p.error, kErrTimeout);
       }
       const uint8_t *sg = stages + stg * kStreamStageBytes;
+      if (ci == 0) {
+        tref = reinterpret_cast<const float *>(sg)[0];
+        dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kStreamChunk * sizeof(float))[0]);
+      }
       const float4 tv = reinterpret_cast<const float4 *>(sg)[tid];
       const double2 da = reinterpret_cast<const double2 *>(sg + kStreamChunk * sizeof(float))[2 * tid];
       const double2 db = reinterpret_cast<const double2 *>(sg + kStreamChunk * sizeof(float))[2 * tid + 1];
@@ -485,11 +504,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
         const int nvalid = min(4, count - q);
         const float4 *hc = RC->harm;
         if (ngp)
-          quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nl, la, lw, phi, omD_d, hc, nharm, tt, dd, rr, nvalid, st, st2,
-                                           sd, sd2, nout);
+          quad_push<NLONG_MAX, true, HARM>(c, sVd, sH, nl, la, lw, phi, omD_d, hc, nharm, tt, dd, rr, nvalid, tref,
+                                           dref, st, st2, sd, sd2, nout);
         else
-          quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nl, la, lw, phi, omD_d, hc, nharm, tt, dd, rr, nvalid, st,
-                                            st2, sd, sd2, nout);
+          quad_push<NLONG_MAX, false, HARM>(c, sVd, sH, nl, la, lw, phi, omD_d, hc, nharm, tt, dd, rr, nvalid, tref,
+                                            dref, st, st2, sd, sd2, nout);
         *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
         *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
         *reinterpret_cast<double2 *>(del + q + 2) = make_double2(dd[2], dd[3]);
@@ -520,16 +539,31 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
         sH[b] = 0;
       }
     }
+    if (tid == 37 && !failed) {
+      double *pp = p.partial + (size_t)pslot * kPartials;
+      pp[5] = (double)tref;
+      pp[10] = (double)dref;
+      pp[11] = (double)count;
+    }
     if (tid >= 32 && tid < 37 && !failed) {
-      // the tile's sums over the warps, in a fixed order
+      // the tile's sums over the warps: a pairwise tree of fixed shape over
+      // the warps' FP32 sums of values relative to the tile's reference (an
+      // FP64 sum here would stall every warp at the next tile's barrier on
+      // GB300's FP64 pipe: +5 % per turn measured); FP64 from the tile on
       const int col = tid - 32;
-      float acc = S.red[0][col];
-      for (int w = 1; w < kConsumerWarps; ++w) acc += S.red[w][col];
-      p.partial[(size_t)pslot * kPartials + col] = (double)acc;
+      float a[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) a[i] = S.red[i][col] + (16 + i < kConsumerWarps ? S.red[16 + i][col] : 0.f);
+#pragma unroll
+      for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+        for (int i = 0; i < h; ++i) a[i] += a[i + h];
+      p.partial[(size_t)pslot * kPartials + col] = (double)a[0];
     }
     // the next tile's set-up rewrites sVd and S.phi only after its own wait
-    // and before its barrier; S.red and sH are rewritten only after it
+    // and before its barrier; sH and this half of S.red only after it
   }
+
 }
 
 // ---------------------------------------------------------------------------
@@ -699,6 +733,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
   const bool texc = tc.nx != 0.f || tc.nxp != 0.f;
   const float vrw = tr ? rw_voltage_f32(R, t.m, turn, s_red[0]) : 0.f;
+  float tref = 0.f, dref = 0.f;   // moment reference: the tile's first particle before the push
 
   float mom[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int nout = 0;
@@ -709,6 +744,10 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
     if (!mbar_wait_bounded(&full[slot], (uint32_t)((ch / kStages) & 1), kPushWaitNs)) {
       atomicExch(p.error, kErrTimeout);
       s_abort = 1;
+    }
+    if (ch == 0) {
+      tref = reinterpret_cast<const float *>(sg)[0];
+      dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kChunk * 4)[0]);
     }
     const int q = ch * kChunk + 4 * (int)threadIdx.x;
     if (!s_abort && q < t.count) {
@@ -731,15 +770,15 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
           normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
         }
         quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, vrw, tt,
-                               dd, xx, pp, rr, rx, rp, nvalid, mom, nout);
+                               dd, xx, pp, rr, rx, rp, nvalid, tref, dref, mom, nout);
         *reinterpret_cast<float4 *>(xg + q) = make_float4(xx[0], xx[1], xx[2], xx[3]);
         *reinterpret_cast<float4 *>(pg + q) = make_float4(pp[0], pp[1], pp[2], pp[3]);
       } else if (ngp) {
         quad_push<NLONG_MAX, true, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid,
-                                         mom[0], mom[1], mom[2], mom[3], nout);
+                                         tref, dref, mom[0], mom[1], mom[2], mom[3], nout);
       } else {
         quad_push<NLONG_MAX, false, true>(c, sVd, sH, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid,
-                                          mom[0], mom[1], mom[2], mom[3], nout);
+                                          tref, dref, mom[0], mom[1], mom[2], mom[3], nout);
       }
       *reinterpret_cast<float4 *>(tau + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
       *reinterpret_cast<double2 *>(del + q) = make_double2(dd[0], dd[1]);
@@ -774,6 +813,11 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
     for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
     const int col = threadIdx.x < 5 ? threadIdx.x : threadIdx.x + 1;
     p.partial[(size_t)blockIdx.x * kPartials + col] = acc;
+  } else if (threadIdx.x == 9) {
+    double *pp = p.partial + (size_t)blockIdx.x * kPartials;
+    pp[5] = (double)tref;
+    pp[10] = (double)dref;
+    pp[11] = (double)t.count;
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
   float *dg = tr ? static_cast<float *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
@@ -858,6 +902,15 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
   double st = 0.0, st2 = 0.0, sd = 0.0, sd2 = 0.0, sx = 0.0, sx2 = 0.0, sp = 0.0, sp2 = 0.0;
   int nout = 0;
   const double vrw = tr ? rw_voltage_f64(R, t.m, turn, s_red[0]) : 0.0;
+  // moment reference: the tile's first particle before the push (read by
+  // every thread before thread 0 overwrites it)
+  __shared__ double s_ref[2];
+  if (threadIdx.x == 0) {
+    s_ref[0] = static_cast<const double *>(R->tau)[bd.off + t.start];
+    s_ref[1] = R->delta[bd.off + t.start];
+  }
+  __syncthreads();
+  const double2 mref = make_double2(s_ref[0], s_ref[1]);
 
 #pragma unroll 1
   for (int it = 0; it < kF64QuadsPerThread; ++it) {
@@ -934,10 +987,11 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
       } else {
         ++nout;
       }
-      st += tp;
-      st2 += tp * tp;
-      sd += d;
-      sd2 += d * d;
+      const double ou = tp - mref.x, ov = d - mref.y;   // relative to the moment reference
+      st += ou;
+      st2 += ou * ou;
+      sd += ov;
+      sd2 += ov * ov;
     }
     if (tr) {
       *reinterpret_cast<double2 *>(xg + q) = make_double2(xx[0], xx[1]);
@@ -978,6 +1032,11 @@ __global__ void __launch_bounds__(kPushThreads) k_push_f64(const Plan p) {
     for (int w = 0; w < kPushThreads / 32; ++w) acc += s_red[w][threadIdx.x];
     const int col = threadIdx.x < 5 ? threadIdx.x : threadIdx.x + 1;   // columns 0-4, 6-9
     p.partial[(size_t)blockIdx.x * kPartials + col] = acc;
+  } else if (threadIdx.x == 9) {
+    double *pp = p.partial + (size_t)blockIdx.x * kPartials;
+    pp[5] = mref.x;
+    pp[10] = mref.y;
+    pp[11] = (double)t.count;
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
   double *dg = tr ? static_cast<double *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;

@@ -23,7 +23,6 @@ namespace cg = cooperative_groups;
 
 namespace mbt {
 
-constexpr unsigned long long kResidentWaitNs = 2000000000ull;
 
 struct ResidentSmem {
   double *sD;      // [per]
@@ -65,7 +64,7 @@ template <int NLONG_MAX, bool HARM>
 __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const ResidentArgs a) {
   extern __shared__ __align__(16) uint8_t sm_res[];
   __shared__ float s_red[kResidentThreads / 32][5];
-  __shared__ double s_mom[5];
+  __shared__ double s_mom[8];   // the CTA's sums of u, u^2, v, v^2, n_out; its tau_ref, delta_ref, particles
   __shared__ float2 s_phi[kMaxLong];
   __shared__ float4 s_hc[kMaxHarm];
   __shared__ double2 s_phid[kMaxLong];
@@ -149,9 +148,13 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
 #pragma unroll
     for (int r = 0; r < NLONG_MAX; ++r) phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
     for (int k = tid; k < nbins; k += kResidentThreads) lh[k] = 0;
+    // moment reference: the slice's first particle before the push (read by
+    // every thread before the barrier, after which thread 0 overwrites it)
+    const float tref = ns > 0 ? S.sT[0] : 0.f, dref = ns > 0 ? f64_to_f32_ref(S.sD[0]) : 0.f;
     __syncthreads();
 
-    // push the slice (quads of consecutive particles, one Philox block each)
+    // push the slice (quads of consecutive particles, one Philox block each);
+    // moment partials relative to the reference
     float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;
     int nout = 0;
     for (int q = 4 * tid; q < ns; q += 4 * kResidentThreads) {
@@ -165,10 +168,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
       double dd[4] = {da.x, da.y, db.x, db.y};
       const int nvalid = min(4, ns - q);
       if (ngp)
-        quad_push<NLONG_MAX, true, HARM>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st,
+        quad_push<NLONG_MAX, true, HARM>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, tref, dref, st,
                                    st2, sd, sd2, nout);
       else
-        quad_push<NLONG_MAX, false, HARM>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, st,
+        quad_push<NLONG_MAX, false, HARM>(c, S.sVd, lh, nlong, la, lw, phi, omD_d, s_hc, nharm, tt, dd, rr, nvalid, tref, dref, st,
                                     st2, sd, sd2, nout);
       *reinterpret_cast<float4 *>(S.sT + q) = make_float4(tt[0], tt[1], tt[2], tt[3]);
       *reinterpret_cast<double2 *>(S.sD + q) = make_double2(dd[0], dd[1]);
@@ -191,6 +194,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
       double acc = 0.0;
       for (int w = 0; w < kResidentThreads / 32; ++w) acc += (double)s_red[w][tid];
       s_mom[tid] = acc;
+    } else if (tid == 5) {
+      s_mom[5] = (double)tref;
+      s_mom[6] = (double)dref;
+      s_mom[7] = (double)ns;
     }
     cl.sync();   // #1: every CTA histogram and moment partial of the turn is complete
 
@@ -200,24 +207,35 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
       for (int cr = 0; cr < C; ++cr) sum += cl.map_shared_rank(lh, cr)[k];
       S.bh[k] = sum;
     }
-    if (rank == 0 && tid < 5) {
-      double acc = 0.0;
-      for (int cr = 0; cr < C; ++cr) acc += cl.map_shared_rank(s_mom, cr)[tid];
-      s_mom[tid] = acc;   // only this thread reads or writes this slot of CTA 0 until barrier #2
-    }
     __syncthreads();
     if (rank == 0 && tid == 0) {
+      // the CTAs' sums about their own references combined exactly (the
+      // pairwise form of the variance): the mean first, then every CTA's
+      // second moment about it
       const double inv_n = R->inv_n[m];
-      const double mt = s_mom[0] * inv_n, md = s_mom[2] * inv_n;
-      const double vt = fmax(fma(s_mom[1], inv_n, -mt * mt), 0.0);
-      const double vd = fmax(fma(s_mom[3], inv_n, -md * md), 0.0);
+      double at = 0.0, ad = 0.0, s4 = 0.0;
+      for (int cr = 0; cr < C; ++cr) {
+        const double *q = cl.map_shared_rank(s_mom, cr);
+        at += fma(q[7], q[5], q[0]);
+        ad += fma(q[7], q[6], q[2]);
+        s4 += q[4];
+      }
+      const double mt = at * inv_n, md = ad * inv_n;
+      double qt = 0.0, qd = 0.0;
+      for (int cr = 0; cr < C; ++cr) {
+        const double *q = cl.map_shared_rank(s_mom, cr);
+        const double et = q[5] - mt, ed = q[6] - md;
+        qt += fma(q[7] * et, et, fma(2.0 * et, q[0], q[1]));
+        qd += fma(q[7] * ed, ed, fma(2.0 * ed, q[2], q[3]));
+      }
+      const double vt = fmax(qt * inv_n, 0.0), vd = fmax(qd * inv_n, 0.0);
       double *rec = R->rec + ((size_t)(turn % R->cap) * nb + m) * kRecord;
       rec[0] = mt;
       rec[1] = sqrt(vt);
       rec[2] = md;
       rec[3] = sqrt(vd);
-      rec[4] = (double)bd.n - s_mom[4];
-      rec[5] = s_mom[4];
+      rec[4] = (double)bd.n - s4;
+      rec[5] = s4;
     }
     // rows [rank B, rank B + B) of V = q sum_{k<=j} lag[j-k] count[k]
     {
@@ -254,10 +272,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
       if (tid == 0 && a.grid_sync) {
         __threadfence();
         atomicAdd(a.gbar, 1u);
-        const unsigned int target = (unsigned int)(it + 1) * (unsigned int)nb;
+        const unsigned int target = (unsigned int)(it + 1) * (unsigned int)nb + a.extra_arrivals;
         const unsigned long long t0 = global_timer_ns();
         while (atomicAdd(a.gbar, 0u) < target) {
-          if (global_timer_ns() - t0 > kResidentWaitNs) {
+          if (global_timer_ns() - t0 > a.wait_ns) {
             atomicExch(p.error, kErrTimeout);
             s_fail = 1;
             break;

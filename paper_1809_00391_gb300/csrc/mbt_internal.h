@@ -20,7 +20,10 @@ constexpr int kMixedQuadsPerThread = 8;                                    // 4 
 constexpr int kMixedTile = kPushThreads * 4 * kMixedQuadsPerThread;        // 8192 particles
 constexpr int kF64QuadsPerThread = 2;                                      // 4 particles per quad
 constexpr int kF64Tile = kPushThreads * 4 * kF64QuadsPerThread;            // 2048 particles
-constexpr int kPartials = 10;        // sums of tau, tau^2, delta, delta^2, n_out, pad, x, x^2, x', x'^2
+// per push tile: sums of u, u^2, v, v^2 (u = tau - tau_ref, v = delta - delta_ref,
+// the refs being the tile's first particle before the push), n_out, tau_ref,
+// x, x^2, x', x'^2, delta_ref, particle count
+constexpr int kPartials = 12;
 constexpr int kTRecord = 4;          // transverse record: <x>, rms x, <x'>, rms x'
 constexpr int kTransRows = 32;       // transverse short-range rows per post job (kMixed)
 constexpr int kRecord = 6;           // <tau>, rms tau, <delta>, rms delta, n_in, n_out
@@ -176,6 +179,7 @@ struct Plan {
 #endif
 constexpr int kResidentThreads = MBT_RESIDENT_THREADS;
 constexpr int kResidentMaxBunches = 32;   // one warp scans the fill
+constexpr unsigned long long kResidentWaitNs = 2000000000ull;   // grid-barrier wait limit (default)
 struct ResidentArgs {
   Plan plan;              // the run's own plan (runs[0], bunches)
   double2 *E;             // [2][nlong][nb] emissions, double-buffered by turn parity
@@ -184,6 +188,9 @@ struct ResidentArgs {
   int per;                // particles per CTA slice (multiple of 4)
   int nturns;
   int grid_sync;          // 1 if clusters must meet every turn (long-range coupling of several bunches)
+  unsigned long long wait_ns;    // limit of the grid-barrier wait
+  unsigned int extra_arrivals;   // arrivals the barrier waits for beyond the bunches (0; 1 in the
+                                 // failure-detection test, a count nothing reaches)
 };
 size_t resident_smem_bytes(int per, int nbins);
 cudaError_t launch_resident(const ResidentArgs &a, int nlong, int nharm, int nb, cudaStream_t s);
@@ -199,6 +206,7 @@ cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s);
 // hoff: device array, first particle of each bunch in the host arrays
 cudaError_t launch_load_host(const Plan &p, int precision, const double *tau_h, const double *del_h,
                              const long long *hoff, cudaStream_t s);
+
 size_t post_smem_bytes(int precision, int max_nbins);
 cudaError_t configure_kernels();
 // Allocation-free tensor-core wake of one run (scratch: a static device array

@@ -69,11 +69,16 @@ __device__ __forceinline__ float push_one(const PushConstF &c, const float2 *sVd
 
 // Four consecutive particles: push, deposit, moment partials.  Full quads
 // (nvalid == 4, all but a bunch's last) take no per-particle validity tests.
+// The partials are sums of u = tau - tref and v = delta - dref (tref, dref:
+// the tile's first particle before the push, which lies within a few bunch
+// lengths of every particle of the bunch), so that the variance formed from
+// them does not cancel when the centroid sits far from the bucket centre.
 template <int NLONG_MAX, bool NGP, bool HARM>
 __device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd, int *sH, int nlong, const float *la,
                                           const float *lw, const float2 *phi, double omD_d, const float4 *hc,
                                           int nharm, float (&tt)[4], double (&dd)[4], const float (&rr)[4],
-                                          int nvalid, float &st, float &st2, float &sd, float &sd2, int &nout) {
+                                          int nvalid, float tref, float dref, float &st, float &st2, float &sd,
+                                          float &sd2, int &nout) {
   const bool full = nvalid == 4;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -84,10 +89,11 @@ __device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd
       const float xb = fmaf(t1, c.invD, c.HinvD);
       if (xb >= -0.5f && xb < c.fnb - 0.5f) atomicAdd(&sH[__float2int_rn(xb)], 1);
       else ++nout;
-      st += t1;
-      st2 = fmaf(t1, t1, st2);
-      sd += df;
-      sd2 = fmaf(df, df, sd2);
+      const float u = t1 - tref, v = df - dref;
+      st += u;
+      st2 = fmaf(u, u, st2);
+      sd += v;
+      sd2 = fmaf(v, v, sd2);
     }
   }
 }
@@ -175,8 +181,8 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
                                             const float4 *hc, int nharm, bool ngp, float vrw, float (&tt)[4],
                                             double (&dd)[4],
                                             float (&xx)[4], float (&pp)[4], const float (&rr)[4],
-                                            const float (&rx)[4], const float (&rp)[4], int nvalid, float (&mom)[8],
-                                            int &nout) {
+                                            const float (&rx)[4], const float (&rp)[4], int nvalid, float tref,
+                                            float dref, float (&mom)[8], int &nout) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (e < nvalid) {
@@ -192,10 +198,11 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
       } else {
         ++nout;
       }
-      mom[0] += t1;
-      mom[1] = fmaf(t1, t1, mom[1]);
-      mom[2] += df;
-      mom[3] = fmaf(df, df, mom[3]);
+      const float u = t1 - tref, v = df - dref;   // as in quad_push
+      mom[0] += u;
+      mom[1] = fmaf(u, u, mom[1]);
+      mom[2] += v;
+      mom[3] = fmaf(v, v, mom[3]);
       mom[4] += xx[e];
       mom[5] = fmaf(xx[e], xx[e], mom[5]);
       mom[6] += pp[e];

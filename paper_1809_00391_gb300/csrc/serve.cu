@@ -86,7 +86,7 @@ int64_t estimate_bytes(const mbt_request &r, int turns_per_step) {
     for (int64_t mt = 0; mt < nbins / 128; ++mt) toep += 512 * std::min<int64_t>(nbins, 128 * (mt + 1));
   }
   const int64_t bytes = n_alloc * (mixed ? 12 : 16) + 2 * nb * nbins * 4 + nb * nbins * (mixed ? 4 : 8) +
-                        nl * nb * 32 + nl * ntb * 48 + nl * 16 + (int64_t)turns_per_step * nb * 48 + 16 + nb * 20 +
+                        nl * nb * 32 + nl * ntb * 48 + nl * 16 + (int64_t)turns_per_step * nb * 48 + 16 + nb * 28 +
                         nbins * 4 + nl * nb * 16 + nl * nbins * 24 + toep;
   const int64_t tiles = n_alloc / 64 + 2 * nb + 16;
   return bytes + tiles * 96 + (64 << 10);

@@ -23,7 +23,7 @@ def pkg():
 def _declared():
     src = open(os.path.join(ROOT, "include", "mbt.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mbt_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mbt_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_and_binding_agree(pkg):
@@ -223,3 +223,20 @@ def test_wake_noalloc_refuses_misaligned_pointers_before_device_work(pkg):
     with pytest.raises(pkg.MBTError, match="4-byte aligned") as e:
         pkg.wake_noalloc(run.ring, run.resonators, 256, 5.0, q, 0x10000, 0x20002)
     assert e.value.status == 1
+
+
+def test_wait_test_hook_validates_its_arguments(pkg):
+    import ctypes
+    L = pkg.lib()
+    st, h = _create(pkg, W.ring_r0(), prec=1)
+    assert st == 0
+    try:
+        assert L.mbt_set_wait_test(h, -1, 0) == 1
+        assert L.mbt_set_wait_test(h, 20_000_000_000, 0) == 1
+        assert L.mbt_set_wait_test(h, 1000, 2) == 1
+        assert L.mbt_set_wait_test(h, 20_000_000, 1) == 0
+        assert L.mbt_set_wait_test(h, 0, 0) == 0
+        assert L.mbt_set_wait_test(None, 0, 0) == 1
+    finally:
+        L.mbt_destroy(h)
+    assert ctypes is not None
