@@ -2,7 +2,7 @@
 
 Coupled-bunch growth rates of the mixed-precision and FP64 paths against the
 oracle and against Eq. 7 (within 2 %); the 390-bunch fill at full size
-(3.9e7 macro-particles) against the oracle for a few turns: moments, exact
+(3.9e7 macro-particles) against the oracle for 30 turns: moments, exact
 short-range convolution of the GPU's own histograms, conservation of
 particles; three bunches at full size over 1000 turns (moments within 1e-3).
 """
@@ -94,8 +94,8 @@ def test_three_adjacent_bunches_growth_rate_matches_oracle(pkg, oracle_mod):
 
 def test_fill390_full_size_against_oracle(pkg, oracle_mod):
     run = W.fill_390(seed=1)
-    turns = 3
-    tr = pkg.tracker_for_run(run, record_turns=16)
+    turns = 30
+    tr = pkg.tracker_for_run(run, record_turns=64)
     tr.init_particles()
     tr.track(turns)
     rec_g = tr.moments(0, turns)
