@@ -46,7 +46,15 @@ push roofline (40 B per macro-particle-turn: tau, delta, x, x').
 
 FP64 tracker: python bench.py --workload three_f64 tracks three bunches of
 1e5 macro-particles (broadband + HOM, long and short range) on the FP64 path
-and prints its throughput and the FP64 push's time per launch.
+and prints its throughput and the FP64 push's time per launch;
+--workload fill390_f64 tracks the 390-bunch fill on the FP64 path and on the
+mixed path, and prints both throughputs and the FP64 push against the GPU's
+measured DFMA throughput.
+
+The default line also carries a bounded serving sample (--serving-requests,
+Poisson requests at about the server's capacity: p50/p99 latency) and the
+FP64 oracle timed on all host cores (one process per core, each tracking a
+contiguous subset of the bunches).
 """
 from __future__ import annotations
 
@@ -88,11 +96,16 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--state-file", default="/tmp/mbt_fill390.state", help="state: checkpoint of the fill")
+    ap.add_argument("--at-turn", type=int, default=1500, help="state: turn at which the checkpoint is taken")
+    ap.add_argument("--serving-requests", type=int, default=40,
+                    help="requests of the bounded serving sample in the default line (0 = skip)")
     ap.add_argument("--saturated-turn", type=int, default=1500,
                     help="also time the push from this turn on (saturated instability); 0 = skip")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
-    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t", "three_f64"],
+    ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t", "three_f64",
+                                           "fill390_f64", "state"],
                     default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
@@ -312,21 +325,51 @@ class ClockSampler:
                 "power_w_max": float(pw.max()), "reasons": reasons, "samples": len(rows), "source": "nvml"}
 
 
-def cpu_baseline(run: W.Run, turns: int = 2):
-    """The FP64 oracle on this host's cores (single-threaded), on a bounded
-    sample: the first `turns` turns of the full fill."""
+def _oracle_part(args):
+    """One worker of the CPU baseline: the oracle (single-threaded) tracking
+    bunches [lo, hi) of the fill as a fill of their own."""
+    sys.path.insert(0, ROOT)
     import oracle
-    oracle.build()
-    s = oracle.OracleSim(run.ring, run.resonators, run.nbins, run.half_width_sigmas, run.buckets,
-                         run.currents_A, run.n_mp, run.seed, run.flags)
+    run, lo, hi, turns = args
+    part = W.Run(run.ring, run.resonators, run.buckets[lo:hi], run.currents_A[lo:hi], run.n_mp[lo:hi],
+                 seed=run.seed, turns=turns, precision=run.precision, flags=run.flags, nbins=run.nbins,
+                 half_width_sigmas=run.half_width_sigmas)
+    s = oracle.OracleSim(part.ring, part.resonators, part.nbins, part.half_width_sigmas, part.buckets,
+                         part.currents_A, part.n_mp, part.seed, part.flags)
     s.init_particles()
     t0 = time.perf_counter()
     s.track(turns, record=False)
     dt = time.perf_counter() - t0
     s.close()
-    v = run.n_particles * turns / dt
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {turns} turns of the full {run.nb}-bunch fill ({run.n_particles} mp), FP64, {dt:.1f} s"}
+    return int(part.n_particles) * turns, dt
+
+
+def cpu_baseline(run: W.Run, turns: int = 2, workers: int = 0):
+    """The FP64 oracle on this host's cores, on a bounded sample: `turns`
+    turns of the full fill, its bunches split into one contiguous subset per
+    core, each tracked by a single-threaded oracle in a worker process as a
+    fill of its own (throughput only: the subsets do not see each other's
+    long-range wake).  The pool is started with spawn before any GPU work of
+    the worker processes."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    n = workers or (os.cpu_count() or 1)
+    n = max(1, min(n, run.nb))
+    bounds = [(k * run.nb) // n for k in range(n + 1)]
+    jobs = [(run, bounds[k], bounds[k + 1], turns) for k in range(n)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_part, jobs)
+    wall = time.perf_counter() - t0
+    work = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    v = work / busy
+    return {"value": v, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{turns} turns of the full {run.nb}-bunch fill ({run.n_particles} mp), FP64, split into "
+                      f"{n} bunch subsets tracked independently by {n} single-threaded oracle processes; "
+                      f"slowest worker {busy:.1f} s (wall {wall:.1f} s with process start)",
+            "per_core": v / n}
 
 
 def reference_arm(args, rank, world):
@@ -371,22 +414,18 @@ def reference_arm(args, rank, world):
     return 0
 
 
-def serving_bench(args, rank, local):
-    """Open-loop replay of a Poisson request stream into mbt_server: each
-    request is submitted at its arrival time (a host thread sleeps until
-    then); latency = result time - submission time on the server's clock."""
-    if rank != 0:
-        return 0
+def serving_sample(n_requests: int, rate_hz: float, max_active: int = 16, turns_per_step: int = 200,
+                   budget: int = 64 << 30, seed: int = 7):
+    """Open-loop replay of a Poisson request stream into the continuous-
+    batching server: each request is submitted at its arrival time (a host
+    thread sleeps until then); latency = result time - submission time on the
+    server's clock.  Returns (latencies, queue waits, delivered mp-turns/s,
+    stats, span)."""
     import threading
-
-    import torch
-    torch.cuda.set_device(local)
     import paper_1809_00391_gb300 as pkg
-    pkg.build()
-    stream = W.serving_stream(args.requests, rate_hz=args.rate, seed=7)
+    stream = W.serving_stream(n_requests, rate_hz=rate_hz, seed=seed)
     work = np.array([rq.run.turns * rq.run.n_particles for rq in stream], np.float64)
-    budget = 64 << 30
-    srv = pkg.Server(hbm_budget_bytes=budget, max_active=args.max_active, turns_per_step=args.turns_per_step)
+    srv = pkg.Server(hbm_budget_bytes=budget, max_active=max_active, turns_per_step=turns_per_step)
     ids = [None] * len(stream)
     t_wall0 = time.perf_counter()
 
@@ -397,19 +436,35 @@ def serving_bench(args, rank, local):
                 time.sleep(delay)
             ids[i] = srv.submit(rq.run)
 
-    with ClockSampler(local) as clk:
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        for rid in ids:
-            srv.wait(rid, timeout_s=3600)
-    clocks = clk.summary()
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    for rid in ids:
+        srv.wait(rid, timeout_s=3600)
     st = [srv.status(rid) for rid in ids]
-    lat = np.array([s["t_finish"] - s["t_submit"] for s in st])
-    queue = np.array([s["t_start"] - s["t_submit"] for s in st])
-    span = max(s["t_finish"] for s in st) - min(s["t_submit"] for s in st)
+    lat = np.array([x["t_finish"] - x["t_submit"] for x in st])
+    queue = np.array([x["t_start"] - x["t_submit"] for x in st])
+    span = max(x["t_finish"] for x in st) - min(x["t_submit"] for x in st)
     stats = srv.stats()
     srv.close()
+    return lat, queue, work, stats, span
+
+
+def serving_bench(args, rank, local):
+    """The serving workload: an open-loop Poisson stream of instability-scan
+    requests into mbt_server (serving_sample), with p50/p99 latency, queue
+    wait and delivered throughput."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    budget = 64 << 30
+    with ClockSampler(local) as clk:
+        lat, queue, work, stats, span = serving_sample(args.requests, args.rate, args.max_active,
+                                                       args.turns_per_step, budget)
+    clocks = clk.summary()
     thr = work.sum() / span
     line = {"metric": "serving latency p99 (instability-scan requests, open-loop Poisson stream)",
             "value": float(np.percentile(lat, 99)), "unit": "s", "n_gpus": 1, "higher_is_better": False,
@@ -666,6 +721,112 @@ def three_f64_bench(args, rank, local):
     return 0
 
 
+FP64_FLOPS_PER_MP_TURN = 182   # FP64 flops of the FP64 push per macro-particle-turn (ncu count: 71 DFMA, 21 DADD, 19 DMUL)
+
+
+def fill390_f64_bench(args, rank, local):
+    """The 390-bunch fill on the plain FP64 tracker (tau and delta FP64, every
+    step in FP64), beside the mixed-precision path on the same fill: both
+    timed as K graph-replayed turns with CUDA events; the FP64 push against
+    the GPU's measured DFMA throughput (mbt_probe_fp64_fma)."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    K, Wm = min(args.steps, 200), max(args.warmup, 3)
+    G = max(1, min(GRAPH_TURNS, K))
+    stream = torch.cuda.current_stream()
+    peak, sms = pkg.probe_fp64_fma(stream=stream)
+
+    def timed(prec):
+        run = W.fill_390(seed=1, precision=prec)
+        tr = pkg.tracker_for_run(run, record_turns=K + Wm + 2 * G + 64)
+        tr.init_particles(stream)
+        tr.set_graph(G)
+        tr.track(max(Wm, G), stream)
+        tr.sync()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            tr.track(K, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        tr.sync()
+        ms = ev0.elapsed_time(ev1)
+        tr.set_timing(True)
+        tr.track(min(K, 50), stream)
+        tr.sync()
+        push_ms, post_ms, launches = tr.timing()
+        tr.close()
+        return run, ms, push_ms / max(1, launches), post_ms / max(1, launches), clk.summary()
+
+    run, ms64, push64, post64, clocks = timed(W.PREC_F64)
+    _, msmx, pushmx, _, _ = timed(W.PREC_MIXED)
+    n = run.n_particles
+    achieved = FP64_FLOPS_PER_MP_TURN * n / (push64 * 1e-3)
+    line = {"metric": "macro-particle-turns/s (390-bunch fill, FP64 tracker)", "value": n * K / (ms64 * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms64 / K, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": run.name + ", FP64 tracker", "turns_timed": K,
+                       "l2": "state 624 MB > 129 MB L2 (no flush needed)"},
+            "roofline": {"bound": "fp64 pipe", "kernel": "k_push_f64", "achieved": achieved, "peak": peak,
+                         "unit": "FLOP/s", "frac": achieved / peak,
+                         "peak_source": f"measured: DFMA throughput probe, 8 CTAs x {sms} SMs x 256 threads, "
+                                        f"CUDA events", "flops_per_unit": FP64_FLOPS_PER_MP_TURN,
+                         "unit_count": n, "push_us": push64 * 1e3, "post_us": post64 * 1e3},
+            "mixed_same_fill": {"value": n * K / (msmx * 1e-3), "ms_per_step": msmx / K, "push_us": pushmx * 1e3,
+                                "speedup_over_f64": ms64 / msmx},
+            "gpu_launches": 2 * K, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def state_bench(args, rank, local):
+    """Profiling helper for the 390-bunch fill at a chosen beam state: if
+    --state-file does not exist yet, track the fill from its matched start
+    for --at-turn turns and save the state there; then load that state into
+    a fresh tracker and track --steps turns with plain launches (so that a
+    profiler run of this command sees only a few launches before the push it
+    captures)."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    run = W.fill_390(seed=1)
+    path = args.state_file
+    made = False
+    if not os.path.exists(path):
+        tr = pkg.tracker_for_run(run, record_turns=64)
+        tr.init_particles()
+        tr.set_graph(GRAPH_TURNS)
+        tr.track(args.at_turn)
+        tr.sync()
+        blob = tr.save_state()
+        tr.close()
+        with open(path, "wb") as f:
+            f.write(blob)
+        made = True
+    with open(path, "rb") as f:
+        blob = f.read()
+    tr = pkg.tracker_for_run(run, record_turns=64)
+    tr.load_state(blob)
+    turn0 = tr.info["turn"]
+    tr.track(args.steps)
+    tr.sync()
+    rec = tr.moments(turn0 + args.steps - 1, 1)[0]
+    tr.close()
+    print(json.dumps({"workload": run.name, "state_file": path, "saved_now": made, "turn_loaded": turn0,
+                      "turns_tracked": args.steps,
+                      "outside_mesh_fraction": float(np.mean(rec[:, 5]) / run.n_mp[0]),
+                      "centroid_rms_ps": float(np.sqrt(np.mean(rec[:, 0] ** 2)) * 1e12)}), flush=True)
+    return 0
+
+
 def fill390t_bench(args, rank, local):
     """The 390-bunch fill with a transverse plane: throughput and push roofline."""
     if rank != 0:
@@ -743,6 +904,10 @@ def main():
         return three_f64_bench(args, rank, local)
     if args.workload == "fill390t":
         return fill390t_bench(args, rank, local)
+    if args.workload == "fill390_f64":
+        return fill390_f64_bench(args, rank, local)
+    if args.workload == "state":
+        return state_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -863,6 +1028,24 @@ def main():
                        "(mbt_set_particles_all), K turns, all K turns of moments read to the host"}
         tr2.close()
 
+    # ---- a bounded sample of the serving workload (Poisson requests at about
+    # the server's capacity, so that the latencies are service times, not a
+    # growing queue); the full-stream figures come from --workload serving
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        tr.close()
+        mean_work = float(np.mean([rq.run.turns * rq.run.n_particles
+                                   for rq in W.serving_stream(200, rate_hz=1.0, seed=7)]))
+        rate = 0.9 * value / mean_work
+        lat, queue, work, stats, span = serving_sample(args.serving_requests, rate)
+        serving = {"requests": args.serving_requests, "rate_hz": rate,
+                   "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                   "queue_p99_s": float(np.percentile(queue, 99)), "delivered": float(work.sum() / span),
+                   "unit": UNIT, "span_s": span, "max_active_seen": stats["max_active_seen"],
+                   "stream": "Poisson, seed 7: 1-484 bunches, 1e4-2e5 mp per bunch, 0.1-5 mA, HOM 1-3 GHz, "
+                             "2000-2e4 turns; 16 active, 200 turns per step; rate = 0.9 x this run's "
+                             "throughput / mean request work"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(run)
@@ -877,11 +1060,12 @@ def main():
                            "l2": "state 468 MB > 129 MB L2 (no flush needed)",
                            "push": "persistent, one 1024-thread CTA per SM, equal per-SM shares of each run",
                            "parallelism": f"{world} independent fill(s), one per GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": 2 * K,
                 "launch_mode": f"CUDA graph of {G} turns, programmatic dependent launch between kernels",
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
-    tr.close()
+    if serving is None:
+        tr.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -295,6 +295,19 @@ mbt_status mbt_resident_shape(mbt_ctx *ctx, int *cluster, int *per_cta);
 /* Wait for the context's work; report device errors. */
 mbt_status mbt_sync(mbt_ctx *ctx);
 
+/* Failure-detection test hook for the bounded device waits.  limit_ns (0 =
+ * the default of 2 s, at most 1e10) replaces the wall-clock limit of
+ * mbt_track_resident's grid barrier (the wait of every cluster for the other
+ * bunches' emissions of the turn, used when a fill of several bunches has a
+ * long-range resonator).  unreachable = 1 makes that barrier wait for one
+ * arrival more than the fill has bunches, a count nothing reaches: every
+ * cluster's wait then runs out after limit_ns, the kernel records
+ * MBT_ERR_TIMEOUT in the context's error word, every CTA of a cluster leaves
+ * the turn loop together and writes its state back, and the next
+ * synchronising call returns MBT_ERR_TIMEOUT.  No fault is involved; the
+ * context can be destroyed normally.  Host only; MBT_ERR_ARG on bad values. */
+mbt_status mbt_set_wait_test(mbt_ctx *ctx, int64_t limit_ns, int unreachable);
+
 /* Per-turn moments of turns [turn0, turn0 + nturns) into out[nturns][nb][6]:
  * <tau>, rms tau, <delta>, rms delta, particles inside the mesh, outside.
  * The statistics are taken after the drift of the turn, before the next
@@ -452,6 +465,15 @@ mbt_status mbt_phasor_segment(int n, const double *step, const double *E, double
 mbt_status mbt_phasor_compose(int nseg, const double *maps, const double *carry, double *entry, double *carry_out);
 /* phi[2 m] = Phi_m of a range's n bunches given the value entering it. */
 mbt_status mbt_phasor_apply(int n, const double *step, const double *E, const double *entry, double *phi);
+
+/* Measures the FP64 fused multiply-add throughput of the current GPU (the
+ * bound of the FP64 tracker): blocks_per_sm x (SM count) CTAs of 256 threads
+ * each run 8 independent chains of iters DFMAs, launched `repeats` times on
+ * stream and timed with CUDA events after one untimed launch.  flops_per_s:
+ * 2 flops per DFMA over the timed launches; sms (optional): the SM count.
+ * Synchronous.  MBT_ERR_ARG on values outside blocks_per_sm 1..32,
+ * iters 1..2^24, repeats >= 1; MBT_ERR_CUDA without a GPU. */
+mbt_status mbt_probe_fp64_fma(int blocks_per_sm, int iters, int repeats, void *stream, double *flops_per_s, int *sms);
 
 /* Batched tracking: n contexts with the same precision, each with its fill
  * set, tracked together in the same kernel launches (one push and one post

@@ -33,14 +33,14 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_add_transverse_resistive_wall",
            "mbt_set_transverse_particles", "mbt_get_transverse_particles", "mbt_read_transverse_moments",
            "mbt_read_transverse_wake", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
-           "mbt_set_particles", "mbt_set_particles_all", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
+           "mbt_set_particles", "mbt_set_particles_all", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_set_wait_test", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
            "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy",
            "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
            "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split", "mbt_phasor_steps",
-           "mbt_phasor_segment", "mbt_phasor_compose", "mbt_phasor_apply"]
+           "mbt_phasor_segment", "mbt_phasor_compose", "mbt_phasor_apply", "mbt_probe_fp64_fma"]
 
 
 class MBTError(RuntimeError):
@@ -130,7 +130,8 @@ def lib() -> ctypes.CDLL:
                 "mbt_set_particles_all": ([_vp, _vp, _vp, _vp], _i),
                 "mbt_get_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_track": ([_vp, _i64, _vp], _i), "mbt_sync": ([_vp], _i),
-                "mbt_track_resident": ([_vp, _i64, _vp], _i), "mbt_resident_shape": ([_vp, _P(_i), _P(_i)], _i),
+                "mbt_track_resident": ([_vp, _i64, _vp], _i),
+                "mbt_set_wait_test": ([_vp, _i64, _i], _i), "mbt_resident_shape": ([_vp, _P(_i), _P(_i)], _i),
                 "mbt_read_moments": ([_vp, _i64, _i64, _P(_d)], _i),
                 "mbt_read_histograms": ([_vp, _P(_i32), _P(_i64)], _i),
                 "mbt_read_wake": ([_vp, _P(_d), _P(_d)], _i), "mbt_get_info": ([_vp, _P(Info)], _i),
@@ -156,6 +157,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_phasor_segment": ([_i, _P(_d), _P(_d), _P(_d)], _i),
                 "mbt_phasor_compose": ([_i, _P(_d), _P(_d), _P(_d), _P(_d)], _i),
                 "mbt_phasor_apply": ([_i, _P(_d), _P(_d), _P(_d), _P(_d)], _i),
+                "mbt_probe_fp64_fma": ([_i, _i, _i, _vp, _P(_d), _P(_i)], _i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -337,6 +339,11 @@ class Tracker:
 
     def sync(self):
         self._chk(self._L.mbt_sync(self._h))
+
+    def set_wait_test(self, limit_ns: int, unreachable: bool):
+        """Failure-detection test hook: the resident grid barrier's wait limit,
+        and a barrier count nothing reaches (mbt_set_wait_test)."""
+        self._chk(self._L.mbt_set_wait_test(self._h, int(limit_ns), 1 if unreachable else 0))
 
     def moments(self, turn0: int, nturns: int) -> np.ndarray:
         out = np.empty((int(nturns), self.nb, 6), np.float64)
@@ -577,6 +584,16 @@ def wake_noalloc(ring: dict, resonators, nbins: int, half_width_sigmas: float, c
                             ctypes.c_void_p(int(hist_ptr)), ctypes.c_void_p(int(V_ptr)), _stream(stream), err, 256)
     if st != 0:
         raise MBTError(st, err.value.decode())
+
+
+def probe_fp64_fma(blocks_per_sm: int = 8, iters: int = 4096, repeats: int = 5, stream=None):
+    """(FP64 DFMA throughput of the GPU [flop/s], SM count), timed with CUDA events."""
+    f, n = _d(), _i()
+    st = lib().mbt_probe_fp64_fma(int(blocks_per_sm), int(iters), int(repeats), _stream(stream), ctypes.byref(f),
+                                  ctypes.byref(n))
+    if st != 0:
+        raise MBTError(st, "mbt_probe_fp64_fma")
+    return f.value, n.value
 
 
 def tracker_for_run(run, precision=None, record_turns: int = 4096) -> Tracker:

@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libmbt.so"
 INCLUDE = PKG.parent / "include"
-SOURCES = ["k_push.cu", "k_post.cu", "k_resident.cu", "api.cu", "serve.cu", "sharded.cu"]
+SOURCES = ["k_push.cu", "k_post.cu", "k_resident.cu", "api.cu", "serve.cu", "sharded.cu", "k_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code is built without floating-point contraction so that it rounds the
 # same on x86-64 and aarch64 (gcc fuses a*b+c into an FMA by default on Arm).
