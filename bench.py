@@ -98,6 +98,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--state-file", default="/tmp/mbt_fill390.state", help="state: checkpoint of the fill")
     ap.add_argument("--at-turn", type=int, default=1500, help="state: turn at which the checkpoint is taken")
+    ap.add_argument("--transverse", action="store_true", help="state: the 390-bunch fill with a transverse plane")
     ap.add_argument("--serving-requests", type=int, default=40,
                     help="requests of the bounded serving sample in the default line (0 = skip)")
     ap.add_argument("--saturated-turn", type=int, default=1500,
@@ -797,7 +798,7 @@ def state_bench(args, rank, local):
     torch.cuda.set_device(local)
     import paper_1809_00391_gb300 as pkg
     pkg.build()
-    run = W.fill_390(seed=1)
+    run = fill390t_run()[0] if args.transverse else W.fill_390(seed=1)
     path = args.state_file
     made = False
     if not os.path.exists(path):
@@ -827,6 +828,16 @@ def state_bench(args, rank, local):
     return 0
 
 
+def fill390t_run():
+    """The 390-bunch fill with a horizontal plane (beta 10 m, tune 0.31,
+    chromaticity 1.5, 1 nm) and a transverse HOM (200 kOhm/m, 1.5 GHz, Q 2e4,
+    short and long range)."""
+    base = W.fill_390(precision=W.PREC_MIXED)
+    tplane = dict(beta_m=10.0, alpha=0.0, tune=0.31, chromaticity=1.5, emittance_m=1e-9,
+                  resonators=[dict(Rs_ohm=2e5, fr_Hz=1.5e9, Q=2e4, range=W.RANGE_BOTH)])
+    return W.Run(**{**base.__dict__, "transverse": tplane, "name": base.name + " + transverse plane"}), tplane
+
+
 def fill390t_bench(args, rank, local):
     """The 390-bunch fill with a transverse plane: throughput and push roofline."""
     if rank != 0:
@@ -835,10 +846,7 @@ def fill390t_bench(args, rank, local):
     torch.cuda.set_device(local)
     import paper_1809_00391_gb300 as pkg
     pkg.build()
-    base = W.fill_390(precision=W.PREC_MIXED)
-    tplane = dict(beta_m=10.0, alpha=0.0, tune=0.31, chromaticity=1.5, emittance_m=1e-9,
-                  resonators=[dict(Rs_ohm=2e5, fr_Hz=1.5e9, Q=2e4, range=W.RANGE_BOTH)])
-    run = W.Run(**{**base.__dict__, "transverse": tplane, "name": base.name + " + transverse plane"})
+    run, tplane = fill390t_run()
     K, Wm = min(args.steps, 5000), max(args.warmup, 3)
     stream = torch.cuda.current_stream()
     tr = pkg.tracker_for_run(run, record_turns=K + Wm + GRAPH_TURNS + 17 * (AUTOTUNE_TURNS + 2) + 600)
