@@ -255,7 +255,7 @@ struct alignas(16) StreamSlot {
   float vrow[kStreamMaxBins];    // short-range voltage of the bunch
 };
 constexpr size_t kStreamSmem = (size_t)kStreamStages * kStreamStageBytes + kSlots * sizeof(StreamSlot) +
-                               kStreamMaxBins * (sizeof(float2) + sizeof(int));
+                               kStreamMaxBins * sizeof(float2) + (kStreamMaxBins + kSpillCells) * sizeof(int);
 
 struct StreamSmem {
   uint64_t full[kStreamStages], empty[kStreamStages];   // stage loaded / handed back by every consumer warp
@@ -574,6 +574,16 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
 // push only tau and delta.  Harmonic cavities are a runtime loop here.
 // ---------------------------------------------------------------------------
 constexpr int kStageBytesT = kChunk * (int)(3 * sizeof(float) + sizeof(double));
+// dynamic shared memory of the per-tile pushes: the stages, then per cell the
+// (V, dV) table(s), the counts (with kSpillCells spill cells) and, with a
+// transverse plane, the dipole sums
+constexpr size_t push_tile_smem(int nbins) {
+  return (size_t)kStages * kStageBytes + (size_t)nbins * sizeof(float2) + (size_t)(nbins + kSpillCells) * sizeof(int);
+}
+constexpr size_t push_t_smem(int nbins) {
+  return (size_t)kStages * kStageBytesT + (size_t)nbins * (2 * sizeof(float2) + sizeof(float)) +
+         (size_t)(nbins + kSpillCells) * sizeof(int);
+}
 #ifndef MBT_PUSH_T_MIN_BLOCKS
 #define MBT_PUSH_T_MIN_BLOCKS 4
 #endif
@@ -659,8 +669,8 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   const bool tr = R->trans != 0;
   uint8_t *stages = sm_pt;
   float2 *sVd = reinterpret_cast<float2 *>(sm_pt + kStages * kStageBytesT);
-  int *sH = reinterpret_cast<int *>(sVd + nbins);
-  float2 *sVt = reinterpret_cast<float2 *>(sH + nbins);
+  int *sH = reinterpret_cast<int *>(sVd + nbins);                  // nbins + kSpillCells counts
+  float2 *sVt = reinterpret_cast<float2 *>(sH + nbins + kSpillCells);
   float *sDip = reinterpret_cast<float *>(sVt + nbins);
   float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
   double *del = R->delta + bd.off + t.start;
@@ -1152,7 +1162,7 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   if (p.ntiles == 0) return cudaSuccess;
   const int max_nbins = p.max_nbins;
   if (precision == kMixed && p.max_trans) {
-    const size_t smem = (size_t)kStages * kStageBytesT + (size_t)max_nbins * (2 * sizeof(float2) + sizeof(int) + sizeof(float));
+    const size_t smem = push_t_smem(max_nbins);
     switch (p.max_nlong) {
       case 0: return launch_ex(k_push_mixed_t<0>, p.ntiles, kPushThreads, smem, s, pdl, p);
       case 1: return launch_ex(k_push_mixed_t<1>, p.ntiles, kPushThreads, smem, s, pdl, p);
@@ -1162,7 +1172,7 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   }
   if (precision == kMixed && p.stream_ctas <= 0) {
     // per-tile push
-    const size_t smem = (size_t)kStages * kStageBytes + (size_t)max_nbins * (sizeof(float2) + sizeof(int));
+    const size_t smem = push_tile_smem(max_nbins);
     const bool harm = p.max_nharm > 0;
     switch (p.max_nlong) {
       case 0: return launch_ex(harm ? k_push_mixed<0, true> : k_push_mixed<0, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
@@ -1228,8 +1238,7 @@ bool plan_streams(const std::vector<int64_t> &n, const std::vector<int> &nb, boo
 // CTAs of a per-tile push (with or without a transverse plane) resident at
 // once on the current device (256 cells).
 cudaError_t push_tile_resident_slots(bool trans, int *slots) {
-  const size_t smem = trans ? (size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float))
-                            : (size_t)kStages * kStageBytes + 256 * (sizeof(float2) + sizeof(int));
+  const size_t smem = trans ? push_t_smem(256) : push_tile_smem(256);
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1247,11 +1256,11 @@ cudaError_t configure_push_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
   int slots = 0;
   if (e == cudaSuccess) e = push_resident_slots(&slots);
-  const int bytes = (int)((size_t)kStages * kStageBytes + 1024 * (sizeof(float2) + sizeof(int)));
+  const int bytes = (int)push_tile_smem(1024);
   for (auto k : {k_push_mixed<0, false>, k_push_mixed<1, false>, k_push_mixed<2, false>, k_push_mixed<kMaxLong, false>,
                  k_push_mixed<0, true>, k_push_mixed<1, true>, k_push_mixed<2, true>, k_push_mixed<kMaxLong, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  const int bytes_t = (int)((size_t)kStages * kStageBytesT + 256 * (2 * sizeof(float2) + sizeof(int) + sizeof(float)));
+  const int bytes_t = (int)push_t_smem(256);
   for (auto k : {k_push_mixed_t<0>, k_push_mixed_t<1>, k_push_mixed_t<2>, k_push_mixed_t<kMaxLong>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_t);
   return e;

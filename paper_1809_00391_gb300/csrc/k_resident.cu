@@ -27,7 +27,7 @@ namespace mbt {
 struct ResidentSmem {
   double *sD;      // [per]
   float *sT;       // [per]
-  int *lh;         // [2][nbins] CTA histograms, double-buffered by turn
+  int *lh;         // [2][nbins + kSpillCells] CTA histograms, double-buffered by turn
   int *bh;         // [nbins] bunch histogram
   float2 *sVd;     // [nbins] (V[j], V[j+1] - V[j])
   float *lag;      // [nbins]
@@ -42,7 +42,7 @@ __host__ __device__ inline size_t resident_layout(int per, int nbins, ResidentSm
     off = (off + bytes + 15) & ~(size_t)15;
     return o;
   };
-  const size_t oD = take((size_t)per * 8), oT = take((size_t)per * 4), oLH = take((size_t)2 * nbins * 4);
+  const size_t oD = take((size_t)per * 8), oT = take((size_t)per * 4), oLH = take((size_t)2 * (nbins + kSpillCells) * 4);
   const size_t oBH = take((size_t)nbins * 4), oV = take((size_t)nbins * 8), oL = take((size_t)nbins * 4);
   const size_t oR = take((size_t)nbins * 4), oX = take((size_t)nbins * 4);
   if (m) {
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     S.sVd[k] = make_float2(v0, v1 - v0);
     S.lag[k] = R->lag_f[k];
     S.lh[k] = 0;
-    S.lh[nbins + k] = 0;
+    S.lh[nbins + kSpillCells + k] = 0;
   }
   if (tid < nlong) {
     const double2 P = R->pq[((size_t)tid * nb + m) * 2];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
   for (int it = 0; it < a.nturns; ++it) {
     const long long turn = turn0 + it;
     const int lp = it & 1;
-    int *lh = S.lh + lp * nbins;
+    int *lh = S.lh + lp * (nbins + kSpillCells);
     float2 phi[NLONG_MAX > 0 ? NLONG_MAX : 1];
 #pragma unroll
     for (int r = 0; r < NLONG_MAX; ++r) phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);

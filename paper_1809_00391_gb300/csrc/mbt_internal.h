@@ -28,6 +28,8 @@ constexpr int kTRecord = 4;          // transverse record: <x>, rms x, <x'>, rms
 constexpr int kTransRows = 32;       // transverse short-range rows per post job (kMixed)
 constexpr int kRecord = 6;           // <tau>, rms tau, <delta>, rms delta, n_in, n_out
 constexpr int kPostThreads = 256;
+constexpr int kSpillCells = 32;      // per-lane extra cells behind a push histogram: outside particles
+                                     // deposit there (never read) instead of taking a branch
 constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
 
 enum Precision { kF64 = 0, kMixed = 1 };

@@ -87,8 +87,11 @@ __device__ __forceinline__ void quad_push(const PushConstF &c, const float2 *sVd
       const float t1 = push_one<NLONG_MAX, NGP, HARM>(c, sVd, nlong, la, lw, phi, omD_d, hc, nharm, tt[e], dd[e], rr[e], df);
       tt[e] = t1;
       const float xb = fmaf(t1, c.invD, c.HinvD);
-      if (xb >= -0.5f && xb < c.fnb - 0.5f) atomicAdd(&sH[__float2int_rn(xb)], 1);
-      else ++nout;
+      // without a branch: a particle outside the mesh counts into its lane's
+      // spill cell behind the histogram (sH holds nbins + kSpillCells cells)
+      const bool in = xb >= -0.5f && xb < c.fnb - 0.5f;
+      atomicAdd(&sH[in ? __float2int_rn(xb) : c.nbins + (int)(threadIdx.x & 31)], 1);
+      nout += in ? 0 : 1;
       const float u = t1 - tref, v = df - dref;
       st += u;
       st2 = fmaf(u, u, st2);
