@@ -165,7 +165,13 @@ mbt_status mbt_add_harmonic_cavity(mbt_ctx *ctx, int n, double V_V, double phi_r
  * sqrt(beta emit D_x) r, sqrt(gamma emit D_x) r' with D_x = U0 / E0 (the
  * damping the momentum ratio produces on average, so emittance_m is the
  * equilibrium; none with MBT_NO_SR / MBT_NO_QE).  Only before mbt_set_fill.
- * Checkpoints include it; mbt_track_resident refuses it (MBT_ERR_UNSUPPORTED). */
+ * Checkpoints include it; mbt_track_resident refuses it (MBT_ERR_UNSUPPORTED).
+ * MBT_PREC_MIXED sums the dipole moments of a cell in fixed point: x in
+ * units of u = 2^(e - 20) m, 2^e = sqrt(beta_m emittance_m) rounded up to a
+ * power of two (at least 2^-16 m), exact sums of the quantised x; it accepts
+ * |x| < 2^(e + 10) m after the turn's map, and a particle beyond that makes
+ * the next synchronising call return MBT_ERR_UNSUPPORTED (its x then
+ * deposits clamped). */
 mbt_status mbt_set_transverse(mbt_ctx *ctx, double beta_m, double alpha, double tune, double chromaticity,
                               double emittance_m);
 
@@ -292,7 +298,11 @@ mbt_status mbt_track_resident(mbt_ctx *ctx, int64_t nturns, void *stream);
  * does not fit on chip) and particles held per CTA. */
 mbt_status mbt_resident_shape(mbt_ctx *ctx, int *cluster, int *per_cta);
 
-/* Wait for the context's work; report device errors. */
+/* Wait for the context's work; report device errors: MBT_ERR_TIMEOUT (a
+ * bounded wait gave up), MBT_ERR_ARG (a cell count of 2^24 or more reached
+ * the tensor-core wake), MBT_ERR_UNSUPPORTED (a transverse coordinate beyond
+ * the mixed dipole range, see mbt_set_transverse), MBT_ERR_CUDA.  The error
+ * word is cleared once reported. */
 mbt_status mbt_sync(mbt_ctx *ctx);
 
 /* Failure-detection test hook for the bounded device waits.  limit_ns (0 =

@@ -646,6 +646,9 @@ mbt_status check_device(mbt_ctx *c, const Plan &pl) {
     cudaMemcpy(pl.error, &zero, sizeof(int), cudaMemcpyHostToDevice);
     if (err == kErrTmem) return fail(c, MBT_ERR_CUDA, "tensor memory could not be allocated");
     if (err == kErrCount) return fail(c, MBT_ERR_ARG, "a cell count outside [0, 2^24) reached the wake");
+    if (err == kErrDipole)
+      return fail(c, MBT_ERR_UNSUPPORTED,
+                  "a transverse coordinate left the mixed push's dipole range (2^10 x the beam size scale)");
     return fail(c, MBT_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", err);
   }
   return MBT_OK;
@@ -1151,6 +1154,16 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     rd.f_tgamma = (float)rd.t_gamma;
     rd.f_tnx = (float)rd.t_nx;
     rd.f_tnxp = (float)rd.t_nxp;
+    // dipole deposit unit of the mixed push: a power of two 2^-20 of the beam
+    // size rounded up to a power of two (at least 2^-16 m), so that |x| up to
+    // 2^10 times that scale (and at least 2^-6 m) is accepted
+    {
+      const double sx = std::sqrt(c->t_beta * c->t_emit);
+      const int e = sx > 0 ? std::max(-16, (int)std::ceil(std::log2(sx))) : -16;
+      rd.dip_unit = std::ldexp(1.0, e - 20);
+      rd.f_dip_inv = (float)std::ldexp(1.0, 20 - e);
+      rd.f_dip_range = (float)std::ldexp(1.0, e + 10);
+    }
     if (c->rw_nh > 0) {
       const size_t nt = (size_t)(c->rw_nh + 1) * c->ring.h;
       std::vector<double> tab(nt, 0.0);

@@ -581,11 +581,11 @@ constexpr size_t push_tile_smem(int nbins) {
   return (size_t)kStages * kStageBytes + (size_t)nbins * sizeof(float2) + (size_t)(nbins + kSpillCells) * sizeof(int);
 }
 constexpr size_t push_t_smem(int nbins) {
-  return (size_t)kStages * kStageBytesT + (size_t)nbins * (2 * sizeof(float2) + sizeof(float)) +
-         (size_t)(nbins + kSpillCells) * sizeof(int);
+  return (size_t)kStages * kStageBytesT + (size_t)nbins * 2 * sizeof(float2) +
+         (size_t)(nbins + kSpillCells) * 3 * sizeof(int);
 }
 #ifndef MBT_PUSH_T_MIN_BLOCKS
-#define MBT_PUSH_T_MIN_BLOCKS 4
+#define MBT_PUSH_T_MIN_BLOCKS 3
 #endif
 
 __device__ __forceinline__ void issue_chunk_t(const TileDev &t, const float *tau, const double *del, const float *x,
@@ -671,7 +671,8 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   float2 *sVd = reinterpret_cast<float2 *>(sm_pt + kStages * kStageBytesT);
   int *sH = reinterpret_cast<int *>(sVd + nbins);                  // nbins + kSpillCells counts
   float2 *sVt = reinterpret_cast<float2 *>(sH + nbins + kSpillCells);
-  float *sDip = reinterpret_cast<float *>(sVt + nbins);
+  unsigned *sLo = reinterpret_cast<unsigned *>(sVt + nbins);     // dipole sums in fixed point (deposit_dip),
+  int *sHi = reinterpret_cast<int *>(sLo + nbins + kSpillCells); // nbins + kSpillCells cells each
   float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
   double *del = R->delta + bd.off + t.start;
   float *xg = tr ? static_cast<float *>(R->x) + bd.off + t.start : nullptr;
@@ -687,9 +688,10 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   }
   const int nharm = R->nharm;
   if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+  for (int k = threadIdx.x; k < nbins + kSpillCells; k += kPushThreads) {
     sH[k] = 0;
-    sDip[k] = 0.f;
+    sLo[k] = 0u;
+    sHi[k] = 0;
   }
   grid_dependents_launch();
   grid_dependency_wait();   // the previous post kernel's wakes, phasors and turn counter are complete
@@ -740,6 +742,16 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
     phi[r] = r < nlong ? s_phi[r] : make_float2(0.f, 0.f);
     plane[r] = r < nlong ? s_plane[r] : 0;
   }
+  // the same entries in the masked form of quad_push_t_full
+  float2 lA[NLONG_MAX > 0 ? NLONG_MAX : 1];
+  float lml[NLONG_MAX > 0 ? NLONG_MAX : 1], lmt[NLONG_MAX > 0 ? NLONG_MAX : 1];
+#pragma unroll
+  for (int r = 0; r < NLONG_MAX; ++r) {
+    lA[r] = plane[r] ? make_float2(phi[r].y, phi[r].x) : make_float2(phi[r].x, -phi[r].y);
+    lml[r] = plane[r] ? 0.f : 1.f;
+    lmt[r] = plane[r] ? 1.f : 0.f;
+  }
+  const bool straight = !ngp && nharm == 0;   // full quads take quad_push_t_full
   const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
   const bool texc = tc.nx != 0.f || tc.nxp != 0.f;
   const float vrw = tr ? rw_voltage_f32(R, t.m, turn, s_red[0]) : 0.f;
@@ -747,6 +759,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
 
   float mom[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int nout = 0;
+  bool dip_ok = true;   // every deposited x within the dipole deposit's range
 #pragma unroll 1
   for (int ch = 0; ch < nchunks; ++ch) {
     const int slot = ch % kStages;
@@ -779,8 +792,12 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
           normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 3u, k0, k1), rx);
           normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
         }
-        quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sDip, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp, vrw, tt,
-                               dd, xx, pp, rr, rx, rp, nvalid, tref, dref, mom, nout);
+        if (straight && nvalid == 4)
+          quad_push_t_full<NLONG_MAX>(c, tc, sVd, sVt, sH, sLo, sHi, nlong, la, lw, lA, lml, lmt, omD_d, vrw, tt, dd,
+                                      xx, pp, rr, rx, rp, tref, dref, mom, nout, dip_ok);
+        else
+          quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sLo, sHi, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp,
+                                 vrw, tt, dd, xx, pp, rr, rx, rp, nvalid, tref, dref, mom, nout, dip_ok);
         *reinterpret_cast<float4 *>(xg + q) = make_float4(xx[0], xx[1], xx[2], xx[3]);
         *reinterpret_cast<float4 *>(pg + q) = make_float4(pp[0], pp[1], pp[2], pp[3]);
       } else if (ngp) {
@@ -816,7 +833,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
 #pragma unroll
     for (int k = 4; k < 8; ++k) s_red[warp][k + 1] = mom[k];
   }
-  __syncthreads();
+  if (__syncthreads_or(!dip_ok) && threadIdx.x == 0) atomicCAS(p.error, kErrNone, kErrDipole);
   if (threadIdx.x < 9) {
     double acc = 0.0;
 #pragma unroll
@@ -831,11 +848,13 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
   float *dg = tr ? static_cast<float *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
+  const double du = tr ? R->dip_unit : 0.0;
   for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
     const int cnt = sH[k];
     if (cnt) {
       atomicAdd(hg + k, cnt);
-      if (tr) atomicAdd(dg + k, sDip[k]);
+      // the tile's exact fixed-point sum (|2^16 hi + lo| < 2^47), scaled by the power of two u
+      if (tr) atomicAdd(dg + k, (float)((double)((long long)sHi[k] * 65536LL + (long long)sLo[k]) * du));
     }
   }
 }

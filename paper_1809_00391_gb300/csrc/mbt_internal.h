@@ -36,8 +36,10 @@ enum Precision { kF64 = 0, kMixed = 1 };
 enum Flags { kNoSR = 1, kNoQE = 2, kKickNGP = 4 };
 enum JobType { kJobWake = 0, kJobTile = 1, kJobTrans = 2, kJobMoments = 3 };
 // kErrCount: a cell count outside [0, 2^24) reached the tensor-core wake,
-// which splits each count into three exact 8-bit planes
-enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2, kErrCount = 3 };
+// which splits each count into three exact 8-bit planes.  kErrDipole: the
+// mixed transverse push met an x outside its dipole deposit's fixed-point
+// range (RunDev::f_dip_range)
+enum DeviceError { kErrNone = 0, kErrTimeout = 1, kErrTmem = 2, kErrCount = 3, kErrDipole = 4 };
 
 // One run's device state and constants.
 struct RunDev {
@@ -101,6 +103,10 @@ struct RunDev {
   int h_rf;                 // harmonic number
   // float copies: 2 pi frac(nu), 2 pi nu xi, beta, alpha, gamma, nx, nxp, 1/(1 - D)
   float f_tmu0, f_tmu0xi, f_tbeta, f_talpha, f_tgamma, f_tnx, f_tnxp, f_inv_omD, f_U0oE0;
+  // fixed-point dipole deposit of the mixed push: unit u = 2^(e - 20) m with
+  // 2^e >= sqrt(beta emit) (e >= -16), 1/u, and the accepted |x| < 2^30 u
+  double dip_unit;
+  float f_dip_inv, f_dip_range;
 };
 
 

@@ -109,7 +109,23 @@ struct TransConstF {
   float beta, alpha, gamma;
   float nx, nxp;               // excitation amplitudes sqrt(beta emit Dx), sqrt(gamma emit Dx)
   float invE0, inv_omD, U0oE0; // 1/E0 (no damping factor), 1/(1 - D), U0/E0
+  float dinv, drange;          // 1/u of the dipole deposit, and the |x| it accepts (2^30 u)
 };
+
+// Dipole deposit in fixed point.  x is quantised to xq = round(x / u), u a
+// power of two (2^-20 times the run's transverse scale), and xq is added as
+// its low 16 bits (unsigned) and its high part xq >> 16 (signed) into two
+// 32-bit counters of the cell: with at most 65536 particles per cell and
+// tile neither sum can overflow, so the cell's sum (2^16 hi + lo) u is the
+// exact sum of the quantised x, in any order of the atomics.  (FP32 shared
+// atomics of x retry under contention and would round every partial sum.)
+// Returns false if |x| is outside the accepted range (or not a number).
+__device__ __forceinline__ bool deposit_dip(unsigned *sLo, int *sHi, int cell, float x, const TransConstF &tc) {
+  const int xq = __float2int_rn(x * tc.dinv);   // |x| < drange: |xq| <= 2^30
+  atomicAdd(sLo + cell, (unsigned)xq & 0xFFFFu);
+  atomicAdd(sHi + cell, xq >> 16);
+  return fabsf(x) < tc.drange;
+}
 
 // One particle with a transverse plane: the longitudinal map of push_one
 // (its long-range sum over the plane-0 entries only) and, with the same
@@ -179,13 +195,13 @@ __device__ __forceinline__ float push_one_t(const PushConstF &c, const TransCons
 // count and of x into the cell, moment partials of both planes.
 template <int NLONG_MAX>
 __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
-                                            const float2 *sVt, int *sH, float *sDip, int nlong, const int *plane,
-                                            const float *la, const float *lw, const float2 *phi, double omD_d,
-                                            const float4 *hc, int nharm, bool ngp, float vrw, float (&tt)[4],
-                                            double (&dd)[4],
-                                            float (&xx)[4], float (&pp)[4], const float (&rr)[4],
-                                            const float (&rx)[4], const float (&rp)[4], int nvalid, float tref,
-                                            float dref, float (&mom)[8], int &nout) {
+                                            const float2 *sVt, int *sH, unsigned *sLo, int *sHi, int nlong,
+                                            const int *plane, const float *la, const float *lw, const float2 *phi,
+                                            double omD_d, const float4 *hc, int nharm, bool ngp, float vrw,
+                                            float (&tt)[4], double (&dd)[4], float (&xx)[4], float (&pp)[4],
+                                            const float (&rr)[4], const float (&rx)[4], const float (&rp)[4],
+                                            int nvalid, float tref, float dref, float (&mom)[8], int &nout,
+                                            bool &ok) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (e < nvalid) {
@@ -194,13 +210,11 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
                                              tt[e], dd[e], rr[e], df, xx[e], pp[e], rx[e], rp[e]);
       tt[e] = t1;
       const float xb = fmaf(t1, c.invD, c.HinvD);
-      if (xb >= -0.5f && xb < c.fnb - 0.5f) {
-        const int kb = __float2int_rn(xb);
-        atomicAdd(&sH[kb], 1);
-        atomicAdd(&sDip[kb], xx[e]);
-      } else {
-        ++nout;
-      }
+      const bool in = xb >= -0.5f && xb < c.fnb - 0.5f;
+      const int cell = in ? __float2int_rn(xb) : c.nbins + (int)(threadIdx.x & 31);   // spill cell outside
+      atomicAdd(&sH[cell], 1);
+      ok &= deposit_dip(sLo, sHi, cell, xx[e], tc);
+      nout += in ? 0 : 1;
       const float u = t1 - tref, v = df - dref;   // as in quad_push
       mom[0] += u;
       mom[1] = fmaf(u, u, mom[1]);
@@ -211,6 +225,84 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
       mom[6] += pp[e];
       mom[7] = fmaf(pp[e], pp[e], mom[7]);
     }
+  }
+}
+
+// A full quad (four valid particles) of a run with a transverse plane,
+// linear kick interpolation and no harmonic cavity: the map of push_one_t in
+// one straight block, so that the four particles overlap.  Each long-range
+// entry adds ea (A.x cos + A.y sin) to the plane its masks select:
+// A = (Re Phi, -Im Phi), ml = 1, mt = 0 for a longitudinal entry (Re(Phi e^{s t}));
+// A = (Im Phi, Re Phi), ml = 0, mt = 1 for a transverse one (Im(Phi e^{s t})).
+// Deposits go to the cell or, outside the mesh, to the lane's spill cell
+// (sH, sLo and sHi hold nbins + kSpillCells cells).
+template <int NLONG_MAX>
+__device__ __forceinline__ void quad_push_t_full(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
+                                                 const float2 *sVt, int *sH, unsigned *sLo, int *sHi, int nlong,
+                                                 const float *la, const float *lw, const float2 *A, const float *ml,
+                                                 const float *mt, double omD_d, float vrw, float (&tt)[4],
+                                                 double (&dd)[4], float (&xx)[4], float (&pp)[4],
+                                                 const float (&rr)[4], const float (&rx)[4], const float (&rp)[4],
+                                                 float tref, float dref, float (&mom)[8], int &nout, bool &ok) {
+  int cell[4];
+  float dfs[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float t0 = tt[e];
+    const float x0 = fmaf(t0, c.invD, c.HinvD);
+    const bool inside = x0 >= -0.5f && x0 < c.fnb - 0.5f;
+    const float u = fminf(fmaxf(x0, 0.f), c.fnb - 1.f);
+    const int j = (int)u;   // <= nbins - 1, where the slopes are 0
+    const float2 vd = sVd[j], vtd = sVt[j];
+    float v = inside ? fmaf(u - (float)j, vd.y, vd.x) : 0.f;
+    float vt = (inside ? fmaf(u - (float)j, vtd.y, vtd.x) : 0.f) + vrw;
+#pragma unroll
+    for (int r2 = 0; r2 < NLONG_MAX; ++r2) {
+      if (r2 < nlong) {
+        float sn, cs;
+        __sincosf(lw[r2] * t0, &sn, &cs);
+        const float w = ex2_approx(-la[r2] * t0) * fmaf(A[r2].x, cs, A[r2].y * sn);
+        v = fmaf(ml[r2], w, v);
+        vt = fmaf(mt[r2], w, vt);
+      }
+    }
+    float sw, cw;
+    __sincosf(c.w * t0, &sw, &cw);
+    const float rf = fmaf(-c.rfB, sw, fmaf(c.rfA, cw, -c.rfA));
+    const float inc = fmaf(-v, c.invE0, fmaf(c.qe, rr[e], rf));
+    const float db = fmaf(-v, tc.invE0, f64_to_f32_trunc(dd[e]));
+    const float g = fmaf(rf, tc.inv_omD, tc.U0oE0);
+    dd[e] = fma(dd[e], omD_d, f32_to_f64_bits(inc));
+    const float df = f64_to_f32_trunc(dd[e]);
+    dfs[e] = df;
+    float p = fmaf(vt, tc.invE0, pp[e]);
+    p = fmaf(-p, __fdividef(g, 1.f + db + g), p);
+    float sp, cp;
+    __sincosf(fmaf(tc.mu0xi, df, tc.mu0), &sp, &cp);
+    const float xn = fmaf(fmaf(tc.alpha, sp, cp), xx[e], tc.beta * sp * p);
+    const float pn = fmaf(-tc.gamma * sp, xx[e], fmaf(-tc.alpha, sp, cp) * p);
+    xx[e] = fmaf(tc.nx, rx[e], xn);
+    pp[e] = fmaf(tc.nxp, rp[e], pn);
+    const float t1 = fmaf(c.aT0, df, t0);
+    tt[e] = t1;
+    const float xb = fmaf(t1, c.invD, c.HinvD);
+    const bool in = xb >= -0.5f && xb < c.fnb - 0.5f;
+    cell[e] = in ? __float2int_rn(xb) : c.nbins + (int)(threadIdx.x & 31);
+    nout += in ? 0 : 1;
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    atomicAdd(&sH[cell[e]], 1);
+    ok &= deposit_dip(sLo, sHi, cell[e], xx[e], tc);
+    const float u = tt[e] - tref, v = dfs[e] - dref;
+    mom[0] += u;
+    mom[1] = fmaf(u, u, mom[1]);
+    mom[2] += v;
+    mom[3] = fmaf(v, v, mom[3]);
+    mom[4] += xx[e];
+    mom[5] = fmaf(xx[e], xx[e], mom[5]);
+    mom[6] += pp[e];
+    mom[7] = fmaf(pp[e], pp[e], mom[7]);
   }
 }
 
@@ -226,6 +318,8 @@ __device__ __forceinline__ TransConstF trans_consts(const RunDev *__restrict__ R
   t.invE0 = R->f_invE0;
   t.inv_omD = R->f_inv_omD;
   t.U0oE0 = R->f_U0oE0;
+  t.dinv = R->f_dip_inv;
+  t.drange = R->f_dip_range;
   return t;
 }
 

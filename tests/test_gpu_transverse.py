@@ -214,3 +214,81 @@ def test_transverse_resistive_wall_matches_oracle(pkg, oracle_mod, prec, tol):
         for col, scale in ((0, sx), (2, sp)):
             assert np.max(np.abs(trec_g[:, :, col] - trec_o[:, :, col]) / scale) <= tol, col
     tr.close()
+
+
+def _dip_unit(tplane):
+    """The mixed push's fixed-point dipole unit u = 2^(e - 20) m and accepted
+    range 2^(e + 10) m, 2^e the beam size sqrt(beta emit) rounded up to a power
+    of two (at least 2^-16 m)."""
+    sx = math.sqrt(tplane["beta_m"] * tplane["emittance_m"])
+    e = max(-16, math.ceil(math.log2(sx))) if sx > 0 else -16
+    return 2.0 ** (e - 20), 2.0 ** (e + 10)
+
+
+def test_mixed_dipole_deposit_sums_every_cell(pkg):
+    """After one turn the dipole sums of the mixed push equal the per-cell sums
+    of x of the GPU's own particles, to u/2 per particle (the fixed-point
+    quantisation) and one FP32 rounding of the sum: one tile of 65536
+    particles, half of them in one cell (the most one cell of a tile can take),
+    x of both signs up to half the accepted range, and particles outside the
+    mesh, which deposit into no cell."""
+    n = 65536
+    tplane = _plane(alpha=0.0)   # x1 = cos(mu) x0 + excitation: |x1| stays within the range
+    u, rng = _dip_unit(tplane)
+    run = _run(W.PREC_MIXED, [0], n, 1, tplane=tplane, res=(), flags=W.NO_SR | W.NO_QE)
+    tr = pkg.tracker_for_run(run, record_turns=2)
+    tr.set_tile(n)
+    info = tr.info
+    H, D, nb = info["half_width_s"], info["bin_width_s"], run.nbins
+    g = np.random.default_rng(3)
+    k = np.where(np.arange(n) < n // 2, 100, g.integers(0, nb, n))
+    tau = -H + (k + 0.5) * D   # cell centres: the turn moves tau by far less than a cell
+    tau[-64:] = H + 3 * D * (1 + np.arange(64))
+    tr.set_particles(0, tau, np.zeros(n))
+    tr.set_transverse_particles(0, g.uniform(-0.5 * rng, 0.5 * rng, n), np.zeros(n))
+    tr.track(1)
+    t1, _ = tr.particles(0)
+    x1, _ = tr.transverse_particles(0)
+    dip, _ = tr.transverse_wake()
+    cell = np.floor((t1 + H) / D).astype(np.int64)
+    inside = (cell >= 0) & (cell < nb)
+    assert inside.sum() == n - 64
+    ref = np.bincount(cell[inside], weights=x1[inside], minlength=nb)
+    cnt = np.bincount(cell[inside], minlength=nb)
+    assert cnt[100] >= n // 2
+    tol = cnt * u / 2 + 2.0 ** -23 * np.abs(ref)
+    assert np.all(np.abs(dip[0] - ref) <= tol), np.max(np.abs(dip[0] - ref) / np.maximum(tol, 1e-300))
+    tr.close()
+
+
+def test_mixed_dipole_range_is_reported(pkg):
+    """A transverse coordinate beyond the fixed-point dipole range makes the
+    mixed push report MBT_ERR_UNSUPPORTED at the next synchronising call; the
+    context stays usable."""
+    tplane = _plane()
+    _, rng = _dip_unit(tplane)
+    run = _run(W.PREC_MIXED, [0], 4096, 4, tplane=tplane, res=())
+    tr = pkg.tracker_for_run(run, record_turns=4)
+    tr.init_particles()
+    x, xp = tr.transverse_particles(0)
+    tr.track(1)
+    tr.sync()
+    x, xp = tr.transverse_particles(0)
+    # eight particles on the betatron ellipse of amplitude sqrt(beta J) = 4
+    # x the range: whatever the phase advance, at least one of them ends the
+    # turn beyond the range (|x| >= 4 cos(pi / 8) x the range)
+    beta, alpha = tplane["beta_m"], tplane["alpha"]
+    a = 4 * rng
+    ph = np.arange(8) * (math.pi / 4)
+    x0, xp0 = x.copy(), xp.copy()
+    x[7:15] = a * np.cos(ph)
+    xp[7:15] = -(a / beta) * (np.sin(ph) + alpha * np.cos(ph))
+    tr.set_transverse_particles(0, x, xp)
+    tr.track(1)
+    with pytest.raises(pkg.MBTError) as e:
+        tr.sync()
+    assert e.value.status == 6
+    tr.set_transverse_particles(0, x0, xp0)
+    tr.track(1)
+    tr.sync()
+    tr.close()
