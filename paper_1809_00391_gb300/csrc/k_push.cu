@@ -569,11 +569,20 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
 // ---------------------------------------------------------------------------
 // Mixed precision with a transverse plane (plans where some run has one).
 // A bulk-copy ring like the streaming push's, a stage holding tau, delta, x and
-// x' of kChunk particles (20 KB); one quad of consecutive particles per
-// thread and chunk.  Runs of the plan without a transverse plane stage and
-// push only tau and delta.  Harmonic cavities are a runtime loop here.
+// x' of kChunkT particles (10 KB at 128 threads); one quad of consecutive
+// particles per thread and chunk.  Runs of the plan without a transverse
+// plane stage and push only tau and delta.  Harmonic cavities are a runtime
+// loop here.  128-thread CTAs, 6 per SM at 80 registers: measured faster on
+// the 390-bunch fill than 256 threads x 3 CTAs (320.6 against 330.3 us per
+// launch, same GPU), 64 x 12 and 96 x 8 (331.9, 341.1 us), and than 72 or 64
+// registers with more CTAs (spills).
 // ---------------------------------------------------------------------------
-constexpr int kStageBytesT = kChunk * (int)(3 * sizeof(float) + sizeof(double));
+#ifndef MBT_PUSH_T_THREADS
+#define MBT_PUSH_T_THREADS 128
+#endif
+constexpr int kTThreads = MBT_PUSH_T_THREADS;   // threads of a transverse push CTA
+constexpr int kChunkT = 4 * kTThreads;          // particles per stage: one quad per thread
+constexpr int kStageBytesT = kChunkT * (int)(3 * sizeof(float) + sizeof(double));
 // dynamic shared memory of the per-tile pushes: the stages, then per cell the
 // (V, dV) table(s), the counts (with kSpillCells spill cells) and, with a
 // transverse plane, the dipole sums
@@ -585,20 +594,20 @@ constexpr size_t push_t_smem(int nbins) {
          (size_t)(nbins + kSpillCells) * 3 * sizeof(int);
 }
 #ifndef MBT_PUSH_T_MIN_BLOCKS
-#define MBT_PUSH_T_MIN_BLOCKS 3
+#define MBT_PUSH_T_MIN_BLOCKS 6
 #endif
 
 __device__ __forceinline__ void issue_chunk_t(const TileDev &t, const float *tau, const double *del, const float *x,
                                               const float *xp, uint8_t *stage, uint64_t *bar, int c, bool tr) {
-  const int n = min(kChunk, t.count - c * kChunk);
+  const int n = min(kChunkT, t.count - c * kChunkT);
   const int n4 = (n + 3) & ~3;   // segments are padded to 4 particles: 16-byte multiples
   const uint32_t fb = (uint32_t)n4 * 4u, db = (uint32_t)n4 * 8u;
   mbar_arrive_expect_tx(bar, fb + db + (tr ? 2u * fb : 0u));
-  bulk_g2s(stage, tau + (size_t)c * kChunk, fb, bar);
-  bulk_g2s(stage + kChunk * 4, del + (size_t)c * kChunk, db, bar);
+  bulk_g2s(stage, tau + (size_t)c * kChunkT, fb, bar);
+  bulk_g2s(stage + kChunkT * 4, del + (size_t)c * kChunkT, db, bar);
   if (tr) {
-    bulk_g2s(stage + kChunk * 12, x + (size_t)c * kChunk, fb, bar);
-    bulk_g2s(stage + kChunk * 16, xp + (size_t)c * kChunk, fb, bar);
+    bulk_g2s(stage + kChunkT * 12, x + (size_t)c * kChunkT, fb, bar);
+    bulk_g2s(stage + kChunkT * 16, xp + (size_t)c * kChunkT, fb, bar);
   }
 }
 
@@ -611,7 +620,7 @@ __device__ float rw_voltage_f32(const RunDev *__restrict__ R, int m, long long t
   if (R->rw_nh <= 0) return 0.f;
   const int nh1 = R->rw_nh + 1, nb = R->nb, h = R->h_rf, bm = R->bucket[m];
   float acc = 0.f;
-  for (int i = threadIdx.x; i < nh1 * nb; i += kPushThreads) {
+  for (int i = threadIdx.x; i < nh1 * nb; i += kTThreads) {
     const int back = i / nb, mp = i - back * nb;
     const long long src = turn - 1 - back;
     const int D = back * h + bm - R->bucket[mp];
@@ -623,7 +632,7 @@ __device__ float rw_voltage_f32(const RunDev *__restrict__ R, int m, long long t
   __syncthreads();
   float v = 0.f;
 #pragma unroll
-  for (int w = 0; w < kPushThreads / 32; ++w) v += red[w];
+  for (int w = 0; w < kTThreads / 32; ++w) v += red[w];
   __syncthreads();
   return v;
 }
@@ -650,9 +659,9 @@ __device__ double rw_voltage_f64(const RunDev *__restrict__ R, int m, long long 
 }
 
 template <int NLONG_MAX>
-__global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed_t(const Plan p) {
+__global__ void __launch_bounds__(kTThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed_t(const Plan p) {
   extern __shared__ __align__(128) uint8_t sm_pt[];
-  __shared__ float s_red[kPushThreads / 32][9];
+  __shared__ float s_red[kTThreads / 32][9];
   __shared__ float2 s_phi[kMaxLong];
   __shared__ int s_plane[kMaxLong];
   __shared__ float4 s_hc[kMaxHarm];
@@ -677,7 +686,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   double *del = R->delta + bd.off + t.start;
   float *xg = tr ? static_cast<float *>(R->x) + bd.off + t.start : nullptr;
   float *pg = tr ? static_cast<float *>(R->xp) + bd.off + t.start : nullptr;
-  const int nchunks = (t.count + kChunk - 1) / kChunk;
+  const int nchunks = (t.count + kChunkT - 1) / kChunkT;
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < kStages; ++st) mbar_init(&full[st], 1);
@@ -688,7 +697,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   }
   const int nharm = R->nharm;
   if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
-  for (int k = threadIdx.x; k < nbins + kSpillCells; k += kPushThreads) {
+  for (int k = threadIdx.x; k < nbins + kSpillCells; k += kTThreads) {
     sH[k] = 0;
     sLo[k] = 0u;
     sHi[k] = 0;
@@ -699,7 +708,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   const int par = (int)(turn & 1);
   const float *vsr = static_cast<const float *>(R->vsr) + (size_t)t.m * nbins;
   const float *vtg = tr ? static_cast<const float *>(R->vt) + (size_t)t.m * nbins : nullptr;
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+  for (int k = threadIdx.x; k < nbins; k += kTThreads) {
     const float v0 = vsr[k];
     const float v1 = k + 1 < nbins ? vsr[k + 1] : v0;
     sVd[k] = make_float2(v0, v1 - v0);
@@ -770,22 +779,22 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
     }
     if (ch == 0) {
       tref = reinterpret_cast<const float *>(sg)[0];
-      dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kChunk * 4)[0]);
+      dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kChunkT * 4)[0]);
     }
-    const int q = ch * kChunk + 4 * (int)threadIdx.x;
+    const int q = ch * kChunkT + 4 * (int)threadIdx.x;
     if (!s_abort && q < t.count) {
       const uint32_t quad = (uint32_t)((t.start + q) >> 2);
       const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
-      const double2 da = reinterpret_cast<const double2 *>(sg + kChunk * 4)[2 * threadIdx.x];
-      const double2 db = reinterpret_cast<const double2 *>(sg + kChunk * 4)[2 * threadIdx.x + 1];
+      const double2 da = reinterpret_cast<const double2 *>(sg + kChunkT * 4)[2 * threadIdx.x];
+      const double2 db = reinterpret_cast<const double2 *>(sg + kChunkT * 4)[2 * threadIdx.x + 1];
       float rr[4] = {0.f, 0.f, 0.f, 0.f};
       if (c.qe != 0.f) normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 0u, k0, k1), rr);
       float tt[4] = {tv.x, tv.y, tv.z, tv.w};
       double dd[4] = {da.x, da.y, db.x, db.y};
       const int nvalid = min(4, t.count - q);
       if (tr) {
-        const float4 xv = reinterpret_cast<const float4 *>(sg + kChunk * 12)[threadIdx.x];
-        const float4 pv = reinterpret_cast<const float4 *>(sg + kChunk * 16)[threadIdx.x];
+        const float4 xv = reinterpret_cast<const float4 *>(sg + kChunkT * 12)[threadIdx.x];
+        const float4 pv = reinterpret_cast<const float4 *>(sg + kChunkT * 16)[threadIdx.x];
         float xx[4] = {xv.x, xv.y, xv.z, xv.w}, pp[4] = {pv.x, pv.y, pv.z, pv.w};
         float rx[4] = {0.f, 0.f, 0.f, 0.f}, rp[4] = {0.f, 0.f, 0.f, 0.f};
         if (texc) {
@@ -837,7 +846,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   if (threadIdx.x < 9) {
     double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
+    for (int w = 0; w < kTThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
     const int col = threadIdx.x < 5 ? threadIdx.x : threadIdx.x + 1;
     p.partial[(size_t)blockIdx.x * kPartials + col] = acc;
   } else if (threadIdx.x == 9) {
@@ -849,7 +858,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mi
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
   float *dg = tr ? static_cast<float *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
   const double du = tr ? R->dip_unit : 0.0;
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+  for (int k = threadIdx.x; k < nbins; k += kTThreads) {
     const int cnt = sH[k];
     if (cnt) {
       atomicAdd(hg + k, cnt);
@@ -1183,10 +1192,10 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
   if (precision == kMixed && p.max_trans) {
     const size_t smem = push_t_smem(max_nbins);
     switch (p.max_nlong) {
-      case 0: return launch_ex(k_push_mixed_t<0>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 1: return launch_ex(k_push_mixed_t<1>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 2: return launch_ex(k_push_mixed_t<2>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      default: return launch_ex(k_push_mixed_t<kMaxLong>, p.ntiles, kPushThreads, smem, s, pdl, p);
+      case 0: return launch_ex(k_push_mixed_t<0>, p.ntiles, kTThreads, smem, s, pdl, p);
+      case 1: return launch_ex(k_push_mixed_t<1>, p.ntiles, kTThreads, smem, s, pdl, p);
+      case 2: return launch_ex(k_push_mixed_t<2>, p.ntiles, kTThreads, smem, s, pdl, p);
+      default: return launch_ex(k_push_mixed_t<kMaxLong>, p.ntiles, kTThreads, smem, s, pdl, p);
     }
   }
   if (precision == kMixed && p.stream_ctas <= 0) {
@@ -1262,7 +1271,7 @@ cudaError_t push_tile_resident_slots(bool trans, int *slots) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = trans ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed_t<1>, kPushThreads, smem)
+    e = trans ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed_t<1>, kTThreads, smem)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1, false>, kPushThreads, smem);
   *slots = per * nsm;
   return e;
