@@ -557,6 +557,37 @@ def l5scan_bench(args, rank, local):
     return 0
 
 
+def resident_scan(pkg, runs, turns, last):
+    """The same scan's runs tracked resident, all members at once
+    (mbt_batch_track_resident: one stream per run, forked from and joined into
+    the current stream): throughput over `turns` turns from the matched start
+    (CUDA events on the current stream) and each run's equilibrium rms length
+    over the last `last` turns."""
+    import torch
+    trackers = [pkg.tracker_for_run(r, record_turns=turns) for r in runs]
+    stream = torch.cuda.current_stream()
+    for t in trackers:
+        t.init_particles(stream)
+    b = pkg.Batch(trackers)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.track_resident(turns, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    b.sync()
+    ms = ev0.elapsed_time(ev1)
+    sig = [round(float(t.moments(turns - last, last)[:, 0, 1].mean()) * 1e12, 4) for t in trackers]
+    b.close()
+    for t in trackers:
+        t.close()
+    mp = sum(r.n_particles for r in runs)
+    return {"value": mp * turns / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / turns, "turns": turns,
+            "mode": "mbt_batch_track_resident: every run's cluster-resident kernel on its own stream, "
+                    "concurrently, clusters capped in size so that all runs' clusters are on the GPU at once",
+            "sigma_tau_ps": sig}
+
+
 def rwscan_bench(args, rank, local):
     """Single-bunch current scan in the resistive-wall wake, one batch."""
     if rank != 0:
@@ -609,6 +640,7 @@ def rwscan_bench(args, rank, local):
                                    f"around the ring, {turns} turns, one batch; mesh 256 cells over +-{hw} sigma",
                        "equilibrium": f"averages over the last {last} turns", "sigma_E": ring["sigma_delta"]},
             "scan": table, "clocks": clocks}
+    line["resident"] = resident_scan(pkg, runs, turns, last)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -670,6 +702,7 @@ def hcscan_bench(args, rank, local):
                                    f" phase {phih:.4f} rad), {n_mp} mp, {turns} turns, one batch",
                        "equilibrium": f"averages over the last {last} turns"},
             "scan": table, "clocks": clocks}
+    line["resident"] = resident_scan(pkg, runs, turns, last)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -37,7 +37,8 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
-           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_destroy",
+           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_autotune", "mbt_batch_track_resident",
+           "mbt_batch_destroy",
            "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
            "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split", "mbt_phasor_steps",
            "mbt_phasor_segment", "mbt_phasor_compose", "mbt_phasor_apply", "mbt_probe_fp64_fma"]
@@ -145,6 +146,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_wake_noalloc": ([_P(Ring), _i, _i, _P(_d), _P(_d), _P(_d), _P(_i32), _i, _d, _i, _P(_d), _vp,
                                       _vp, _vp, ctypes.c_char_p, _sz], _i),
                 "mbt_batch_create": ([_P(_vp), _i, _P(_vp)], _i), "mbt_batch_track": ([_vp, _i64, _vp], _i),
+                "mbt_batch_track_resident": ([_vp, _i64, _vp], _i),
                 "mbt_batch_sync": ([_vp], _i), "mbt_batch_destroy": ([_vp], None),
                 "mbt_server_create": ([_P(ServerConfig), _P(_vp)], _i),
                 "mbt_server_submit": ([_vp, _P(Request), _P(_i64)], _i),
@@ -452,6 +454,13 @@ class Batch:
 
     def track(self, nturns: int, stream=None):
         st = self._L.mbt_batch_track(self._h, int(nturns), _stream(stream))
+        if st != 0:
+            raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+
+    def track_resident(self, nturns: int, stream=None):
+        """Every member tracked resident at the same time (one stream each,
+        forked from and joined into `stream`)."""
+        st = self._L.mbt_batch_track_resident(self._h, int(nturns), _stream(stream))
         if st != 0:
             raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
 

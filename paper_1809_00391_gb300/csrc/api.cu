@@ -193,6 +193,9 @@ struct mbt_batch {
   int graph_turns = 0;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t capture_stream = nullptr;
+  // concurrent resident tracking: one stream per member, fork / join events
+  std::vector<cudaStream_t> res_streams;
+  std::vector<cudaEvent_t> res_events;   // [0] fork, [1 + i] member i done
 };
 
 namespace {
@@ -1601,7 +1604,9 @@ mbt_status mbt_autotune(mbt_ctx *c, int turns_per_trial, int *chosen_tile) {
 // Cluster shape for resident tracking: the largest power-of-two cluster (<= 16
 // CTAs) whose slices fit in shared memory and whose clusters can all be
 // resident at once.  Returns MBT_OK with *cluster = 0 if the fill does not fit.
-static mbt_status resident_shape(mbt_ctx *c, int *cluster, int *per, size_t *smem) {
+// The largest cluster size C <= cmax (16, 8, 4, 2, 1) whose CTAs hold the
+// longest bunch in shared memory, with a cluster per bunch on the GPU at once.
+static mbt_status resident_shape(mbt_ctx *c, int *cluster, int *per, size_t *smem, int cmax = 16) {
   *cluster = 0;
   int64_t nmax = 0;
   for (int64_t n : c->nmp) nmax = std::max(nmax, n);
@@ -1610,6 +1615,7 @@ static mbt_status resident_shape(mbt_ctx *c, int *cluster, int *per, size_t *sme
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(c, e, "device query");
   for (int C = 16; C >= 1; C /= 2) {
+    if (C > cmax) continue;
     const int64_t p4 = ((nmax + C - 1) / C + 3) / 4 * 4;
     const size_t sm = resident_smem_bytes((int)p4, c->nbins);
     if (sm > 220 * 1024 || (int64_t)c->nb * C > nsm) continue;
@@ -1640,9 +1646,24 @@ mbt_status mbt_resident_shape(mbt_ctx *c, int *cluster, int *per_cta) {
   return resident_shape(c, cluster, per_cta, &sm);
 }
 
+// Emission and grid-barrier buffers of resident tracking, allocated once
+// (cudaMalloc may synchronise the device: never between concurrent launches)
+static mbt_status resident_alloc(mbt_ctx *c) {
+  if (c->d_resE) return MBT_OK;
+  mbt_status st = dalloc(c, &c->d_resE, (size_t)2 * std::max(1, c->nlong) * c->nb * sizeof(double2));
+  if (st == MBT_OK) st = dalloc(c, &c->d_gbar, 16);
+  return st;
+}
+
+static mbt_status track_resident_impl(mbt_ctx *c, int64_t nturns, void *stream, int cmax);
+
 mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
   if (!c) return MBT_ERR_ARG;
   c->err.clear();
+  return track_resident_impl(c, nturns, stream, 16);
+}
+
+static mbt_status track_resident_impl(mbt_ctx *c, int64_t nturns, void *stream, int cmax) {
   if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
   if (nturns < 0 || nturns > (1LL << 30)) return fail(c, MBT_ERR_ARG, "nturns out of range");
   if (nturns == 0) return MBT_OK;
@@ -1653,14 +1674,10 @@ mbt_status mbt_track_resident(mbt_ctx *c, int64_t nturns, void *stream) {
     return fail(c, MBT_ERR_UNSUPPORTED, "resident tracking holds at most %d bunches", kResidentMaxBunches);
   int C = 0, per = 0;
   size_t sm = 0;
-  mbt_status st = resident_shape(c, &C, &per, &sm);
+  mbt_status st = resident_shape(c, &C, &per, &sm, cmax);
   if (st != MBT_OK) return st;
   if (C == 0) return fail(c, MBT_ERR_UNSUPPORTED, "the fill does not fit in shared memory of co-resident clusters");
-  const int nl = std::max(1, c->nlong);
-  if (!c->d_resE) {
-    if ((st = dalloc(c, &c->d_resE, (size_t)2 * nl * c->nb * sizeof(double2))) != MBT_OK) return st;
-    if ((st = dalloc(c, &c->d_gbar, 16)) != MBT_OK) return st;
-  }
+  if ((st = resident_alloc(c)) != MBT_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ResidentArgs a{};
   a.plan = c->own.plan;
@@ -2155,7 +2172,101 @@ void mbt_batch_destroy(mbt_batch *b) {
   cudaDeviceSynchronize();
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  for (cudaStream_t st : b->res_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->res_events) cudaEventDestroy(ev);
   delete b;
+}
+
+// Each member's resident kernel on a stream of its own, all forked from and
+// joined back into `stream`.  Members run concurrently only because no
+// cluster of theirs waits for another cluster (one bunch per member, or no
+// long-range resonator): a member whose clusters meet in a grid barrier
+// needs all of them co-resident, which kernels sharing the GPU cannot
+// promise, so such a batch is refused before any launch.
+mbt_status mbt_batch_track_resident(mbt_batch *b, int64_t nturns, void *stream) {
+  if (!b || nturns < 0) return MBT_ERR_ARG;
+  mbt_ctx *c0 = b->ctx[0];
+  c0->err.clear();
+  if (nturns == 0) return MBT_OK;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    mbt_ctx *c = b->ctx[i];
+    if (!c->filled) return fail(c0, MBT_ERR_STATE, "member %zu: fill not set", i);
+    if (c->precision != MBT_PREC_MIXED || c->trans || c->nb > kResidentMaxBunches)
+      return fail(c0, MBT_ERR_UNSUPPORTED, "member %zu cannot be tracked resident", i);
+    if (c->nlong > 0 && c->nb > 1)
+      return fail(c0, MBT_ERR_UNSUPPORTED,
+                  "member %zu couples several bunches over long range: its clusters meet every turn and it "
+                  "must be tracked resident alone", i);
+    int C = 0, per = 0;
+    size_t sm = 0;
+    mbt_status st = resident_shape(c, &C, &per, &sm);
+    if (st != MBT_OK) return fail(c0, st, "member %zu: %s", i, c->err.c_str());
+    if (C == 0) return fail(c0, MBT_ERR_UNSUPPORTED, "member %zu does not fit in shared memory", i);
+    if ((st = resident_alloc(c)) != MBT_OK) return fail(c0, st, "member %zu: %s", i, c->err.c_str());
+  }
+  // the largest cluster-size cap at which every member's clusters fit on the
+  // SMs together (one resident CTA per SM); else each member's own shape
+  int dev = 0, nsm = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e0 != cudaSuccess) return cuda_fail(c0, e0, "device query");
+  // (a cluster occupies SMs of one GPC, so the count of clusters the GPU
+  // holds at once comes from the occupancy query, not from the SM count)
+  int cmax = 16;
+  for (int cap = 16; cap >= 1; cap /= 2) {
+    int64_t ctas = 0, clusters = 0;
+    size_t sm_max = 0;
+    bool fits = true;
+    for (mbt_ctx *c : b->ctx) {
+      int C = 0, per = 0;
+      size_t sm = 0;
+      if (resident_shape(c, &C, &per, &sm, cap) != MBT_OK || C == 0) {
+        fits = false;
+        break;
+      }
+      ctas += (int64_t)C * c->nb;
+      clusters += c->nb;
+      sm_max = std::max(sm_max, sm);
+    }
+    if (!fits) break;
+    int maxc = 0;
+    if (resident_max_clusters(cap, sm_max, &maxc) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (ctas <= nsm && clusters <= maxc) {
+      cmax = cap;
+      break;
+    }
+  }
+  if (b->res_streams.empty()) {
+    for (size_t i = 0; i <= b->ctx.size(); ++i) {
+      cudaEvent_t ev = nullptr;
+      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(c0, e, "event");
+      b->res_events.push_back(ev);
+    }
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+      cudaStream_t st = nullptr;
+      cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(c0, e, "stream");
+      b->res_streams.push_back(st);
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaEventRecord(b->res_events[0], s);
+  if (e != cudaSuccess) return cuda_fail(c0, e, "fork");
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    e = cudaStreamWaitEvent(b->res_streams[i], b->res_events[0], 0);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "fork");
+    b->ctx[i]->err.clear();
+    mbt_status st = track_resident_impl(b->ctx[i], nturns, b->res_streams[i], cmax);
+    if (st != MBT_OK) return fail(c0, st, "member %zu: %s", i, b->ctx[i]->err.c_str());
+    e = cudaEventRecord(b->res_events[1 + i], b->res_streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->res_events[1 + i], 0);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "join");
+  }
+  return MBT_OK;
 }
 
 mbt_status mbt_plan_streams(int nruns, const int64_t *run_n, const int32_t *run_nb, int any_transverse, int ctas,
