@@ -208,7 +208,9 @@ mbt_status mbt_read_transverse_moments(mbt_ctx *ctx, int64_t turn0, int64_t ntur
 
 /* Dipole sums (sum of x over each cell's particles, [nb][nbins]) of the last
  * completed turn and the transverse short-range voltage [V] built from them
- * for the next kick ([nb][nbins]); either may be NULL.  Synchronous. */
+ * for the next kick ([nb][nbins]); either may be NULL.  MBT_PREC_MIXED
+ * returns the exact sums of the quantised x (see mbt_set_transverse), which
+ * do not depend on the push tiling.  Synchronous. */
 mbt_status mbt_read_transverse_wake(mbt_ctx *ctx, double *dipoles, double *V);
 
 /* Add a tabulated short-range wake (Sec. 2.3: other wakes, such as the

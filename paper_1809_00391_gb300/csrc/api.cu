@@ -965,7 +965,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
     const size_t fs = mixed ? sizeof(float) : sizeof(double);
     ALLOC(c->d_x, (size_t)c->n_alloc * fs);
     ALLOC(c->d_xp, (size_t)c->n_alloc * fs);
-    ALLOC(c->d_dip, (size_t)2 * nb * nbins * fs);
+    ALLOC(c->d_dip, (size_t)2 * nb * nbins * 8);   // int64 fixed point (kMixed) or double
     ALLOC(c->d_vt, (size_t)nb * nbins * fs);
     ALLOC(c->d_trec, (size_t)c->cap * nb * kTRecord * sizeof(double));
     ALLOC(c->d_tlag, (size_t)nbins * sizeof(double));
@@ -1164,6 +1164,7 @@ mbt_status mbt_set_fill(mbt_ctx *c, int nb, const int32_t *bucket, const double 
       const double sx = std::sqrt(c->t_beta * c->t_emit);
       const int e = sx > 0 ? std::max(-16, (int)std::ceil(std::log2(sx))) : -16;
       rd.dip_unit = std::ldexp(1.0, e - 20);
+      rd.f_dip_unit = (float)rd.dip_unit;
       rd.f_dip_inv = (float)std::ldexp(1.0, 20 - e);
       rd.f_dip_range = (float)std::ldexp(1.0, e + 10);
     }
@@ -1240,7 +1241,7 @@ mbt_status mbt_init_particles(mbt_ctx *c, void *stream) {
   cudaMemsetAsync(c->d_turn, 0, 16, s);
   if (c->trans) {
     const size_t fs = c->precision == MBT_PREC_MIXED ? sizeof(float) : sizeof(double);
-    cudaMemsetAsync(c->d_dip, 0, (size_t)2 * c->nb * c->nbins * fs, s);
+    cudaMemsetAsync(c->d_dip, 0, (size_t)2 * c->nb * c->nbins * 8, s);
     cudaMemsetAsync(c->d_vt, 0, (size_t)c->nb * c->nbins * fs, s);
     if (c->rw_nh > 0) cudaMemsetAsync(c->d_rwcent, 0, (size_t)(c->rw_nh + 1) * c->nb * sizeof(double), s);
   }
@@ -1842,11 +1843,15 @@ mbt_status mbt_read_transverse_wake(mbt_ctx *c, double *dip, double *V) {
   const int par = (int)((turn - 1) & 1);
   const bool mixed = c->precision == MBT_PREC_MIXED;
   double *outs[2] = {dip, V};
-  const void *srcs[2] = {static_cast<const char *>(c->d_dip) + (size_t)par * n * (mixed ? 4 : 8), c->d_vt};
+  const void *srcs[2] = {static_cast<const char *>(c->d_dip) + (size_t)par * n * 8, c->d_vt};
   for (int a = 0; a < 2; ++a) {
     if (!outs[a]) continue;
     cudaError_t e;
-    if (mixed) {
+    if (mixed && a == 0) {   // exact fixed-point sums: q u
+      std::vector<long long> q(n);
+      e = cudaMemcpy(q.data(), srcs[a], n * sizeof(long long), cudaMemcpyDeviceToHost);
+      for (size_t i = 0; i < n; ++i) outs[a][i] = (double)q[i] * c->rundev.dip_unit;
+    } else if (mixed) {
       std::vector<float> v(n);
       e = cudaMemcpy(v.data(), srcs[a], n * sizeof(float), cudaMemcpyDeviceToHost);
       for (size_t i = 0; i < n; ++i) outs[a][i] = v[i];
@@ -1917,7 +1922,7 @@ std::vector<Section> state_sections(mbt_ctx *c) {
     const size_t fs = mixed ? sizeof(float) : sizeof(double);
     out.push_back({c->d_x, (size_t)c->n_alloc * fs});
     out.push_back({c->d_xp, (size_t)c->n_alloc * fs});
-    out.push_back({c->d_dip, (size_t)2 * c->nb * c->nbins * fs});
+    out.push_back({c->d_dip, (size_t)2 * c->nb * c->nbins * 8});
     out.push_back({c->d_vt, (size_t)c->nb * c->nbins * fs});
     if (c->rw_nh > 0) out.push_back({c->d_rwcent, (size_t)(c->rw_nh + 1) * c->nb * sizeof(double)});
   }

@@ -108,6 +108,14 @@ __device__ __forceinline__ float f64_to_f32_trunc(double d) {
 // A float near d for every finite |d| < 2^128 (a reference value for moment
 // sums, not a rounding): 0 for |d| < 2^-100, where the narrowing above does
 // not apply, the truncated value otherwise.  Integer pipe only.
+// A fixed-point dipole sum (int64 in units of u, a power of two) as FP32:
+// its high and low 32-bit words converted separately, q = hi 2^32 + lo, so
+// that no 64-bit conversion is needed (the result is within 2^-23 of q u).
+__device__ __forceinline__ float dip_q_to_f(long long q, float u) {
+  const float hi = (float)(int)(q >> 32), lo = (float)(unsigned)(q & 0xFFFFFFFFLL);
+  return fmaf(hi, 4294967296.f, lo) * u;
+}
+
 __device__ __forceinline__ float f64_to_f32_ref(double d) {
   const uint32_t hi = (uint32_t)__double2hiint(d);
   return (hi & 0x7FF00000u) < ((1023u - 100u) << 20) ? 0.f : f64_to_f32_trunc(d);

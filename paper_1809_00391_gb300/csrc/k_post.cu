@@ -155,10 +155,10 @@ __device__ void moments_job(const Plan &p, const RunDev *__restrict__ R, int m0,
   int32_t *hz = R->hist + ((size_t)(par ^ 1) * nb + m0) * nbins;
   for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) hz[i] = 0;
   if (R->trans) {
-    // the other dipole buffer too (float for kMixed, double for kF64)
+    // the other dipole buffer too (int64 fixed point for kMixed, double for kF64)
     const size_t off = ((size_t)(par ^ 1) * nb + m0) * nbins;
     if (R->precision == kMixed)
-      for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) static_cast<float *>(R->dip)[off + i] = 0.f;
+      for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) static_cast<long long *>(R->dip)[off + i] = 0;
     else
       for (int i = threadIdx.x; i < nbt * nbins; i += kPostThreads) static_cast<double *>(R->dip)[off + i] = 0.0;
   }
@@ -202,12 +202,14 @@ __device__ void trans_job_f32(const RunDev *__restrict__ R, const PostJob &job, 
   const int m0 = job.bt * kBunchTile, nbt = min(kBunchTile, nb - m0);
   float *sWp = reinterpret_cast<float *>(smem);   // [nbins zeros | Wx[0 .. nbins)]
   float *sD = sWp + 2 * nbins;                     // [kBunchTile][nbins], rows past nbt zero
-  const float *dg = static_cast<const float *>(R->dip) + ((size_t)par * nb + m0) * nbins;
+  const long long *dg = static_cast<const long long *>(R->dip) + ((size_t)par * nb + m0) * nbins;
+  const float du = R->f_dip_unit;
   for (int k = threadIdx.x; k < nbins; k += kPostThreads) {
     sWp[k] = 0.f;
     sWp[nbins + k] = R->tlag_f[k];
   }
-  for (int i = threadIdx.x; i < kBunchTile * nbins; i += kPostThreads) sD[i] = i < nbt * nbins ? dg[i] : 0.f;
+  for (int i = threadIdx.x; i < kBunchTile * nbins; i += kPostThreads)
+    sD[i] = i < nbt * nbins ? dip_q_to_f(dg[i], du) : 0.f;
   __syncthreads();
   const int r = threadIdx.x % kTransRows, g = threadIdx.x / kTransRows, j = job.sub * kTransRows + r;
   float acc[kPer];
@@ -316,10 +318,15 @@ __device__ void tile_job(const Plan &p, const RunDev *__restrict__ R, const Post
       if (b < nbt) {
         float4 cnt[kGroups];
         if (tplane) {
-          const float4 *d4 = reinterpret_cast<const float4 *>(static_cast<const float *>(R->dip) +
-                                                              ((size_t)par * nb + m0 + b) * nbins);
+          const longlong2 *d2 = reinterpret_cast<const longlong2 *>(static_cast<const long long *>(R->dip) +
+                                                                    ((size_t)par * nb + m0 + b) * nbins);
+          const float du = R->f_dip_unit;
 #pragma unroll
-          for (int i = 0; i < kGroups; ++i) cnt[i] = i < ng ? d4[sub + 8 * i] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int i = 0; i < kGroups; ++i) {
+            const longlong2 a = i < ng ? d2[2 * (sub + 8 * i)] : make_longlong2(0, 0);
+            const longlong2 c = i < ng ? d2[2 * (sub + 8 * i) + 1] : make_longlong2(0, 0);
+            cnt[i] = make_float4(dip_q_to_f(a.x, du), dip_q_to_f(a.y, du), dip_q_to_f(c.x, du), dip_q_to_f(c.y, du));
+          }
         } else {
           const int4 *h4 = reinterpret_cast<const int4 *>(hcur + (size_t)b * nbins);
 #pragma unroll

@@ -532,10 +532,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_push_stream(const Plan p)
     st = st2 = sd = sd2 = 0.f;
     nout = 0;
     consumers_sync();   // every deposit of the tile made, S.red complete
-    for (int b = tid; b < nbins; b += kConsumers) {
+    // (the spill cells behind this mesh are cleared too: a later tile of a
+    // run with a larger mesh counts into those cells)
+    for (int b = tid; b < nbins + kSpillCells; b += kConsumers) {
       const int cnt = sH[b];
       if (cnt) {
-        if (!failed) atomicAdd(hg + b, cnt);
+        if (!failed && b < nbins) atomicAdd(hg + b, cnt);
         sH[b] = 0;
       }
     }
@@ -856,14 +858,14 @@ __global__ void __launch_bounds__(kTThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed
     pp[11] = (double)t.count;
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
-  float *dg = tr ? static_cast<float *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
-  const double du = tr ? R->dip_unit : 0.0;
+  unsigned long long *dg =
+      tr ? static_cast<unsigned long long *>(R->dip) + ((size_t)par * R->nb + t.m) * nbins : nullptr;
   for (int k = threadIdx.x; k < nbins; k += kTThreads) {
     const int cnt = sH[k];
     if (cnt) {
       atomicAdd(hg + k, cnt);
-      // the tile's exact fixed-point sum (|2^16 hi + lo| < 2^47), scaled by the power of two u
-      if (tr) atomicAdd(dg + k, (float)((double)((long long)sHi[k] * 65536LL + (long long)sLo[k]) * du));
+      // the tile's exact fixed-point sum (|2^16 hi + lo| < 2^47) into the bunch's int64 sum (two's complement)
+      if (tr) atomicAdd(dg + k, (unsigned long long)((long long)sHi[k] * 65536LL + (long long)sLo[k]));
     }
   }
 }

@@ -88,6 +88,8 @@ struct RunDev {
   int trans;
   void *x, *xp;
   void *dip;                // [2][nb][nbins] sum of x over each cell's particles; turn parity selects
+                            // (kF64: double; kMixed: int64 in units of dip_unit, summed exactly, so
+                            // that the sums do not depend on the order of the tiles' atomics)
   void *vt;                 // [nb][nbins] transverse short-range voltage [V] for the next kick
   double *trec;             // [cap][nb][kTRecord]
   const double *tlag;       // [nbins] transverse wake per lag [V/(C m)]
@@ -106,7 +108,7 @@ struct RunDev {
   // fixed-point dipole deposit of the mixed push: unit u = 2^(e - 20) m with
   // 2^e >= sqrt(beta emit) (e >= -16), 1/u, and the accepted |x| < 2^30 u
   double dip_unit;
-  float f_dip_inv, f_dip_range;
+  float f_dip_unit, f_dip_inv, f_dip_range;
 };
 
 

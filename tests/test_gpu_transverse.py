@@ -292,3 +292,56 @@ def test_mixed_dipole_range_is_reported(pkg):
     tr.track(1)
     tr.sync()
     tr.close()
+
+
+def test_mixed_transverse_multi_tile_bunches(pkg, oracle_mod):
+    """Bunches that span several push tiles: 24 bunches of ~8e4
+    macro-particles (ragged sizes, ten tiles each) with a longitudinal and a
+    transverse long-range resonator against the oracle over 30 turns (moments
+    of both planes 1e-3 of the rms, counts exact in total); and, since the
+    tiles add their dipole sums into the bunch's sums exactly (integers), the
+    same run in a batch with another large run gives its particles and
+    moments of both planes bit for bit."""
+    ring = W.ring_r0()
+    buckets = np.array([0, 1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144, 150, 160, 170, 180, 200, 220, 240, 260, 280, 300,
+                        320, 340], np.int32)
+    n = np.full(buckets.size, 80_000, np.int64)
+    n[3], n[10], n[17] = 80_001, 79_998, 80_003
+    c = np.full(buckets.size, 1.5e-3)
+    tplane = _plane(resonators=[dict(TRES), dict(BBT)])
+    run = W.Run(ring, [dict(W.BROADBAND), dict(W.HOM)], buckets, c, n, seed=23, turns=30, precision=W.PREC_MIXED,
+                transverse=tplane, name="transverse, multi-tile bunches")
+    tr = pkg.tracker_for_run(run, record_turns=run.turns)
+    tr.init_particles()
+    tr.track(run.turns)
+    rec_g = tr.moments(0, run.turns)
+    trec_g = tr.transverse_moments(0, run.turns)
+    h, out = tr.histograms()
+    assert h.sum() + out.sum() == n.sum()
+    orc = _oracle(oracle_mod, run)
+    orc.init_particles()
+    rec_o, trec_o = orc.track2(run.turns)
+    st, sd = rec_o[:, :, 1], rec_o[:, :, 3]
+    for col, scale in ((0, st), (1, st), (2, sd), (3, sd)):
+        assert np.max(np.abs(rec_g[:, :, col] - rec_o[:, :, col]) / scale) <= 1e-3, col
+    sx, sp = trec_o[:, :, 1], trec_o[:, :, 3]
+    for col, scale in ((0, sx), (1, sx), (2, sp), (3, sp)):
+        assert np.max(np.abs(trec_g[:, :, col] - trec_o[:, :, col]) / scale) <= 1e-3, col
+    # alone = in a batch with another large transverse run
+    other = W.Run(ring, [dict(W.BROADBAND)], buckets[:20], c[:20], np.full(20, 100_000, np.int64), seed=24,
+                  turns=30, precision=W.PREC_MIXED, transverse=_plane(resonators=[dict(TRES)]), name="other")
+    t1 = pkg.tracker_for_run(run, record_turns=run.turns)
+    t2 = pkg.tracker_for_run(other, record_turns=run.turns)
+    t1.init_particles()
+    t2.init_particles()
+    bt = pkg.Batch([t1, t2])
+    bt.track(run.turns)
+    bt.sync()
+    assert np.array_equal(t1.moments(0, run.turns), rec_g)
+    assert np.array_equal(t1.transverse_moments(0, run.turns), trec_g)
+    for m in (0, 3, 23):
+        assert np.array_equal(t1.transverse_particles(m)[0], tr.transverse_particles(m)[0])
+        assert np.array_equal(t1.particles(m)[0], tr.particles(m)[0])
+    bt.close()
+    for t in (tr, t1, t2):
+        t.close()
