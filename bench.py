@@ -51,6 +51,12 @@ and prints its throughput and the FP64 push's time per launch;
 mixed path, and prints both throughputs and the FP64 push against the GPU's
 measured DFMA throughput.
 
+Cluster-resident tracking: python bench.py --workload resident [--steps K]
+tracks one bunch of 1e4 and one of 1e5 macro-particles (broadband wake) and
+three bunches of 1e5 with the long-range HOM resident (mbt_track_resident, K
+turns in one launch) and through the per-turn kernels, and prints the time
+per turn of each.
+
 The default line also carries a bounded serving sample (--serving-requests,
 Poisson requests at about the server's capacity: p50/p99 latency) and the
 FP64 oracle timed on all host cores (one process per core, each tracking a
@@ -106,7 +112,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
     ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t", "three_f64",
-                                           "fill390_f64", "state"],
+                                           "fill390_f64", "state", "resident"],
                     default="fill390")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (1/s)")
@@ -707,6 +713,54 @@ def hcscan_bench(args, rank, local):
     return 0
 
 
+def resident_bench(args, rank, local):
+    """Time per turn of small fills held in cluster shared memory
+    (mbt_track_resident: all K turns in one launch, CUDA events) against the
+    same runs through the per-turn kernels (graph replay)."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1809_00391_gb300 as pkg
+    pkg.build()
+    K = max(args.steps, 50)
+    ring = W.ring_r0()
+    cases = []
+    for name, buckets, n_mp, res in (("1 bunch x 1e4, BB", [0], 10_000, [dict(W.BROADBAND)]),
+                                     ("1 bunch x 1e5, BB", [0], 100_000, [dict(W.BROADBAND)]),
+                                     ("3 bunches x 1e5, BB + HOM (long range)", [0, 1, 2], 100_000,
+                                      [dict(W.BROADBAND), dict(W.HOM)])):
+        b, c, n = W._fill(buckets, 1e-3, n_mp)
+        run = W.Run(ring, res, b, c, n, seed=3, turns=K, precision=W.PREC_MIXED, name=name)
+        out = {"case": name}
+        stream = torch.cuda.current_stream()
+        for mode in ("resident", "per-turn kernels"):
+            tr = pkg.tracker_for_run(run, record_turns=max(K, 64))
+            tr.init_particles(stream)
+            if mode == "resident":
+                tr.track_resident(max(3, args.warmup), stream)
+            else:
+                tr.set_graph(min(K, GRAPH_TURNS))
+                tr.track(min(K, GRAPH_TURNS) * 2, stream)
+            tr.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if mode == "resident":
+                tr.track_resident(K, stream)
+            else:
+                tr.track(K, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tr.sync()
+            out[mode + " us_per_turn"] = e0.elapsed_time(e1) * 1e3 / K
+            if mode == "resident":
+                out["cluster"], out["per_cta"] = tr.resident_shape()
+            tr.close()
+        cases.append(out)
+    print(json.dumps({"workload": "cluster-resident tracking", "turns": K, "cases": cases}), flush=True)
+    return 0
+
+
 def three_f64_bench(args, rank, local):
     """Three bunches x 1e5 macro-particles, broadband + HOM, on the FP64
     tracker: throughput, and the FP64 push's time per launch.  The FP64 path
@@ -949,6 +1003,8 @@ def main():
         return fill390_f64_bench(args, rank, local)
     if args.workload == "state":
         return state_bench(args, rank, local)
+    if args.workload == "resident":
+        return resident_bench(args, rank, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -1044,7 +1100,8 @@ def main():
     if not args.no_e2e:
         rng = np.random.default_rng(100 + rank)
         n = run.n_particles
-        host_tau = torch.from_numpy(rng.normal(0.0, 13.2e-12, n)).pin_memory()
+        # tau in FP32, the precision the mixed path keeps it in (mbt_set_particles_all_f32)
+        host_tau = torch.from_numpy(rng.normal(0.0, 13.2e-12, n).astype(np.float32)).pin_memory()
         host_del = torch.from_numpy(rng.normal(0.0, 9e-4, n)).pin_memory()
         tr2 = pkg.tracker_for_run(run, record_turns=max(K, 16))
         tr2.set_tile(tile)
@@ -1061,12 +1118,12 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-        h2d = n * (8 + 8)
+        h2d = host_tau.numel() * host_tau.element_size() + host_del.numel() * host_del.element_size()
         d2h = mom.nbytes
         e2e = {"value": n_part * K * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K, "ms": e2e_s * 1e3,
-               "note": "host clock around: tau, delta (FP64) of every bunch from page-locked host memory "
-                       "(mbt_set_particles_all), K turns, all K turns of moments read to the host"}
+               "note": "host clock around: tau (FP32) and delta (FP64) of every bunch from page-locked host "
+                       "memory (mbt_set_particles_all_f32), K turns, all K turns of moments read to the host"}
         tr2.close()
 
     # ---- a bounded sample of the serving workload (Poisson requests at about

@@ -276,6 +276,13 @@ mbt_status mbt_set_particles(mbt_ctx *ctx, int bunch, const double *tau_s, const
  * n_particles doubles. */
 mbt_status mbt_set_particles_all(mbt_ctx *ctx, const double *tau_s, const double *delta, void *stream);
 
+/* The same with tau in FP32 host arrays (n_particles floats; delta stays
+ * n_particles doubles): the precision MBT_PREC_MIXED stores tau in, so 12
+ * bytes per particle cross the host link instead of 16.  MBT_PREC_F64
+ * widens tau exactly.  Same fallback, errors and synchronisation as
+ * mbt_set_particles_all. */
+mbt_status mbt_set_particles_all_f32(mbt_ctx *ctx, const float *tau_s, const double *delta, void *stream);
+
 /* Copy one bunch's coordinates to host arrays of n_mp[bunch] doubles.
  * Synchronous (waits for tracking in flight). */
 mbt_status mbt_get_particles(mbt_ctx *ctx, int bunch, double *tau_s, double *delta);

@@ -33,7 +33,7 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_add_transverse_resistive_wall",
            "mbt_set_transverse_particles", "mbt_get_transverse_particles", "mbt_read_transverse_moments",
            "mbt_read_transverse_wake", "mbt_set_grid", "mbt_set_fill", "mbt_set_record", "mbt_init_particles",
-           "mbt_set_particles", "mbt_set_particles_all", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_set_wait_test", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
+           "mbt_set_particles", "mbt_set_particles_all", "mbt_set_particles_all_f32", "mbt_get_particles", "mbt_track", "mbt_track_resident", "mbt_set_wait_test", "mbt_resident_shape", "mbt_sync", "mbt_read_moments",
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
@@ -129,6 +129,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_set_record": ([_vp, _i64], _i), "mbt_init_particles": ([_vp, _vp], _i),
                 "mbt_set_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_set_particles_all": ([_vp, _vp, _vp, _vp], _i),
+                "mbt_set_particles_all_f32": ([_vp, _vp, _vp, _vp], _i),
                 "mbt_get_particles": ([_vp, _i, _P(_d), _P(_d)], _i),
                 "mbt_track": ([_vp, _i64, _vp], _i), "mbt_sync": ([_vp], _i),
                 "mbt_track_resident": ([_vp, _i64, _vp], _i),
@@ -303,21 +304,23 @@ class Tracker:
         numpy arrays or CPU torch tensors; page-locked ones (e.g. torch
         ``pin_memory()``) are read by the device directly."""
         n = int(self.n_mp.sum())
+        # tau may be FP32 (mbt_set_particles_all_f32: the mixed path's own precision)
+        t32 = str(getattr(tau, "dtype", "")) in ("torch.float32", "float32")
         ptrs = []
         keep = []
-        for a in (tau, delta):
+        for a, want in ((tau, "float32" if t32 else "float64"), (delta, "float64")):
             if hasattr(a, "data_ptr"):
-                if a.dtype.__str__() != "torch.float64" or a.numel() != n or not a.is_contiguous() or a.is_cuda:
-                    raise ValueError("need contiguous CPU float64 tensors of n_particles values")
+                if a.dtype.__str__() != "torch." + want or a.numel() != n or not a.is_contiguous() or a.is_cuda:
+                    raise ValueError(f"need contiguous CPU {want} tensors of n_particles values")
                 ptrs.append(a.data_ptr())
             else:
-                arr = np.ascontiguousarray(a, np.float64)
+                arr = np.ascontiguousarray(a, np.dtype(want))
                 if arr.size != n:
                     raise ValueError("need n_particles values")
                 keep.append(arr)
                 ptrs.append(arr.ctypes.data)
-        self._chk(self._L.mbt_set_particles_all(self._h, ctypes.c_void_p(ptrs[0]), ctypes.c_void_p(ptrs[1]),
-                                                _stream(stream)))
+        call = self._L.mbt_set_particles_all_f32 if t32 else self._L.mbt_set_particles_all
+        self._chk(call(self._h, ctypes.c_void_p(ptrs[0]), ctypes.c_void_p(ptrs[1]), _stream(stream)))
 
     def particles(self, bunch: int):
         n = int(self.n_mp[bunch])

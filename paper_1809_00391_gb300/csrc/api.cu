@@ -1304,6 +1304,36 @@ mbt_status mbt_set_particles_all(mbt_ctx *c, const double *tau, const double *de
   return MBT_OK;
 }
 
+mbt_status mbt_set_particles_all_f32(mbt_ctx *c, const float *tau, const double *delta, void *stream) {
+  if (!c || !tau || !delta) return fail(c, MBT_ERR_ARG, "null argument");
+  c->err.clear();
+  if (!c->filled) return fail(c, MBT_ERR_STATE, "fill not set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaPointerAttributes at{}, ad{};
+  const bool pinned = cudaPointerGetAttributes(&at, tau) == cudaSuccess &&
+                      cudaPointerGetAttributes(&ad, delta) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                      ad.type == cudaMemoryTypeHost && at.devicePointer && ad.devicePointer;
+  cudaGetLastError();
+  if (!pinned) {
+    // widened bunch by bunch (exact), then as mbt_set_particles
+    std::vector<double> t;
+    size_t h = 0;
+    for (int m = 0; m < c->nb; ++m) {
+      const size_t n = (size_t)c->nmp[m];
+      t.assign(tau + h, tau + h + n);
+      const mbt_status st = mbt_set_particles(c, m, t.data(), delta + h);
+      if (st != MBT_OK) return st;
+      h += n;
+    }
+    return MBT_OK;
+  }
+  cudaError_t e = launch_load_host_f32(c->own.plan, c->precision, static_cast<const float *>(at.devicePointer),
+                                       static_cast<const double *>(ad.devicePointer), c->d_hoff, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set particles from host");
+  return MBT_OK;
+}
+
 mbt_status mbt_get_particles(mbt_ctx *c, int bunch, double *tau, double *delta) {
   if (!c || !tau || !delta) return fail(c, MBT_ERR_ARG, "null argument");
   c->err.clear();

@@ -1138,7 +1138,8 @@ __global__ void __launch_bounds__(kPushThreads) k_init(const Plan p, int precisi
 // to FP32 by rounding for kMixed, as a per-bunch copy does).  hoff[m]: first
 // particle of bunch m in the host arrays.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPushThreads) k_load_host(const Plan p, int precision, const double *tau_h,
+template <typename TT>
+__global__ void __launch_bounds__(kPushThreads) k_load_host(const Plan p, int precision, const TT *tau_h,
                                                             const double *del_h, const long long *hoff) {
   const TileDev t = p.tiles[blockIdx.x];
   const RunDev *__restrict__ R = p.runs + t.run;
@@ -1146,7 +1147,8 @@ __global__ void __launch_bounds__(kPushThreads) k_load_host(const Plan p, int pr
   const long long h0 = hoff[t.m] + t.start, d0 = bd.off + t.start;
   for (int q = 4 * (int)threadIdx.x; q < t.count; q += 4 * kPushThreads) {
     const int nv = min(4, t.count - q);
-    double tv[4], dv[4];
+    TT tv[4];
+    double dv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (e < nv) {
@@ -1158,7 +1160,7 @@ __global__ void __launch_bounds__(kPushThreads) k_load_host(const Plan p, int pr
     for (int e = 0; e < 4; ++e) {
       if (e < nv) {
         if (precision == kMixed) static_cast<float *>(R->tau)[d0 + q + e] = (float)tv[e];
-        else static_cast<double *>(R->tau)[d0 + q + e] = tv[e];
+        else static_cast<double *>(R->tau)[d0 + q + e] = (double)tv[e];
         R->delta[d0 + q + e] = dv[e];
       }
     }
@@ -1168,7 +1170,14 @@ __global__ void __launch_bounds__(kPushThreads) k_load_host(const Plan p, int pr
 cudaError_t launch_load_host(const Plan &p, int precision, const double *tau_h, const double *del_h,
                              const long long *hoff, cudaStream_t s) {
   if (p.ntiles == 0) return cudaSuccess;
-  k_load_host<<<p.ntiles, kPushThreads, 0, s>>>(p, precision, tau_h, del_h, hoff);
+  k_load_host<double><<<p.ntiles, kPushThreads, 0, s>>>(p, precision, tau_h, del_h, hoff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_host_f32(const Plan &p, int precision, const float *tau_h, const double *del_h,
+                                 const long long *hoff, cudaStream_t s) {
+  if (p.ntiles == 0) return cudaSuccess;
+  k_load_host<float><<<p.ntiles, kPushThreads, 0, s>>>(p, precision, tau_h, del_h, hoff);
   return cudaGetLastError();
 }
 

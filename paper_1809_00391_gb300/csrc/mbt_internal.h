@@ -216,6 +216,8 @@ cudaError_t launch_init(const Plan &p, int precision, cudaStream_t s);
 // hoff: device array, first particle of each bunch in the host arrays
 cudaError_t launch_load_host(const Plan &p, int precision, const double *tau_h, const double *del_h,
                              const long long *hoff, cudaStream_t s);
+cudaError_t launch_load_host_f32(const Plan &p, int precision, const float *tau_h, const double *del_h,
+                                 const long long *hoff, cudaStream_t s);
 
 size_t post_smem_bytes(int precision, int max_nbins);
 cudaError_t configure_kernels();

@@ -85,3 +85,40 @@ def test_batched_64_runs_full_size(pkg, oracle_mod):
     batch.close()
     for t in ts:
         t.close()
+
+
+def test_streaming_batch_of_two_meshes(pkg):
+    """A batch of two large runs on the streaming push with meshes of 128 and
+    256 cells: each CTA pushes a tile of one run, then of the other, and the
+    first run's particles outside its narrow mesh (which count into spill
+    cells behind its 128 cells) must not reach the second run's cells 128 and
+    up.  Histograms and moments equal the runs tracked alone, bit for bit."""
+    ring = W.ring_r0()
+    b, c, n = W._fill(range(30), 0.5e-3, 100_000)
+    narrow = W.Run(ring, [dict(W.BROADBAND), dict(W.HOM)], b, c, n, seed=61, turns=3, precision=W.PREC_MIXED,
+                   nbins=128, half_width_sigmas=2.0, name="128 cells over +-2 sigma")
+    wide = W.Run(ring, [dict(W.BROADBAND), dict(W.HOM)], b, c, n, seed=62, turns=3, precision=W.PREC_MIXED,
+                 name="256 cells over +-5 sigma")
+    alone = []
+    for r in (narrow, wide):
+        t = pkg.tracker_for_run(r, record_turns=3)
+        assert t.info["push_ctas"] > 0
+        t.init_particles()
+        t.track(3)
+        h, out = t.histograms()
+        alone.append((h, out, t.moments(0, 3)))
+        t.close()
+    assert alone[0][1].sum() > 10_000   # the narrow mesh leaves many particles outside
+    trs = [pkg.tracker_for_run(r, record_turns=3) for r in (narrow, wide)]
+    for t in trs:
+        t.init_particles()
+    bt = pkg.Batch(trs)
+    bt.track(3)
+    bt.sync()
+    for t, (h, out, rec) in zip(trs, alone):
+        h2, out2 = t.histograms()
+        assert np.array_equal(h2, h) and np.array_equal(out2, out)
+        assert np.array_equal(t.moments(0, 3), rec)
+    bt.close()
+    for t in trs:
+        t.close()
