@@ -191,9 +191,17 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     }
     __syncthreads();
     if (tid < 5) {
-      double acc = 0.0;
-      for (int w = 0; w < kResidentThreads / 32; ++w) acc += (double)s_red[w][tid];
-      s_mom[tid] = acc;
+      // the warps' FP32 sums by a pairwise tree of fixed shape (a serial FP64
+      // chain over the warps would wait 64 cycles per add), FP64 from the CTA on
+      constexpr int kW = kResidentThreads / 32, kH = kW / 2;
+      float a[kH];
+#pragma unroll
+      for (int i = 0; i < kH; ++i) a[i] = s_red[i][tid] + s_red[kH + i][tid];
+#pragma unroll
+      for (int h = kH / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int i = 0; i < h; ++i) a[i] += a[i + h];
+      s_mom[tid] = (double)a[0];
     } else if (tid == 5) {
       s_mom[5] = (double)tref;
       s_mom[6] = (double)dref;
@@ -201,41 +209,45 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     }
     cl.sync();   // #1: every CTA histogram and moment partial of the turn is complete
 
-    // bunch histogram (every CTA), moments (CTA 0)
+    // bunch histogram (every CTA: all remote loads of a cell issued before
+    // the sum), moments (CTA 0)
     for (int k = tid; k < nbins; k += kResidentThreads) {
+      int v[16];
+#pragma unroll
+      for (int cr = 0; cr < 16; ++cr) v[cr] = cr < C ? cl.map_shared_rank(lh, cr)[k] : 0;
       int sum = 0;
-      for (int cr = 0; cr < C; ++cr) sum += cl.map_shared_rank(lh, cr)[k];
+#pragma unroll
+      for (int cr = 0; cr < 16; ++cr) sum += v[cr];
       S.bh[k] = sum;
     }
     __syncthreads();
-    if (rank == 0 && tid == 0) {
+    if (rank == 0 && warp == 0) {
       // the CTAs' sums about their own references combined exactly (the
       // pairwise form of the variance): the mean first, then every CTA's
-      // second moment about it
+      // second moment about it; lane cr holds CTA cr's sums
       const double inv_n = R->inv_n[m];
-      double at = 0.0, ad = 0.0, s4 = 0.0;
-      for (int cr = 0; cr < C; ++cr) {
-        const double *q = cl.map_shared_rank(s_mom, cr);
-        at += fma(q[7], q[5], q[0]);
-        ad += fma(q[7], q[6], q[2]);
-        s4 += q[4];
+      double q[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      if (lane < C) {
+        const double *r = cl.map_shared_rank(s_mom, lane);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) q[i] = r[i];
       }
+      const double at = warp_sum_d(fma(q[7], q[5], q[0])), ad = warp_sum_d(fma(q[7], q[6], q[2]));
+      const double s4 = warp_sum_d(q[4]);
       const double mt = at * inv_n, md = ad * inv_n;
-      double qt = 0.0, qd = 0.0;
-      for (int cr = 0; cr < C; ++cr) {
-        const double *q = cl.map_shared_rank(s_mom, cr);
-        const double et = q[5] - mt, ed = q[6] - md;
-        qt += fma(q[7] * et, et, fma(2.0 * et, q[0], q[1]));
-        qd += fma(q[7] * ed, ed, fma(2.0 * ed, q[2], q[3]));
+      const double et = q[5] - mt, ed = q[6] - md;
+      const double qt = warp_sum_d(lane < C ? fma(q[7] * et, et, fma(2.0 * et, q[0], q[1])) : 0.0);
+      const double qd = warp_sum_d(lane < C ? fma(q[7] * ed, ed, fma(2.0 * ed, q[2], q[3])) : 0.0);
+      if (lane == 0) {
+        const double vt = fmax(qt * inv_n, 0.0), vd = fmax(qd * inv_n, 0.0);
+        double *rec = R->rec + ((size_t)(turn % R->cap) * nb + m) * kRecord;
+        rec[0] = mt;
+        rec[1] = sqrt(vt);
+        rec[2] = md;
+        rec[3] = sqrt(vd);
+        rec[4] = (double)bd.n - s4;
+        rec[5] = s4;
       }
-      const double vt = fmax(qt * inv_n, 0.0), vd = fmax(qd * inv_n, 0.0);
-      double *rec = R->rec + ((size_t)(turn % R->cap) * nb + m) * kRecord;
-      rec[0] = mt;
-      rec[1] = sqrt(vt);
-      rec[2] = md;
-      rec[3] = sqrt(vd);
-      rec[4] = (double)bd.n - s4;
-      rec[5] = s4;
     }
     // rows [rank B, rank B + B) of V = q sum_{k<=j} lag[j-k] count[k]
     {
