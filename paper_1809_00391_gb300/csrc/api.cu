@@ -491,6 +491,19 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
       fold = true;
       st.jobs.erase(std::remove_if(st.jobs.begin(), st.jobs.end(), [](const PostJob &j) { return j.type == kJobMoments; }),
                     st.jobs.end());
+      // and one wake job per bunch tile of a 256-cell mesh instead of one per
+      // M-tile (B built once; the jobs fill fewer waves)
+      std::vector<PostJob> merged;
+      merged.reserve(st.jobs.size());
+      for (const PostJob &j : st.jobs) {
+        if (j.type == kJobWake && st.runs[(size_t)j.run].nbins == 256) {
+          if (j.sub == 1) continue;   // folded into the job of M-tile 0
+          merged.push_back(PostJob{j.run, kJobWake, j.bt, kWakeBoth});
+        } else {
+          merged.push_back(j);
+        }
+      }
+      st.jobs.swap(merged);
     }
   }
   Plan pl{};

@@ -480,7 +480,7 @@ __device__ void finish_turn(const Plan &p, int own, const RunDev *Rown) {
 //   D (tensor memory) = 128 lanes x 96 FP32 columns.
 // ---------------------------------------------------------------------------
 constexpr int kWakeN = 3 * kBunchTile;   // 96
-constexpr uint32_t kTmemCols = 256;      // power of two >= kWakeN, with headroom
+constexpr uint32_t kTmemCols = 256;      // power of two >= kWakeN, with headroom (two accumulators for kWakeBoth)
 
 // Operand A of M-tile mt: rows [128 mt, 128 mt + 128) of the lower triangular
 // Toeplitz matrix only involve columns k < Kmt = 128 (mt + 1), so the image
@@ -494,12 +494,13 @@ __device__ __forceinline__ size_t wake_img_offset(int mt) { return (size_t)512 *
 __device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, uint8_t *smem, uint64_t *bars,
                               uint32_t *tmem_slot, int *s_flag) {
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int mt = job.sub;
+  const int mt = job.sub == kWakeBoth ? 0 : job.sub;   // both M-tiles: M-tile 0 first
   const int kmt = wake_kmt(mt, R->nbins);
   const uint32_t a_bytes = (uint32_t)kmt * 512u;
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
     fence_mbar_init();
     *s_flag = 0;
     const uint8_t *src = static_cast<const uint8_t *>(R->toep) + wake_img_offset(mt);
@@ -513,28 +514,15 @@ __device__ void wake_prologue(const RunDev *__restrict__ R, const PostJob &job, 
   tc_fence_after();
 }
 
-// Main part: B from the turn's counts, the MMAs (issued by one thread, run
-// asynchronously), then the epilogue from tensor memory.
-// qf: the charges of the tile's 32 bunches (staged, or the run's array at
-// the tile).  check_counts: record kErrCount in the error word if a count
-// lies outside [0, 2^24) (counts from a caller; tracking caps its bunches
-// below 2^24 particles, so its counts never need the test).
-__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem,
-                            uint64_t *bars, uint32_t *tmem_slot, int *s_flag, const float *qf,
-                            bool check_counts = false) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// B of a wake job: the counts of the tile's 32 bunches over cells [0, kmt)
+// split into three exact BF16 byte planes (K-major core matrices).
+__device__ __forceinline__ void wake_build_b(const Plan &p, const RunDev *__restrict__ R, int bt, int par, uint8_t *sB,
+                                             int kmt, bool check_counts) {
+  const int tid = threadIdx.x;
   const int nbins = R->nbins;
   const int nb = R->nb;
-  const int mt = job.sub;
-  const int kmt = wake_kmt(mt, nbins);
-  const int m0 = job.bt * kBunchTile;
+  const int m0 = bt * kBunchTile;
   const int nbt = min(kBunchTile, nb - m0);
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + (size_t)nbins * 512u;   // after the largest A image
-  const uint32_t lboA = 16u * 128u;           // next 8-column K group: 16 row groups later
-  const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
-  const uint32_t tmem = *tmem_slot;
-
   // B: counts of the 32 bunches split into three exact BF16 byte planes.
   // Item (bunch b, 8-cell group kg) = idx = kg * 32 + b; a thread's items are
   // idx = tid + i kPostThreads (at most kItems with nbins <= 256), and all of
@@ -581,6 +569,31 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
       *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
+}
+
+// Main part: B from the turn's counts, the MMAs (issued by one thread, run
+// asynchronously), then the epilogue from tensor memory.
+// qf: the charges of the tile's 32 bunches (staged, or the run's array at
+// the tile).  check_counts: record kErrCount in the error word if a count
+// lies outside [0, 2^24) (counts from a caller; tracking caps its bunches
+// below 2^24 particles, so its counts never need the test).
+__device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem,
+                            uint64_t *bars, uint32_t *tmem_slot, int *s_flag, const float *qf,
+                            bool check_counts = false) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbins = R->nbins;
+  const int nb = R->nb;
+  const int mt = job.sub;
+  const int kmt = wake_kmt(mt, nbins);
+  const int m0 = job.bt * kBunchTile;
+  const int nbt = min(kBunchTile, nb - m0);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + (size_t)nbins * 512u;   // after the largest A image
+  const uint32_t lboA = 16u * 128u;           // next 8-column K group: 16 row groups later
+  const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
+  const uint32_t tmem = *tmem_slot;
+
+  wake_build_b(p, R, job.bt, par, sB, kmt, check_counts);
   fence_proxy_async_smem();
   __syncthreads();
 
@@ -633,13 +646,128 @@ __device__ void wake_job_tc(const Plan &p, const RunDev *__restrict__ R, const P
   }
 }
 
+// Epilogue of M-tile mt of wake_job_both (a warp of warps 0-3): its 32 rows
+// from tensor-memory columns [128 mt, 128 mt + 96), the byte planes
+// recombined, times the bunch charges.  Not inlined, so that the two
+// accumulators' registers are not live at once.
+__device__ __noinline__ void wake_epilogue(const RunDev *__restrict__ R, uint32_t tl, int mt, int m0, int nbt,
+                                           const float *qf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nbins = R->nbins;
+  tc_fence_after();
+  float d0[32], d1[32], d2[32];
+  const uint32_t col = 128u * (uint32_t)mt;
+  tmem_ld32(tl + col + 0, d0);
+  tmem_ld32(tl + col + 32, d1);
+  tmem_ld32(tl + col + 64, d2);
+  const int j = mt * 128 + warp * 32 + lane;
+  float *vsr = static_cast<float *>(R->vsr);
+#pragma unroll
+  for (int b = 0; b < kBunchTile; ++b) {
+    if (b < nbt) {
+      const float q = qf[b];
+      vsr[(size_t)(m0 + b) * nbins + j] = q * fmaf(65536.f, d2[b], fmaf(256.f, d1[b], d0[b]));
+    }
+  }
+}
+
+// Both M-tiles of a 256-cell mesh in one job (plans whose post jobs fill
+// several waves: one job fewer per bunch tile, and B built once).  M-tile 0's
+// image (64 KB, from the prologue) is contracted into tensor-memory columns
+// [0, 96); once those MMAs have read it, M-tile 1's image (128 KB) is copied
+// over it and contracted into columns [128, 224).  Thread 128 (warp 4) issues
+// and sequences; warps 0-3 read the two accumulators as they complete.
+// Barriers: bars[0] image copies (phase 0: M-tile 0, phase 1: M-tile 1),
+// bars[1] / bars[2] the MMAs of M-tile 0 / 1 (one phase each, so that no
+// waiter can miss a phase).
+__device__ void wake_job_both(const Plan &p, const RunDev *__restrict__ R, const PostJob &job, int par, uint8_t *smem,
+                              uint64_t *bars, uint32_t *tmem_slot, int *s_flag, const float *qf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nbins = R->nbins;   // 256
+  const int m0 = job.bt * kBunchTile;
+  const int nbt = min(kBunchTile, R->nb - m0);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + (size_t)nbins * 512u;
+  const uint32_t lboA = 16u * 128u;
+  const uint32_t lboB = (uint32_t)(kWakeN / 8) * 128u;
+  const uint32_t tmem = *tmem_slot;
+  wake_build_b(p, R, job.bt, par, sB, nbins, false);
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  constexpr int kIssuer = 128;
+  if (tid == kIssuer) {
+    const uint32_t idesc = idesc_bf16_f32(128, kWakeN);
+    const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+    bool ok = mbar_wait_bounded(&bars[0], 0, kWaitLimitNs);   // M-tile 0's image
+    if (ok) {
+      tc_fence_after();
+      const int ks_half = wake_kmt(0, nbins) / 16;
+      for (int ks = 0; ks < 2 * ks_half; ++ks) {
+        const uint64_t ad = smem_desc_kmajor(a0 + (uint32_t)ks * 2u * lboA, lboA, 128u);
+        const uint64_t bd = smem_desc_kmajor(b0 + (uint32_t)(ks % ks_half) * 2u * lboB, lboB, 128u);
+        umma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
+      umma_commit(&bars[1]);
+      ok = mbar_wait_bounded(&bars[1], 0, kWaitLimitNs);   // those MMAs have read the image
+    }
+    bool copied = false;
+    if (ok) {
+      tc_fence_after();
+      fence_proxy_async_smem();
+      const uint32_t a_bytes = (uint32_t)wake_kmt(1, nbins) * 512u;
+      const uint8_t *src = static_cast<const uint8_t *>(R->toep) + wake_img_offset(1);
+      mbar_arrive_expect_tx(&bars[0], a_bytes);
+      for (uint32_t off = 0; off < a_bytes; off += 32768u)
+        bulk_g2s(sA + off, src + off, min(32768u, a_bytes - off), &bars[0]);
+      copied = true;
+      ok = mbar_wait_bounded(&bars[0], 1, kWaitLimitNs);   // M-tile 1's image
+    }
+    if (ok) {
+      tc_fence_after();
+      const int ks_half = wake_kmt(1, nbins) / 16;
+      for (int ks = 0; ks < 2 * ks_half; ++ks) {
+        const uint64_t ad = smem_desc_kmajor(a0 + (uint32_t)ks * 2u * lboA, lboA, 128u);
+        const uint64_t bd = smem_desc_kmajor(b0 + (uint32_t)(ks % ks_half) * 2u * lboB, lboB, 128u);
+        umma_bf16(tmem + 128u, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
+      umma_commit(&bars[2]);
+    } else {
+      atomicExch(p.error, kErrTimeout);
+      *s_flag = 1;
+      // let the copies in flight land before the CTA exits
+      mbar_wait_bounded(&bars[0], 0, kWaitLimitNs);
+      if (copied) mbar_wait_bounded(&bars[0], 1, kWaitLimitNs);
+    }
+  }
+  if (warp < 4) {
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    if (!mbar_wait_bounded(&bars[1], 0, kWaitLimitNs)) {
+      if (lane == 0) atomicExch(p.error, kErrTimeout);
+    } else {
+      wake_epilogue(R, tl, 0, m0, nbt, qf);
+      if (!mbar_wait_bounded(&bars[2], 0, kWaitLimitNs)) {
+        if (lane == 0) atomicExch(p.error, kErrTimeout);
+      } else {
+        wake_epilogue(R, tl, 1, m0, nbt, qf);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 __device__ __forceinline__ void trace_mark(const Plan &p, int slot) {
   if (p.trace != nullptr && threadIdx.x == 0) p.trace[(size_t)blockIdx.x * 3 + slot] = global_timer_ns();
 }
 
 __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   extern __shared__ __align__(1024) uint8_t sm_post[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[3];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_flag;
   __shared__ double2 sE[kBunchTile];
@@ -670,7 +798,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   grid_dependents_launch();   // the next push may start its prologue (particle prefetch)
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
-  if (job.type == kJobWake)
+  if (job.type == kJobWake && job.sub == kWakeBoth)
+    wake_job_both(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
+  else if (job.type == kJobWake)
     wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
   else if (job.type == kJobTile) {
     if (p.fold_moments) {
@@ -776,7 +906,7 @@ static __device__ __align__(256) unsigned char g_wake_scratch[kNoAllocScratchByt
 
 __global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) {
   extern __shared__ __align__(1024) uint8_t sm_wna[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[3];   // wake_prologue initialises three
   __shared__ uint32_t tmem_slot;
   __shared__ int s_flag;
   __shared__ double s_sum[9][kBunchTile];

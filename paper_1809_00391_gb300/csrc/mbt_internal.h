@@ -35,6 +35,9 @@ constexpr int kF64RowChunk = 32;     // FP64 Toeplitz rows per post job
 enum Precision { kF64 = 0, kMixed = 1 };
 enum Flags { kNoSR = 1, kNoQE = 2, kKickNGP = 4 };
 enum JobType { kJobWake = 0, kJobTile = 1, kJobTrans = 2, kJobMoments = 3 };
+// PostJob::sub of a kMixed wake job over both M-tiles of a 256-cell mesh
+// (plans whose post jobs fill several waves); otherwise sub is the M-tile
+constexpr int kWakeBoth = 2;
 // kErrCount: a cell count outside [0, 2^24) reached the tensor-core wake,
 // which splits each count into three exact 8-bit planes.  kErrDipole: the
 // mixed transverse push met an x outside its dipole deposit's fixed-point
