@@ -500,24 +500,27 @@ mbt_status mbt_probe_fp64_fma(int blocks_per_sm, int iters, int repeats, void *s
  * and must outlive the batch. */
 mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out);
 mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream);
-mbt_status mbt_batch_sync(mbt_batch *b);   /* wait; report device errors of the batch */
+mbt_status mbt_batch_sync(mbt_batch *b);   /* wait; report device errors of the batch and of its members
+                                              (the first one; the message on the first member) */
 /* Graph replay and push-tile autotuning for a batch, as for a context. */
 mbt_status mbt_batch_set_graph(mbt_batch *b, int turns_per_graph);
 mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_tile);
 /* Track every member resident (as mbt_track_resident) at the same time: each
  * member's kernel on a stream of the batch's own, forked from and joined back
- * into `stream` (asynchronous on it; errors of the kernels surface at
- * mbt_batch_sync or a member's synchronising call).  For scans of many small
- * runs, whose turns in the per-tile push are bound by launch latency.  Every
- * member must fit resident and must not couple several bunches over long
- * range (its clusters would meet in a grid barrier, which needs all of them
- * on the GPU at once): otherwise MBT_ERR_UNSUPPORTED before any launch.
- * The cluster size is capped (16, 8, 4, 2 or 1 CTAs) at the largest value
- * for which the clusters of all members fit on the GPU together (one CTA
- * per SM, and no more clusters than the occupancy query for that size
- * allows: a cluster takes SMs of one GPC); a member whose own size (mbt_resident_shape) is within the cap gets
- * the results of mbt_track_resident bit for bit, a smaller cluster the same
- * map with its sums in another order. */
+ * into `stream` (asynchronous on it).  Errors of the kernels surface at
+ * mbt_batch_sync or a member's synchronising call; if a launch fails after
+ * others have started, those keep running and the next sync waits for them.
+ * For scans of many small runs, whose turns in the per-tile push are bound by
+ * launch latency.  Every member must fit resident and must not couple
+ * several bunches over long range (its clusters would meet in a grid
+ * barrier, which needs all of them on the GPU at once): otherwise
+ * MBT_ERR_UNSUPPORTED before any launch.  The cluster size is capped (16, 8,
+ * 4, 2 or 1 CTAs) at the largest value for which the clusters of all members
+ * fit on the GPU together (one CTA per SM, and no more clusters than the
+ * occupancy query for that size allows: a cluster takes SMs of one GPC); a
+ * member whose own size (mbt_resident_shape) is within the cap gets the
+ * results of mbt_track_resident bit for bit, a smaller cluster the same map
+ * with its sums in another order. */
 mbt_status mbt_batch_track_resident(mbt_batch *b, int64_t nturns, void *stream);
 void mbt_batch_destroy(mbt_batch *b);
 

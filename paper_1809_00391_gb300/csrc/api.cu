@@ -2212,7 +2212,13 @@ mbt_status mbt_batch_sync(mbt_batch *b) {
   if (!b) return MBT_ERR_ARG;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(b->ctx[0], e, "sync");
-  return check_device(b->ctx[0], b->store.plan);
+  mbt_status st = check_device(b->ctx[0], b->store.plan);
+  // the members' own error words (their resident kernels, mbt_batch_track_resident)
+  for (size_t i = 0; i < b->ctx.size() && st == MBT_OK; ++i) {
+    st = check_device(b->ctx[i], b->ctx[i]->own.plan);
+    if (st != MBT_OK && i > 0) fail(b->ctx[0], st, "member %zu: %s", i, b->ctx[i]->err.c_str());
+  }
+  return st;
 }
 
 void mbt_batch_destroy(mbt_batch *b) {
