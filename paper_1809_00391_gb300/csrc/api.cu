@@ -508,6 +508,15 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
   }
   Plan pl{};
   pl.fold_moments = fold ? 1 : 0;
+  // the per-tile push in 128-thread CTAs when its tiles fill at least four
+  // waves of the 256-thread kernel's resident slots (k_push.cu, LShape)
+  if (mixed && !streaming && !any_trans) {
+    int tslots = 0;
+    if (push_tile_resident_slots(false, &tslots) == cudaSuccess && tslots > 0)
+      pl.push_small_ctas = (int64_t)st.tiles.size() >= 4 * (int64_t)tslots ? 1 : 0;
+    else
+      cudaGetLastError();
+  }
   if (!up(st.runs, &pl.runs) || !up(st.bunches, &pl.bunches) || !up(st.tiles, &pl.tiles) || !up(st.jobs, &pl.jobs))
     return fail(c, MBT_ERR_NOMEM, "plan upload failed");
   if (streaming) {

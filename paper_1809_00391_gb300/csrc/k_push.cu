@@ -38,27 +38,46 @@ namespace mbt {
 constexpr int kChunk = 1024;
 constexpr int kStages = MBT_PUSH_STAGES;
 static_assert(kStages >= 2, "the stage being refilled must differ from the next one read");
-constexpr int kStageBytes = kChunk * (int)(sizeof(float) + sizeof(double));
+// Per-tile push CTA shapes (runs without a transverse plane): 256 threads x 6
+// CTAs per SM, or for plans of many waves of small tiles 128 threads x 12
+// (measured: the L5 scan's 21 175 tiles of 5000 particles 594 -> 549 us per
+// turn; single-wave plans lose: 24.5 -> 29.8 us on the resistive-wall scan).
+template <int THREADS>
+struct LShape {
+  static constexpr int kChunk = 4 * THREADS;   // particles per stage: one quad per thread
+  static constexpr int kStageBytes = kChunk * (int)(sizeof(float) + sizeof(double));
+  static constexpr int kMinBlocks = THREADS == 256 ? MBT_PUSH_MIN_BLOCKS : 12;
+};
 constexpr unsigned long long kPushWaitNs = 2000000000ull;
 
 // Per-tile push (plans with small runs or small bunches: the streaming push
 // below needs a share of several stages per SM to fill its lanes): one CTA
 // per tile of one bunch, six CTAs per SM; the hardware hands a finished CTA's
 // slot to the next tile.
+template <int THREADS>
 __device__ __forceinline__ void issue_chunk(const TileDev &t, const float *tau, const double *del, uint8_t *stage,
                                             uint64_t *bar, int c) {
-  const int n = min(kChunk, t.count - c * kChunk);
+  constexpr int kChunkL = LShape<THREADS>::kChunk;
+  const int n = min(kChunkL, t.count - c * kChunkL);
   const int n4 = (n + 3) & ~3;   // segments are padded to 4 particles: 16-byte multiples
   const uint32_t tb = (uint32_t)n4 * 4u, db = (uint32_t)n4 * 8u;
   mbar_arrive_expect_tx(bar, tb + db);
-  bulk_g2s(stage, tau + (size_t)c * kChunk, tb, bar);
-  bulk_g2s(stage + kChunk * sizeof(float), del + (size_t)c * kChunk, db, bar);
+  bulk_g2s(stage, tau + (size_t)c * kChunkL, tb, bar);
+  bulk_g2s(stage + kChunkL * sizeof(float), del + (size_t)c * kChunkL, db, bar);
 }
 
-template <int NLONG_MAX, bool HARM>
-__global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixed(const Plan p) {
+template <int NLONG_MAX, bool HARM, int THREADS>
+__global__ void __launch_bounds__(THREADS, LShape<THREADS>::kMinBlocks) k_push_mixed(const Plan p) {
+  constexpr int kLThreads = THREADS, kChunkL = LShape<THREADS>::kChunk, kStageBytesL = LShape<THREADS>::kStageBytes;
   extern __shared__ __align__(128) uint8_t sm_push[];
-  __shared__ float s_red[kPushThreads / 32][5];
+  // The moment partials are summed as the 256-thread layout sums them, in
+  // either shape, so that a run's moments do not depend on the shape its plan
+  // chose: per 256-layout thread over its quads in chunk order, a warp tree,
+  // the 8 warps in order.  A 128-thread CTA's thread t holds two of those
+  // threads, t (its even chunks) and t + 128 (its odd chunks).
+  constexpr int kVW = 8;
+  static_assert(THREADS == 256 || THREADS == 128, "per-tile push CTA shapes");
+  __shared__ float s_red[kVW][5];
   __shared__ float2 s_phi[kMaxLong];
   __shared__ float4 s_hc[kMaxHarm];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -75,17 +94,17 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
   const int nbins = c.nbins;
   const int nlong = R->nlong;
   uint8_t *stages = sm_push;
-  float2 *sVd = reinterpret_cast<float2 *>(sm_push + kStages * kStageBytes);   // (V[j], V[j+1] - V[j])
+  float2 *sVd = reinterpret_cast<float2 *>(sm_push + kStages * kStageBytesL);   // (V[j], V[j+1] - V[j])
   int *sH = reinterpret_cast<int *>(sVd + nbins);
   float *tau = static_cast<float *>(R->tau) + bd.off + t.start;
   double *del = R->delta + bd.off + t.start;
-  const int nchunks = (t.count + kChunk - 1) / kChunk;
+  const int nchunks = (t.count + kChunkL - 1) / kChunkL;
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < kStages; ++st) mbar_init(&full[st], 1);
     fence_mbar_init();
     s_abort = 0;
-    for (int ch = 0; ch < min(kStages, nchunks); ++ch) issue_chunk(t, tau, del, stages + ch * kStageBytes, &full[ch], ch);
+    for (int ch = 0; ch < min(kStages, nchunks); ++ch) issue_chunk<THREADS>(t, tau, del, stages + ch * kStageBytesL, &full[ch], ch);
   }
   const int nharm = R->nharm;
   if (threadIdx.x < nharm) s_hc[threadIdx.x] = R->f_harm[threadIdx.x];
@@ -94,7 +113,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
   const float *vsr = static_cast<const float *>(R->vsr) + (size_t)t.m * nbins;
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+  for (int k = threadIdx.x; k < nbins; k += kLThreads) {
     const float v0 = vsr[k];
     const float v1 = k + 1 < nbins ? vsr[k + 1] : v0;
     sVd[k] = make_float2(v0, v1 - v0);
@@ -133,26 +152,25 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
   const uint32_t k0 = R->key0, k1 = R->key1, turn32 = (uint32_t)turn, bunch32 = (uint32_t)t.m;
   float tref = 0.f, dref = 0.f;   // moment reference: the tile's first particle before the push
 
-  float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;
+  float st = 0.f, st2 = 0.f, sd = 0.f, sd2 = 0.f;      // this thread's (even chunks)
+  float st_b = 0.f, st2_b = 0.f, sd_b = 0.f, sd2_b = 0.f;  // THREADS == 128: thread t + 128's (odd chunks)
   int nout = 0;
-
-#pragma unroll 1
-  for (int ch = 0; ch < nchunks; ++ch) {
+  auto chunk = [&](int ch, float &st, float &st2, float &sd, float &sd2) {
     const int slot = ch % kStages;
-    uint8_t *sg = stages + slot * kStageBytes;
+    uint8_t *sg = stages + slot * kStageBytesL;
     if (!mbar_wait_bounded(&full[slot], (uint32_t)((ch / kStages) & 1), kPushWaitNs)) {
       atomicExch(p.error, kErrTimeout);
       s_abort = 1;
     }
     if (ch == 0) {
       tref = reinterpret_cast<const float *>(sg)[0];
-      dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kChunk * sizeof(float))[0]);
+      dref = f64_to_f32_ref(reinterpret_cast<const double *>(sg + kChunkL * sizeof(float))[0]);
     }
-    const int q = ch * kChunk + 4 * (int)threadIdx.x;   // first particle of this thread's quad in the tile
+    const int q = ch * kChunkL + 4 * (int)threadIdx.x;   // first particle of this thread's quad in the tile
     if (!s_abort && q < t.count) {
       const float4 tv = reinterpret_cast<const float4 *>(sg)[threadIdx.x];
-      const double2 da = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x];
-      const double2 db = reinterpret_cast<const double2 *>(sg + kChunk * sizeof(float))[2 * threadIdx.x + 1];
+      const double2 da = reinterpret_cast<const double2 *>(sg + kChunkL * sizeof(float))[2 * threadIdx.x];
+      const double2 db = reinterpret_cast<const double2 *>(sg + kChunkL * sizeof(float))[2 * threadIdx.x + 1];
       float rr[4] = {0.f, 0.f, 0.f, 0.f};
       if (c.qe != 0.f) normal_quad_f32(philox4x32_10((uint32_t)((t.start + q) >> 2), bunch32, turn32, 0u, k0, k1), rr);
       float tt[4] = {tv.x, tv.y, tv.z, tv.w};
@@ -171,33 +189,42 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
     __syncthreads();   // stage `slot` consumed by every thread
     if (threadIdx.x == 0 && !s_abort && ch + kStages < nchunks) {
       fence_proxy_async_smem();   // order the generic-proxy reads of the stage before its refill
-      issue_chunk(t, tau, del, sg, &full[slot], ch + kStages);
+      issue_chunk<THREADS>(t, tau, del, sg, &full[slot], ch + kStages);
     }
+  };
+#pragma unroll 1
+  for (int ch = 0; ch < nchunks; ch += (THREADS == 128 ? 2 : 1)) {
+    chunk(ch, st, st2, sd, sd2);
+    if (THREADS == 128 && ch + 1 < nchunks) chunk(ch + 1, st_b, st2_b, sd_b, sd2_b);
   }
   if (s_abort && threadIdx.x == 0) {
     // let the copies still in flight land before the CTA exits
     for (int ch = 0; ch < nchunks; ++ch) mbar_wait_bounded(&full[ch % kStages], (uint32_t)((ch / kStages) & 1), kPushWaitNs);
   }
 
-  // moment partials: FP32 within a warp, FP64 across the CTA's warps
+  // moment partials: FP32 within a warp, FP64 across the (256-layout) warps
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  st = warp_sum_f(st);
-  st2 = warp_sum_f(st2);
-  sd = warp_sum_f(sd);
-  sd2 = warp_sum_f(sd2);
   const int no = __reduce_add_sync(0xFFFFFFFFu, nout);
-  if (lane == 0) {
-    s_red[warp][0] = st;
-    s_red[warp][1] = st2;
-    s_red[warp][2] = sd;
-    s_red[warp][3] = sd2;
-    s_red[warp][4] = (float)no;
-  }
+  auto hand_in = [&](float a, float a2, float b, float b2, int vw, float n) {
+    a = warp_sum_f(a);
+    a2 = warp_sum_f(a2);
+    b = warp_sum_f(b);
+    b2 = warp_sum_f(b2);
+    if (lane == 0) {
+      s_red[vw][0] = a;
+      s_red[vw][1] = a2;
+      s_red[vw][2] = b;
+      s_red[vw][3] = b2;
+      s_red[vw][4] = n;   // counts are exact in any split
+    }
+  };
+  hand_in(st, st2, sd, sd2, warp, (float)no);
+  if (THREADS == 128) hand_in(st_b, st2_b, sd_b, sd2_b, warp + 4, 0.f);
   __syncthreads();
   if (threadIdx.x < 5) {
     double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < kPushThreads / 32; ++w) acc += (double)s_red[w][threadIdx.x];
+    for (int w = 0; w < kVW; ++w) acc += (double)s_red[w][threadIdx.x];
     p.partial[(size_t)blockIdx.x * kPartials + threadIdx.x] = acc;
   } else if (threadIdx.x == 5) {
     double *pp = p.partial + (size_t)blockIdx.x * kPartials;
@@ -206,7 +233,7 @@ __global__ void __launch_bounds__(kPushThreads, MBT_PUSH_MIN_BLOCKS) k_push_mixe
     pp[11] = (double)t.count;
   }
   int32_t *hg = R->hist + ((size_t)par * R->nb + t.m) * nbins;
-  for (int k = threadIdx.x; k < nbins; k += kPushThreads) {
+  for (int k = threadIdx.x; k < nbins; k += kLThreads) {
     const int cnt = sH[k];
     if (cnt) atomicAdd(hg + k, cnt);
   }
@@ -588,8 +615,9 @@ constexpr int kStageBytesT = kChunkT * (int)(3 * sizeof(float) + sizeof(double))
 // dynamic shared memory of the per-tile pushes: the stages, then per cell the
 // (V, dV) table(s), the counts (with kSpillCells spill cells) and, with a
 // transverse plane, the dipole sums
-constexpr size_t push_tile_smem(int nbins) {
-  return (size_t)kStages * kStageBytes + (size_t)nbins * sizeof(float2) + (size_t)(nbins + kSpillCells) * sizeof(int);
+constexpr size_t push_tile_smem(int nbins, int threads = 256) {
+  return (size_t)kStages * (size_t)(threads * 4 * 12) + (size_t)nbins * sizeof(float2) +
+         (size_t)(nbins + kSpillCells) * sizeof(int);
 }
 constexpr size_t push_t_smem(int nbins) {
   return (size_t)kStages * kStageBytesT + (size_t)nbins * 2 * sizeof(float2) +
@@ -1210,16 +1238,21 @@ cudaError_t launch_push(const Plan &p, int precision, cudaStream_t s, bool pdl) 
     }
   }
   if (precision == kMixed && p.stream_ctas <= 0) {
-    // per-tile push
-    const size_t smem = push_tile_smem(max_nbins);
+    // per-tile push, in the CTA shape the plan chose
     const bool harm = p.max_nharm > 0;
+    auto go = [&](auto k256, auto k128) -> cudaError_t {
+      if (p.push_small_ctas) return launch_ex(k128, p.ntiles, 128, push_tile_smem(max_nbins, 128), s, pdl, p);
+      return launch_ex(k256, p.ntiles, 256, push_tile_smem(max_nbins, 256), s, pdl, p);
+    };
     switch (p.max_nlong) {
-      case 0: return launch_ex(harm ? k_push_mixed<0, true> : k_push_mixed<0, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 1: return launch_ex(harm ? k_push_mixed<1, true> : k_push_mixed<1, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      case 2: return launch_ex(harm ? k_push_mixed<2, true> : k_push_mixed<2, false>, p.ntiles, kPushThreads, smem, s, pdl, p);
-      default:
-        return launch_ex(harm ? k_push_mixed<kMaxLong, true> : k_push_mixed<kMaxLong, false>, p.ntiles, kPushThreads,
-                         smem, s, pdl, p);
+      case 0: return harm ? go(k_push_mixed<0, true, 256>, k_push_mixed<0, true, 128>)
+                          : go(k_push_mixed<0, false, 256>, k_push_mixed<0, false, 128>);
+      case 1: return harm ? go(k_push_mixed<1, true, 256>, k_push_mixed<1, true, 128>)
+                          : go(k_push_mixed<1, false, 256>, k_push_mixed<1, false, 128>);
+      case 2: return harm ? go(k_push_mixed<2, true, 256>, k_push_mixed<2, true, 128>)
+                          : go(k_push_mixed<2, false, 256>, k_push_mixed<2, false, 128>);
+      default: return harm ? go(k_push_mixed<kMaxLong, true, 256>, k_push_mixed<kMaxLong, true, 128>)
+                           : go(k_push_mixed<kMaxLong, false, 256>, k_push_mixed<kMaxLong, false, 128>);
     }
   }
   if (precision == kMixed) {
@@ -1283,7 +1316,7 @@ cudaError_t push_tile_resident_slots(bool trans, int *slots) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
     e = trans ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed_t<1>, kTThreads, smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1, false>, kPushThreads, smem);
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push_mixed<1, false, 256>, 256, smem);
   *slots = per * nsm;
   return e;
 }
@@ -1295,10 +1328,15 @@ cudaError_t configure_push_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
   int slots = 0;
   if (e == cudaSuccess) e = push_resident_slots(&slots);
-  const int bytes = (int)push_tile_smem(1024);
-  for (auto k : {k_push_mixed<0, false>, k_push_mixed<1, false>, k_push_mixed<2, false>, k_push_mixed<kMaxLong, false>,
-                 k_push_mixed<0, true>, k_push_mixed<1, true>, k_push_mixed<2, true>, k_push_mixed<kMaxLong, true>})
+  const int bytes = (int)push_tile_smem(1024, 256), bytes128 = (int)push_tile_smem(1024, 128);
+  for (auto k : {k_push_mixed<0, false, 256>, k_push_mixed<1, false, 256>, k_push_mixed<2, false, 256>,
+                 k_push_mixed<kMaxLong, false, 256>, k_push_mixed<0, true, 256>, k_push_mixed<1, true, 256>,
+                 k_push_mixed<2, true, 256>, k_push_mixed<kMaxLong, true, 256>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for (auto k : {k_push_mixed<0, false, 128>, k_push_mixed<1, false, 128>, k_push_mixed<2, false, 128>,
+                 k_push_mixed<kMaxLong, false, 128>, k_push_mixed<0, true, 128>, k_push_mixed<1, true, 128>,
+                 k_push_mixed<2, true, 128>, k_push_mixed<kMaxLong, true, 128>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes128);
   const int bytes_t = (int)push_t_smem(256);
   for (auto k : {k_push_mixed_t<0>, k_push_mixed_t<1>, k_push_mixed_t<2>, k_push_mixed_t<kMaxLong>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_t);

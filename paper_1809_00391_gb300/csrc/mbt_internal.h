@@ -182,6 +182,7 @@ struct Plan {
   int *stream_first;          // [stream_ctas + 1]: CTA b of the streaming push takes tiles stream_first[b] .. [b + 1] - 1
   int stream_ctas;            // 0 if the plan is not split for the streaming push
   int fold_moments;           // kMixed: no moments jobs; each tile job sums its bunches' moments first
+  int push_small_ctas;        // per-tile push (no transverse plane) in 128-thread CTAs (plans of many waves)
 };
 
 // Cluster-resident tracking of one run: one thread-block cluster per bunch,
