@@ -49,6 +49,9 @@ struct PlanStore {
   int precision = 0;
   ~PlanStore() { release(); }
   void release() {
+    if (plan.side) cudaStreamDestroy(plan.side);
+    if (plan.ev_fork) cudaEventDestroy(plan.ev_fork);
+    if (plan.ev_join) cudaEventDestroy(plan.ev_join);
     for (void *a : allocs) cudaFree(a);
     allocs.clear();
     bytes = 0;
@@ -504,6 +507,8 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
         }
       }
       st.jobs.swap(merged);
+      // the wake jobs first: they run in a kernel of their own (Plan::post_split)
+      std::stable_partition(st.jobs.begin(), st.jobs.end(), [](const PostJob &j) { return j.type == kJobWake; });
     }
   }
   Plan pl{};
@@ -608,6 +613,23 @@ mbt_status upload_plan(mbt_ctx *c, PlanStore &st) {
     pl.max_trans = std::max(pl.max_trans, r.trans);
   }
   st.bytes += pb + 16;
+  // plans of many post waves: the wake jobs (at the front of the list) in a
+  // kernel of their own, the others beside them on a stream of the plan's own
+  if (fold) {
+    int nw = 0;
+    for (const PostJob &j : st.jobs) nw += j.type == kJobWake ? 1 : 0;
+    if (nw > 0 && nw < (int)st.jobs.size()) {
+      if (cudaStreamCreateWithFlags(&pl.side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&pl.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&pl.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (pl.side) cudaStreamDestroy(pl.side);
+        if (pl.ev_fork) cudaEventDestroy(pl.ev_fork);
+        if (pl.ev_join) cudaEventDestroy(pl.ev_join);
+        return fail(c, MBT_ERR_CUDA, "post-kernel stream");
+      }
+      pl.post_split = nw;
+    }
+  }
   st.plan = pl;
   return MBT_OK;
 }
@@ -686,7 +708,8 @@ mbt_status check_device(mbt_ctx *c, const Plan &pl) {
 mbt_status launch_turns(mbt_ctx *c, const Plan &pl, int prec, int64_t nturns, cudaStream_t s, bool timed) {
   if (!timed) {
     for (int64_t t = 0; t < nturns; ++t) {
-      cudaError_t e = launch_push(pl, prec, s, t > 0);
+      // (after a split post kernel the stream's last step is an event wait: a plain launch)
+      cudaError_t e = launch_push(pl, prec, s, t > 0 && pl.post_split == 0);
       if (e != cudaSuccess) return cuda_fail(c, e, "push launch");
       e = launch_post(pl, prec, s, true);
       if (e != cudaSuccess) return cuda_fail(c, e, "post launch");

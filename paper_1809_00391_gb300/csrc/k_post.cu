@@ -28,6 +28,7 @@
 // writes the value entering every tile and the new carry, and advances the
 // turn counter of every run.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <mutex>
 #include "device_common.cuh"
 
@@ -420,7 +421,7 @@ __device__ __forceinline__ void finish_pair(int nt, double2 K, const double2 *ag
 }
 
 // own, Rown: the run of this CTA's job and its descriptor (a staged copy).
-__device__ void finish_turn(const Plan &p, int own, const RunDev *Rown) {
+__device__ void finish_turn(const Plan &p, int own, const RunDev *Rown, unsigned int njobs) {
   __shared__ int s_last;
   const int warp = threadIdx.x >> 5;
   // Read before the count, so that the last CTA's chain after it is the
@@ -448,7 +449,7 @@ __device__ void finish_turn(const Plan &p, int own, const RunDev *Rown) {
   if (threadIdx.x == 0) {
     __threadfence();   // this CTA's results before its count (release)
     const unsigned int prev = atomicAdd(p.done, 1u);
-    s_last = (prev == gridDim.x - 1) ? 1 : 0;
+    s_last = (prev == njobs - 1u) ? 1 : 0;   // njobs: of every kernel of the turn's post
     if (s_last) __threadfence();   // acquire: every thread of the CTA reads after the barrier below
   }
   __syncthreads();
@@ -761,11 +762,14 @@ __device__ void wake_job_both(const Plan &p, const RunDev *__restrict__ R, const
   }
 }
 
-__device__ __forceinline__ void trace_mark(const Plan &p, int slot) {
-  if (p.trace != nullptr && threadIdx.x == 0) p.trace[(size_t)blockIdx.x * 3 + slot] = global_timer_ns();
+__device__ __forceinline__ void trace_mark(const Plan &p, int slot, int jobi) {
+  if (p.trace != nullptr && threadIdx.x == 0) p.trace[(size_t)jobi * 3 + slot] = global_timer_ns();
 }
 
+// Every job of the plan, one CTA per job.
 __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
+  constexpr int MODE = 0;
+  const int job0 = 0;
   extern __shared__ __align__(1024) uint8_t sm_post[];
   __shared__ __align__(8) uint64_t bars[3];
   __shared__ uint32_t tmem_slot;
@@ -776,8 +780,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   __shared__ PostStage st;
   __shared__ RunDev sR;
   __shared__ double2 s_scr[2 * kBunchTile + 2];
-  const PostJob job = p.jobs[blockIdx.x];
-  trace_mark(p, 0);
+  const int jobi = job0 + (int)blockIdx.x;
+  const PostJob job = p.jobs[jobi];
+  trace_mark(p, 0, jobi);
   // The run descriptor, copied before the wait: the push streams the particle
   // state through L2 and evicts it, and after the wait every read of it would
   // be a miss behind the next push's first bulk copies.
@@ -788,9 +793,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   const RunDev *R = &sR;
   // tile jobs keep the emission table where wake jobs keep their operands
   float2 *tabf = reinterpret_cast<float2 *>(sm_post);
-  if (job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);   // A-image copy first
+  if (MODE != 2 && job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);   // A image first
   post_stage(p, R, job, &st, tabf);
-  if (job.type == kJobTile && threadIdx.x < 32)   // code warm-up, into shared scratch
+  if (MODE != 1 && job.type == kJobTile && threadIdx.x < 32)   // code warm-up, into shared scratch
     tile_scan_warp(make_double2(0.0, 0.0), make_double2(0.0, 0.0), 0.0, make_double2(1.0, 0.0), kBunchTile, s_scr,
                    s_scr + 2 * kBunchTile);
   __syncthreads();
@@ -798,23 +803,82 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_post_mixed(const Plan p) {
   grid_dependents_launch();   // the next push may start its prologue (particle prefetch)
   const long long turn = *R->turn;
   const int par = (int)(turn & 1);
-  if (job.type == kJobWake && job.sub == kWakeBoth)
+  if (MODE != 2 && job.type == kJobWake && job.sub == kWakeBoth)
     wake_job_both(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
-  else if (job.type == kJobWake)
+  else if (MODE != 2 && job.type == kJobWake)
     wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
-  else if (job.type == kJobTile) {
+  else if (MODE != 1 && job.type == kJobTile) {
     if (p.fold_moments) {
       moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
       __syncthreads();
     }
     tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
-  } else if (job.type == kJobMoments)
+  } else if (MODE != 1 && job.type == kJobMoments)
     moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
   else
     trans_job_f32(R, job, par, sm_post);
-  trace_mark(p, 1);
-  finish_turn(p, job.run, R);
-  trace_mark(p, 2);
+  trace_mark(p, 1, jobi);
+  finish_turn(p, job.run, R, gridDim.x);
+  trace_mark(p, 2, jobi);
+}
+
+// The two kernels of a split post (Plan::post_split): MODE 1 the wake jobs
+// p.jobs[0, post_split), MODE 2 the other jobs p.jobs[job0 + blockIdx.x] (no
+// wake job: a small shared-memory footprint, two CTAs per SM).  Both count
+// into the same completion counter, so that the last CTA of either finishes
+// the turn after every job of both.
+template <int MODE>
+__global__ void __launch_bounds__(kPostThreads, MODE == 2 ? 2 : 1) k_post_split(const Plan p, int job0) {
+  extern __shared__ __align__(1024) uint8_t sm_post[];
+  __shared__ __align__(8) uint64_t bars[3];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_flag;
+  __shared__ double2 sE[kBunchTile];
+  __shared__ float2 sEf[kBunchTile];
+  __shared__ double s_sum[9][kBunchTile];
+  __shared__ PostStage st;
+  __shared__ RunDev sR;
+  __shared__ double2 s_scr[2 * kBunchTile + 2];
+  const int jobi = job0 + (int)blockIdx.x;
+  const PostJob job = p.jobs[jobi];
+  trace_mark(p, 0, jobi);
+  // The run descriptor, copied before the wait: the push streams the particle
+  // state through L2 and evicts it, and after the wait every read of it would
+  // be a miss behind the next push's first bulk copies.
+  static_assert(sizeof(RunDev) % 16 == 0 && sizeof(RunDev) / 16 <= kPostThreads, "run descriptor copy");
+  if (threadIdx.x < sizeof(RunDev) / 16)
+    reinterpret_cast<int4 *>(&sR)[threadIdx.x] = reinterpret_cast<const int4 *>(p.runs + job.run)[threadIdx.x];
+  __syncthreads();
+  const RunDev *R = &sR;
+  // tile jobs keep the emission table where wake jobs keep their operands
+  float2 *tabf = reinterpret_cast<float2 *>(sm_post);
+  if (MODE != 2 && job.type == kJobWake) wake_prologue(R, job, sm_post, bars, &tmem_slot, &s_flag);   // A image first
+  post_stage(p, R, job, &st, tabf);
+  if (MODE != 1 && job.type == kJobTile && threadIdx.x < 32)   // code warm-up, into shared scratch
+    tile_scan_warp(make_double2(0.0, 0.0), make_double2(0.0, 0.0), 0.0, make_double2(1.0, 0.0), kBunchTile, s_scr,
+                   s_scr + 2 * kBunchTile);
+  __syncthreads();
+  grid_dependency_wait();     // the push of this turn has completed
+  grid_dependents_launch();   // the next push may start its prologue (particle prefetch)
+  const long long turn = *R->turn;
+  const int par = (int)(turn & 1);
+  if (MODE != 2 && job.type == kJobWake && job.sub == kWakeBoth)
+    wake_job_both(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
+  else if (MODE != 2 && job.type == kJobWake)
+    wake_job_tc(p, R, job, par, sm_post, bars, &tmem_slot, &s_flag, st.qf);
+  else if (MODE != 1 && job.type == kJobTile) {
+    if (p.fold_moments) {
+      moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
+      __syncthreads();
+    }
+    tile_job<kMixed>(p, R, job, par, sE, sEf, tabf, &st);
+  } else if (MODE != 1 && job.type == kJobMoments)
+    moments_job(p, R, job.bt * kBunchTile, min(kBunchTile, R->nb - job.bt * kBunchTile), par, turn, s_sum, &st);
+  else if (MODE != 1 && job.type == kJobTrans)
+    trans_job_f32(R, job, par, sm_post);
+  trace_mark(p, 1, jobi);
+  finish_turn(p, job.run, R, (unsigned int)p.njobs);
+  trace_mark(p, 2, jobi);
 }
 
 // ---------------------------------------------------------------------------
@@ -850,7 +914,7 @@ __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
   __shared__ double s_sum[9][kBunchTile];
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
-  trace_mark(p, 0);
+  trace_mark(p, 0, (int)blockIdx.x);
   grid_dependency_wait();
   grid_dependents_launch();
   const long long turn = *R->turn;
@@ -865,9 +929,9 @@ __global__ void __launch_bounds__(kPostThreads) k_post_f64(const Plan p) {
     __syncthreads();
     tile_job<kF64>(p, R, job, par, sE, sEf, nullptr, nullptr);
   }
-  trace_mark(p, 1);
-  finish_turn(p, job.run, R);
-  trace_mark(p, 2);
+  trace_mark(p, 1, (int)blockIdx.x);
+  finish_turn(p, job.run, R, gridDim.x);
+  trace_mark(p, 2, (int)blockIdx.x);
 }
 
 size_t post_smem_bytes(int precision, int max_nbins) {
@@ -878,9 +942,25 @@ size_t post_smem_bytes(int precision, int max_nbins) {
   return (size_t)max_nbins * 2 * sizeof(double);   // lag table + counts, or (transverse) lag table + dipole sums
 }
 
+// dynamic shared memory of the post kernel without wake jobs (MODE 2): the
+// emission table of a tile job, and with a transverse plane the lag table and
+// dipole sums of a transverse job (small enough without one that a CTA of it
+// fits on an SM beside a wake-job CTA)
+static size_t post_small_smem_bytes(int max_nbins, bool trans) {
+  const size_t tile = (size_t)kMaxLong * max_nbins * sizeof(float2);
+  return trans ? std::max(tile, (size_t)(2 + kBunchTile) * max_nbins * sizeof(float)) : tile;
+}
+
 cudaError_t configure_kernels() {
-  return cudaFuncSetAttribute(k_post_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)post_smem_bytes(kMixed, 256));
+  cudaError_t e = cudaFuncSetAttribute(k_post_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)post_smem_bytes(kMixed, 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_post_split<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)post_smem_bytes(kMixed, 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_post_split<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)post_small_smem_bytes(256, true));
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -985,6 +1065,34 @@ cudaError_t wake_noalloc_launch(const RunDev &proto, const void *img, size_t img
 
 cudaError_t launch_post(const Plan &p, int precision, cudaStream_t s, bool pdl) {
   if (p.njobs == 0) return cudaSuccess;
+  if (precision == kMixed && p.post_split > 0) {
+    // the other jobs on the plan's side stream once the push is complete,
+    // the wake jobs here (after the push, programmatically); joined back
+    cudaError_t e = cudaEventRecord(p.ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p.side, p.ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t c2{};
+    c2.gridDim = dim3((unsigned)(p.njobs - p.post_split));
+    c2.blockDim = dim3((unsigned)kPostThreads);
+    c2.dynamicSmemBytes = post_small_smem_bytes(p.max_nbins, p.max_trans != 0);
+    c2.stream = p.side;
+    e = cudaLaunchKernelEx(&c2, k_post_split<2>, p, p.post_split);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t c1{};
+    c1.gridDim = dim3((unsigned)p.post_split);
+    c1.blockDim = dim3((unsigned)kPostThreads);
+    c1.dynamicSmemBytes = post_smem_bytes(kMixed, p.max_nbins);
+    c1.stream = s;
+    cudaLaunchAttribute a1[1];
+    a1[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a1[0].val.programmaticStreamSerializationAllowed = 1;
+    c1.attrs = a1;
+    c1.numAttrs = pdl ? 1 : 0;
+    e = cudaLaunchKernelEx(&c1, k_post_split<1>, p, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(p.ev_join, p.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p.ev_join, 0);
+    return e;
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)p.njobs);
   cfg.blockDim = dim3((unsigned)kPostThreads);

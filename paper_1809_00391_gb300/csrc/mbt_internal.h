@@ -183,6 +183,13 @@ struct Plan {
   int stream_ctas;            // 0 if the plan is not split for the streaming push
   int fold_moments;           // kMixed: no moments jobs; each tile job sums its bunches' moments first
   int push_small_ctas;        // per-tile push (no transverse plane) in 128-thread CTAs (plans of many waves)
+  // kMixed plans of many post waves: the first post_split jobs (the wake
+  // jobs) run in a kernel of their own on the launching stream, the others in
+  // a kernel with a small shared-memory footprint on `side` (forked at
+  // ev_fork after the push, joined at ev_join); 0: one post kernel
+  int post_split;
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 // Cluster-resident tracking of one run: one thread-block cluster per bunch,
