@@ -620,7 +620,7 @@ constexpr size_t push_tile_smem(int nbins, int threads = 256) {
          (size_t)(nbins + kSpillCells) * sizeof(int);
 }
 constexpr size_t push_t_smem(int nbins) {
-  return (size_t)kStages * kStageBytesT + (size_t)nbins * 2 * sizeof(float2) +
+  return (size_t)kStages * kStageBytesT + (size_t)nbins * (2 * sizeof(float2) + sizeof(float4)) +
          (size_t)(nbins + kSpillCells) * 3 * sizeof(int);
 }
 #ifndef MBT_PUSH_T_MIN_BLOCKS
@@ -707,7 +707,10 @@ __global__ void __launch_bounds__(kTThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed
   const int nlong = R->nlong;
   const bool tr = R->trans != 0;
   uint8_t *stages = sm_pt;
-  float2 *sVd = reinterpret_cast<float2 *>(sm_pt + kStages * kStageBytesT);
+  // per cell (V, dV) of the longitudinal kick, and for quad_push_t_full the
+  // same interleaved with the transverse kick: (V, dV, V_x, dV_x)
+  float4 *sV4 = reinterpret_cast<float4 *>(sm_pt + kStages * kStageBytesT);
+  float2 *sVd = reinterpret_cast<float2 *>(sV4 + nbins);
   int *sH = reinterpret_cast<int *>(sVd + nbins);                  // nbins + kSpillCells counts
   float2 *sVt = reinterpret_cast<float2 *>(sH + nbins + kSpillCells);
   unsigned *sLo = reinterpret_cast<unsigned *>(sVt + nbins);     // dipole sums in fixed point (deposit_dip),
@@ -746,6 +749,7 @@ __global__ void __launch_bounds__(kTThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed
       const float w0 = vtg[k];
       const float w1 = k + 1 < nbins ? vtg[k + 1] : w0;
       sVt[k] = make_float2(w0, w1 - w0);
+      sV4[k] = make_float4(v0, v1 - v0, w0, w1 - w0);
     }
   }
   if (threadIdx.x < nlong) {
@@ -832,8 +836,8 @@ __global__ void __launch_bounds__(kTThreads, MBT_PUSH_T_MIN_BLOCKS) k_push_mixed
           normal_quad_f32(philox4x32_10(quad, bunch32, turn32, 4u, k0, k1), rp);
         }
         if (straight && nvalid == 4)
-          quad_push_t_full<NLONG_MAX>(c, tc, sVd, sVt, sH, sLo, sHi, nlong, la, lw, lA, lml, lmt, omD_d, vrw, tt, dd,
-                                      xx, pp, rr, rx, rp, tref, dref, mom, nout, dip_ok);
+          quad_push_t_full<NLONG_MAX>(c, tc, sV4, sH, sLo, sHi, la, lw, lA, lml, lmt, omD_d, vrw, tt, dd, xx, pp,
+                                      rr, rx, rp, tref, dref, mom, nout, dip_ok);
         else
           quad_push_t<NLONG_MAX>(c, tc, sVd, sVt, sH, sLo, sHi, nlong, plane, la, lw, phi, omD_d, s_hc, nharm, ngp,
                                  vrw, tt, dd, xx, pp, rr, rx, rp, nvalid, tref, dref, mom, nout, dip_ok);

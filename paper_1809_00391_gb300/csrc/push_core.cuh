@@ -237,8 +237,8 @@ __device__ __forceinline__ void quad_push_t(const PushConstF &c, const TransCons
 // Deposits go to the cell or, outside the mesh, to the lane's spill cell
 // (sH, sLo and sHi hold nbins + kSpillCells cells).
 template <int NLONG_MAX>
-__device__ __forceinline__ void quad_push_t_full(const PushConstF &c, const TransConstF &tc, const float2 *sVd,
-                                                 const float2 *sVt, int *sH, unsigned *sLo, int *sHi, int nlong,
+__device__ __forceinline__ void quad_push_t_full(const PushConstF &c, const TransConstF &tc, const float4 *sV4,
+                                                 int *sH, unsigned *sLo, int *sHi,
                                                  const float *la, const float *lw, const float2 *A, const float *ml,
                                                  const float *mt, double omD_d, float vrw, float (&tt)[4],
                                                  double (&dd)[4], float (&xx)[4], float (&pp)[4],
@@ -253,18 +253,18 @@ __device__ __forceinline__ void quad_push_t_full(const PushConstF &c, const Tran
     const bool inside = x0 >= -0.5f && x0 < c.fnb - 0.5f;
     const float u = fminf(fmaxf(x0, 0.f), c.fnb - 1.f);
     const int j = (int)u;   // <= nbins - 1, where the slopes are 0
-    const float2 vd = sVd[j], vtd = sVt[j];
-    float v = inside ? fmaf(u - (float)j, vd.y, vd.x) : 0.f;
-    float vt = (inside ? fmaf(u - (float)j, vtd.y, vtd.x) : 0.f) + vrw;
+    const float4 w4 = sV4[j];   // (V, dV, V_x, dV_x) of cell j
+    float v = inside ? fmaf(u - (float)j, w4.y, w4.x) : 0.f;
+    float vt = (inside ? fmaf(u - (float)j, w4.w, w4.z) : 0.f) + vrw;
+    // every entry up to NLONG_MAX: the caller zeroes la, lw, A and the masks
+    // of the entries a run does not have, which then add exactly zero
 #pragma unroll
     for (int r2 = 0; r2 < NLONG_MAX; ++r2) {
-      if (r2 < nlong) {
-        float sn, cs;
-        __sincosf(lw[r2] * t0, &sn, &cs);
-        const float w = ex2_approx(-la[r2] * t0) * fmaf(A[r2].x, cs, A[r2].y * sn);
-        v = fmaf(ml[r2], w, v);
-        vt = fmaf(mt[r2], w, vt);
-      }
+      float sn, cs;
+      __sincosf(lw[r2] * t0, &sn, &cs);
+      const float w = ex2_approx(-la[r2] * t0) * fmaf(A[r2].x, cs, A[r2].y * sn);
+      v = fmaf(ml[r2], w, v);
+      vt = fmaf(mt[r2], w, vt);
     }
     float sw, cw;
     __sincosf(c.w * t0, &sw, &cw);
