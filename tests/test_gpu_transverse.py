@@ -103,6 +103,30 @@ def test_mixed_transverse_matches_oracle(pkg, oracle_mod):
     tr.close()
 
 
+def test_mixed_transverse_three_long_range_entries(pkg, oracle_mod):
+    """Two longitudinal long-range resonators and a transverse one: three of
+    the push's four long-range slots in use (the fourth runs with zero
+    coefficients), entries of both planes, against the oracle."""
+    hom2 = dict(Rs_ohm=5e5, fr_Hz=2.2e9, Q=1e4, range=W.RANGE_LONG)
+    run = _run(W.PREC_MIXED, [0, 1, 7], 20_000, 200, I=2e-3, tplane=_plane(resonators=[dict(TRES), dict(BBT)]),
+               res=(W.BROADBAND, W.HOM, hom2))
+    tr = pkg.tracker_for_run(run, record_turns=run.turns)
+    orc = _oracle(oracle_mod, run)
+    tr.init_particles()
+    orc.init_particles()
+    tr.track(run.turns)
+    rec_o, trec_o = orc.track2(run.turns)
+    rec_g = tr.moments(0, run.turns)
+    trec_g = tr.transverse_moments(0, run.turns)
+    st, sd = rec_o[:, :, 1], rec_o[:, :, 3]
+    for col, scale in ((0, st), (1, st), (2, sd), (3, sd)):
+        assert np.max(np.abs(rec_g[:, :, col] - rec_o[:, :, col]) / scale) <= 1e-3, col
+    sx, sp = trec_o[:, :, 1], trec_o[:, :, 3]
+    for col, scale in ((0, sx), (1, sx), (2, sp), (3, sp)):
+        assert np.max(np.abs(trec_g[:, :, col] - trec_o[:, :, col]) / scale) <= 1e-3, col
+    tr.close()
+
+
 @pytest.mark.parametrize("prec", [W.PREC_MIXED, W.PREC_F64], ids=["mixed", "f64"])
 def test_transverse_coupled_bunch_growth_rate(pkg, prec):
     ring = W.ring_r0()
