@@ -193,10 +193,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     if (tid < 5) {
       // the warps' FP32 sums by a pairwise tree of fixed shape (a serial FP64
       // chain over the warps would wait 64 cycles per add), FP64 from the CTA on
-      constexpr int kW = kResidentThreads / 32, kH = kW / 2;
+      // (over the warp count rounded up to a power of two, the missing warps zero)
+      constexpr int kW = kResidentThreads / 32;
+      constexpr int kH = (kW <= 2 ? 2 : kW <= 4 ? 4 : kW <= 8 ? 8 : kW <= 16 ? 16 : 32) / 2;
       float a[kH];
 #pragma unroll
-      for (int i = 0; i < kH; ++i) a[i] = s_red[i][tid] + s_red[kH + i][tid];
+      for (int i = 0; i < kH; ++i) a[i] = (i < kW ? s_red[i][tid] : 0.f) + (kH + i < kW ? s_red[kH + i][tid] : 0.f);
 #pragma unroll
       for (int h = kH / 2; h > 0; h >>= 1)
 #pragma unroll
@@ -251,7 +253,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const Resident
     }
     // rows [rank B, rank B + B) of V = q sum_{k<=j} lag[j-k] count[k]
     {
-      const int G = min(32, kResidentThreads / B);   // threads per row (a power of two, <= 32)
+      // threads per row: the largest power of two <= min(32, threads / B); B is
+      // a power of two (nbins 128 or 256, C a power of two), so B G is a
+      // multiple of 32 and every warp's lanes all take the shuffles or none
+      const int G = 1 << (31 - __clz(min(32, kResidentThreads / B)));
       const int row = tid / G, sub = tid % G;
       const int j = rank * B + row;
       if (row < B) {
