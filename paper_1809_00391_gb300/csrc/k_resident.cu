@@ -60,6 +60,8 @@ __host__ __device__ inline size_t resident_layout(int per, int nbins, ResidentSm
 
 size_t resident_smem_bytes(int per, int nbins) { return resident_layout(per, nbins, nullptr, nullptr); }
 
+static_assert(kResidentThreads % 32 == 0 && kResidentThreads >= 64 && kResidentThreads <= 1024, "whole warps, 2-32 of them");
+
 template <int NLONG_MAX, bool HARM>
 __global__ void __launch_bounds__(kResidentThreads, 1) k_resident(const ResidentArgs a) {
   extern __shared__ __align__(16) uint8_t sm_res[];

@@ -199,7 +199,6 @@ struct Plan {
 #define MBT_RESIDENT_THREADS 512
 #endif
 constexpr int kResidentThreads = MBT_RESIDENT_THREADS;
-static_assert(kResidentThreads % 32 == 0 && kResidentThreads >= 64 && kResidentThreads <= 1024, "whole warps, 2-32 of them");
 constexpr int kResidentMaxBunches = 32;   // one warp scans the fill
 constexpr unsigned long long kResidentWaitNs = 2000000000ull;   // grid-barrier wait limit (default)
 struct ResidentArgs {
