@@ -89,6 +89,8 @@ PUSH_SOURCES = ["paper_1809_00391_gb300/csrc/k_push.cu", "paper_1809_00391_gb300
                 "paper_1809_00391_gb300/csrc/device_common.cuh", "paper_1809_00391_gb300/csrc/mbt_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_stream_fill390_traffic.json")
 GRAPH_TURNS = 100      # turns per captured CUDA graph
+# batch lanes (mbt_batch_set_lanes) per scan workload: the measured best
+LANES = {"l5scan": 4, "rwscan": 3, "hcscan": 2}
 AUTOTUNE_TURNS = 20    # timed turns per push-tile candidate
 ROOFLINE_TURNS = 4000  # turns of the event-timed roofline region
 SATURATED_TURNS = 200  # turns of the event-timed region in the saturated instability
@@ -109,6 +111,9 @@ def parse():
                     help="requests of the bounded serving sample in the default line (0 = skip)")
     ap.add_argument("--saturated-turn", type=int, default=1500,
                     help="also time the push from this turn on (saturated instability); 0 = skip")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="l5scan, rwscan, hcscan: groups of runs tracked on streams of their own "
+                         "(mbt_batch_set_lanes); 0: the workload's default (LANES)")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
     ap.add_argument("--workload", choices=["fill390", "serving", "l5scan", "rwscan", "hcscan", "fill390t", "three_f64",
@@ -513,6 +518,8 @@ def l5scan_bench(args, rank, local):
         t.init_particles(stream)
     b = pkg.Batch(trackers)
     b.set_graph(GRAPH_TURNS)
+    lanes = args.lanes or LANES["l5scan"]
+    b.set_lanes(lanes)   # groups of runs on streams of their own: one group's push beside another's post
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -556,6 +563,7 @@ def l5scan_bench(args, rank, local):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"SLS-2 L5 scan: {len(det)} HOM detunings x (uniform 484 + 3/4 363 bunches), "
                                    f"{n_mp} mp per bunch, 400 mA, {turns} turns, one batch of {len(runs)} runs",
+                       "lanes": lanes,
                        "revolution_frequency_Hz": f0, "hom": {"fr_Hz": W.L5_FR_HZ, "Rs_ohm": W.L5_RS_OHM, "Q": W.L5_Q},
                        "radiation_damping_per_s": damp, "fit_turns": list(fit)},
             "growth_rates": table, "clocks": clocks}
@@ -617,6 +625,7 @@ def rwscan_bench(args, rank, local):
         t.init_particles(stream)
     b = pkg.Batch(trackers)
     b.set_graph(GRAPH_TURNS)
+    b.set_lanes(args.lanes or LANES["rwscan"])
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -679,6 +688,7 @@ def hcscan_bench(args, rank, local):
         t.init_particles(stream)
     b = pkg.Batch(trackers)
     b.set_graph(GRAPH_TURNS)
+    b.set_lanes(args.lanes or LANES["hcscan"])
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:

@@ -505,6 +505,21 @@ mbt_status mbt_batch_sync(mbt_batch *b);   /* wait; report device errors of the 
 /* Graph replay and push-tile autotuning for a batch, as for a context. */
 mbt_status mbt_batch_set_graph(mbt_batch *b, int turns_per_graph);
 mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_tile);
+/* Lanes: mbt_batch_track splits the members into nlanes groups of about equal
+ * particle counts (largest member first, each into the group with the fewest
+ * particles so far; members keep the batch order within a group), each group
+ * with launches of its own on a stream of the batch's own, forked from and
+ * joined back into the caller's stream (asynchronous on it).  One group's
+ * push then runs beside another's post kernel, whose turns are bound by
+ * latency rather than bandwidth (scans of many runs of small bunches).  The
+ * turn map is per run (runs share no state), so every member's results are
+ * the same bit for bit with any number of lanes, alone or in a batch.
+ * nlanes 1..8 (1: one plan for the whole batch, the default); more lanes
+ * than members give one member per lane.  Synchronises the device; takes
+ * the batch's push tile (mbt_batch_autotune rebuilds the lanes with the tile
+ * it chooses) and graph setting.  Errors of a lane's kernels surface at
+ * mbt_batch_sync.  MBT_ERR_ARG for nlanes outside 1..8. */
+mbt_status mbt_batch_set_lanes(mbt_batch *b, int nlanes);
 /* Track every member resident (as mbt_track_resident) at the same time: each
  * member's kernel on a stream of the batch's own, forked from and joined back
  * into `stream` (asynchronous on it).  Errors of the kernels surface at

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -188,6 +189,24 @@ struct mbt_ctx {
   std::string err;
 };
 
+// One lane of a batch: a group of its members with a plan of their own,
+// tracked on a stream of its own beside the other lanes.
+constexpr int kMaxLanes = 8;
+struct BatchLane {
+  std::vector<int> members;   // indices into mbt_batch::ctx, increasing
+  PlanStore store;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  ~BatchLane() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (stream) cudaStreamDestroy(stream);
+    if (done) cudaEventDestroy(done);
+  }
+};
+
 struct mbt_batch {
   std::vector<mbt_ctx *> ctx;
   PlanStore store;
@@ -199,6 +218,10 @@ struct mbt_batch {
   // concurrent resident tracking: one stream per member, fork / join events
   std::vector<cudaStream_t> res_streams;
   std::vector<cudaEvent_t> res_events;   // [0] fork, [1 + i] member i done
+  // lanes (mbt_batch_set_lanes): empty = the whole batch in one plan
+  std::vector<std::unique_ptr<BatchLane>> lanes;
+  int nlanes = 1;
+  cudaEvent_t lane_fork = nullptr;
 };
 
 namespace {
@@ -2180,8 +2203,101 @@ mbt_status mbt_batch_create(mbt_ctx *const *ctxs, int n, mbt_batch **out) {
 
 mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream) {
   if (!b || nturns < 0) return MBT_ERR_ARG;
-  return track_plan(b->ctx[0], b->store.plan, b->precision, nturns, static_cast<cudaStream_t>(stream), b->graph_turns,
-                    &b->graph_exec, &b->capture_stream);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->lanes.empty())
+    return track_plan(b->ctx[0], b->store.plan, b->precision, nturns, s, b->graph_turns, &b->graph_exec,
+                      &b->capture_stream);
+  // every lane forked from `stream`, tracked on its own stream, joined back
+  mbt_ctx *c0 = b->ctx[0];
+  cudaError_t e = cudaEventRecord(b->lane_fork, s);
+  if (e != cudaSuccess) return cuda_fail(c0, e, "lane fork");
+  for (auto &L : b->lanes) {
+    e = cudaStreamWaitEvent(L->stream, b->lane_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "lane fork");
+  }
+  // the lanes' launches interleaved a graph (or a chunk of turns) at a time,
+  // so that no lane's queue fills up before the next lane has work queued
+  mbt_status first = MBT_OK;
+  const int64_t chunk = b->graph_turns > 0 ? b->graph_turns : 64;
+  for (int64_t done = 0; done < nturns && first == MBT_OK; done += chunk) {
+    const int64_t n = std::min(chunk, nturns - done);
+    for (auto &L : b->lanes) {
+      const mbt_status st = track_plan(b->ctx[(size_t)L->members[0]], L->store.plan, b->precision, n, L->stream,
+                                       b->graph_turns, &L->graph_exec, &L->capture_stream);
+      if (st != MBT_OK) {
+        first = st;
+        if (L->members[0] != 0) fail(c0, st, "%s", b->ctx[(size_t)L->members[0]]->err.c_str());
+        break;
+      }
+    }
+  }
+  for (auto &L : b->lanes) {
+    // joined even after a failed launch, so that `stream` orders after what did start
+    e = cudaEventRecord(L->done, L->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, L->done, 0);
+    if (e != cudaSuccess && first == MBT_OK) first = cuda_fail(c0, e, "lane join");
+  }
+  return first;
+}
+
+// Members into k lanes of about equal particle counts: largest first, each
+// to the lane with the fewest particles so far (ties: the lower lane);
+// members keep their batch order within a lane.
+static std::vector<std::vector<int>> lane_partition(const std::vector<mbt_ctx *> &ctx, int k) {
+  std::vector<int> order(ctx.size());
+  for (size_t i = 0; i < ctx.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return ctx[(size_t)a]->n_particles > ctx[(size_t)b]->n_particles; });
+  std::vector<int64_t> load((size_t)k, 0);
+  std::vector<std::vector<int>> lanes((size_t)k);
+  for (int i : order) {
+    const size_t j = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+    lanes[j].push_back(i);
+    load[j] += ctx[(size_t)i]->n_particles;
+  }
+  for (auto &l : lanes) std::sort(l.begin(), l.end());
+  return lanes;
+}
+
+// (Re)build the lanes' plans with the batch's push tile.
+static mbt_status build_lanes(mbt_batch *b) {
+  mbt_ctx *c0 = b->ctx[0];
+  b->lanes.clear();
+  if (b->nlanes <= 1) return MBT_OK;
+  if (!b->lane_fork && cudaEventCreateWithFlags(&b->lane_fork, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c0, MBT_ERR_CUDA, "lane event");
+  for (const std::vector<int> &members : lane_partition(b->ctx, b->nlanes)) {
+    std::unique_ptr<BatchLane> L(new (std::nothrow) BatchLane());
+    if (!L) return fail(c0, MBT_ERR_NOMEM, "lane");
+    L->members = members;
+    L->store.precision = b->precision;
+    for (int i : members) append_run(L->store, b->ctx[(size_t)i], b->tile);
+    mbt_status st = upload_plan(b->ctx[(size_t)members[0]], L->store);
+    if (st != MBT_OK) {
+      if (members[0] != 0) fail(c0, st, "%s", b->ctx[(size_t)members[0]]->err.c_str());
+      b->lanes.clear();
+      return st;
+    }
+    if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      b->lanes.clear();
+      return fail(c0, MBT_ERR_CUDA, "lane stream");
+    }
+    b->lanes.push_back(std::move(L));
+  }
+  return MBT_OK;
+}
+
+mbt_status mbt_batch_set_lanes(mbt_batch *b, int nlanes) {
+  if (!b) return MBT_ERR_ARG;
+  mbt_ctx *c0 = b->ctx[0];
+  c0->err.clear();
+  if (nlanes < 1 || nlanes > kMaxLanes) return fail(c0, MBT_ERR_ARG, "lanes must be 1..%d", kMaxLanes);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c0, e, "sync");
+  b->nlanes = std::min(nlanes, (int)b->ctx.size());
+  return build_lanes(b);
 }
 
 mbt_status mbt_batch_set_graph(mbt_batch *b, int turns) {
@@ -2190,6 +2306,11 @@ mbt_status mbt_batch_set_graph(mbt_batch *b, int turns) {
     cudaGraphExecDestroy(b->graph_exec);
     b->graph_exec = nullptr;
   }
+  for (auto &L : b->lanes)
+    if (L->graph_exec) {
+      cudaGraphExecDestroy(L->graph_exec);
+      L->graph_exec = nullptr;
+    }
   b->graph_turns = turns;
   return MBT_OK;
 }
@@ -2206,7 +2327,8 @@ static mbt_status rebuild_batch_plan(mbt_batch *b) {
     cudaGraphExecDestroy(b->graph_exec);
     b->graph_exec = nullptr;
   }
-  return upload_plan(b->ctx[0], b->store);
+  mbt_status st = upload_plan(b->ctx[0], b->store);
+  return st == MBT_OK ? build_lanes(b) : st;
 }
 
 mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_tile) {
@@ -2252,6 +2374,7 @@ mbt_status mbt_batch_sync(mbt_batch *b) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(b->ctx[0], e, "sync");
   mbt_status st = check_device(b->ctx[0], b->store.plan);
+  for (size_t i = 0; i < b->lanes.size() && st == MBT_OK; ++i) st = check_device(b->ctx[0], b->lanes[i]->store.plan);
   // the members' own error words (their resident kernels, mbt_batch_track_resident)
   for (size_t i = 0; i < b->ctx.size() && st == MBT_OK; ++i) {
     st = check_device(b->ctx[i], b->ctx[i]->own.plan);
@@ -2267,6 +2390,8 @@ void mbt_batch_destroy(mbt_batch *b) {
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   for (cudaStream_t st : b->res_streams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : b->res_events) cudaEventDestroy(ev);
+  b->lanes.clear();
+  if (b->lane_fork) cudaEventDestroy(b->lane_fork);
   delete b;
 }
 

@@ -188,9 +188,11 @@ def eq7_growth_rates(ring: dict, M: int, I_bunch_A: float, Rs_ohm: float, fr_Hz:
     return ring["alpha_c"] * M * I_bunch_A * wr / (2 * ring["E0_eV"] * T0 * ws) * (up - lo)
 
 
-def track_scan(runs: List, graph_turns: int = 100, stream=None) -> List[np.ndarray]:
+def track_scan(runs: List, graph_turns: int = 100, stream=None, lanes: int = 1) -> List[np.ndarray]:
     """Track every run (same turn count) in one batch from its matched start;
-    returns each run's moments [turns][nb][6]."""
+    returns each run's moments [turns][nb][6].  lanes > 1: the runs in that
+    many groups on streams of their own (mbt_batch_set_lanes; the same
+    results bit for bit)."""
     turns = runs[0].turns
     if any(r.turns != turns for r in runs):
         raise ValueError("a scan tracks every run for the same number of turns")
@@ -202,6 +204,8 @@ def track_scan(runs: List, graph_turns: int = 100, stream=None) -> List[np.ndarr
         try:
             if graph_turns:
                 b.set_graph(min(graph_turns, turns))
+            if lanes > 1:
+                b.set_lanes(lanes)
             b.track(turns, stream)
             b.sync()
         finally:

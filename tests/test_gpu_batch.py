@@ -122,3 +122,48 @@ def test_streaming_batch_of_two_meshes(pkg):
     bt.close()
     for t in trs:
         t.close()
+
+
+def test_batch_lanes_equal_one_plan(pkg):
+    """mbt_batch_set_lanes: the members tracked as 3 groups on streams of
+    their own (graph replay, uneven runs: two rings, sizes 5 to 400 bunches)
+    give every member's moments, histograms and particles bit for bit as the
+    batch in one plan; 8 lanes for 5 members give one member per lane."""
+    det = np.linspace(-300e3, 300e3, 3)
+    runs = W.l5_scan_runs(det, "uniform", n_mp=2000, turns=40) + \
+        W.l5_scan_runs(det[:1], "three_quarter", n_mp=3000, turns=40, seed=5) + \
+        [W.fill_390().scaled(n_mp_per_bunch=4000, nb=5, turns=40)]
+    turns = 40
+
+    def track(nlanes):
+        trs = [pkg.tracker_for_run(r, record_turns=turns) for r in runs]
+        for t in trs:
+            t.init_particles()
+        b = pkg.Batch(trs)
+        b.set_graph(10)
+        if nlanes > 1:
+            b.set_lanes(nlanes)
+        b.track(turns - 5)
+        b.track(5)
+        b.sync()
+        out = [(t.moments(0, turns), t.histograms()[0], t.particles(t.nb - 1)) for t in trs]
+        b.close()
+        for t in trs:
+            t.close()
+        return out
+
+    ref = track(1)
+    for nl in (3, 8):
+        got = track(nl)
+        for i, ((ma, ha, (ta, da)), (mb, hb, (tb, db))) in enumerate(zip(got, ref)):
+            assert np.array_equal(ma, mb), (nl, i)
+            assert np.array_equal(ha, hb), (nl, i)
+            assert np.array_equal(ta, tb) and np.array_equal(da, db), (nl, i)
+    trs = [pkg.tracker_for_run(runs[0], record_turns=4)]
+    b = pkg.Batch(trs)
+    with pytest.raises(pkg.MBTError):
+        b.set_lanes(9)
+    with pytest.raises(pkg.MBTError):
+        b.set_lanes(0)
+    b.close()
+    trs[0].close()

@@ -37,7 +37,7 @@ def scan_results(pkg):
     from paper_1809_00391_gb300 import scan as S
     uni = W.l5_scan_runs(UNSTABLE + [STABLE], fill="uniform", n_mp=20000, turns=TURNS)
     tq = W.l5_scan_runs([UNSTABLE[1], STABLE], fill="three_quarter", n_mp=20000, turns=TURNS, seed=31)
-    recs = S.track_scan(uni + tq)
+    recs = S.track_scan(uni + tq, lanes=4)
     return S, recs[:4], recs[4:]
 
 
