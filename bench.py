@@ -90,7 +90,7 @@ PUSH_SOURCES = ["paper_1809_00391_gb300/csrc/k_push.cu", "paper_1809_00391_gb300
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "push_stream_fill390_traffic.json")
 GRAPH_TURNS = 100      # turns per captured CUDA graph
 # batch lanes (mbt_batch_set_lanes) per scan workload: the measured best
-LANES = {"l5scan": 4, "rwscan": 3, "hcscan": 2}
+LANES = {"l5scan": 4, "rwscan": 3, "hcscan": 2, "serving": 2}
 AUTOTUNE_TURNS = 20    # timed turns per push-tile candidate
 ROOFLINE_TURNS = 4000  # turns of the event-timed roofline region
 SATURATED_TURNS = 200  # turns of the event-timed region in the saturated instability
@@ -112,7 +112,7 @@ def parse():
     ap.add_argument("--saturated-turn", type=int, default=1500,
                     help="also time the push from this turn on (saturated instability); 0 = skip")
     ap.add_argument("--lanes", type=int, default=0,
-                    help="l5scan, rwscan, hcscan: groups of runs tracked on streams of their own "
+                    help="l5scan, rwscan, hcscan, serving: groups of runs tracked on streams of their own "
                          "(mbt_batch_set_lanes); 0: the workload's default (LANES)")
     ap.add_argument("--tile", type=int, default=0,
                     help="particles per push CTA; 0 = autotune (timed trial turns during warm-up)")
@@ -427,7 +427,7 @@ def reference_arm(args, rank, world):
 
 
 def serving_sample(n_requests: int, rate_hz: float, max_active: int = 16, turns_per_step: int = 200,
-                   budget: int = 64 << 30, seed: int = 7):
+                   budget: int = 64 << 30, seed: int = 7, lanes: int = 1):
     """Open-loop replay of a Poisson request stream into the continuous-
     batching server: each request is submitted at its arrival time (a host
     thread sleeps until then); latency = result time - submission time on the
@@ -437,7 +437,7 @@ def serving_sample(n_requests: int, rate_hz: float, max_active: int = 16, turns_
     import paper_1809_00391_gb300 as pkg
     stream = W.serving_stream(n_requests, rate_hz=rate_hz, seed=seed)
     work = np.array([rq.run.turns * rq.run.n_particles for rq in stream], np.float64)
-    srv = pkg.Server(hbm_budget_bytes=budget, max_active=max_active, turns_per_step=turns_per_step)
+    srv = pkg.Server(hbm_budget_bytes=budget, max_active=max_active, turns_per_step=turns_per_step, lanes=lanes)
     ids = [None] * len(stream)
     t_wall0 = time.perf_counter()
 
@@ -475,7 +475,8 @@ def serving_bench(args, rank, local):
     budget = 64 << 30
     with ClockSampler(local) as clk:
         lat, queue, work, stats, span = serving_sample(args.requests, args.rate, args.max_active,
-                                                       args.turns_per_step, budget)
+                                                       args.turns_per_step, budget,
+                                                       lanes=args.lanes or LANES["serving"])
     clocks = clk.summary()
     thr = work.sum() / span
     line = {"metric": "serving latency p99 (instability-scan requests, open-loop Poisson stream)",
@@ -490,6 +491,7 @@ def serving_bench(args, rank, local):
                        "mean_mp_turns_per_request": float(work.mean()), "offered_mp_turns_per_s":
                        float(work.mean() * args.rate), "max_active": args.max_active,
                        "turns_per_step": args.turns_per_step, "hbm_budget_bytes": budget,
+                       "lanes": args.lanes or LANES["serving"],
                        "max_active_seen": stats["max_active_seen"], "max_bytes_seen": stats["max_bytes_seen"]},
             "clocks": clocks}
     print(json.dumps(line), flush=True)
@@ -1145,7 +1147,7 @@ def main():
         mean_work = float(np.mean([rq.run.turns * rq.run.n_particles
                                    for rq in W.serving_stream(200, rate_hz=1.0, seed=7)]))
         rate = 0.9 * value / mean_work
-        lat, queue, work, stats, span = serving_sample(args.serving_requests, rate)
+        lat, queue, work, stats, span = serving_sample(args.serving_requests, rate, lanes=LANES["serving"])
         serving = {"requests": args.serving_requests, "rate_hz": rate,
                    "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                    "queue_p99_s": float(np.percentile(queue, 99)), "delivered": float(work.sum() / span),

@@ -556,6 +556,8 @@ typedef struct {
     size_t hbm_budget_bytes;  /* device memory admitted requests may hold (estimate), > 0 */
     int max_active;           /* requests tracked together, >= 1                          */
     int turns_per_step;       /* turns between admission points, >= 1                     */
+    int lanes;                /* active requests in that many groups on streams of their
+                                 own (mbt_batch_set_lanes); 0 or 1: one plan, up to 8      */
 } mbt_server_config;
 
 /* One request: a run as for mbt_create / mbt_add_resonator / mbt_set_grid /

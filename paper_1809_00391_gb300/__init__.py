@@ -67,7 +67,8 @@ class Info(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("turns_per_step", ctypes.c_int)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("turns_per_step", ctypes.c_int),
+                ("lanes", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -509,10 +510,10 @@ class Server:
 
     STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, turns_per_step: int = 100):
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, turns_per_step: int = 100, lanes: int = 1):
         self._L = lib()
         self._h = ctypes.c_void_p()
-        cfg = ServerConfig(int(hbm_budget_bytes), int(max_active), int(turns_per_step))
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_active), int(turns_per_step), int(lanes))
         st = self._L.mbt_server_create(ctypes.byref(cfg), ctypes.byref(self._h))
         if st != 0:
             raise MBTError(st, "mbt_server_create failed")

@@ -166,7 +166,12 @@ void serve_loop(mbt_server *S) {
       drop_batch();
       std::vector<mbt_ctx *> members;
       for (auto &q : S->active) members.push_back(q->ctx);
-      if (mbt_batch_create(members.data(), (int)members.size(), &batch) != MBT_OK) {
+      mbt_status bst = mbt_batch_create(members.data(), (int)members.size(), &batch);
+      if (bst == MBT_OK && S->cfg.lanes > 1 && members.size() > 1) {
+        bst = mbt_batch_set_lanes(batch, std::min<int>(S->cfg.lanes, (int)members.size()));
+        if (bst != MBT_OK) mbt_batch_destroy(batch);
+      }
+      if (bst != MBT_OK) {
         batch = nullptr;
         std::lock_guard<std::mutex> lk(S->mu);
         for (auto &q : S->active) {
@@ -258,7 +263,9 @@ void serve_loop(mbt_server *S) {
 extern "C" {
 
 mbt_status mbt_server_create(const mbt_server_config *cfg, mbt_server **out) {
-  if (!cfg || !out || cfg->max_active < 1 || cfg->turns_per_step < 1 || cfg->hbm_budget_bytes == 0) return MBT_ERR_ARG;
+  if (!cfg || !out || cfg->max_active < 1 || cfg->turns_per_step < 1 || cfg->hbm_budget_bytes == 0 ||
+      cfg->lanes < 0 || cfg->lanes > 8)
+    return MBT_ERR_ARG;
   mbt_server *S = new (std::nothrow) mbt_server();
   if (!S) return MBT_ERR_NOMEM;
   S->cfg = *cfg;

@@ -53,9 +53,10 @@ def _check_against_alone(pkg, srv, ids, runs):
         assert np.array_equal(hist, hist_a), f"request {rid}: centroid history differs"
 
 
-def test_results_are_the_same_alone_and_in_the_mix(pkg):
+@pytest.mark.parametrize("lanes", [1, 2], ids=["one_plan", "two_lanes"])
+def test_results_are_the_same_alone_and_in_the_mix(pkg, lanes):
     runs = _requests()
-    srv = pkg.Server(hbm_budget_bytes=8 << 30, max_active=3, turns_per_step=25)
+    srv = pkg.Server(hbm_budget_bytes=8 << 30, max_active=3, turns_per_step=25, lanes=lanes)
     ids = []
     for i, r in enumerate(runs):
         ids.append(srv.submit(r))
