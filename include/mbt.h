@@ -520,6 +520,14 @@ mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_til
  * it chooses) and graph setting.  Errors of a lane's kernels surface at
  * mbt_batch_sync.  MBT_ERR_ARG for nlanes outside 1..8. */
 mbt_status mbt_batch_set_lanes(mbt_batch *b, int nlanes);
+/* Chooses the lane count: each count 1..max_lanes (at most the member count)
+ * tracked for turns_per_trial warm-up turns and turns_per_trial timed turns
+ * (CUDA events; graph replay where the batch's graph setting covers
+ * turns_per_trial), the fastest set and returned in *chosen (optional).
+ * The trials are real turns of every member: they advance the runs by
+ * 2 x turns_per_trial x (counts tried) turns.  Synchronous.  MBT_ERR_ARG for
+ * turns_per_trial < 1 or max_lanes outside 1..8. */
+mbt_status mbt_batch_autotune_lanes(mbt_batch *b, int turns_per_trial, int max_lanes, int *chosen);
 /* Track every member resident (as mbt_track_resident) at the same time: each
  * member's kernel on a stream of the batch's own, forked from and joined back
  * into `stream` (asynchronous on it).  Errors of the kernels surface at

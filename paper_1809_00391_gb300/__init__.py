@@ -37,7 +37,7 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_read_histograms", "mbt_read_wake", "mbt_get_info", "mbt_set_graph", "mbt_set_tile", "mbt_autotune",
            "mbt_set_timing",
            "mbt_get_timing", "mbt_set_trace", "mbt_read_trace", "mbt_state_size", "mbt_save_state", "mbt_load_state", "mbt_wake_noalloc", "mbt_batch_create",
-           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_set_lanes", "mbt_batch_autotune",
+           "mbt_batch_track", "mbt_batch_sync", "mbt_batch_set_graph", "mbt_batch_set_lanes", "mbt_batch_autotune_lanes", "mbt_batch_autotune",
            "mbt_batch_track_resident",
            "mbt_batch_destroy",
            "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
@@ -141,7 +141,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_read_wake": ([_vp, _P(_d), _P(_d)], _i), "mbt_get_info": ([_vp, _P(Info)], _i),
                 "mbt_set_graph": ([_vp, _i], _i), "mbt_set_timing": ([_vp, _i], _i),
                 "mbt_set_tile": ([_vp, _i], _i), "mbt_autotune": ([_vp, _i, _P(_i)], _i),
-                "mbt_batch_set_graph": ([_vp, _i], _i), "mbt_batch_set_lanes": ([_vp, _i], _i),
+                "mbt_batch_set_graph": ([_vp, _i], _i), "mbt_batch_set_lanes": ([_vp, _i], _i), "mbt_batch_autotune_lanes": ([_vp, _i, _i, _P(_i)], _i),
                 "mbt_batch_autotune": ([_vp, _i, _P(_i)], _i),
                 "mbt_get_timing": ([_vp, _P(_d), _P(_d), _P(_i64)], _i),
                 "mbt_set_trace": ([_vp, _i], _i), "mbt_read_trace": ([_vp, _P(_i64), _i, _P(_i)], _i),
@@ -480,6 +480,14 @@ class Batch:
         st = self._L.mbt_batch_set_lanes(self._h, int(nlanes))
         if st != 0:
             raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+
+    def autotune_lanes(self, turns_per_trial: int = 20, max_lanes: int = 4) -> int:
+        """Choose the lane count by timing 1..max_lanes (mbt_batch_autotune_lanes; real turns)."""
+        k = _i()
+        st = self._L.mbt_batch_autotune_lanes(self._h, int(turns_per_trial), int(max_lanes), ctypes.byref(k))
+        if st != 0:
+            raise MBTError(st, self._L.mbt_last_error(self.trackers[0].handle).decode())
+        return k.value
 
     def autotune(self, turns_per_trial: int = 5) -> int:
         t = _i()

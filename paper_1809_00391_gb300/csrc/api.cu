@@ -2369,6 +2369,50 @@ mbt_status mbt_batch_autotune(mbt_batch *b, int turns_per_trial, int *chosen_til
   return rebuild_batch_plan(b);
 }
 
+// Lane-count autotuning: each count from 1 to max_lanes tracked for a
+// warm-up and a timed trial of turns_per_trial turns (real turns; graph
+// replay where the batch's graph setting covers the trial), the fastest kept.
+mbt_status mbt_batch_autotune_lanes(mbt_batch *b, int turns_per_trial, int max_lanes, int *chosen) {
+  if (!b || turns_per_trial < 1 || max_lanes < 1 || max_lanes > kMaxLanes) return MBT_ERR_ARG;
+  mbt_ctx *c0 = b->ctx[0];
+  c0->err.clear();
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    return fail(c0, MBT_ERR_CUDA, "autotune stream");
+  }
+  const int top = std::min(max_lanes, (int)b->ctx.size());
+  float best = 1e30f;
+  int best_k = 1;
+  mbt_status st = MBT_OK;
+  for (int k = 1; k <= top && st == MBT_OK; ++k) {
+    st = mbt_batch_set_lanes(b, k);
+    if (st == MBT_OK) st = mbt_batch_track(b, turns_per_trial, s);   // warm-up (captures the lanes' graphs)
+    if (st != MBT_OK) break;
+    cudaEventRecord(e0, s);
+    st = mbt_batch_track(b, turns_per_trial, s);
+    cudaEventRecord(e1, s);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (st == MBT_OK && e != cudaSuccess) st = cuda_fail(c0, e, "autotune timing");
+    float ms = 0.f;
+    if (st == MBT_OK) cudaEventElapsedTime(&ms, e0, e1);
+    if (st == MBT_OK && ms < best) {
+      best = ms;
+      best_k = k;
+    }
+  }
+  if (st == MBT_OK) st = mbt_batch_set_lanes(b, best_k);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (st == MBT_OK && chosen) *chosen = best_k;
+  return st;
+}
+
 mbt_status mbt_batch_sync(mbt_batch *b) {
   if (!b) return MBT_ERR_ARG;
   cudaError_t e = cudaDeviceSynchronize();

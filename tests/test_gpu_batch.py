@@ -167,3 +167,38 @@ def test_batch_lanes_equal_one_plan(pkg):
         b.set_lanes(0)
     b.close()
     trs[0].close()
+
+
+def test_autotune_lanes_keeps_the_physics(pkg):
+    """mbt_batch_autotune_lanes tracks real turns with 1..3 lanes and keeps the
+    fastest: the runs continue bit for bit as one plan tracked as many turns."""
+    det = np.linspace(-300e3, 300e3, 4)
+    runs = W.l5_scan_runs(det, "uniform", n_mp=1000, turns=60)
+    trial, top, more = 6, 3, 10
+    total = 2 * trial * top + more
+    a = [pkg.tracker_for_run(r, record_turns=total) for r in runs]
+    for t in a:
+        t.init_particles()
+    ba = pkg.Batch(a)
+    ba.set_graph(trial)
+    k = ba.autotune_lanes(trial, top)
+    assert 1 <= k <= top
+    assert a[0].info["turn"] == 2 * trial * top
+    ba.track(more)
+    ba.sync()
+    b = [pkg.tracker_for_run(r, record_turns=total) for r in runs]
+    for t in b:
+        t.init_particles()
+    bb = pkg.Batch(b)
+    bb.track(total)
+    bb.sync()
+    for ta, tb in zip(a, b):
+        assert np.array_equal(ta.moments(0, total), tb.moments(0, total))
+        pa, pb = ta.particles(ta.nb - 1), tb.particles(tb.nb - 1)
+        assert np.array_equal(pa[0], pb[0]) and np.array_equal(pa[1], pb[1])
+    with pytest.raises(pkg.MBTError):
+        ba.autotune_lanes(trial, 9)
+    ba.close()
+    bb.close()
+    for t in a + b:
+        t.close()
