@@ -385,6 +385,13 @@ mbt_status mbt_plan_streams(int nruns, const int64_t *run_n, const int32_t *run_
                             int *streams);
 mbt_status mbt_plan_stream_split(int nb, const int32_t *run, const int64_t *n_mp, int ctas, int64_t *out,
                                  int64_t cap, int64_t *ntiles);
+/* mbt_plan_lanes: the groups mbt_batch_set_lanes forms from nmembers members
+ * of n_particles[i] >= 0 macro-particles: lane[i] in 0 .. min(nlanes,
+ * nmembers) - 1 (caller-owned, nmembers entries).  Members are taken largest
+ * first (ties in member order), each into the lane with the fewest particles
+ * so far (ties: the lower lane).  MBT_ERR_ARG for nmembers < 1, nlanes
+ * outside 1..8, a negative count or a NULL pointer, nothing written. */
+mbt_status mbt_plan_lanes(int nmembers, const int64_t *n_particles, int nlanes, int32_t *lane);
 
 /* Autotuner (plans on the per-tile push): times turns_per_trial turns for
  * each candidate push tile (2048 .. 32768 particles, plus tiles that make the

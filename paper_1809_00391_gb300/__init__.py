@@ -41,7 +41,7 @@ EXPORTS = ["mbt_version", "mbt_status_string", "mbt_create", "mbt_destroy", "mbt
            "mbt_batch_track_resident",
            "mbt_batch_destroy",
            "mbt_server_create", "mbt_server_submit", "mbt_server_poll", "mbt_server_wait", "mbt_server_get_stats",
-           "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split", "mbt_phasor_steps",
+           "mbt_server_destroy", "mbt_plan_streams", "mbt_plan_stream_split", "mbt_plan_lanes", "mbt_phasor_steps",
            "mbt_phasor_segment", "mbt_phasor_compose", "mbt_phasor_apply", "mbt_probe_fp64_fma"]
 
 
@@ -159,6 +159,7 @@ def lib() -> ctypes.CDLL:
                 "mbt_server_destroy": ([_vp], None),
                 "mbt_plan_streams": ([_i, _P(_i64), _P(_i32), _i, _i, _P(_i)], _i),
                 "mbt_plan_stream_split": ([_i, _P(_i32), _P(_i64), _i, _P(_i64), _i64, _P(_i64)], _i),
+                "mbt_plan_lanes": ([_i, _P(_i64), _i, _P(_i32)], _i),
                 "mbt_phasor_steps": ([_P(Ring), _d, _d, _i, _P(_i32), _P(_d)], _i),
                 "mbt_phasor_segment": ([_i, _P(_d), _P(_d), _P(_d)], _i),
                 "mbt_phasor_compose": ([_i, _P(_d), _P(_d), _P(_d), _P(_d)], _i),
@@ -202,6 +203,16 @@ def stream_split(run, n_mp, ctas: int) -> np.ndarray:
                                      ctypes.byref(cnt))
         if st != 0:
             raise MBTError(st, "mbt_plan_stream_split")
+    return out
+
+
+def plan_lanes(n_particles, nlanes: int) -> np.ndarray:
+    """The lane of each batch member that mbt_batch_set_lanes forms (host only)."""
+    n = np.ascontiguousarray(n_particles, np.int64)
+    out = np.zeros(len(n), np.int32)
+    st = lib().mbt_plan_lanes(len(n), _ptr(n, _i64), int(nlanes), _ptr(out, _i32))
+    if st != 0:
+        raise MBTError(st, "mbt_plan_lanes")
     return out
 
 

@@ -2243,17 +2243,16 @@ mbt_status mbt_batch_track(mbt_batch *b, int64_t nturns, void *stream) {
 // Members into k lanes of about equal particle counts: largest first, each
 // to the lane with the fewest particles so far (ties: the lower lane);
 // members keep their batch order within a lane.
-static std::vector<std::vector<int>> lane_partition(const std::vector<mbt_ctx *> &ctx, int k) {
-  std::vector<int> order(ctx.size());
-  for (size_t i = 0; i < ctx.size(); ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return ctx[(size_t)a]->n_particles > ctx[(size_t)b]->n_particles; });
+static std::vector<std::vector<int>> lane_partition(const std::vector<int64_t> &n, int k) {
+  std::vector<int> order(n.size());
+  for (size_t i = 0; i < n.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[(size_t)a] > n[(size_t)b]; });
   std::vector<int64_t> load((size_t)k, 0);
   std::vector<std::vector<int>> lanes((size_t)k);
   for (int i : order) {
     const size_t j = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
     lanes[j].push_back(i);
-    load[j] += ctx[(size_t)i]->n_particles;
+    load[j] += n[(size_t)i];
   }
   for (auto &l : lanes) std::sort(l.begin(), l.end());
   return lanes;
@@ -2266,7 +2265,9 @@ static mbt_status build_lanes(mbt_batch *b) {
   if (b->nlanes <= 1) return MBT_OK;
   if (!b->lane_fork && cudaEventCreateWithFlags(&b->lane_fork, cudaEventDisableTiming) != cudaSuccess)
     return fail(c0, MBT_ERR_CUDA, "lane event");
-  for (const std::vector<int> &members : lane_partition(b->ctx, b->nlanes)) {
+  std::vector<int64_t> n;
+  for (const mbt_ctx *c : b->ctx) n.push_back(c->n_particles);
+  for (const std::vector<int> &members : lane_partition(n, b->nlanes)) {
     std::unique_ptr<BatchLane> L(new (std::nothrow) BatchLane());
     if (!L) return fail(c0, MBT_ERR_NOMEM, "lane");
     L->members = members;
@@ -2539,6 +2540,19 @@ mbt_status mbt_plan_streams(int nruns, const int64_t *run_n, const int32_t *run_
   for (int i = 0; i < nruns; ++i)
     if (n[(size_t)i] < 1 || nb[(size_t)i] < 1) return MBT_ERR_ARG;
   *streams = plan_streams(n, nb, any_transverse != 0, ctas) ? 1 : 0;
+  return MBT_OK;
+}
+
+mbt_status mbt_plan_lanes(int nmembers, const int64_t *n_particles, int nlanes, int32_t *lane) {
+  if (nmembers < 1 || !n_particles || !lane || nlanes < 1 || nlanes > kMaxLanes) return MBT_ERR_ARG;
+  std::vector<int64_t> n((size_t)nmembers);
+  for (int i = 0; i < nmembers; ++i) {
+    if (n_particles[i] < 0) return MBT_ERR_ARG;
+    n[(size_t)i] = n_particles[i];
+  }
+  const std::vector<std::vector<int>> lanes = lane_partition(n, std::min(nlanes, nmembers));
+  for (size_t j = 0; j < lanes.size(); ++j)
+    for (int i : lanes[j]) lane[i] = (int32_t)j;
   return MBT_OK;
 }
 

@@ -127,3 +127,38 @@ def test_streaming_choice(pkg):
     from paper_1809_00391_gb300 import MBTError
     with pytest.raises(MBTError):
         pkg.plan_streams([big], [0], False, G)
+
+
+def _lanes_reference(n, k):
+    """Largest first (ties in member order), each into the lane holding the
+    fewest particles so far (ties: the lower lane), written from the rule."""
+    k = min(k, len(n))
+    load = [0] * k
+    lane = [None] * len(n)
+    for i in sorted(range(len(n)), key=lambda i: (-n[i], i)):
+        j = min(range(k), key=lambda j: (load[j], j))
+        lane[i] = j
+        load[j] += n[i]
+    return lane
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lane_partition_follows_the_rule_and_balances(pkg, seed):
+    g = np.random.default_rng(seed)
+    n = [int(x) for x in g.integers(1, 10, 37) * 10 ** g.integers(3, 7, 37)]
+    for k in (1, 2, 3, 4, 8):
+        lane = pkg.plan_lanes(n, k)
+        assert lane.tolist() == _lanes_reference(n, k)
+        loads = np.bincount(lane, weights=n, minlength=min(k, len(n)))
+        assert set(lane.tolist()) == set(range(min(k, len(n))))   # no lane left empty
+        # greedy bound: no lane exceeds the mean by more than the largest member
+        assert loads.max() <= np.sum(n) / len(loads) + max(n)
+
+
+def test_lane_partition_edges(pkg):
+    assert pkg.plan_lanes([5, 5, 5], 8).tolist() == [0, 1, 2]   # more lanes than members
+    assert pkg.plan_lanes([1, 2, 3, 4], 1).tolist() == [0, 0, 0, 0]
+    assert pkg.plan_lanes([0, 0, 7], 2).tolist() == [1, 1, 0]
+    for bad in (([], 2), ([1, 2], 0), ([1, 2], 9), ([1, -1], 2)):
+        with pytest.raises(pkg.MBTError):
+            pkg.plan_lanes(*bad)
