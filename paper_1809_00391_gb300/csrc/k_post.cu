@@ -989,7 +989,6 @@ __global__ void __launch_bounds__(kPostThreads, 1) k_wake_noalloc(const Plan p) 
   __shared__ __align__(8) uint64_t bars[3];   // wake_prologue initialises three
   __shared__ uint32_t tmem_slot;
   __shared__ int s_flag;
-  __shared__ double s_sum[9][kBunchTile];
   const PostJob job = p.jobs[blockIdx.x];
   const RunDev *R = p.runs + job.run;
   wake_prologue(R, job, sm_wna, bars, &tmem_slot, &s_flag);
