@@ -612,7 +612,9 @@ typedef struct {
     double now;                /* seconds since the server started                        */
 } mbt_server_stats;
 
-/* Start a server on the calling thread's current device. */
+/* Start a server on the calling thread's current device.  MBT_ERR_ARG for a
+ * NULL pointer, max_active or turns_per_step below 1, a zero budget or lanes
+ * outside 0..8. */
 mbt_status mbt_server_create(const mbt_server_config *cfg, mbt_server **out);
 /* Queue a request (non-blocking); *id identifies it.  MBT_ERR_BUDGET if its
  * estimated memory alone exceeds the budget, MBT_ERR_ARG on a malformed request. */
