@@ -240,3 +240,20 @@ def test_wait_test_hook_validates_its_arguments(pkg):
     finally:
         L.mbt_destroy(h)
     assert ctypes is not None
+
+
+def test_server_and_lane_arguments_are_validated_before_device_work(pkg):
+    """mbt_server_create refuses a bad configuration (lanes outside 0..8
+    among them) before it starts a thread or touches a device; the batch
+    lane calls refuse a NULL batch."""
+    import ctypes
+    L = pkg.lib()
+    out = ctypes.c_void_p()
+    for budget, active, step, lanes in ((1 << 30, 4, 10, 9), (1 << 30, 4, 10, -1), (0, 4, 10, 1),
+                                        (1 << 30, 0, 10, 1), (1 << 30, 4, 0, 1)):
+        cfg = pkg.ServerConfig(budget, active, step, lanes)
+        assert L.mbt_server_create(ctypes.byref(cfg), ctypes.byref(out)) == 1
+        assert not out.value
+    k = ctypes.c_int()
+    assert L.mbt_batch_set_lanes(None, 2) == 1
+    assert L.mbt_batch_autotune_lanes(None, 5, 2, ctypes.byref(k)) == 1
