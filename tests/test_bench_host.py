@@ -107,3 +107,14 @@ def test_reference_arm_prints_a_complete_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_lane_defaults_and_flag(monkeypatch):
+    """The scan and serving workloads take their measured lane counts unless
+    --lanes names one (1..8, the library's range)."""
+    assert set(bench.LANES) == {"l5scan", "rwscan", "hcscan", "serving"}
+    assert all(1 <= v <= 8 for v in bench.LANES.values())
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "l5scan"])
+    assert bench.parse().lanes == 0   # 0: the workload's default
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "rwscan", "--lanes", "2"])
+    assert bench.parse().lanes == 2
