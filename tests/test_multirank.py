@@ -158,3 +158,58 @@ def test_sharded_phasor_scan_is_one_process_scan_on_one_rank():
         X = ref[-1] + E[m]
     assert np.max(np.abs(np.array(ref) - whole)) <= 1e-14 * np.max(np.abs(whole))
     assert abs(X - c1) <= 1e-14 * abs(X)
+
+
+def test_phasor_steps_and_empty_ranges():
+    """a_m is the resonator's decay and rotation e^{s dt} over the bucket
+    distance from the bunch before (the first bunch: from the last bunch of the
+    previous turn across the gap), s = -w_r/(2Q) + i w_r sqrt(1 - 1/(4Q^2));
+    a rank holding no bunches contributes the identity map and meets its entry
+    value unchanged."""
+    import math
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from paper_1809_00391_gb300 import sharded
+    ring, buckets, currents, res = _shard_fill()
+    r = res[0]
+    step = sharded.phasor_steps(ring, r, buckets)
+    wr = 2 * math.pi * r["fr_Hz"]
+    s = complex(-wr / (2 * r["Q"]), wr * math.sqrt(1 - 1 / (4 * r["Q"] ** 2)))
+    T_rf = ring["T0_s"] / ring["h"]
+    gaps = np.diff(np.concatenate([[buckets[-1] - ring["h"]], buckets]))
+    assert np.all(gaps > 0) and gaps.sum() == ring["h"]
+    for m in range(len(buckets)):
+        ref = complex(np.exp(s * gaps[m] * T_rf))
+        assert abs(step[m] - ref) <= 1e-12 * abs(ref), m
+    empty = np.zeros(0, np.complex128)
+    A, B = sharded.segment_map(empty, empty)
+    assert A == 1 and B == 0
+    entry, carry = sharded.compose(np.array([[A, B], [0.5 + 0.5j, 2.0 - 1j]]), 1.0 + 1.0j)
+    assert entry[0] == 1.0 + 1.0j and entry[1] == 1.0 + 1.0j
+    assert carry == (0.5 + 0.5j) * (1.0 + 1.0j) + (2.0 - 1j)
+    assert len(sharded.apply(empty, empty, 3.0 + 0j)) == 0
+
+
+def test_phasor_calls_refuse_bad_arguments():
+    """Buckets out of the ring, not increasing, or a resonator with Q <= 1/2
+    (no oscillating wake) are refused with MBT_ERR_ARG, as is a composition of
+    no maps; nothing is written on refusal."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import paper_1809_00391_gb300 as p
+    from paper_1809_00391_gb300 import sharded
+    MBT_ERR_ARG = 1   # include/mbt.h
+    ring, buckets, currents, res = _shard_fill()
+    r = res[0]
+    h = ring["h"]
+    for bad in ([3, 2], [0, 0], [-1, 4], [0, h]):
+        with pytest.raises(p.MBTError) as ei:
+            sharded.phasor_steps(ring, r, bad)
+        assert ei.value.status == MBT_ERR_ARG, bad
+    with pytest.raises(p.MBTError) as ei:
+        sharded.phasor_steps(ring, dict(r, Q=0.5), buckets)
+    assert ei.value.status == MBT_ERR_ARG
+    with pytest.raises(p.MBTError) as ei:
+        sharded.compose(np.zeros((0, 2), np.complex128), 0j)
+    assert ei.value.status == MBT_ERR_ARG
